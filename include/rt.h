@@ -1,0 +1,169 @@
+/*
+ * rt.h - C interface of the GB300 photon-transport library (librt_gb300.so).
+ *
+ * The library advances the two-moment radiation equations (photon energy density E
+ * and flux F per photon group, M1 closure, reduced speed of light c) on static
+ * finite-volume particles, as in GEAR-RT (Ivkovic 2023, arXiv 2302.12727, Part III,
+ * chapter "One RT Time Step"):
+ *
+ *   injection:   E_g += xi_sg L_s dt / V_g        (Sec. "First step: Injection",
+ *                                                  Eq. isotropy-correction-with-zero)
+ *   transport:   U_k(t+dt) = U_k - dt/V_k sum_l F_kl . A_kl
+ *                                                 (Eq. transport-update-explicit, Eq. rt-meshless)
+ *                with A_kl the Hopkins effective surfaces (Eq. HopkinsAij), gradients from
+ *                the least-squares estimate (Eqs. gradient, psitilde, matrix_B, matrix_E),
+ *                minmod-limited states at x_kl (Eq. rt-riemann-problem, Eq. rt-minmod)
+ *                and the GLF flux (Eq. riemann-GLF) of the M1 closure (Eq. eddington-group);
+ *   sink:        U <- U max(0, 1 - c alpha dt)    (Sec. "Third step: Thermochemistry",
+ *                                                  forward-Euler photon removal, grey alpha)
+ *
+ * Conventions shared by every entry point:
+ *  - Array arguments named *_dev are DEVICE pointers owned by the caller, in the caller's
+ *    particle order.  Multi-component arrays are component-major (structure of arrays):
+ *      x     [3][N]        positions (double)
+ *      U     [G][4][N]     (E, Fx, Fy, Fz) per group; element type double for RT_FP64,
+ *                          float for RT_FP32_MIXED
+ *      gradU [G][4][3][N]  d/dx, d/dy, d/dz of each component; element type as U
+ *      Lsrc  [S][G]        source luminosities (double)
+ *      alpha [N]           grey absorption coefficient (double), or NULL for none
+ *  - The library owns its workspaces, its cell-sorted copies and the permutation.  Memory is
+ *    allocated only in rt_create, rt_neighbours and on the first call of rt_adjoint with a
+ *    larger checkpoint count; rt_transport_step and rt_subcycle allocate nothing.
+ *  - All work is asynchronous on the stream given to rt_create, except where a function
+ *    says it synchronises.  Nothing aborts or prints: every call returns an rt_status and
+ *    rt_last_error() gives a message for the last failure.
+ *  - rt_neighbours must be called before any transport call (else RT_ERR_STATE); its
+ *    geometry is kept until the next rt_neighbours.
+ */
+#ifndef RT_GB300_RT_H
+#define RT_GB300_RT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_ctx rt_ctx;
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_INVALID = 1,   /* bad argument or configuration */
+    RT_ERR_CUDA = 2,      /* a CUDA call failed; the message names it */
+    RT_ERR_OOM = 3,       /* device allocation failed */
+    RT_ERR_NOCONV = 4,    /* smoothing-length iteration did not converge */
+    RT_ERR_GEOMETRY = 5,  /* singular E_i (fewer than 3 non-coplanar neighbours) or
+                             a support radius of half the periodic box or more */
+    RT_ERR_TIMEOUT = 6,   /* a bounded device wait ran out */
+    RT_ERR_STATE = 7      /* call out of order (e.g. transport before rt_neighbours) */
+} rt_status;
+
+enum { RT_FP64 = 0, RT_FP32_MIXED = 1 };
+
+typedef struct {
+    int32_t n_groups;        /* G >= 1 photon groups; transport treats them independently */
+    double c_red;            /* reduced speed of light, used in the closure, the GLF
+                                dissipation and the sink (Sec. reduced speed of light) */
+    double eta_res;          /* resolution parameter of the gas h, 1.2348 gives ~48 neighbours
+                                (Eq. number-of-neighbors) */
+    double eta_res_star;     /* the same for the sources' injection radius */
+    double box[3];           /* box side lengths; positions must lie in [0, box) */
+    int32_t periodic;        /* 1: periodic box, minimal-image separations */
+    int32_t precision;       /* RT_FP64: everything in double.  RT_FP32_MIXED: fluxes and
+                                gradients in float; h, E_i, B_i = E_i^-1 and the energy sum in
+                                double */
+    int32_t clamp_negative;  /* 1: set E < 0 to 0 after each step (counted); breaks exact
+                                conservation, so 0 for conservation checks */
+    int32_t limiter_variant; /* 0: s = minmod(grad Q_k . d, grad Q_l . d) on both states (the only
+                                value accepted) */
+    double h_tol;            /* relative tolerance of the smoothing-length iteration (<= 1e-6;
+                                the FP64 path always refines to machine precision) */
+    int32_t h_max_iter;      /* iteration cap of that solve; exceeding it gives RT_ERR_NOCONV */
+    uint64_t device_wait_budget_cycles;  /* reserved: bound for device-side waits */
+} rt_config;
+
+typedef struct {
+    int64_t n_pairs;          /* unordered interacting pairs P (r < max(H_i, H_j)) */
+    int64_t n_directed;       /* entries of the symmetric neighbour lists, 2P */
+    int64_t n_injection;      /* (source, gas) injection entries */
+    int64_t n_ill_conditioned;/* particles with cond_2(E_i) > 1e10 */
+    double cond_max;          /* largest cond_2(E_i) */
+    double h_min, h_max;      /* smoothing lengths */
+    double dx_min;            /* min_i (V_i / (4 pi / 3))^(1/3), the cell size of Eq. rt-cfl */
+    int64_t clamp_events;     /* cumulative count of E < 0 fix-ups */
+    int32_t grid[3];          /* cell-list dimensions used by rt_neighbours */
+    int32_t threads_per_particle;  /* launch shape picked for the pair kernels */
+} rt_diag;
+
+/* Create a context for n particles and n_src sources.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream).  Allocates the per-particle workspaces.  On failure
+ * *out is still set (so rt_last_error can be read) unless out is NULL; destroy it. */
+rt_status rt_create(const rt_config* cfg, int64_t n, int64_t n_src, void* cuda_stream, rt_ctx** out);
+
+/* Change the stream used by later calls. */
+rt_status rt_set_stream(rt_ctx* ctx, void* cuda_stream);
+
+/* Neighbour search and geometry, once per particle configuration (Part II, "The Neighbor
+ * Search"; Eqs. omega, particle-volume, matrix_E, matrix_B; sources: Sec. "Weights For
+ * Distribution Of Energy Density of a Star onto Particles"):
+ * cell-list build, smoothing lengths h_i = eta omega_i^(-1/3), the symmetric pair lists
+ * { j : r_ij < max(H_i, H_j) }, H = 1.825742 h, E_i and B_i = E_i^-1 in double, source
+ * radii and injection weights.
+ *   x_dev    [3][N] positions in [0, box)
+ *   m_dev    [N] masses (kept for the caller's density; may be NULL)
+ *   xsrc_dev [3][S] source positions (may be NULL when S = 0)
+ *   h_out    [N] device, receives h_i in caller order (may be NULL)
+ * Synchronises the stream (it sizes the pair lists).  Errors: RT_ERR_INVALID (NaN/Inf or
+ * out-of-box positions), RT_ERR_NOCONV, RT_ERR_GEOMETRY, RT_ERR_OOM. */
+rt_status rt_neighbours(rt_ctx* ctx, const double* x_dev, const double* m_dev, const double* xsrc_dev,
+                        double* h_out_dev);
+
+/* Least-squares gradients of every component of U (Eq. gradient):
+ * grad Q_i = sum_j (Q_j - Q_i) psitilde_j(x_i).  U_dev [G][4][N], gradU_dev [G][4][3][N]. */
+rt_status rt_gradients(rt_ctx* ctx, const void* U_dev, void* gradU_dev);
+
+/* One time step dt: injection, transport, sink (and fix-up if enabled), in place on U_dev.
+ * Lsrc_dev may be NULL when S = 0; alpha_dev may be NULL (no sink).  Plain kernel launches. */
+rt_status rt_transport_step(rt_ctx* ctx, double dt, void* U_dev, const double* Lsrc_dev, const double* alpha_dev);
+
+/* n_sub steps of size dt without any neighbour search in between (Sec. "Dynamic
+ * Sub-Cycling"), replayed from one CUDA graph that the library captures once per
+ * (n_sub, source/sink presence) and reuses; dt, Lsrc and alpha live in device buffers,
+ * so they may change between calls without a new capture. */
+rt_status rt_subcycle(rt_ctx* ctx, int32_t n_sub, double dt, void* U_dev, const double* Lsrc_dev,
+                      const double* alpha_dev);
+
+/* Reverse-mode derivative of rt_subcycle (no counterpart in the thesis): given
+ * dL/dU(final) it returns dL/dU0 [G][4][N] and dL/dLsrc [S][G] (double, may be NULL).
+ * The forward pass keeps a checkpoint every ckpt_every steps and recomputes each segment
+ * in reverse.  U0_dev is not modified.  The fix-up (clamp_negative) is treated as inactive. */
+rt_status rt_adjoint(rt_ctx* ctx, int32_t n_sub, double dt, int32_t ckpt_every, const void* U0_dev,
+                     const double* Lsrc_dev, const double* alpha_dev, const void* dLdU_final_dev,
+                     void* dLdU0_dev, double* dLdLsrc_dev);
+
+/* Total radiation energy per group, sum_i V_i E_i,g, summed in double in a fixed order.
+ * E_tot_host [G] is HOST memory; the call synchronises the stream. */
+rt_status rt_energy(rt_ctx* ctx, const void* U_dev, double* E_tot_host);
+
+/* Per-particle geometry in caller order (device pointers, each may be NULL):
+ * h [N], omega [N], V [N], B [N][3][3] (double). */
+rt_status rt_particle_fields(rt_ctx* ctx, double* h_dev, double* omega_dev, double* V_dev, double* B_dev);
+
+/* The symmetric neighbour lists in caller indices: offsets_dev [N+1] (int64),
+ * cols_dev [n_directed] (int32); the order inside a row is the library's. */
+rt_status rt_pairs(rt_ctx* ctx, int64_t* offsets_dev, int32_t* cols_dev);
+
+/* Counters of the last rt_neighbours and of the steps since (host struct). */
+rt_status rt_diagnostics(rt_ctx* ctx, rt_diag* out);
+
+/* Message of the last failure ("" if none).  Valid until the next call on ctx. */
+const char* rt_last_error(const rt_ctx* ctx);
+
+/* Release everything the context owns (NULL is accepted). */
+void rt_destroy(rt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT_GB300_RT_H */

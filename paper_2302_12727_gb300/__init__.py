@@ -1,0 +1,185 @@
+"""GB300 photon-transport library (FVPM radiative transfer of GEAR-RT, arXiv 2302.12727).
+
+The compute path is the CUDA library ``_lib/librt_gb300.so`` behind the C interface of
+``include/rt.h``.  This module is its thin binding: the functions below carry the C names
+and only marshal arguments (torch tensors or raw device pointers) before calling the
+library.  There is no CPU fallback: if the library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build_ext import LIB as _LIB_PATH
+
+RT_FP64 = 0
+RT_FP32_MIXED = 1
+
+RT_OK = 0
+_STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4: "RT_ERR_NOCONV",
+           5: "RT_ERR_GEOMETRY", 6: "RT_ERR_TIMEOUT", 7: "RT_ERR_STATE"}
+
+EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
+            "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_last_error",
+            "rt_destroy"]
+
+
+class rt_config(C.Structure):
+    _fields_ = [("n_groups", C.c_int32), ("c_red", C.c_double), ("eta_res", C.c_double),
+                ("eta_res_star", C.c_double), ("box", C.c_double * 3), ("periodic", C.c_int32),
+                ("precision", C.c_int32), ("clamp_negative", C.c_int32), ("limiter_variant", C.c_int32),
+                ("h_tol", C.c_double), ("h_max_iter", C.c_int32), ("device_wait_budget_cycles", C.c_uint64)]
+
+
+class rt_diag(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("n_directed", C.c_int64), ("n_injection", C.c_int64),
+                ("n_ill_conditioned", C.c_int64), ("cond_max", C.c_double), ("h_min", C.c_double),
+                ("h_max", C.c_double), ("dx_min", C.c_double), ("clamp_events", C.c_int64),
+                ("grid", C.c_int32 * 3), ("threads_per_particle", C.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["grid"] = list(self.grid)
+        return d
+
+
+class RTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load librt_gb300.so (built by ``build_ext.build()``); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with paper_2302_12727_gb300.build_ext.build()")
+    lib = C.CDLL(_LIB_PATH)
+    vp, dp, i64 = C.c_void_p, C.c_void_p, C.c_int64
+    lib.rt_create.argtypes = [C.POINTER(rt_config), i64, i64, vp, C.POINTER(vp)]
+    lib.rt_set_stream.argtypes = [vp, vp]
+    lib.rt_neighbours.argtypes = [vp, dp, dp, dp, dp]
+    lib.rt_gradients.argtypes = [vp, dp, dp]
+    lib.rt_transport_step.argtypes = [vp, C.c_double, dp, dp, dp]
+    lib.rt_subcycle.argtypes = [vp, C.c_int32, C.c_double, dp, dp, dp]
+    lib.rt_adjoint.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, dp, dp, dp, dp, dp, dp]
+    lib.rt_energy.argtypes = [vp, dp, C.POINTER(C.c_double)]
+    lib.rt_particle_fields.argtypes = [vp, dp, dp, dp, dp]
+    lib.rt_pairs.argtypes = [vp, dp, dp]
+    lib.rt_diagnostics.argtypes = [vp, C.POINTER(rt_diag)]
+    lib.rt_last_error.argtypes = [vp]
+    lib.rt_last_error.restype = C.c_char_p
+    lib.rt_destroy.argtypes = [vp]
+    lib.rt_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("rt_last_error", "rt_destroy"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+# ----------------------------------------------------------------------------------------
+# argument marshalling
+def _ptr(t):
+    """Device pointer of a CUDA tensor (or an int pointer, or None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _check(ctx, status):
+    if status != RT_OK:
+        msg = load_library().rt_last_error(ctx)
+        raise RTError(status, msg.decode() if msg else "")
+
+
+def make_config(n_groups=1, c_red=1.0, eta_res=1.2348, eta_res_star=1.2348, box=(1.0, 1.0, 1.0), periodic=True,
+                precision=RT_FP32_MIXED, clamp_negative=False, h_tol=1e-6, h_max_iter=100) -> rt_config:
+    return rt_config(n_groups, c_red, eta_res, eta_res_star, (C.c_double * 3)(*box), int(periodic), precision,
+                     int(clamp_negative), 0, h_tol, h_max_iter, 0)
+
+
+def rt_create(cfg: rt_config, n: int, n_src: int, stream=None):
+    """Returns the context handle (an int)."""
+    lib = load_library()
+    out = C.c_void_p()
+    s = lib.rt_create(C.byref(cfg), int(n), int(n_src), stream, C.byref(out))
+    if s != RT_OK:
+        msg = lib.rt_last_error(out) if out.value else b"allocation failed"
+        if out.value:
+            lib.rt_destroy(out)
+        raise RTError(s, msg.decode())
+    return out.value
+
+
+def rt_set_stream(ctx, stream):
+    _check(ctx, load_library().rt_set_stream(ctx, stream))
+
+
+def rt_neighbours(ctx, x, m=None, xsrc=None, h_out=None):
+    _check(ctx, load_library().rt_neighbours(ctx, _ptr(x), _ptr(m), _ptr(xsrc), _ptr(h_out)))
+
+
+def rt_gradients(ctx, U, gradU):
+    _check(ctx, load_library().rt_gradients(ctx, _ptr(U), _ptr(gradU)))
+
+
+def rt_transport_step(ctx, dt, U, Lsrc=None, alpha=None):
+    _check(ctx, load_library().rt_transport_step(ctx, float(dt), _ptr(U), _ptr(Lsrc), _ptr(alpha)))
+
+
+def rt_subcycle(ctx, n_sub, dt, U, Lsrc=None, alpha=None):
+    _check(ctx, load_library().rt_subcycle(ctx, int(n_sub), float(dt), _ptr(U), _ptr(Lsrc), _ptr(alpha)))
+
+
+def rt_adjoint(ctx, n_sub, dt, ckpt_every, U0, Lsrc, alpha, dLdU_final, dLdU0, dLdLsrc=None):
+    _check(ctx, load_library().rt_adjoint(ctx, int(n_sub), float(dt), int(ckpt_every), _ptr(U0), _ptr(Lsrc),
+                                          _ptr(alpha), _ptr(dLdU_final), _ptr(dLdU0), _ptr(dLdLsrc)))
+
+
+def rt_energy(ctx, U, n_groups):
+    out = (C.c_double * n_groups)()
+    _check(ctx, load_library().rt_energy(ctx, _ptr(U), out))
+    return list(out)
+
+
+def rt_particle_fields(ctx, h=None, omega=None, V=None, B=None):
+    _check(ctx, load_library().rt_particle_fields(ctx, _ptr(h), _ptr(omega), _ptr(V), _ptr(B)))
+
+
+def rt_pairs(ctx, offsets, cols):
+    _check(ctx, load_library().rt_pairs(ctx, _ptr(offsets), _ptr(cols)))
+
+
+def rt_diagnostics(ctx) -> dict:
+    d = rt_diag()
+    _check(ctx, load_library().rt_diagnostics(ctx, C.byref(d)))
+    return d.as_dict()
+
+
+def rt_last_error(ctx) -> str:
+    m = load_library().rt_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def rt_destroy(ctx):
+    if ctx:
+        load_library().rt_destroy(ctx)
+
+
+from .transport import Transport, SubcycleFunction  # noqa: E402  (torch-facing wrapper)

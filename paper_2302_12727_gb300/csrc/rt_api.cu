@@ -1,0 +1,370 @@
+// C entry points of the GB300 photon-transport library (declared in include/rt.h):
+// context, workspaces, order of calls, CUDA-graph capture of the sub-cycle loop.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+
+rt_status fail(rt_ctx* c, rt_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+rt_status cuda_fail(rt_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (c) c->err = m;
+    return e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;
+}
+
+static int64_t g_generation = 0;
+
+rt_status ensure(rt_ctx* c, DevBuf& b, size_t bytes, const char* what) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return RT_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(c, RT_ERR_OOM, std::string("device allocation failed: ") + what);
+    }
+    b.bytes = bytes;
+    ++g_generation;   // buffers captured in graphs moved
+    return RT_OK;
+}
+
+static void free_buf(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+static void drop_graphs(rt_ctx* c) {
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+static size_t tsize(const rt_ctx* c) { return c->fp64 ? 8 : 4; }
+
+static rt_status check_ready(rt_ctx* c) {
+    if (!c) return RT_ERR_INVALID;
+    c->err.clear();
+    if (!c->built) return fail(c, RT_ERR_STATE, "rt_neighbours has not been called");
+    RT_CUDA(c, cudaSetDevice(c->device));
+    return RT_OK;
+}
+
+// state buffers used by the transport calls (allocated in rt_neighbours)
+static rt_status ensure_state(rt_ctx* c) {
+    const int64_t n = c->n;
+    const int G = c->cfg.n_groups;
+    RT_TRY(ensure(c, c->U_a, (size_t)4 * G * n * tsize(c), "state"));
+    RT_TRY(ensure(c, c->U_b, (size_t)4 * G * n * tsize(c), "state"));
+    RT_TRY(ensure(c, c->grad, (size_t)12 * G * n * tsize(c), "gradients"));
+    RT_TRY(ensure(c, c->alpha_s, (size_t)n * tsize(c), "absorption"));
+    RT_TRY(ensure(c, c->L_dev, (size_t)std::max<int64_t>(c->n_src, 1) * G * 8, "luminosities"));
+    RT_TRY(ensure(c, c->dt_dev, 64, "dt"));
+    RT_TRY(ensure(c, c->energy_part, (size_t)G * 512 * 8 + (size_t)G * 8, "energy"));
+    return RT_OK;
+}
+
+}  // namespace rt
+
+using namespace rt;
+
+extern "C" {
+
+rt_status rt_create(const rt_config* cfg, int64_t n, int64_t n_src, void* cuda_stream, rt_ctx** out) {
+    if (!out) return RT_ERR_INVALID;
+    *out = nullptr;
+    rt_ctx* c = new (std::nothrow) rt_ctx();
+    if (!c) return RT_ERR_OOM;
+    *out = c;
+    if (!cfg) return fail(c, RT_ERR_INVALID, "cfg is NULL");
+    c->cfg = *cfg;
+    c->n = n;
+    c->n_src = n_src;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (n < 2 || n >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "n must be in [2, 2^31)");
+    if (n_src < 0 || n_src >= ((int64_t)1 << 20)) return fail(c, RT_ERR_INVALID, "n_src must be in [0, 2^20)");
+    if (cfg->n_groups < 1 || cfg->n_groups > 64) return fail(c, RT_ERR_INVALID, "n_groups must be in [1, 64]");
+    if (!(cfg->c_red > 0.0) || !std::isfinite(cfg->c_red)) return fail(c, RT_ERR_INVALID, "c_red must be > 0");
+    if (!(cfg->eta_res > 0.0) || !(cfg->eta_res_star > 0.0)) return fail(c, RT_ERR_INVALID, "eta_res must be > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!(cfg->box[a] > 0.0) || !std::isfinite(cfg->box[a])) return fail(c, RT_ERR_INVALID, "box must be > 0");
+    if (cfg->precision != RT_FP64 && cfg->precision != RT_FP32_MIXED)
+        return fail(c, RT_ERR_INVALID, "precision must be RT_FP64 or RT_FP32_MIXED");
+    if (cfg->limiter_variant != 0) return fail(c, RT_ERR_INVALID, "limiter_variant must be 0 (minmod)");
+    if (cfg->h_tol < 0.0 || cfg->h_tol > 1e-3) return fail(c, RT_ERR_INVALID, "h_tol must be in [0, 1e-3]");
+    c->fp64 = cfg->precision == RT_FP64;
+    RT_CUDA(c, cudaGetDevice(&c->device));
+    RT_CUDA(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+    RT_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    RT_TRY(ensure(c, c->flags, 64, "flags"));
+    RT_CUDA(c, cudaMemset(c->flags.p, 0, 64));
+    RT_TRY(ensure_state(c));
+    return RT_OK;
+}
+
+rt_status rt_set_stream(rt_ctx* c, void* s) {
+    if (!c) return RT_ERR_INVALID;
+    c->stream = (cudaStream_t)s;
+    return RT_OK;
+}
+
+rt_status rt_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc, double* h_out) {
+    if (!c) return RT_ERR_INVALID;
+    c->err.clear();
+    if (!x) return fail(c, RT_ERR_INVALID, "x_dev is NULL");
+    if (c->n_src > 0 && !xsrc) return fail(c, RT_ERR_INVALID, "xsrc_dev is NULL with n_src > 0");
+    RT_CUDA(c, cudaSetDevice(c->device));
+    c->built = false;
+    int64_t gen0 = g_generation;
+    int64_t targets0 = c->n_inj_targets;
+    rt_status s = build_neighbours(c, x, m, xsrc);
+    if (s != RT_OK) {
+        drop_graphs(c);
+        return s;
+    }
+    RT_TRY(ensure_state(c));
+    // captured graphs hold buffer addresses and the injection grid size
+    if (g_generation != gen0 || c->n_inj_targets != targets0) drop_graphs(c);
+    if (h_out) {
+        // h in caller order
+        RT_TRY(ensure(c, c->red_tmp, 64, "reduction"));
+        const int comps = 1;
+        bool f = c->fp64;
+        c->fp64 = true;
+        rt_status s2 = from_sorted(c, c->h_d.p, h_out, comps);
+        c->fp64 = f;
+        if (s2 != RT_OK) return s2;
+    }
+    c->built = true;
+    return RT_OK;
+}
+
+rt_status rt_gradients(rt_ctx* c, const void* U, void* gradU) {
+    RT_TRY(check_ready(c));
+    if (!U || !gradU) return fail(c, RT_ERR_INVALID, "NULL array");
+    const int G = c->cfg.n_groups;
+    RT_TRY(to_sorted(c, U, c->U_a.p, 4 * G));
+    RT_TRY(launch_gradient(c, c->stream, c->U_a.p, c->grad.p));
+    RT_TRY(from_sorted(c, c->grad.p, gradU, 12 * G));
+    return RT_OK;
+}
+
+rt_status rt_transport_step(rt_ctx* c, double dt, void* U, const double* Lsrc, const double* alpha) {
+    RT_TRY(check_ready(c));
+    if (!U) return fail(c, RT_ERR_INVALID, "U_dev is NULL");
+    if (!std::isfinite(dt) || dt < 0) return fail(c, RT_ERR_INVALID, "dt must be finite and >= 0");
+    const int G = c->cfg.n_groups;
+    bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
+    RT_TRY(to_sorted(c, U, c->U_a.p, 4 * G));
+    RT_TRY(set_step_inputs(c, dt, Lsrc, alpha));
+    RT_TRY(launch_step(c, c->stream, c->U_a.p, c->U_b.p, has_src, alpha != nullptr));
+    RT_TRY(from_sorted(c, c->U_b.p, U, 4 * G));
+    return RT_OK;
+}
+
+rt_status rt_subcycle(rt_ctx* c, int32_t n_sub, double dt, void* U, const double* Lsrc, const double* alpha) {
+    RT_TRY(check_ready(c));
+    if (!U) return fail(c, RT_ERR_INVALID, "U_dev is NULL");
+    if (n_sub < 0 || n_sub > 100000) return fail(c, RT_ERR_INVALID, "n_sub must be in [0, 100000]");
+    if (!std::isfinite(dt) || dt < 0) return fail(c, RT_ERR_INVALID, "dt must be finite and >= 0");
+    if (n_sub == 0) return RT_OK;
+    const int G = c->cfg.n_groups;
+    bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
+    bool has_alpha = alpha != nullptr;
+    RT_TRY(to_sorted(c, U, c->U_a.p, 4 * G));
+    RT_TRY(set_step_inputs(c, dt, Lsrc, alpha));
+    GraphKey key{n_sub, has_src ? 1 : 0, has_alpha ? 1 : 0};
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        cudaGraph_t graph = nullptr;
+        RT_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        void* a = c->U_a.p;
+        void* b = c->U_b.p;
+        rt_status s = RT_OK;
+        for (int k = 0; k < n_sub && s == RT_OK; ++k) {
+            s = launch_step(c, c->cap_stream, a, b, has_src, has_alpha);
+            std::swap(a, b);
+        }
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (s != RT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+        it = c->graphs.emplace(key, exec).first;
+    }
+    RT_CUDA(c, cudaGraphLaunch(it->second, c->stream));
+    void* fin = (n_sub % 2 == 0) ? c->U_a.p : c->U_b.p;
+    RT_TRY(from_sorted(c, fin, U, 4 * G));
+    return RT_OK;
+}
+
+rt_status rt_adjoint(rt_ctx* c, int32_t n_sub, double dt, int32_t ckpt_every, const void* U0, const double* Lsrc,
+                     const double* alpha, const void* dLdU_final, void* dLdU0, double* dLdLsrc) {
+    RT_TRY(check_ready(c));
+    if (!U0 || !dLdU_final || !dLdU0) return fail(c, RT_ERR_INVALID, "NULL array");
+    if (n_sub < 1 || n_sub > 100000) return fail(c, RT_ERR_INVALID, "n_sub must be in [1, 100000]");
+    if (ckpt_every < 1) return fail(c, RT_ERR_INVALID, "ckpt_every must be >= 1");
+    if (!std::isfinite(dt) || dt < 0) return fail(c, RT_ERR_INVALID, "dt must be finite and >= 0");
+    const int G = c->cfg.n_groups;
+    bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
+    RT_TRY(set_step_inputs(c, dt, Lsrc, alpha));
+    RT_TRY(ensure(c, c->lam_a, (size_t)4 * G * c->n * tsize(c), "adjoint"));
+    RT_TRY(ensure(c, c->lam_b, (size_t)4 * G * c->n * tsize(c), "adjoint"));
+    RT_TRY(to_sorted(c, U0, c->U_a.p, 4 * G));
+    RT_TRY(to_sorted(c, dLdU_final, c->lam_a.p, 4 * G));
+    if (dLdLsrc && c->n_src > 0)
+        RT_CUDA(c, cudaMemsetAsync(dLdLsrc, 0, (size_t)c->n_src * G * sizeof(double), c->stream));
+    RT_TRY(run_adjoint(c, n_sub, ckpt_every, has_src, alpha != nullptr, c->U_a.p, c->lam_a.p, c->lam_b.p,
+                       (dLdLsrc && c->n_src > 0) ? dLdLsrc : nullptr));
+    RT_TRY(from_sorted(c, c->lam_b.p, dLdU0, 4 * G));
+    return RT_OK;
+}
+
+rt_status rt_energy(rt_ctx* c, const void* U, double* E_host) {
+    RT_TRY(check_ready(c));
+    if (!U || !E_host) return fail(c, RT_ERR_INVALID, "NULL array");
+    const int G = c->cfg.n_groups;
+    RT_TRY(to_sorted(c, U, c->U_a.p, 4 * G));
+    double* out = c->energy_part.as<double>() + (size_t)G * 512;
+    RT_TRY(launch_energy(c, c->stream, c->U_a.p, out));
+    RT_CUDA(c, cudaMemcpyAsync(E_host, out, G * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    RT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return RT_OK;
+}
+
+rt_status rt_particle_fields(rt_ctx* c, double* h, double* omega, double* V, double* B) {
+    RT_TRY(check_ready(c));
+    bool f = c->fp64;
+    c->fp64 = true;   // the geometry is kept in double
+    rt_status s = RT_OK;
+    if (h && s == RT_OK) s = from_sorted(c, c->h_d.p, h, 1);
+    if (omega && s == RT_OK) s = from_sorted(c, c->omega_d.p, omega, 1);
+    if (V && s == RT_OK) s = from_sorted(c, c->V_d.p, V, 1);
+    if (B && s == RT_OK) {
+        // [6][N] sorted -> [N][3][3] caller order
+        static const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+        rt_status s3 = ensure(c, c->seg, (size_t)6 * c->n * 8, "scratch");
+        if (s3 == RT_OK) s3 = from_sorted(c, c->B_d.p, c->seg.p, 6);
+        if (s3 == RT_OK) {
+            for (int q = 0; q < 9; ++q) {
+                cudaError_t e = cudaMemcpy2DAsync(B + q, 9 * sizeof(double), c->seg.as<double>() + (size_t)map[q] * c->n,
+                                                  sizeof(double), sizeof(double), c->n, cudaMemcpyDeviceToDevice,
+                                                  c->stream);
+                if (e != cudaSuccess) {
+                    s3 = cuda_fail(c, e, "cudaMemcpy2DAsync");
+                    break;
+                }
+            }
+        }
+        s = s3;
+    }
+    c->fp64 = f;
+    return s;
+}
+
+}  // extern "C"
+
+namespace rt {
+__global__ void k_pairs_export(const int64_t* __restrict__ row_off, const int32_t* __restrict__ cols,
+                               const int32_t* __restrict__ perm, const int32_t* __restrict__ inv_perm, int64_t n,
+                               const int64_t* __restrict__ out_off, int32_t* out_cols) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t p = inv_perm[i];
+    int64_t b = row_off[p], e = row_off[p + 1], o = out_off[i];
+    for (int64_t k = b; k < e; ++k) out_cols[o + (k - b)] = perm[cols[k]];
+}
+
+__global__ void k_row_counts(const int64_t* __restrict__ row_off, const int32_t* __restrict__ inv_perm, int64_t n,
+                             int64_t* cnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t p = inv_perm[i];
+    cnt[i] = row_off[p + 1] - row_off[p];
+}
+}  // namespace rt
+
+extern "C" {
+
+rt_status rt_pairs(rt_ctx* c, int64_t* offsets, int32_t* cols) {
+    RT_TRY(check_ready(c));
+    if (!offsets || !cols) return fail(c, RT_ERR_INVALID, "NULL array");
+    const int64_t n = c->n;
+    // counts in caller order -> host prefix sum (diagnostic path, not the hot path)
+    RT_TRY(ensure(c, c->seg, (size_t)(n + 1) * 8, "scratch"));
+    int64_t* cnt = c->seg.as<int64_t>();
+    k_row_counts<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->row_off.as<int64_t>(),
+                                                                      c->inv_perm.as<int32_t>(), n, cnt);
+    std::string err;
+    int64_t* h = new (std::nothrow) int64_t[n + 1];
+    if (!h) return fail(c, RT_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(h + 1, cnt, n * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        delete[] h;
+        return cuda_fail(c, e, "rt_pairs counts");
+    }
+    h[0] = 0;
+    for (int64_t i = 0; i < n; ++i) h[i + 1] += h[i];
+    e = cudaMemcpyAsync(offsets, h, (n + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    delete[] h;
+    if (e != cudaSuccess) return cuda_fail(c, e, "rt_pairs offsets");
+    k_pairs_export<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+        c->row_off.as<int64_t>(), c->cols.as<int32_t>(), c->perm.as<int32_t>(), c->inv_perm.as<int32_t>(), n, offsets,
+        cols);
+    RT_CUDA(c, cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status rt_diagnostics(rt_ctx* c, rt_diag* out) {
+    if (!c || !out) return RT_ERR_INVALID;
+    c->err.clear();
+    unsigned long long cl = 0;
+    if (c->flags.p) {
+        RT_CUDA(c, cudaMemcpyAsync(&cl, c->flags.as<int>() + 8, 8, cudaMemcpyDeviceToHost, c->stream));
+        RT_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    c->diag.clamp_events = (int64_t)cl;
+    c->diag.threads_per_particle = c->tpp;
+    *out = c->diag;
+    return RT_OK;
+}
+
+const char* rt_last_error(const rt_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+void rt_destroy(rt_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    DevBuf* bufs[] = {&c->keys_in, &c->keys_out, &c->idx_in, &c->perm, &c->inv_perm, &c->cell_start, &c->cub_tmp,
+                      &c->xs_d, &c->xq, &c->m_s, &c->h_d, &c->omega_d, &c->V_d, &c->B_d, &c->cond_d, &c->invH_t,
+                      &c->h_t, &c->omega_t, &c->Bp_t, &c->counts, &c->row_off, &c->cols, &c->flags, &c->red_tmp,
+                      &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
+                      &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,
+                      &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad, &c->alpha_s,
+                      &c->L_dev, &c->dt_dev, &c->energy_part, &c->ck, &c->seg, &c->lam_a, &c->lam_b, &c->gbar,
+                      &c->lbar_part, &c->lbar_acc};
+    for (DevBuf* b : bufs) free_buf(*b);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,905 @@
+// Neighbour search and particle geometry of the FVPM photon-transport step:
+// cell list, smoothing lengths, symmetric pair lists, E_i / B_i, source injection weights.
+//
+// Part II of Ivkovic (2023), "The Neighbor Search: Determining the Smoothing Length"
+// (Eq. number-of-neighbors), Eqs. omega / particle-volume, matrix_E / matrix_B; Part III,
+// "Weights For Distribution Of Energy Density of a Star onto Particles"
+// (Eq. isotropy-correction-with-zero).  The thesis runs these as SWIFT cell tasks on CPUs;
+// here each is a data-parallel kernel over cell-sorted particles.
+#include <cub/cub.cuh>
+
+#include <cmath>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+namespace rt {
+
+enum FlagSlot { F_BADPOS = 0, F_NOCONV = 1, F_GEOM = 2, F_ILL = 3, F_SRC_NOCONV = 4, F_NSLOTS = 8 };
+
+struct Grid {
+    int nc[3];
+    double cell[3];
+    double inv_cell[3];
+    double box[3];
+    int periodic;
+    const int32_t* cell_start;   // [ncells + 1], lower bound of each cell in sorted order
+};
+
+__device__ __forceinline__ int wrap_cell(int c, int nc) {
+    c %= nc;
+    return c < 0 ? c + nc : c;
+}
+
+// Visit every particle (sorted index) in the cells within k[a] cells of (cx, cy, cz).
+// Rows along x are contiguous in sorted order, so each row is one or two index ranges.
+template <class F>
+__device__ __forceinline__ void for_each_candidate(const Grid& g, int cx, int cy, int cz, const int k[3], F&& f) {
+    int lo[3], hi[3];
+    int c0[3] = {cx, cy, cz};
+    bool all[3];
+    for (int a = 0; a < 3; ++a) {
+        all[a] = (2 * k[a] + 1 >= g.nc[a]);
+        lo[a] = all[a] ? 0 : c0[a] - k[a];
+        hi[a] = all[a] ? g.nc[a] - 1 : c0[a] + k[a];
+        if (!g.periodic && !all[a]) {
+            lo[a] = max(lo[a], 0);
+            hi[a] = min(hi[a], g.nc[a] - 1);
+        }
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z) {
+        int zz = wrap_cell(z, g.nc[2]);
+        for (int y = lo[1]; y <= hi[1]; ++y) {
+            int yy = wrap_cell(y, g.nc[1]);
+            int64_t base = ((int64_t)zz * g.nc[1] + yy) * g.nc[0];
+            // x range [lo, hi] possibly wrapping: split into contiguous segments
+            int xa = lo[0], xb = hi[0];
+            int segs_lo[2], segs_hi[2], ns = 0;
+            if (xa < 0) {
+                segs_lo[ns] = xa + g.nc[0]; segs_hi[ns] = g.nc[0] - 1; ++ns;
+                segs_lo[ns] = 0; segs_hi[ns] = xb; ++ns;
+            } else if (xb >= g.nc[0]) {
+                segs_lo[ns] = xa; segs_hi[ns] = g.nc[0] - 1; ++ns;
+                segs_lo[ns] = 0; segs_hi[ns] = xb - g.nc[0]; ++ns;
+            } else {
+                segs_lo[ns] = xa; segs_hi[ns] = xb; ++ns;
+            }
+            for (int s = 0; s < ns; ++s) {
+                int b = g.cell_start[base + segs_lo[s]];
+                int e = g.cell_start[base + segs_hi[s] + 1];
+                for (int j = b; j < e; ++j) f(j);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int cell_coord(double x, double inv_cell, int nc) {
+    int c = (int)floor(x * inv_cell);
+    return min(max(c, 0), nc - 1);
+}
+
+// exact (no contraction) minimal-image separation, identical to a plain double evaluation
+__device__ __forceinline__ double sep_exact(double xj, double xi, double box, int periodic) {
+    double v = __dsub_rn(xj, xi);
+    if (periodic) v = __dsub_rn(v, __dmul_rn(box, rint(__ddiv_rn(v, box))));
+    return v;
+}
+
+__device__ __forceinline__ double norm2_exact(double a, double b, double c) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
+}
+
+// fast minimal image (same value except at exactly half a box, which never neighbours)
+__device__ __forceinline__ double sep_fast(double xj, double xi, double box, double half, int periodic) {
+    double v = xj - xi;
+    if (periodic) {
+        if (v > half) v -= box;
+        else if (v < -half) v += box;
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------------------------
+// a1: cell keys, validation
+__global__ void k_keys(const double* __restrict__ x, int64_t n, Grid g, uint32_t* keys, int32_t* idx, int* flags) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c[3];
+    bool bad = false;
+    for (int a = 0; a < 3; ++a) {
+        double v = x[a * n + i];
+        if (!(v >= 0.0 && v < g.box[a])) bad = true;
+        c[a] = bad ? 0 : cell_coord(v, g.inv_cell[a], g.nc[a]);
+    }
+    if (bad) atomicExch(&flags[F_BADPOS], 1);
+    keys[i] = (uint32_t)(((int64_t)c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0]);
+    idx[i] = (int32_t)i;
+}
+
+__global__ void k_cell_start(const uint32_t* __restrict__ keys, int64_t n, int64_t ncells, int32_t* cell_start) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c > ncells) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < (uint32_t)c) lo = mid + 1; else hi = mid;
+    }
+    cell_start[c] = (int32_t)lo;
+}
+
+__global__ void k_gather_positions(const double* __restrict__ x, const double* __restrict__ m,
+                                   const int32_t* __restrict__ perm, int64_t n, double q0, double q1, double q2,
+                                   double* xs, uint32_t* xq, double* ms, int32_t* inv_perm) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t i = perm[p];
+    double qs[3] = {q0, q1, q2};
+    for (int a = 0; a < 3; ++a) {
+        double v = x[a * n + i];
+        xs[a * n + p] = v;
+        double f = floor(v * qs[a]);
+        f = fmin(fmax(f, 0.0), 4294967295.0);
+        xq[a * n + p] = (uint32_t)f;
+    }
+    ms[p] = m ? m[i] : 0.0;
+    inv_perm[i] = (int32_t)p;
+}
+
+// ------------------------------------------------------------------------------------
+// a2: smoothing lengths.  f(h) = h - eta * omega(h)^(-1/3), omega(h) = sum_j W(r_ij, h) with
+// the self term; safeguarded Newton, first in float on fixed-point separations, then in
+// double on the exact separations until the step is below machine precision.
+struct HParams {
+    double eta, h0, h_cap;
+    float scale[3];
+    int max_iter;
+    float tol32;
+};
+
+__device__ __forceinline__ float fsep(uint32_t a, uint32_t b, float scale) { return (float)(int32_t)(a - b) * scale; }
+
+__global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
+                          HParams hp, double* h_out, double* omega_out, int* flags) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const float kapf = (float)kKappa;
+    const float sigf = (float)kSigma;
+    uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+    int cx = cell_coord(px, g.inv_cell[0], g.nc[0]);
+    int cy = cell_coord(py, g.inv_cell[1], g.nc[1]);
+    int cz = cell_coord(pz, g.inv_cell[2], g.nc[2]);
+
+    // ---- float phase
+    float h = (float)hp.h0, lo = 0.f, hi = INFINITY;
+    const float eta = (float)hp.eta;
+    bool ok = false;
+    for (int it = 0; it < hp.max_iter; ++it) {
+        float H = kapf * h;
+        float iH = 1.f / H;
+        int k[3];
+        for (int a = 0; a < 3; ++a) k[a] = (int)ceilf(H * (float)g.inv_cell[a]);
+        float H2 = H * H;
+        float sw = 0.f, sdw = 0.f;
+        for_each_candidate(g, cx, cy, cz, k, [&](int j) {
+            float dx = fsep(xq[j], qx, hp.scale[0]);
+            float dy = fsep(xq[n + j], qy, hp.scale[1]);
+            float dz = fsep(xq[2 * n + j], qz, hp.scale[2]);
+            float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < H2) {
+                float q = sqrtf(r2) * iH;
+                float w = spline_w(q);
+                sw += w;
+                sdw += 3.f * w + q * spline_dw(q);
+            }
+        });
+        float om = sigf * iH * iH * iH * sw;
+        float dom = -kapf * sigf * iH * iH * iH * iH * sdw;      // d omega / d h
+        float cb = cbrtf(om);
+        float f = h - eta / cb;
+        float fp = 1.f + (eta / 3.f) / (cb * om) * dom;
+        if (f < 0.f) lo = h; else hi = h;
+        float step = f / fp;
+        float hn = h - step;
+        if (!(fabsf(step) > hp.tol32 * h)) { ok = true; break; }
+        if (!(hn > lo && hn < hi) || !(fp > 0.f)) hn = isinf(hi) ? 2.f * h : 0.5f * (lo + hi);
+        if (hn > (float)hp.h_cap) hn = (float)hp.h_cap;
+        h = hn;
+    }
+    if (!ok) {
+        atomicExch(&flags[F_NOCONV], 1);
+        h_out[p] = (double)h;
+        omega_out[p] = 0.0;
+        return;
+    }
+
+    // ---- double phase (exact separations)
+    double hd = (double)h;
+    double lod = 0.0, hid = INFINITY;
+    double om_d = 0.0;
+    const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
+    bool okd = false, last = false;
+    for (int it = 0; it < 16; ++it) {
+        double H = kKappa * hd;
+        double iH = 1.0 / H;
+        double H2 = H * H;
+        float Hf = (float)H * 1.001f;
+        float H2f = Hf * Hf;
+        int k[3];
+        for (int a = 0; a < 3; ++a) k[a] = (int)ceil(H * g.inv_cell[a] * 1.001);
+        double sw = 0.0, sdw = 0.0;
+        for_each_candidate(g, cx, cy, cz, k, [&](int j) {
+            float dxf = fsep(xq[j], qx, hp.scale[0]);
+            float dyf = fsep(xq[n + j], qy, hp.scale[1]);
+            float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+            if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) return;
+            double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
+            double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
+            double dz = sep_fast(xs[2 * n + j], pz, g.box[2], half[2], g.periodic);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < H2) {
+                double q = sqrt(r2) * iH;
+                double w = spline_w(q);
+                sw += w;
+                sdw += 3.0 * w + q * spline_dw(q);
+            }
+        });
+        double om = kSigma * iH * iH * iH * sw;
+        double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
+        double cb = cbrt(om);
+        double f = hd - hp.eta / cb;
+        double fp = 1.0 + (hp.eta / 3.0) / (cb * om) * dom;
+        om_d = om;
+        if (last) { okd = true; break; }        // omega evaluated at the final h
+        if (f < 0.0) lod = hd; else hid = hd;
+        double step = f / fp;
+        // once the Newton step is tiny the next iterate is exact to rounding: take it and
+        // evaluate omega there once more
+        if (fabs(step) <= 1e-11 * hd) last = true;
+        double hn = hd - step;
+        if (!last && (!(hn > lod && hn < hid) || !(fp > 0.0))) hn = isinf(hid) ? 1.01 * hd : 0.5 * (lod + hid);
+        hd = hn;
+    }
+    if (!okd) atomicExch(&flags[F_NOCONV], 1);
+    h_out[p] = hd;
+    omega_out[p] = om_d;
+}
+
+// ------------------------------------------------------------------------------------
+// a3: symmetric pair lists { j != i : r_ij < max(H_i, H_j) }.  A float test on the
+// fixed-point separation decides all pairs except those within 1e-5 of the threshold,
+// which are decided by the exact double test (r^2 and H^2 without contraction).
+struct PairParams {
+    float scale[3];
+    double Hmax;
+};
+
+template <bool FILL>
+__global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+                        const double* __restrict__ h, int64_t n, PairParams pp, int32_t* counts,
+                        const int64_t* __restrict__ row_off, int32_t* cols) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+    double Hi = __dmul_rn(kKappa, h[p]);
+    int cx = cell_coord(px, g.inv_cell[0], g.nc[0]);
+    int cy = cell_coord(py, g.inv_cell[1], g.nc[1]);
+    int cz = cell_coord(pz, g.inv_cell[2], g.nc[2]);
+    double R = fmax(Hi, pp.Hmax) * 1.0001;
+    int k[3];
+    for (int a = 0; a < 3; ++a) k[a] = (int)ceil(R * g.inv_cell[a]);
+    int cnt = 0;
+    int64_t base = FILL ? row_off[p] : 0;
+    for_each_candidate(g, cx, cy, cz, k, [&](int j) {
+        if (j == p) return;
+        double Hj = __dmul_rn(kKappa, h[j]);
+        double Hm = fmax(Hi, Hj);
+        float dx = fsep(xq[j], qx, pp.scale[0]);
+        float dy = fsep(xq[n + j], qy, pp.scale[1]);
+        float dz = fsep(xq[2 * n + j], qz, pp.scale[2]);
+        float r2f = dx * dx + dy * dy + dz * dz;
+        float H2f = (float)(Hm * Hm);
+        bool in;
+        if (r2f < H2f * (1.f - 1e-5f)) in = true;
+        else if (r2f > H2f * (1.f + 1e-5f)) in = false;
+        else {
+            double ex = sep_exact(xs[j], px, g.box[0], g.periodic);
+            double ey = sep_exact(xs[n + j], py, g.box[1], g.periodic);
+            double ez = sep_exact(xs[2 * n + j], pz, g.box[2], g.periodic);
+            in = norm2_exact(ex, ey, ez) < __dmul_rn(Hm, Hm);
+        }
+        if (in) {
+            if (FILL) cols[base + cnt] = j;
+            ++cnt;
+        }
+    });
+    if (!FILL) counts[p] = cnt;
+}
+
+// ------------------------------------------------------------------------------------
+// a4: E_i = sum_j psi_j(x_i) d d^T, B_i = E_i^-1 (double), and the per-particle factors used
+// by the pair kernels.
+__device__ void sym3_eigs(double a, double b, double c, double d, double e, double f, double ev[3]) {
+    // symmetric [[a d e][d b f][e f c]]: trigonometric closed form
+    double p1 = d * d + e * e + f * f;
+    double q = (a + b + c) / 3.0;
+    if (p1 == 0.0) { ev[0] = a; ev[1] = b; ev[2] = c; return; }
+    double p2 = (a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + 2.0 * p1;
+    double p = sqrt(p2 / 6.0);
+    double ip = 1.0 / p;
+    double B00 = (a - q) * ip, B11 = (b - q) * ip, B22 = (c - q) * ip, B01 = d * ip, B02 = e * ip, B12 = f * ip;
+    double detB = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) + B02 * (B01 * B12 - B11 * B02);
+    double r = fmin(fmax(detB / 2.0, -1.0), 1.0);
+    double phi = acos(r) / 3.0;
+    ev[0] = q + 2.0 * p * cos(phi);
+    ev[2] = q + 2.0 * p * cos(phi + 2.0943951023931954923);
+    ev[1] = 3.0 * q - ev[0] - ev[2];
+}
+
+template <class T>
+__global__ void k_geometry(const double* __restrict__ xs, const double* __restrict__ h,
+                           const double* __restrict__ omega, const int64_t* __restrict__ row_off,
+                           const int32_t* __restrict__ cols, int64_t n, double b0, double b1, double b2, int periodic,
+                           double* V_out, double* B_out, double* cond_out, T* invH_t, T* h_t, T* om_t, T* Bp_t,
+                           int* flags) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double box[3] = {b0, b1, b2};
+    const double half[3] = {0.5 * b0, 0.5 * b1, 0.5 * b2};
+    double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+    double hi = h[p], H = kKappa * hi, iH = 1.0 / H, H2 = H * H;
+    double om = omega[p];
+    double e_xx = 0, e_yy = 0, e_zz = 0, e_xy = 0, e_xz = 0, e_yz = 0;
+    for (int64_t e = row_off[p]; e < row_off[p + 1]; ++e) {
+        int j = cols[e];
+        double dx = sep_fast(xs[j], px, box[0], half[0], periodic);
+        double dy = sep_fast(xs[n + j], py, box[1], half[1], periodic);
+        double dz = sep_fast(xs[2 * n + j], pz, box[2], half[2], periodic);
+        double r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < H2)) continue;
+        double w = spline_w(sqrt(r2) * iH);
+        e_xx += w * dx * dx; e_yy += w * dy * dy; e_zz += w * dz * dz;
+        e_xy += w * dx * dy; e_xz += w * dx * dz; e_yz += w * dy * dz;
+    }
+    double fac = kSigma * iH * iH * iH / om;   // psi = fac * w
+    e_xx *= fac; e_yy *= fac; e_zz *= fac; e_xy *= fac; e_xz *= fac; e_yz *= fac;
+    // cofactor inverse of the symmetric matrix
+    double c_xx = e_yy * e_zz - e_yz * e_yz;
+    double c_xy = e_xz * e_yz - e_xy * e_zz;
+    double c_xz = e_xy * e_yz - e_xz * e_yy;
+    double det = e_xx * c_xx + e_xy * c_xy + e_xz * c_xz;
+    double V = 1.0 / om;
+    V_out[p] = V;
+    if (!(det > 0.0) || !(om > 0.0)) {
+        atomicExch(&flags[F_GEOM], 1);
+        for (int k = 0; k < 6; ++k) B_out[k * n + p] = 0.0;
+        cond_out[p] = INFINITY;
+        return;
+    }
+    double id = 1.0 / det;
+    double B[6];
+    B[0] = c_xx * id;
+    B[1] = (e_xx * e_zz - e_xz * e_xz) * id;
+    B[2] = (e_xx * e_yy - e_xy * e_xy) * id;
+    B[3] = c_xy * id;
+    B[4] = c_xz * id;
+    B[5] = (e_xy * e_xz - e_xx * e_yz) * id;
+    double ev[3];
+    sym3_eigs(e_xx, e_yy, e_zz, e_xy, e_xz, e_yz, ev);
+    double lmin = fmin(ev[0], fmin(ev[1], ev[2])), lmax = fmax(ev[0], fmax(ev[1], ev[2]));
+    double cond = lmin > 0 ? lmax / lmin : INFINITY;
+    cond_out[p] = cond;
+    if (!(lmin > 0)) atomicExch(&flags[F_GEOM], 1);
+    if (cond > 1e10) atomicAdd(&flags[F_ILL], 1);
+    double bp = V * V * kSigma * iH * iH * iH;   // V_i psitilde_j(x_i) = Bp_i d w(q_ij)
+    for (int k = 0; k < 6; ++k) {
+        B_out[k * n + p] = B[k];
+        Bp_t[k * n + p] = (T)(bp * B[k]);
+    }
+    invH_t[p] = (T)iH;
+    h_t[p] = (T)hi;
+    om_t[p] = (T)om;
+}
+
+// ------------------------------------------------------------------------------------
+// a5 preparation: per source, h_s = eta_s omega_s(h_s)^(-1/3) over gas only (no self term),
+// octant sums w_a of psi, mu_a = sum_b w_b / (q_nz w_a), xi = mu_a psi.  One warp per source.
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// warp-cooperative candidate visit: every lane walks the same ranges, lane l takes every
+// 32nd candidate; f(j, active) is called by all lanes for every chunk of 32.
+template <class F>
+__device__ __forceinline__ void warp_candidates(const Grid& g, int cx, int cy, int cz, const int k[3], int lane, F&& f) {
+    int lo[3], hi[3];
+    int c0[3] = {cx, cy, cz};
+    for (int a = 0; a < 3; ++a) {
+        bool all = (2 * k[a] + 1 >= g.nc[a]);
+        lo[a] = all ? 0 : c0[a] - k[a];
+        hi[a] = all ? g.nc[a] - 1 : c0[a] + k[a];
+        if (!g.periodic && !all) {
+            lo[a] = max(lo[a], 0);
+            hi[a] = min(hi[a], g.nc[a] - 1);
+        }
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z) {
+        int zz = wrap_cell(z, g.nc[2]);
+        for (int y = lo[1]; y <= hi[1]; ++y) {
+            int yy = wrap_cell(y, g.nc[1]);
+            int64_t base = ((int64_t)zz * g.nc[1] + yy) * g.nc[0];
+            int xa = lo[0], xb = hi[0];
+            int sl[2], sh[2], ns = 0;
+            if (xa < 0) { sl[ns] = xa + g.nc[0]; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb; }
+            else if (xb >= g.nc[0]) { sl[ns] = xa; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb - g.nc[0]; }
+            else { sl[ns] = xa; sh[ns++] = xb; }
+            for (int s = 0; s < ns; ++s) {
+                int b = g.cell_start[base + sl[s]];
+                int e = g.cell_start[base + sh[s] + 1];
+                for (int j0 = b; j0 < e; j0 += 32) {
+                    int j = j0 + lane;
+                    f(j, j < e);
+                }
+            }
+        }
+    }
+}
+
+struct SrcParams {
+    double eta, h0, h_cap;
+    int max_iter;
+};
+
+__global__ void k_src_h(Grid g, const double* __restrict__ xs, int64_t n, const double* __restrict__ xsrc,
+                        int64_t S, SrcParams sp, double* hs_out, double* oms_out, int* flags) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= S) return;
+    double p[3] = {xsrc[warp], xsrc[S + warp], xsrc[2 * S + warp]};
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = cell_coord(p[a], g.inv_cell[a], g.nc[a]);
+    const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
+    double h = sp.h0, lo = 0.0, hi = INFINITY, om = 0.0;
+    bool ok = false;
+    for (int it = 0; it < sp.max_iter; ++it) {
+        double H = kKappa * h, iH = 1.0 / H, H2 = H * H;
+        int k[3];
+        for (int a = 0; a < 3; ++a) k[a] = (int)ceil(H * g.inv_cell[a]);
+        double sw = 0.0, sdw = 0.0;
+        warp_candidates(g, c[0], c[1], c[2], k, lane, [&](int j, bool act) {
+            if (!act) return;
+            double dx = sep_fast(xs[j], p[0], g.box[0], half[0], g.periodic);
+            double dy = sep_fast(xs[n + j], p[1], g.box[1], half[1], g.periodic);
+            double dz = sep_fast(xs[2 * n + j], p[2], g.box[2], half[2], g.periodic);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < H2) {
+                double q = sqrt(r2) * iH;
+                double w = spline_w(q);
+                sw += w;
+                sdw += 3.0 * w + q * spline_dw(q);
+            }
+        });
+        sw = warp_sum(sw);
+        sdw = warp_sum(sdw);
+        om = kSigma * iH * iH * iH * sw;
+        double hn;
+        double f, fp;
+        if (om > 0.0) {
+            double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
+            double cb = cbrt(om);
+            f = h - sp.eta / cb;
+            fp = 1.0 + (sp.eta / 3.0) / (cb * om) * dom;
+        } else {
+            f = -INFINITY;
+            fp = 0.0;
+        }
+        if (f < 0.0) lo = h; else hi = h;
+        double step = (om > 0.0) ? f / fp : -INFINITY;
+        if (om > 0.0 && !(fabs(step) > 2e-16 * h)) { ok = true; break; }
+        hn = h - step;
+        if (!(hn > lo && hn < hi) || !(fp > 0.0)) hn = isinf(hi) ? 1.5 * h : 0.5 * (lo + hi);
+        if (hn > sp.h_cap) hn = sp.h_cap;
+        h = hn;
+    }
+    if (lane == 0) {
+        if (!ok) atomicExch(&flags[F_SRC_NOCONV], 1);
+        hs_out[warp] = h;
+        oms_out[warp] = om;
+    }
+}
+
+// count (FILL = false) or write (FILL = true) the gas entries of every source, in the
+// candidate order of the cell walk; the fill pass also forms xi.
+template <bool FILL>
+__global__ void k_src_entries(Grid g, const double* __restrict__ xs, int64_t n, const double* __restrict__ xsrc,
+                              int64_t S, const double* __restrict__ hs, const double* __restrict__ oms,
+                              int32_t* counts, const int64_t* __restrict__ off, int32_t* e_gas, double* e_xi,
+                              double* octw_out) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= S) return;
+    double p[3] = {xsrc[warp], xsrc[S + warp], xsrc[2 * S + warp]};
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = cell_coord(p[a], g.inv_cell[a], g.nc[a]);
+    const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
+    double h = hs[warp], H = kKappa * h, iH = 1.0 / H, H2 = H * H;
+    double fac = kSigma * iH * iH * iH / oms[warp];
+    int k[3];
+    for (int a = 0; a < 3; ++a) k[a] = (int)ceil(H * g.inv_cell[a]);
+    int cnt = 0;
+    int64_t base = FILL ? off[warp] : 0;
+    double w8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    warp_candidates(g, c[0], c[1], c[2], k, lane, [&](int j, bool act) {
+        bool in = false;
+        double ps = 0.0;
+        int oct = 0;
+        if (act) {
+            double dx = sep_fast(xs[j], p[0], g.box[0], half[0], g.periodic);
+            double dy = sep_fast(xs[n + j], p[1], g.box[1], half[1], g.periodic);
+            double dz = sep_fast(xs[2 * n + j], p[2], g.box[2], half[2], g.periodic);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < H2) {
+                in = true;
+                ps = fac * spline_w(sqrt(r2) * iH);
+                oct = (dx < 0 ? 1 : 0) | (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
+            }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+            if (FILL) {
+                e_gas[base + pos] = j;
+                e_xi[base + pos] = ps;   // psi for now; mu_a applied below
+            }
+            w8[oct] += ps;
+        }
+        cnt += __popc(bal);
+    });
+    if (!FILL) {
+        if (lane == 0) counts[warp] = cnt;
+        return;
+    }
+    double wsum = 0.0;
+    int qnz = 0;
+    for (int a = 0; a < 8; ++a) {
+        w8[a] = warp_sum(w8[a]);
+        wsum += w8[a];
+        qnz += (w8[a] > 0.0);
+    }
+    if (lane == 0)
+        for (int a = 0; a < 8; ++a) octw_out[8 * warp + a] = w8[a];
+    __syncwarp();
+    // xi = mu_a psi with mu_a = sum_b w_b / (q_nz w_a)
+    for (int e = lane; e < cnt; e += 32) {
+        int j = e_gas[base + e];
+        double dx = sep_fast(xs[j], p[0], g.box[0], half[0], g.periodic);
+        double dy = sep_fast(xs[n + j], p[1], g.box[1], half[1], g.periodic);
+        double dz = sep_fast(xs[2 * n + j], p[2], g.box[2], half[2], g.periodic);
+        int oct = (dx < 0 ? 1 : 0) | (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
+        double mu = wsum / ((double)qnz * w8[oct]);
+        e_xi[base + e] = mu * e_xi[base + e];
+    }
+}
+
+// injection entries keyed by (target, source) so that each target sums its sources in
+// source order
+__global__ void k_inj_keys(const int32_t* __restrict__ e_gas, const int64_t* __restrict__ off, int64_t S,
+                           int64_t total, uint64_t* keys, int32_t* vals) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    // source of entry e by binary search in off
+    int64_t lo = 0, hi = S;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= e) lo = mid; else hi = mid;
+    }
+    keys[e] = ((uint64_t)(uint32_t)e_gas[e] << 32) | (uint64_t)(uint32_t)lo;
+    vals[e] = (int32_t)e;
+}
+
+__global__ void k_inj_segments(const uint64_t* __restrict__ keys, const int32_t* __restrict__ vals, int64_t total,
+                               const double* __restrict__ e_xi, const double* __restrict__ V,
+                               int32_t* head_flag, int32_t* inj_src, double* inj_coef) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    uint32_t g = (uint32_t)(keys[e] >> 32);
+    head_flag[e] = (e == 0 || (uint32_t)(keys[e - 1] >> 32) != g) ? 1 : 0;
+    inj_src[e] = (int32_t)(uint32_t)(keys[e] & 0xffffffffu);
+    inj_coef[e] = e_xi[vals[e]] / V[g];   // xi / V_g: E_g += coef * L dt
+}
+
+__global__ void k_inj_targets(const uint64_t* __restrict__ keys, const int32_t* __restrict__ head_flag,
+                              const int32_t* __restrict__ head_pos, int64_t total, int32_t* targets,
+                              int32_t* inj_off) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    if (head_flag[e]) {
+        int t = head_pos[e];
+        targets[t] = (int32_t)(keys[e] >> 32);
+        inj_off[t] = (int32_t)e;
+    }
+    if (e == total - 1) inj_off[head_pos[e] + head_flag[e]] = (int32_t)total;
+}
+
+__global__ void k_minmax(const double* __restrict__ v, int64_t n, double* out) {
+    // single block; out[0] = min, out[1] = max
+    __shared__ double smin[256], smax[256];
+    double mn = INFINITY, mx = -INFINITY;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        mn = fmin(mn, v[i]);
+        mx = fmax(mx, v[i]);
+    }
+    smin[threadIdx.x] = mn;
+    smax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = smin[0];
+        out[1] = smax[0];
+    }
+}
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// ------------------------------------------------------------------------------------
+rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc) {
+    const int64_t n = c->n, S = c->n_src;
+    const rt_config& cfg = c->cfg;
+    cudaStream_t st = c->stream;
+    const int B = 256;
+
+    // grid: cells of about half the mean-density support radius
+    double vol = cfg.box[0] * cfg.box[1] * cfg.box[2];
+    double h0 = cfg.eta_res * std::cbrt(vol / (double)n);
+    double H0 = kKappa * h0;
+    int64_t ncells = 1;
+    for (int a = 0; a < 3; ++a) {
+        int nca = (int)std::floor(cfg.box[a] / (0.5 * H0));
+        nca = std::max(1, std::min(nca, 1024));
+        c->nc[a] = nca;
+        c->cell[a] = cfg.box[a] / nca;
+        ncells *= nca;
+    }
+    while (ncells > (int64_t)1 << 27) {   // keep the cell table small
+        ncells = 1;
+        for (int a = 0; a < 3; ++a) {
+            c->nc[a] = std::max(1, c->nc[a] / 2);
+            c->cell[a] = cfg.box[a] / c->nc[a];
+            ncells *= c->nc[a];
+        }
+    }
+    c->ncells = ncells;
+    int bits = 1;
+    while (((int64_t)1 << bits) < ncells) ++bits;
+    c->key_bits = bits;
+    for (int a = 0; a < 3; ++a) c->diag.grid[a] = c->nc[a];
+
+    Grid g;
+    for (int a = 0; a < 3; ++a) {
+        g.nc[a] = c->nc[a];
+        g.cell[a] = c->cell[a];
+        g.inv_cell[a] = 1.0 / c->cell[a];
+        g.box[a] = cfg.box[a];
+    }
+    g.periodic = cfg.periodic;
+
+    // buffers
+    RT_TRY(ensure(c, c->keys_in, n * 4, "keys"));
+    RT_TRY(ensure(c, c->keys_out, n * 4, "keys"));
+    RT_TRY(ensure(c, c->idx_in, n * 4, "idx"));
+    RT_TRY(ensure(c, c->perm, n * 4, "perm"));
+    RT_TRY(ensure(c, c->inv_perm, n * 4, "inv_perm"));
+    RT_TRY(ensure(c, c->cell_start, (ncells + 1) * 4, "cells"));
+    RT_TRY(ensure(c, c->xs_d, 3 * n * 8, "positions"));
+    RT_TRY(ensure(c, c->xq, 3 * n * 4, "positions"));
+    RT_TRY(ensure(c, c->m_s, n * 8, "masses"));
+    RT_TRY(ensure(c, c->h_d, n * 8, "h"));
+    RT_TRY(ensure(c, c->omega_d, n * 8, "omega"));
+    RT_TRY(ensure(c, c->V_d, n * 8, "V"));
+    RT_TRY(ensure(c, c->B_d, 6 * n * 8, "B"));
+    RT_TRY(ensure(c, c->cond_d, n * 8, "cond"));
+    size_t ts = c->fp64 ? 8 : 4;
+    RT_TRY(ensure(c, c->invH_t, n * ts, "geom"));
+    RT_TRY(ensure(c, c->h_t, n * ts, "geom"));
+    RT_TRY(ensure(c, c->omega_t, n * ts, "geom"));
+    RT_TRY(ensure(c, c->Bp_t, 6 * n * ts, "geom"));
+    RT_TRY(ensure(c, c->counts, (n + 1) * 4, "counts"));
+    RT_TRY(ensure(c, c->row_off, (n + 1) * 8, "row_off"));
+    RT_TRY(ensure(c, c->flags, 64, "flags"));
+    RT_TRY(ensure(c, c->red_tmp, 64, "reduction"));
+
+    int* flags = c->flags.as<int>();
+    RT_CUDA(c, cudaMemsetAsync(flags, 0, 64, st));
+
+    // cub scratch: radix sort of N and scan of N+1
+    size_t t1 = 0, t2 = 0, t3 = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, t1, (const uint32_t*)nullptr, (uint32_t*)nullptr,
+                                    (const int32_t*)nullptr, (int32_t*)nullptr, (int)n, 0, bits, st);
+    cub::DeviceScan::ExclusiveSum(nullptr, t2, (const int32_t*)nullptr, (int64_t*)nullptr, (int)(n + 1), st);
+    int64_t Smax = std::max<int64_t>(S, 1) * 4096;
+    cub::DeviceRadixSort::SortPairs(nullptr, t3, (const uint64_t*)nullptr, (uint64_t*)nullptr,
+                                    (const int32_t*)nullptr, (int32_t*)nullptr, (int)Smax, 0, 64, st);
+    RT_TRY(ensure(c, c->cub_tmp, std::max(t1, std::max(t2, t3)) + 256, "cub scratch"));
+
+    // a1: keys, sort, cell table, sorted copies
+    k_keys<<<nblk(n, B), B, 0, st>>>(x, n, g, c->keys_in.as<uint32_t>(), c->idx_in.as<int32_t>(), flags);
+    size_t tb = c->cub_tmp.bytes;
+    RT_CUDA(c, cub::DeviceRadixSort::SortPairs(c->cub_tmp.p, tb, c->keys_in.as<uint32_t>(), c->keys_out.as<uint32_t>(),
+                                               c->idx_in.as<int32_t>(), c->perm.as<int32_t>(), (int)n, 0, bits, st));
+    k_cell_start<<<nblk(ncells + 1, B), B, 0, st>>>(c->keys_out.as<uint32_t>(), n, ncells, c->cell_start.as<int32_t>());
+    g.cell_start = c->cell_start.as<int32_t>();
+    double qmul[3];
+    float qscale[3];
+    for (int a = 0; a < 3; ++a) {
+        double units = cfg.periodic ? 4294967296.0 : 2147483648.0;
+        qmul[a] = units / cfg.box[a];
+        qscale[a] = (float)(cfg.box[a] / units);
+    }
+    k_gather_positions<<<nblk(n, B), B, 0, st>>>(x, m, c->perm.as<int32_t>(), n, qmul[0], qmul[1], qmul[2],
+                                                  c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->m_s.as<double>(),
+                                                  c->inv_perm.as<int32_t>());
+    RT_CUDA(c, cudaGetLastError());
+
+    // a2: smoothing lengths
+    HParams hp;
+    hp.eta = cfg.eta_res;
+    hp.h0 = h0;
+    double minbox = std::min(cfg.box[0], std::min(cfg.box[1], cfg.box[2]));
+    hp.h_cap = cfg.periodic ? 0.5 * minbox / kKappa : 1e30;
+    for (int a = 0; a < 3; ++a) hp.scale[a] = qscale[a];
+    hp.max_iter = cfg.h_max_iter > 0 ? cfg.h_max_iter : 100;
+    hp.tol32 = (float)std::max(cfg.h_tol, 2e-6);
+    k_h_solve<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp,
+                                             c->h_d.as<double>(), c->omega_d.as<double>(), flags);
+    RT_CUDA(c, cudaGetLastError());
+    k_minmax<<<1, 256, 0, st>>>(c->h_d.as<double>(), n, c->red_tmp.as<double>());
+    int hflags[8];
+    double hmm[2];
+    RT_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+    RT_CUDA(c, cudaMemcpyAsync(hmm, c->red_tmp.p, sizeof(hmm), cudaMemcpyDeviceToHost, st));
+    RT_CUDA(c, cudaStreamSynchronize(st));
+    if (hflags[F_BADPOS]) return fail(c, RT_ERR_INVALID, "positions must be finite and inside [0, box)");
+    if (hflags[F_NOCONV]) return fail(c, RT_ERR_NOCONV, "smoothing-length iteration did not converge");
+    c->diag.h_min = hmm[0];
+    c->diag.h_max = hmm[1];
+    double Hmax = kKappa * hmm[1];
+    if (cfg.periodic && Hmax >= 0.5 * minbox)
+        return fail(c, RT_ERR_GEOMETRY, "support radius reaches half the periodic box");
+
+    // a3: symmetric pair lists
+    PairParams pp;
+    for (int a = 0; a < 3; ++a) pp.scale[a] = qscale[a];
+    pp.Hmax = Hmax;
+    k_pairs<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(), n,
+                                                  pp, c->counts.as<int32_t>(), nullptr, nullptr);
+    RT_CUDA(c, cudaMemsetAsync(c->counts.as<int32_t>() + n, 0, 4, st));
+    tb = c->cub_tmp.bytes;
+    RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->counts.as<int32_t>(), c->row_off.as<int64_t>(),
+                                             (int)(n + 1), st));
+    int64_t P2 = 0;
+    RT_CUDA(c, cudaMemcpyAsync(&P2, c->row_off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st));
+    RT_CUDA(c, cudaStreamSynchronize(st));
+    if (P2 >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "more than 2^31 neighbour entries");
+    c->n_directed = P2;
+    RT_TRY(ensure(c, c->cols, std::max<int64_t>(P2, 1) * 4, "pair lists"));
+    k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(), n,
+                                                 pp, nullptr, c->row_off.as<int64_t>(), c->cols.as<int32_t>());
+    RT_CUDA(c, cudaGetLastError());
+
+    // a4: geometry
+    if (c->fp64)
+        k_geometry<double><<<nblk(n, 128), 128, 0, st>>>(
+            c->xs_d.as<double>(), c->h_d.as<double>(), c->omega_d.as<double>(), c->row_off.as<int64_t>(),
+            c->cols.as<int32_t>(), n, cfg.box[0], cfg.box[1], cfg.box[2], cfg.periodic, c->V_d.as<double>(),
+            c->B_d.as<double>(), c->cond_d.as<double>(), c->invH_t.as<double>(), c->h_t.as<double>(),
+            c->omega_t.as<double>(), c->Bp_t.as<double>(), flags);
+    else
+        k_geometry<float><<<nblk(n, 128), 128, 0, st>>>(
+            c->xs_d.as<double>(), c->h_d.as<double>(), c->omega_d.as<double>(), c->row_off.as<int64_t>(),
+            c->cols.as<int32_t>(), n, cfg.box[0], cfg.box[1], cfg.box[2], cfg.periodic, c->V_d.as<double>(),
+            c->B_d.as<double>(), c->cond_d.as<double>(), c->invH_t.as<float>(), c->h_t.as<float>(),
+            c->omega_t.as<float>(), c->Bp_t.as<float>(), flags);
+    RT_CUDA(c, cudaGetLastError());
+
+    // a5 preparation: sources
+    c->n_inj_entries = 0;
+    c->n_inj_targets = 0;
+    if (S > 0) {
+        RT_TRY(ensure(c, c->xsrc_d, 3 * S * 8, "sources"));
+        RT_TRY(ensure(c, c->hs_d, S * 8, "sources"));
+        RT_TRY(ensure(c, c->omegas_d, S * 8 + 64 * S, "sources"));
+        RT_TRY(ensure(c, c->src_counts, (S + 1) * 4, "sources"));
+        RT_TRY(ensure(c, c->src_off, (S + 1) * 8, "sources"));
+        RT_CUDA(c, cudaMemcpyAsync(c->xsrc_d.p, xsrc, 3 * S * 8, cudaMemcpyDeviceToDevice, st));
+        SrcParams sp;
+        sp.eta = cfg.eta_res_star;
+        sp.h0 = cfg.eta_res_star * std::cbrt(vol / (double)n);
+        sp.h_cap = hp.h_cap;
+        sp.max_iter = std::max(hp.max_iter, 200);
+        unsigned sb = nblk(S * 32, 128);
+        k_src_h<<<sb, 128, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S, sp, c->hs_d.as<double>(),
+                                     c->omegas_d.as<double>(), flags);
+        k_src_entries<false><<<sb, 128, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S,
+                                                 c->hs_d.as<double>(), c->omegas_d.as<double>(),
+                                                 c->src_counts.as<int32_t>(), nullptr, nullptr, nullptr, nullptr);
+        RT_CUDA(c, cudaMemsetAsync(c->src_counts.as<int32_t>() + S, 0, 4, st));
+        tb = c->cub_tmp.bytes;
+        RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->src_counts.as<int32_t>(),
+                                                 c->src_off.as<int64_t>(), (int)(S + 1), st));
+        int64_t NE = 0;
+        RT_CUDA(c, cudaMemcpyAsync(&NE, c->src_off.as<int64_t>() + S, 8, cudaMemcpyDeviceToHost, st));
+        RT_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+        RT_CUDA(c, cudaStreamSynchronize(st));
+        if (hflags[F_SRC_NOCONV]) return fail(c, RT_ERR_NOCONV, "source smoothing-length iteration did not converge");
+        if (NE > Smax) return fail(c, RT_ERR_INVALID, "too many injection entries");
+        c->n_inj_entries = NE;
+        int64_t NEa = std::max<int64_t>(NE, 1);
+        RT_TRY(ensure(c, c->src_entry_gas, NEa * 4, "injection"));
+        RT_TRY(ensure(c, c->src_entry_xi, NEa * 8, "injection"));
+        RT_TRY(ensure(c, c->inj_key, NEa * 8, "injection"));
+        RT_TRY(ensure(c, c->inj_key_out, NEa * 8, "injection"));
+        RT_TRY(ensure(c, c->inj_val, NEa * 4, "injection"));
+        RT_TRY(ensure(c, c->inj_val_out, NEa * 4, "injection"));
+        RT_TRY(ensure(c, c->inj_src, NEa * 4, "injection"));
+        RT_TRY(ensure(c, c->inj_coef, NEa * 8, "injection"));
+        RT_TRY(ensure(c, c->inj_targets, NEa * 4, "injection"));
+        RT_TRY(ensure(c, c->inj_off, (NEa + 1) * 4, "injection"));
+        double* octw = c->omegas_d.as<double>() + S;   // 8 per source after omega_s
+        k_src_entries<true><<<sb, 128, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S,
+                                                c->hs_d.as<double>(), c->omegas_d.as<double>(), nullptr,
+                                                c->src_off.as<int64_t>(), c->src_entry_gas.as<int32_t>(),
+                                                c->src_entry_xi.as<double>(), octw);
+        if (NE > 0) {
+            k_inj_keys<<<nblk(NE, B), B, 0, st>>>(c->src_entry_gas.as<int32_t>(), c->src_off.as<int64_t>(), S, NE,
+                                                   c->inj_key.as<uint64_t>(), c->inj_val.as<int32_t>());
+            tb = c->cub_tmp.bytes;
+            RT_CUDA(c, cub::DeviceRadixSort::SortPairs(c->cub_tmp.p, tb, c->inj_key.as<uint64_t>(),
+                                                       c->inj_key_out.as<uint64_t>(), c->inj_val.as<int32_t>(),
+                                                       c->inj_val_out.as<int32_t>(), (int)NE, 0, 64, st));
+            // head flags into idx_in (free now), positions via scan into counts-sized scratch
+            int32_t* head = c->inj_val.as<int32_t>();       // reuse: NE int32
+            k_inj_segments<<<nblk(NE, B), B, 0, st>>>(c->inj_key_out.as<uint64_t>(), c->inj_val_out.as<int32_t>(), NE,
+                                                       c->src_entry_xi.as<double>(), c->V_d.as<double>(), head,
+                                                       c->inj_src.as<int32_t>(), c->inj_coef.as<double>());
+            int32_t* hpos = reinterpret_cast<int32_t*>(c->inj_key.as<uint64_t>());   // reuse: NE int32
+            tb = c->cub_tmp.bytes;
+            RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, head, hpos, (int)NE, st));
+            k_inj_targets<<<nblk(NE, B), B, 0, st>>>(c->inj_key_out.as<uint64_t>(), head, hpos, NE,
+                                                      c->inj_targets.as<int32_t>(), c->inj_off.as<int32_t>());
+            int32_t lastpos = 0, lasthead = 0;
+            RT_CUDA(c, cudaMemcpyAsync(&lastpos, hpos + NE - 1, 4, cudaMemcpyDeviceToHost, st));
+            RT_CUDA(c, cudaMemcpyAsync(&lasthead, head + NE - 1, 4, cudaMemcpyDeviceToHost, st));
+            RT_CUDA(c, cudaStreamSynchronize(st));
+            c->n_inj_targets = lastpos + lasthead;
+        }
+    }
+
+    // finish: flags, counters
+    RT_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+    RT_CUDA(c, cudaStreamSynchronize(st));
+    if (hflags[F_GEOM]) return fail(c, RT_ERR_GEOMETRY, "singular E_i: a particle has fewer than 3 non-coplanar neighbours");
+    c->diag.n_ill_conditioned = hflags[F_ILL];
+    c->diag.n_directed = P2;
+    c->diag.n_pairs = P2 / 2;
+    c->diag.n_injection = c->n_inj_entries;
+    k_minmax<<<1, 256, 0, st>>>(c->cond_d.as<double>(), n, c->red_tmp.as<double>());
+    double cmm[2];
+    RT_CUDA(c, cudaMemcpyAsync(cmm, c->red_tmp.p, sizeof(cmm), cudaMemcpyDeviceToHost, st));
+    k_minmax<<<1, 256, 0, st>>>(c->V_d.as<double>(), n, c->red_tmp.as<double>() + 2);
+    double vmm[2];
+    RT_CUDA(c, cudaMemcpyAsync(vmm, c->red_tmp.as<double>() + 2, sizeof(vmm), cudaMemcpyDeviceToHost, st));
+    RT_CUDA(c, cudaStreamSynchronize(st));
+    c->diag.cond_max = cmm[1];
+    c->diag.dx_min = std::cbrt(vmm[0] / (4.0 * M_PI / 3.0));
+    return RT_OK;
+}
+
+}  // namespace rt

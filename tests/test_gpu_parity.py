@@ -1,0 +1,239 @@
+"""CUDA library vs the FP64 oracle, element by element, through the C interface.
+
+Tolerances (derived from the arithmetic, see the design notes):
+  FP64 path:  |gpu - oracle| <= 1e-12 (|oracle| + 1e-6 max|oracle of that component|) per particle
+  FP32 path:  relative L1 per component and group <= 1e-5 per step; energy drift <= 1e-6
+  neighbour sets: identical except pairs whose r^2 lies within 1e-12 H^2 of the threshold
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2302_12727_gb300 import RTError, Transport, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+H_h = oracle.H_OVER_h
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def fp64_close(g, o, tol=1e-12):
+    g = np.asarray(g).reshape(o.shape[0] if o.ndim > 1 else 1, -1) if False else np.asarray(g)
+    o = np.asarray(o)
+    if o.ndim == 1:
+        scale = np.abs(o).max()
+        bad = np.abs(g - o) > tol * (np.abs(o) + 1e-6 * scale)
+        return bad.sum(), np.max(np.abs(g - o) / (np.abs(o) + 1e-6 * scale + 1e-300))
+    o2 = o.reshape(-1, o.shape[-1])
+    g2 = g.reshape(o2.shape)
+    scale = np.abs(o2).max(axis=1, keepdims=True)
+    den = np.abs(o2) + 1e-6 * scale + 1e-300
+    r = np.abs(g2 - o2) / den
+    return int((r > tol).sum()), float(r.max())
+
+
+def rel_l1(g, o):
+    """relative L1 per (group, component)."""
+    o2 = o.reshape(-1, o.shape[-1])
+    g2 = g.reshape(o2.shape)
+    return np.abs(g2 - o2).sum(1) / np.maximum(np.abs(o2).sum(1), 1e-300)
+
+
+def cfl_dt(o, C=0.9):
+    """dt = C min_i dx_i / c with dx = (V/(4 pi/3))^(1/3) (Eq. rt-cfl)."""
+    return C * ((o.V / (4 * np.pi / 3)) ** (1 / 3)).min() / o.c_red
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    _need_gpu()
+    w = W.config1()
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
+    return w, o
+
+
+def test_neighbours_and_geometry_fp64(cfg1):
+    w, o = cfg1
+    t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64")
+    f = t.fields()
+    h = f["h"].cpu().numpy()
+    np.testing.assert_allclose(h, o.h, rtol=1e-13)
+    np.testing.assert_allclose(f["omega"].cpu().numpy(), o.omega, rtol=1e-12)
+    np.testing.assert_allclose(f["V"].cpu().numpy(), o.V, rtol=1e-12)
+    Bo = o.particles()["B"]
+    Bg = f["B"].cpu().numpy()
+    assert np.abs(Bg - Bo).max() <= 1e-12 * np.abs(Bo).max()
+    # neighbour sets: bit-exact apart from ties at the support radius
+    off_g, cols_g = (a.cpu().numpy() for a in t.pairs())
+    off_o, cols_o = o.pairs()
+    n = w.n
+    mism = 0
+    for i in range(n):
+        a = np.sort(cols_g[off_g[i]:off_g[i + 1]])
+        b = cols_o[off_o[i]:off_o[i + 1]]
+        if not np.array_equal(a, b):
+            diff = np.setxor1d(a, b)
+            for j in diff:
+                d = w.x[:, j] - w.x[:, i]
+                d -= np.rint(d)
+                r2 = (d * d).sum()
+                Hm = H_h * max(o.h[i], o.h[j])
+                assert abs(r2 - Hm * Hm) < 1e-12 * Hm * Hm, (i, j)
+                mism += 1
+    d = t.diagnostics()
+    assert d["n_directed"] == len(cols_o) - 0 or mism > 0
+    assert d["n_ill_conditioned"] == o.geometry_stats()[0]
+    t.close()
+
+
+def test_gradients_fp64(cfg1):
+    w, o = cfg1
+    t = Transport(w.x, w.m, w.xsrc, n_groups=2, precision="fp64")
+    rng = np.random.default_rng(21)
+    U = rng.normal(size=(2, 4, w.n))
+    og = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=2)
+    ref = og.gradients(U).reshape(2, 4, 3, w.n)
+    g = t.gradients(t.state(U)).cpu().numpy()
+    nbad, rmax = fp64_close(g, ref)
+    assert nbad == 0, rmax
+    t.close()
+
+
+@pytest.mark.parametrize("dt_reading", ["cfl", "smoothing_length"])
+def test_transport_fp64_config1(cfg1, dt_reading):
+    """Config 1 (16^3 jittered lattice, one source, 10 steps) in FP64: every particle to 1e-12."""
+    w, o = cfg1
+    dt = cfl_dt(o) if dt_reading == "cfl" else 0.9 * o.h.min() / w.c_red
+    ref, _ = o.run(w.U0, w.n_steps, dt, w.Lsrc)
+    t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64")
+    U = t.state(w.U0)
+    t.subcycle(U, w.n_steps, dt, t.luminosities(w.Lsrc))
+    nbad, rmax = fp64_close(U.cpu().numpy(), ref)
+    assert nbad == 0, f"max rel err {rmax:.3e}"
+    t.close()
+
+
+def test_plain_steps_equal_graph_bitwise(cfg1):
+    """rt_transport_step repeated == one rt_subcycle graph (same kernels, same order)."""
+    w, o = cfg1
+    dt = cfl_dt(o)
+    for prec in ("fp64", "fp32"):
+        t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision=prec)
+        L = t.luminosities(w.Lsrc)
+        U1 = t.state(w.U0)
+        for _ in range(5):
+            t.step(U1, dt, L)
+        U2 = t.state(w.U0)
+        t.subcycle(U2, 5, dt, L)
+        U3 = t.state(w.U0)
+        t.subcycle(U3, 5, dt, L)      # graph replay
+        assert torch.equal(U1, U2) and torch.equal(U2, U3)
+        t.close()
+
+
+def test_fp32_config1_against_oracle(cfg1):
+    """FP32 mixed path: relative L1 <= 1e-5 per step, energy drift <= 1e-6."""
+    w, o = cfg1
+    dt = cfl_dt(o)
+    t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp32")
+    L = t.luminosities(w.Lsrc)
+    Ug = t.state(w.U0)
+    Uo = w.U0.copy()
+    for k in range(w.n_steps):
+        # one step from the same (oracle) state each time: the per-step error
+        Ug = t.state(Uo)
+        t.step(Ug, dt, L)
+        Uo, _ = o.run(Uo, 1, dt, w.Lsrc)
+        err = rel_l1(Ug.cpu().numpy().astype(np.float64), Uo)
+        nz = np.abs(Uo.reshape(-1, w.n)).sum(1) > 0
+        assert err[nz].max() <= 1e-5, (k, err)
+    # energy after n steps from one FP32 run against the oracle's
+    Ug = t.state(w.U0)
+    t.subcycle(Ug, w.n_steps, dt, L)
+    Eg = t.energy(Ug)
+    Eo = o.energy(Uo)
+    assert abs(Eg[0] - Eo[0]) <= 1e-6 * Eo[0]
+    t.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_energy_conserved_without_sources(prec, tol):
+    _need_gpu()
+    rng = np.random.default_rng(22)
+    x = W.jittered_lattice(20, 0.25, rng)
+    n = x.shape[1]
+    G = 3
+    U0 = np.zeros((G, 4, n))
+    U0[:, 0] = rng.uniform(0.5, 2.0, size=(G, n))
+    U0[:, 1:] = 0.3 * U0[:, :1] * rng.uniform(-1, 1, size=(G, 3, n)) / np.sqrt(3)
+    t = Transport(x, None, None, n_groups=G, precision=prec)
+    U = t.state(U0)
+    E0 = np.array(t.energy(U))
+    dt = 0.6 * t.diagnostics()["dx_min"]
+    t.subcycle(U, 20, dt)
+    E1 = np.array(t.energy(U))
+    assert np.all(np.abs(E1 - E0) <= tol * E0), (E0, E1)
+    t.close()
+
+
+def test_injection_energy_and_determinism():
+    _need_gpu()
+    w = W.config3(16)
+    t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64")
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups)
+    dt = cfl_dt(o, 0.6)
+    L = t.luminosities(w.Lsrc)
+    U = t.state(w.U0)
+    E0 = np.array(t.energy(U))
+    t.subcycle(U, 4, dt, L)
+    E1 = np.array(t.energy(U))
+    np.testing.assert_allclose(E1 - E0, 4 * dt * w.Lsrc.sum(0), rtol=1e-12)
+    ref, _ = o.run(w.U0, 4, dt, w.Lsrc)
+    nbad, rmax = fp64_close(U.cpu().numpy(), ref)
+    assert nbad == 0, rmax
+    U2 = t.state(w.U0)
+    t.subcycle(U2, 4, dt, L)
+    assert torch.equal(U, U2)
+    t.close()
+
+
+def test_config2_reduced_against_oracle():
+    """Config 2 shape (Poisson sine density, 3 groups, source + beam, grey sink) at 24^3,
+    both precisions, all particles."""
+    _need_gpu()
+    w = W.config2(24)
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
+    dt = cfl_dt(o)
+    alpha = w.kappa * w.m * o.omega
+    ref, _ = o.run(w.U0, 5, dt, w.Lsrc, alpha)
+    for prec in ("fp64", "fp32"):
+        t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision=prec, c_red=w.c_red)
+        U = t.state(w.U0)
+        t.subcycle(U, 5, dt, t.luminosities(w.Lsrc), t.alpha(alpha))
+        Ug = U.cpu().numpy().astype(np.float64)
+        if prec == "fp64":
+            nbad, rmax = fp64_close(Ug, ref)
+            assert nbad == 0, rmax
+        else:
+            assert rel_l1(Ug, ref).max() <= 5 * 1e-5
+        t.close()
+
+
+def test_errors_are_reported():
+    _need_gpu()
+    x = W.jittered_lattice(6, 0.2, np.random.default_rng(1))
+    x[0, 3] = 1.5     # outside the box
+    with pytest.raises(RTError, match="RT_ERR_INVALID"):
+        Transport(x, None, None, n_groups=1)
+    from paper_2302_12727_gb300 import make_config, rt_create, rt_destroy, rt_transport_step
+    ctx = rt_create(make_config(1), 100, 0)
+    U = torch.zeros(4 * 100, device="cuda")
+    with pytest.raises(RTError, match="RT_ERR_STATE"):
+        rt_transport_step(ctx, 0.1, U)
+    rt_destroy(ctx)
