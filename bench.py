@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Throughput of the FVPM photon-transport hot path on GB300.
+
+One step = one hydro step of the radiation solver on a fixed synthetic particle set:
+rt_neighbours (cell list, h, pair lists, geometry, source weights) + rt_subcycle
+(n_sub x [injection, gradients, pair fluxes + update + grey sink]) + rt_energy.
+
+Metric: pair-group interactions per second, R = P * G * n_sub / t_step, with P the
+unordered interacting pairs (r < max(H_i, H_j)) and G the photon groups.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling); the time
+is the max over ranks and the value sums all ranks' units.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RT pair interactions/s/group, FP32 vs FP64 at rel err<=1e-5; % of HBM peak"
+UNIT = "pair-group interactions/s"
+H_OVER_h = 1.825742
+
+# Algorithmic FP32 operations of one pair in one sub-cycle (one evaluation per unordered
+# pair; FMA = 2): flux kernel 70 + 174 G, gradient kernel 2 x (21 + 28 G).  Derivation in
+# the design notes.
+def flux_flops_per_pair(G):
+    return 70 + 174 * G
+
+
+def grad_flops_per_pair(G):
+    return 2 * (21 + 28 * G)
+
+
+# Algorithmic bytes per particle of the flux kernel: geometry 48, U in 16G, grad U in 48G,
+# U out 16G, alpha 4.
+def flux_bytes_per_particle(G):
+    return 52 + 80 * G
+
+
+def sub_bytes_per_particle(G):
+    """gradient pass (44 + 16G + 48G) + flux pass (52 + 80G)."""
+    return 96 + 144 * G
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def workload(cfg_id):
+    from paper_2302_12727_gb300 import workloads as W
+    return W.CONFIGS[cfg_id]()
+
+
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flux_traffic_from_profile(G):
+    """DRAM bytes per flux launch from the committed ncu summary, if it was taken on the
+    current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_flux_poisson-sine-64^3-G3.md")
+    src = os.path.join(ROOT, "paper_2302_12727_gb300", "csrc", "rt_transport.cu")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"source_sha1:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    cur = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    return float(m.group(1)) if h.group(1) == cur else None
+
+
+# ---------------------------------------------------------------------------------------
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2302_12727_gb300 import Transport, rt_kernel_times, rt_set_profiling
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w = workload(args.config)
+    G, n_sub, n = w.n_groups, w.n_steps, w.n
+    prec = args.precision
+    T = Transport(w.x, w.m, w.xsrc, n_groups=G, c_red=w.c_red, precision=prec, device=dev)
+    diag = T.diagnostics()
+    P = diag["n_pairs"]
+    dt = args.cfl * diag["dx_min"] / w.c_red
+    alpha = None
+    if w.kappa:
+        f = T.fields()
+        alpha = (w.kappa * torch.as_tensor(w.m, device=dev) * f["omega"]).contiguous()
+    L = T.luminosities(w.Lsrc)
+    U0 = T.state(w.U0)
+    U = U0.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    rt_set_profiling(T.ctx, True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        T.rebuild()
+        T.subcycle(U, n_sub, dt, L, alpha)
+        return T.energy(U)
+
+    for _ in range(args.warmup):
+        U.copy_(U0)
+        step()
+    torch.cuda.synchronize()
+
+    kflux_ms, kflux_n, kgrad_ms, kgrad_n = 0.0, 0, 0.0, 0
+    times = []
+    launches0 = T.diagnostics()["kernel_launches"]
+    sampler = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        U.copy_(U0)
+        flush.fill_(1.0)           # evict the previous step's working set from L2
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        kt = rt_kernel_times(T.ctx)
+        kflux_ms += kt["flux"][0]
+        kflux_n += kt["flux"][1]
+        kgrad_ms += kt["gradient"][0]
+        kgrad_n += kt["gradient"][1]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = T.diagnostics()["kernel_launches"] - launches0
+    # U.copy_ and flush.fill_ are torch's kernels, outside the per-step events
+    t_total = sum(times) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    units_rank = P * G * n_sub * args.steps
+    value = units_rank * ws / t_total
+    ms_step = t_total / args.steps * 1e3
+
+    out = None
+    if rank == 0:
+        hbm_gbs, sm_max_mhz, peak_kind = measured_peaks()
+        flux_avg_s = kflux_ms / max(kflux_n, 1) / 1e3
+        grad_avg_s = kgrad_ms / max(kgrad_n, 1) / 1e3
+        alu_peak = 152 * 128 * 2 * 2070e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x max clock
+        flux_flops = P * flux_flops_per_pair(G)
+        achieved = flux_flops / flux_avg_s / 1e12 if kflux_n else None
+        traffic = flux_traffic_from_profile(G) if (args.config == 2 and prec == "fp32") else None
+        sub_s = (kflux_ms + kgrad_ms) / 1e3 / args.steps
+        out = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "particles": n, "groups": G, "sub_cycles": n_sub,
+                       "sources": w.n_src, "pairs": P, "dt": dt, "dt_rule": f"{args.cfl} * min dx / c (Eq. rt-cfl)",
+                       "precision": "fp32 fluxes/gradients, fp64 h/E_i/B_i/energy" if prec == "fp32" else "fp64",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "alu", "kernel": "k_flux", "achieved": achieved, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
+                         "traffic": traffic, "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                         "flops_per_launch": flux_flops, "avg_launch_ms": flux_avg_s * 1e3,
+                         "hbm_frac_of_" + peak_kind: (flux_bytes_per_particle(G) * n / flux_avg_s / 1e9) / hbm_gbs
+                         if kflux_n else None},
+            "kernels": {"flux_ms_avg": flux_avg_s * 1e3, "gradient_ms_avg": grad_avg_s * 1e3,
+                        "flux_launches": kflux_n, "gradient_launches": kgrad_n},
+            "subcycle_only": {"value": P * G * n_sub / sub_s if sub_s > 0 else None, "unit": UNIT,
+                              "note": "gradient + flux kernel time only (events around each launch)",
+                              "hbm_frac_of_" + peak_kind: sub_bytes_per_particle(G) * n * n_sub / sub_s / 1e9 / hbm_gbs
+                              if sub_s > 0 else None},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "wall_s_timed": wall,
+        }
+    # end-to-end through the public API with host buffers
+    if not args.no_e2e:
+        e2e = run_e2e(args, T, w, dt, alpha, L, dev, flush, P)
+        if rank == 0:
+            out["e2e"] = e2e
+    T.close()
+    if rank == 0 and not args.no_fp64_plain:
+        out["fp64_plain"] = run_fp64_plain(w, args, dev, out["ms_per_step"], P)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, args, P)
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_e2e(args, T, w, dt, alpha, L, dev, flush, P):
+    """Same steps through the Python API, every step copying the positions and the initial
+    state from pinned host memory and the final state and energy back."""
+    import torch
+    x_h = torch.from_numpy(np.ascontiguousarray(w.x)).pin_memory()
+    U_h = torch.from_numpy(np.ascontiguousarray(w.U0).astype(np.float32 if T.precision == "fp32" else np.float64)).pin_memory()
+    out_h = torch.empty_like(U_h).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    G, n_sub = w.n_groups, w.n_steps
+    times = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xd = x_h.to(dev, non_blocking=True)
+        U = U_h.to(dev, non_blocking=True)
+        T.rebuild(xd)
+        T.subcycle(U, n_sub, dt, L, alpha)
+        E = T.energy(U)
+        out_h.copy_(U, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    t = sum(times) / 1e3
+    bi = x_h.numel() * 8 + U_h.numel() * U_h.element_size()
+    bo = out_h.numel() * out_h.element_size() + 8 * G
+    return {"value": P * G * n_sub * len(times) / t, "unit": UNIT, "h2d_bytes_per_step": int(bi),
+            "d2h_bytes_per_step": int(bo), "ms_per_step": t / len(times) * 1e3}
+
+
+def run_fp64_plain(w, args, dev, ms_fp32, P):
+    """The plain FP64 path: FP64 kernels launched one step at a time (no graph)."""
+    import torch
+    from paper_2302_12727_gb300 import Transport
+    G, n_sub = w.n_groups, w.n_steps
+    T = Transport(w.x, w.m, w.xsrc, n_groups=G, c_red=w.c_red, precision="fp64", device=dev)
+    d = T.diagnostics()
+    dt = args.cfl * d["dx_min"] / w.c_red
+    alpha = None
+    if w.kappa:
+        f = T.fields()
+        alpha = (w.kappa * torch.as_tensor(w.m, device=dev) * f["omega"]).contiguous()
+    L = T.luminosities(w.Lsrc)
+    U0 = T.state(w.U0)
+    reps = 2
+    times = []
+    for k in range(reps + 1):
+        U = U0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T.rebuild()
+        for _ in range(n_sub):
+            T.step(U, dt, L, alpha)
+        T.energy(U)
+        torch.cuda.synchronize()
+        if k:
+            times.append(time.perf_counter() - t0)
+    T.close()
+    ms = statistics.median(times) * 1e3
+    return {"ms_per_step": ms, "value": P * G * n_sub / (ms / 1e3), "unit": UNIT,
+            "speedup_of_fp32_graph": ms / ms_fp32}
+
+
+def oracle_step_times(w, P, n_src_steps=2):
+    import oracle
+    o_t0 = time.perf_counter()
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
+    t_build = time.perf_counter() - o_t0
+    dx = (o.V / (4 * np.pi / 3)) ** (1 / 3)
+    dt = 0.9 * dx.min() / w.c_red
+    alpha = w.kappa * w.m * o.omega if w.kappa else None
+    t0 = time.perf_counter()
+    o.run(w.U0, n_src_steps, dt, w.Lsrc, alpha)
+    t_step = (time.perf_counter() - t0) / n_src_steps
+    return t_build, t_step, oracle.num_threads()
+
+
+def cpu_baseline(w, args, P):
+    t_build, t_step, cores = oracle_step_times(w, P)
+    T = t_build + w.n_steps * t_step
+    return {"value": P * w.n_groups * w.n_steps / T, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"full {w.n}-particle set: oracle build ({t_build:.2f} s) + 2 of the {w.n_steps} steps "
+                      f"({t_step:.2f} s each) timed; the {w.n_steps}-step figure extrapolated from them"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return
+    w = workload(args.config)
+    import oracle
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
+    off, _ = o.pairs()
+    P = int(off[-1]) // 2
+    del o
+    times = []
+    for k in range(args.warmup + args.steps):
+        t_build, t_step, cores = oracle_step_times(w, P, 1)
+        if k >= args.warmup:
+            times.append(t_build + w.n_steps * t_step)
+    T = sum(times) / len(times)
+    val = P * w.n_groups * w.n_steps / T
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": T * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "particles": w.n, "groups": w.n_groups, "sub_cycles": w.n_steps,
+                      "pairs": P},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"each step: oracle build + 1 of the {w.n_steps} sub-cycle steps timed on the "
+                                      f"full {w.n}-particle set, the step time extrapolated to {w.n_steps} sub-cycles"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--cfl", type=float, default=0.9)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-plain", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -93,7 +93,13 @@ typedef struct {
     int64_t clamp_events;     /* cumulative count of E < 0 fix-ups */
     int32_t grid[3];          /* cell-list dimensions used by rt_neighbours */
     int32_t threads_per_particle;  /* launch shape picked for the pair kernels */
+    int64_t kernel_launches;  /* cumulative launches of the library's own kernels (graph
+                                 replays count every kernel node; library sorts and scans
+                                 that the build calls are not counted) */
 } rt_diag;
+
+/* Kernel kinds reported by rt_kernel_times. */
+enum { RT_KERNEL_INJECT = 0, RT_KERNEL_GRADIENT = 1, RT_KERNEL_FLUX = 2, RT_KERNEL_KINDS = 3 };
 
 /* Create a context for n particles and n_src sources.  cuda_stream is a cudaStream_t
  * (NULL = legacy default stream).  Allocates the per-particle workspaces.  On failure
@@ -155,6 +161,18 @@ rt_status rt_pairs(rt_ctx* ctx, int64_t* offsets_dev, int32_t* cols_dev);
 
 /* Counters of the last rt_neighbours and of the steps since (host struct). */
 rt_status rt_diagnostics(rt_ctx* ctx, rt_diag* out);
+
+/* Per-kernel timing (tracing aid, no counterpart in the thesis).  With on = 1, later
+ * rt_transport_step / rt_subcycle calls record CUDA events around every injection,
+ * gradient and flux launch (inside the captured graph as event nodes).  Changing the
+ * setting discards the captured graphs. */
+rt_status rt_set_profiling(rt_ctx* ctx, int32_t on);
+
+/* Summed device time in milliseconds and number of launches per kernel kind
+ * (ms_host[RT_KERNEL_KINDS], launches_host[RT_KERNEL_KINDS], host arrays) of the most
+ * recent rt_transport_step or rt_subcycle call made with profiling on; zeros if none.
+ * Synchronises the stream. */
+rt_status rt_kernel_times(rt_ctx* ctx, double* ms_host, int64_t* launches_host);
 
 /* Message of the last failure ("" if none).  Valid until the next call on ctx. */
 const char* rt_last_error(const rt_ctx* ctx);

@@ -20,8 +20,10 @@ _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4
            5: "RT_ERR_GEOMETRY", 6: "RT_ERR_TIMEOUT", 7: "RT_ERR_STATE"}
 
 EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
-            "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_last_error",
-            "rt_destroy"]
+            "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
+            "rt_kernel_times", "rt_last_error", "rt_destroy"]
+
+RT_KERNEL_INJECT, RT_KERNEL_GRADIENT, RT_KERNEL_FLUX, RT_KERNEL_KINDS = 0, 1, 2, 3
 
 
 class rt_config(C.Structure):
@@ -35,7 +37,7 @@ class rt_diag(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("n_directed", C.c_int64), ("n_injection", C.c_int64),
                 ("n_ill_conditioned", C.c_int64), ("cond_max", C.c_double), ("h_min", C.c_double),
                 ("h_max", C.c_double), ("dx_min", C.c_double), ("clamp_events", C.c_int64),
-                ("grid", C.c_int32 * 3), ("threads_per_particle", C.c_int32)]
+                ("grid", C.c_int32 * 3), ("threads_per_particle", C.c_int32), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +78,8 @@ def load_library():
     lib.rt_particle_fields.argtypes = [vp, dp, dp, dp, dp]
     lib.rt_pairs.argtypes = [vp, dp, dp]
     lib.rt_diagnostics.argtypes = [vp, C.POINTER(rt_diag)]
+    lib.rt_set_profiling.argtypes = [vp, C.c_int32]
+    lib.rt_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     lib.rt_last_error.argtypes = [vp]
     lib.rt_last_error.restype = C.c_char_p
     lib.rt_destroy.argtypes = [vp]
@@ -170,6 +174,19 @@ def rt_diagnostics(ctx) -> dict:
     d = rt_diag()
     _check(ctx, load_library().rt_diagnostics(ctx, C.byref(d)))
     return d.as_dict()
+
+
+def rt_set_profiling(ctx, on: bool):
+    _check(ctx, load_library().rt_set_profiling(ctx, 1 if on else 0))
+
+
+def rt_kernel_times(ctx):
+    """{kind: (ms, launches)} of the most recent profiled step or sub-cycle call."""
+    ms = (C.c_double * RT_KERNEL_KINDS)()
+    nl = (C.c_int64 * RT_KERNEL_KINDS)()
+    _check(ctx, load_library().rt_kernel_times(ctx, ms, nl))
+    names = ("inject", "gradient", "flux")
+    return {names[k]: (ms[k], nl[k]) for k in range(RT_KERNEL_KINDS)}
 
 
 def rt_last_error(ctx) -> str:

@@ -46,9 +46,49 @@ static void free_buf(DevBuf& b) {
     b.bytes = 0;
 }
 
+static void destroy_prof(std::vector<ProfRec>& v) {
+    for (auto& r : v) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    v.clear();
+}
+
 static void drop_graphs(rt_ctx* c) {
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : c->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        destroy_prof(kv.second.prof);
+    }
     c->graphs.clear();
+    c->last_prof = nullptr;
+}
+
+// inside a stream capture a plain record only orders the capture; an external record
+// becomes an event-record node that fires on every replay
+static void record_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &st);
+    if (st == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else cudaEventRecord(e, s);
+}
+
+int prof_begin(rt_ctx* c, cudaStream_t s, int kind) {
+    if (!c->profiling || !c->prof_sink) return -1;
+    ProfRec r;
+    r.kind = kind;
+    if (cudaEventCreate(&r.start) != cudaSuccess) return -1;
+    if (cudaEventCreate(&r.stop) != cudaSuccess) {
+        cudaEventDestroy(r.start);
+        return -1;
+    }
+    record_event(r.start, s);
+    c->prof_sink->push_back(r);
+    return (int)c->prof_sink->size() - 1;
+}
+
+void prof_end(rt_ctx* c, cudaStream_t s, int idx) {
+    if (idx < 0 || !c->prof_sink) return;
+    record_event((*c->prof_sink)[idx].stop, s);
 }
 
 static size_t tsize(const rt_ctx* c) { return c->fp64 ? 8 : 4; }
@@ -67,7 +107,7 @@ static rt_status ensure_state(rt_ctx* c) {
     const int G = c->cfg.n_groups;
     RT_TRY(ensure(c, c->U_a, (size_t)4 * G * n * tsize(c), "state"));
     RT_TRY(ensure(c, c->U_b, (size_t)4 * G * n * tsize(c), "state"));
-    RT_TRY(ensure(c, c->grad, (size_t)12 * G * n * tsize(c), "gradients"));
+    RT_TRY(ensure(c, c->grad_t, (size_t)12 * G * n * tsize(c), "gradients"));
     RT_TRY(ensure(c, c->alpha_s, (size_t)n * tsize(c), "absorption"));
     RT_TRY(ensure(c, c->L_dev, (size_t)std::max<int64_t>(c->n_src, 1) * G * 8, "luminosities"));
     RT_TRY(ensure(c, c->dt_dev, 64, "dt"));
@@ -138,13 +178,7 @@ rt_status rt_neighbours(rt_ctx* c, const double* x, const double* m, const doubl
     if (g_generation != gen0 || c->n_inj_targets != targets0) drop_graphs(c);
     if (h_out) {
         // h in caller order
-        RT_TRY(ensure(c, c->red_tmp, 64, "reduction"));
-        const int comps = 1;
-        bool f = c->fp64;
-        c->fp64 = true;
-        rt_status s2 = from_sorted(c, c->h_d.p, h_out, comps);
-        c->fp64 = f;
-        if (s2 != RT_OK) return s2;
+        RT_TRY(field_out(c, c->h_d.as<double>(), h_out, 1));
     }
     c->built = true;
     return RT_OK;
@@ -154,9 +188,9 @@ rt_status rt_gradients(rt_ctx* c, const void* U, void* gradU) {
     RT_TRY(check_ready(c));
     if (!U || !gradU) return fail(c, RT_ERR_INVALID, "NULL array");
     const int G = c->cfg.n_groups;
-    RT_TRY(to_sorted(c, U, c->U_a.p, 4 * G));
-    RT_TRY(launch_gradient(c, c->stream, c->U_a.p, c->grad.p));
-    RT_TRY(from_sorted(c, c->grad.p, gradU, 12 * G));
+    RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
+    RT_TRY(launch_gradient(c, c->stream, c->U_a.p));
+    RT_TRY(state_out(c, c->grad_t.p, gradU, 12 * G, 12 * G, 0));
     return RT_OK;
 }
 
@@ -166,10 +200,17 @@ rt_status rt_transport_step(rt_ctx* c, double dt, void* U, const double* Lsrc, c
     if (!std::isfinite(dt) || dt < 0) return fail(c, RT_ERR_INVALID, "dt must be finite and >= 0");
     const int G = c->cfg.n_groups;
     bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
-    RT_TRY(to_sorted(c, U, c->U_a.p, 4 * G));
+    RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
     RT_TRY(set_step_inputs(c, dt, Lsrc, alpha));
-    RT_TRY(launch_step(c, c->stream, c->U_a.p, c->U_b.p, has_src, alpha != nullptr));
-    RT_TRY(from_sorted(c, c->U_b.p, U, 4 * G));
+    if (c->profiling) {
+        destroy_prof(c->plain_prof);
+        c->prof_sink = &c->plain_prof;
+    }
+    rt_status s = launch_step(c, c->stream, c->U_a.p, c->U_b.p, has_src, alpha != nullptr);
+    c->prof_sink = nullptr;
+    if (c->profiling) c->last_prof = &c->plain_prof;
+    RT_TRY(s);
+    RT_TRY(state_out(c, c->U_b.p, U, 4 * G, 4 * G, 0));
     return RT_OK;
 }
 
@@ -182,35 +223,46 @@ rt_status rt_subcycle(rt_ctx* c, int32_t n_sub, double dt, void* U, const double
     const int G = c->cfg.n_groups;
     bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
     bool has_alpha = alpha != nullptr;
-    RT_TRY(to_sorted(c, U, c->U_a.p, 4 * G));
+    RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
     RT_TRY(set_step_inputs(c, dt, Lsrc, alpha));
     GraphKey key{n_sub, has_src ? 1 : 0, has_alpha ? 1 : 0};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
+        GraphEntry entry;
         cudaGraph_t graph = nullptr;
         RT_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         void* a = c->U_a.p;
         void* b = c->U_b.p;
         rt_status s = RT_OK;
+        int64_t l0 = c->launches;
+        c->prof_sink = c->profiling ? &entry.prof : nullptr;
         for (int k = 0; k < n_sub && s == RT_OK; ++k) {
             s = launch_step(c, c->cap_stream, a, b, has_src, has_alpha);
             std::swap(a, b);
         }
+        c->prof_sink = nullptr;
+        entry.kernels = c->launches - l0;
+        c->launches = l0;
         cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
-        if (s != RT_OK) {
+        if (s != RT_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            return s;
+            destroy_prof(entry.prof);
+            if (s != RT_OK) return s;
+            return cuda_fail(c, e, "cudaStreamEndCapture");
         }
-        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
-        cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, graph, 0);
+        e = cudaGraphInstantiate(&entry.exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
-        it = c->graphs.emplace(key, exec).first;
+        if (e != cudaSuccess) {
+            destroy_prof(entry.prof);
+            return cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+        it = c->graphs.emplace(key, entry).first;
     }
-    RT_CUDA(c, cudaGraphLaunch(it->second, c->stream));
+    RT_CUDA(c, cudaGraphLaunch(it->second.exec, c->stream));
+    c->launches += it->second.kernels;
+    if (c->profiling) c->last_prof = &it->second.prof;
     void* fin = (n_sub % 2 == 0) ? c->U_a.p : c->U_b.p;
-    RT_TRY(from_sorted(c, fin, U, 4 * G));
+    RT_TRY(state_out(c, fin, U, 4 * G, 4 * G, 0));
     return RT_OK;
 }
 
@@ -226,13 +278,13 @@ rt_status rt_adjoint(rt_ctx* c, int32_t n_sub, double dt, int32_t ckpt_every, co
     RT_TRY(set_step_inputs(c, dt, Lsrc, alpha));
     RT_TRY(ensure(c, c->lam_a, (size_t)4 * G * c->n * tsize(c), "adjoint"));
     RT_TRY(ensure(c, c->lam_b, (size_t)4 * G * c->n * tsize(c), "adjoint"));
-    RT_TRY(to_sorted(c, U0, c->U_a.p, 4 * G));
-    RT_TRY(to_sorted(c, dLdU_final, c->lam_a.p, 4 * G));
+    RT_TRY(state_in(c, U0, c->U_a.p, 4 * G, 4 * G, 0));
+    RT_TRY(state_in(c, dLdU_final, c->lam_a.p, 4 * G, 4 * G, 0));
     if (dLdLsrc && c->n_src > 0)
         RT_CUDA(c, cudaMemsetAsync(dLdLsrc, 0, (size_t)c->n_src * G * sizeof(double), c->stream));
     RT_TRY(run_adjoint(c, n_sub, ckpt_every, has_src, alpha != nullptr, c->U_a.p, c->lam_a.p, c->lam_b.p,
                        (dLdLsrc && c->n_src > 0) ? dLdLsrc : nullptr));
-    RT_TRY(from_sorted(c, c->lam_b.p, dLdU0, 4 * G));
+    RT_TRY(state_out(c, c->lam_b.p, dLdU0, 4 * G, 4 * G, 0));
     return RT_OK;
 }
 
@@ -240,7 +292,7 @@ rt_status rt_energy(rt_ctx* c, const void* U, double* E_host) {
     RT_TRY(check_ready(c));
     if (!U || !E_host) return fail(c, RT_ERR_INVALID, "NULL array");
     const int G = c->cfg.n_groups;
-    RT_TRY(to_sorted(c, U, c->U_a.p, 4 * G));
+    RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
     double* out = c->energy_part.as<double>() + (size_t)G * 512;
     RT_TRY(launch_energy(c, c->stream, c->U_a.p, out));
     RT_CUDA(c, cudaMemcpyAsync(E_host, out, G * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -250,32 +302,19 @@ rt_status rt_energy(rt_ctx* c, const void* U, double* E_host) {
 
 rt_status rt_particle_fields(rt_ctx* c, double* h, double* omega, double* V, double* B) {
     RT_TRY(check_ready(c));
-    bool f = c->fp64;
-    c->fp64 = true;   // the geometry is kept in double
-    rt_status s = RT_OK;
-    if (h && s == RT_OK) s = from_sorted(c, c->h_d.p, h, 1);
-    if (omega && s == RT_OK) s = from_sorted(c, c->omega_d.p, omega, 1);
-    if (V && s == RT_OK) s = from_sorted(c, c->V_d.p, V, 1);
-    if (B && s == RT_OK) {
+    if (h) RT_TRY(field_out(c, c->h_d.as<double>(), h, 1));
+    if (omega) RT_TRY(field_out(c, c->omega_d.as<double>(), omega, 1));
+    if (V) RT_TRY(field_out(c, c->V_d.as<double>(), V, 1));
+    if (B) {
         // [6][N] sorted -> [N][3][3] caller order
         static const int map[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
-        rt_status s3 = ensure(c, c->seg, (size_t)6 * c->n * 8, "scratch");
-        if (s3 == RT_OK) s3 = from_sorted(c, c->B_d.p, c->seg.p, 6);
-        if (s3 == RT_OK) {
-            for (int q = 0; q < 9; ++q) {
-                cudaError_t e = cudaMemcpy2DAsync(B + q, 9 * sizeof(double), c->seg.as<double>() + (size_t)map[q] * c->n,
-                                                  sizeof(double), sizeof(double), c->n, cudaMemcpyDeviceToDevice,
-                                                  c->stream);
-                if (e != cudaSuccess) {
-                    s3 = cuda_fail(c, e, "cudaMemcpy2DAsync");
-                    break;
-                }
-            }
-        }
-        s = s3;
+        RT_TRY(ensure(c, c->seg, (size_t)6 * c->n * 8, "scratch"));
+        RT_TRY(field_out(c, c->B_d.as<double>(), c->seg.as<double>(), 6));
+        for (int q = 0; q < 9; ++q)
+            RT_CUDA(c, cudaMemcpy2DAsync(B + q, 9 * sizeof(double), c->seg.as<double>() + (size_t)map[q] * c->n,
+                                         sizeof(double), sizeof(double), c->n, cudaMemcpyDeviceToDevice, c->stream));
     }
-    c->fp64 = f;
-    return s;
+    return RT_OK;
 }
 
 }  // extern "C"
@@ -311,6 +350,7 @@ rt_status rt_pairs(rt_ctx* c, int64_t* offsets, int32_t* cols) {
     int64_t* cnt = c->seg.as<int64_t>();
     k_row_counts<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->row_off.as<int64_t>(),
                                                                       c->inv_perm.as<int32_t>(), n, cnt);
+    ++c->launches;
     std::string err;
     int64_t* h = new (std::nothrow) int64_t[n + 1];
     if (!h) return fail(c, RT_ERR_OOM, "host allocation failed");
@@ -329,6 +369,7 @@ rt_status rt_pairs(rt_ctx* c, int64_t* offsets, int32_t* cols) {
     k_pairs_export<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
         c->row_off.as<int64_t>(), c->cols.as<int32_t>(), c->perm.as<int32_t>(), c->inv_perm.as<int32_t>(), n, offsets,
         cols);
+    ++c->launches;
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
 }
@@ -343,7 +384,41 @@ rt_status rt_diagnostics(rt_ctx* c, rt_diag* out) {
     }
     c->diag.clamp_events = (int64_t)cl;
     c->diag.threads_per_particle = c->tpp;
+    c->diag.kernel_launches = c->launches;
     *out = c->diag;
+    return RT_OK;
+}
+
+rt_status rt_set_profiling(rt_ctx* c, int32_t on) {
+    if (!c) return RT_ERR_INVALID;
+    c->err.clear();
+    int v = on ? 1 : 0;
+    if (v != c->profiling) {
+        RT_CUDA(c, cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+        destroy_prof(c->plain_prof);
+        c->profiling = v;
+    }
+    return RT_OK;
+}
+
+rt_status rt_kernel_times(rt_ctx* c, double* ms, int64_t* launches) {
+    if (!c || !ms || !launches) return RT_ERR_INVALID;
+    c->err.clear();
+    for (int k = 0; k < RT_KERNEL_KINDS; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    if (!c->last_prof) return RT_OK;
+    RT_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (const ProfRec& r : *c->last_prof) {
+        float t = 0.f;
+        RT_CUDA(c, cudaEventElapsedTime(&t, r.start, r.stop));
+        if (r.kind >= 0 && r.kind < RT_KERNEL_KINDS) {
+            ms[r.kind] += t;
+            launches[r.kind] += 1;
+        }
+    }
     return RT_OK;
 }
 
@@ -354,12 +429,13 @@ void rt_destroy(rt_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
+    destroy_prof(c->plain_prof);
     DevBuf* bufs[] = {&c->keys_in, &c->keys_out, &c->idx_in, &c->perm, &c->inv_perm, &c->cell_start, &c->cub_tmp,
-                      &c->xs_d, &c->xq, &c->m_s, &c->h_d, &c->omega_d, &c->V_d, &c->B_d, &c->cond_d, &c->invH_t,
-                      &c->h_t, &c->omega_t, &c->Bp_t, &c->counts, &c->row_off, &c->cols, &c->flags, &c->red_tmp,
+                      &c->xs_d, &c->xq, &c->m_s, &c->h_d, &c->H2f, &c->omega_d, &c->V_d, &c->B_d, &c->cond_d, &c->pos_t,
+                      &c->geo_t, &c->omega_t, &c->counts, &c->row_off, &c->cols, &c->flags, &c->red_tmp,
                       &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
                       &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,
-                      &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad, &c->alpha_s,
+                      &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->alpha_s,
                       &c->L_dev, &c->dt_dev, &c->energy_part, &c->ck, &c->seg, &c->lam_a, &c->lam_b, &c->gbar,
                       &c->lbar_part, &c->lbar_acc};
     for (DevBuf* b : bufs) free_buf(*b);

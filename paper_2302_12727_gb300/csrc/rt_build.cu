@@ -21,56 +21,116 @@ struct Grid {
     int nc[3];
     double cell[3];
     double inv_cell[3];
+    float cellf[3], inv_cellf[3];
     double box[3];
     int periodic;
     const int32_t* cell_start;   // [ncells + 1], lower bound of each cell in sorted order
 };
+
+// atomic min / max of positive doubles through their bit patterns (ordered like integers)
+__device__ __forceinline__ void atomic_min_pos(unsigned long long* a, double v) {
+    atomicMin(a, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
+    atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void warp_minmax(double& mn, double& mx) {
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+}
 
 __device__ __forceinline__ int wrap_cell(int c, int nc) {
     c %= nc;
     return c < 0 ? c + nc : c;
 }
 
-// Visit every particle (sorted index) in the cells within k[a] cells of (cx, cy, cz).
-// Rows along x are contiguous in sorted order, so each row is one or two index ranges.
+// Visit every particle (sorted index) whose cell can hold points within R of p.  Rows of
+// cells along x are contiguous in sorted order; rows whose (y, z) extent is farther than R
+// are skipped and each row is clipped to the chord of the sphere, so the visited volume
+// is close to the sphere plus one cell layer.  An axis whose span covers the whole grid is
+// walked once without clipping.
 template <class F>
-__device__ __forceinline__ void for_each_candidate(const Grid& g, int cx, int cy, int cz, const int k[3], F&& f) {
+__device__ __forceinline__ void for_each_candidate(const Grid& g, float px, float py, float pz, float R, F&& f) {
+    // float arithmetic with a relative margin of 1e-4 on R: cells are never missed
+    const float Rc = R * 1.0001f + 1e-6f * (g.cellf[0] + g.cellf[1] + g.cellf[2]);
+    const float R2 = Rc * Rc;
+    const float p[3] = {px, py, pz};
     int lo[3], hi[3];
-    int c0[3] = {cx, cy, cz};
     bool all[3];
     for (int a = 0; a < 3; ++a) {
-        all[a] = (2 * k[a] + 1 >= g.nc[a]);
-        lo[a] = all[a] ? 0 : c0[a] - k[a];
-        hi[a] = all[a] ? g.nc[a] - 1 : c0[a] + k[a];
-        if (!g.periodic && !all[a]) {
+        lo[a] = (int)floorf((p[a] - Rc) * g.inv_cellf[a]);
+        hi[a] = (int)floorf((p[a] + Rc) * g.inv_cellf[a]);
+        all[a] = (hi[a] - lo[a] + 1 >= g.nc[a]);
+        if (all[a]) {
+            lo[a] = 0;
+            hi[a] = g.nc[a] - 1;
+        } else if (!g.periodic) {
             lo[a] = max(lo[a], 0);
             hi[a] = min(hi[a], g.nc[a] - 1);
         }
     }
     for (int z = lo[2]; z <= hi[2]; ++z) {
+        float dz = 0.f;
+        if (!all[2]) dz = fmaxf(0.f, fmaxf(z * g.cellf[2] - pz, pz - (z + 1) * g.cellf[2]));
+        if (dz * dz >= R2) continue;
         int zz = wrap_cell(z, g.nc[2]);
         for (int y = lo[1]; y <= hi[1]; ++y) {
+            float dy = 0.f;
+            if (!all[1]) dy = fmaxf(0.f, fmaxf(y * g.cellf[1] - py, py - (y + 1) * g.cellf[1]));
+            float rem = R2 - dy * dy - dz * dz;
+            if (rem <= 0.f) continue;
             int yy = wrap_cell(y, g.nc[1]);
             int64_t base = ((int64_t)zz * g.nc[1] + yy) * g.nc[0];
-            // x range [lo, hi] possibly wrapping: split into contiguous segments
-            int xa = lo[0], xb = hi[0];
-            int segs_lo[2], segs_hi[2], ns = 0;
-            if (xa < 0) {
-                segs_lo[ns] = xa + g.nc[0]; segs_hi[ns] = g.nc[0] - 1; ++ns;
-                segs_lo[ns] = 0; segs_hi[ns] = xb; ++ns;
-            } else if (xb >= g.nc[0]) {
-                segs_lo[ns] = xa; segs_hi[ns] = g.nc[0] - 1; ++ns;
-                segs_lo[ns] = 0; segs_hi[ns] = xb - g.nc[0]; ++ns;
+            int xa, xb;
+            if (all[0]) {
+                xa = 0;
+                xb = g.nc[0] - 1;
             } else {
-                segs_lo[ns] = xa; segs_hi[ns] = xb; ++ns;
+                float w = sqrtf(rem);
+                xa = (int)floorf((px - w) * g.inv_cellf[0]);
+                xb = (int)floorf((px + w) * g.inv_cellf[0]);
+                if (!g.periodic) {
+                    xa = max(xa, 0);
+                    xb = min(xb, g.nc[0] - 1);
+                }
             }
-            for (int s = 0; s < ns; ++s) {
-                int b = g.cell_start[base + segs_lo[s]];
-                int e = g.cell_start[base + segs_hi[s] + 1];
+            int sl[2], sh[2], ns = 0;
+            if (xa < 0) { sl[ns] = xa + g.nc[0]; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb; }
+            else if (xb >= g.nc[0]) { sl[ns] = xa; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb - g.nc[0]; }
+            else { sl[ns] = xa; sh[ns++] = xb; }
+            for (int sI = 0; sI < ns; ++sI) {
+                int b = g.cell_start[base + sl[sI]];
+                int e = g.cell_start[base + sh[sI] + 1];
                 for (int j = b; j < e; ++j) f(j);
             }
         }
     }
+}
+
+// number of particles in the 3 x 3 x 3 cells around (cx, cy, cz): a local density for the
+// first guess of h
+__device__ __forceinline__ int count_27(const Grid& g, int cx, int cy, int cz) {
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+        if (!g.periodic && (z < 0 || z >= g.nc[2])) continue;
+        int zz = wrap_cell(z, g.nc[2]);
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (!g.periodic && (y < 0 || y >= g.nc[1])) continue;
+            int yy = wrap_cell(y, g.nc[1]);
+            int64_t base = ((int64_t)zz * g.nc[1] + yy) * g.nc[0];
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = cx + dx;
+                if (!g.periodic && (x < 0 || x >= g.nc[0])) continue;
+                int xx = wrap_cell(x, g.nc[0]);
+                cnt += g.cell_start[base + xx + 1] - g.cell_start[base + xx];
+            }
+        }
+    }
+    return cnt;
 }
 
 __device__ __forceinline__ int cell_coord(double x, double inv_cell, int nc) {
@@ -154,115 +214,132 @@ struct HParams {
     float scale[3];
     int max_iter;
     float tol32;
+    int refine64;   // 1: Newton in double to machine precision (FP64 path); 0: omega in double at the float root
 };
 
 __device__ __forceinline__ float fsep(uint32_t a, uint32_t b, float scale) { return (float)(int32_t)(a - b) * scale; }
 
 __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
-                          HParams hp, double* h_out, double* omega_out, int* flags) {
+                          HParams hp, double* h_out, double* omega_out, float* H2f_out, unsigned long long* hminmax,
+                          int* flags) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const float kapf = (float)kKappa;
-    const float sigf = (float)kSigma;
-    uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
-    double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
-    int cx = cell_coord(px, g.inv_cell[0], g.nc[0]);
-    int cy = cell_coord(py, g.inv_cell[1], g.nc[1]);
-    int cz = cell_coord(pz, g.inv_cell[2], g.nc[2]);
+    double hd = 0.0, om_d = 0.0;
+    bool active = p < n;
+    if (active) {
+        const float kapf = (float)kKappa;
+        const float sigf = (float)kSigma;
+        uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+        double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+        float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
 
-    // ---- float phase
-    float h = (float)hp.h0, lo = 0.f, hi = INFINITY;
-    const float eta = (float)hp.eta;
-    bool ok = false;
-    for (int it = 0; it < hp.max_iter; ++it) {
-        float H = kapf * h;
-        float iH = 1.f / H;
-        int k[3];
-        for (int a = 0; a < 3; ++a) k[a] = (int)ceilf(H * (float)g.inv_cell[a]);
-        float H2 = H * H;
-        float sw = 0.f, sdw = 0.f;
-        for_each_candidate(g, cx, cy, cz, k, [&](int j) {
-            float dx = fsep(xq[j], qx, hp.scale[0]);
-            float dy = fsep(xq[n + j], qy, hp.scale[1]);
-            float dz = fsep(xq[2 * n + j], qz, hp.scale[2]);
-            float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < H2) {
-                float q = sqrtf(r2) * iH;
-                float w = spline_w(q);
-                sw += w;
-                sdw += 3.f * w + q * spline_dw(q);
-            }
-        });
-        float om = sigf * iH * iH * iH * sw;
-        float dom = -kapf * sigf * iH * iH * iH * iH * sdw;      // d omega / d h
-        float cb = cbrtf(om);
-        float f = h - eta / cb;
-        float fp = 1.f + (eta / 3.f) / (cb * om) * dom;
-        if (f < 0.f) lo = h; else hi = h;
-        float step = f / fp;
-        float hn = h - step;
-        if (!(fabsf(step) > hp.tol32 * h)) { ok = true; break; }
-        if (!(hn > lo && hn < hi) || !(fp > 0.f)) hn = isinf(hi) ? 2.f * h : 0.5f * (lo + hi);
-        if (hn > (float)hp.h_cap) hn = (float)hp.h_cap;
-        h = hn;
-    }
-    if (!ok) {
-        atomicExch(&flags[F_NOCONV], 1);
-        h_out[p] = (double)h;
-        omega_out[p] = 0.0;
-        return;
-    }
+        // first guess from the particle count of the surrounding 27 cells
+        int cnt = count_27(g, cell_coord(px, g.inv_cell[0], g.nc[0]), cell_coord(py, g.inv_cell[1], g.nc[1]),
+                           cell_coord(pz, g.inv_cell[2], g.nc[2]));
+        double vol27 = 27.0 * g.cell[0] * g.cell[1] * g.cell[2];
+        float h = cnt > 1 ? (float)(hp.eta * cbrt(vol27 / (double)cnt)) : (float)hp.h0;
 
-    // ---- double phase (exact separations)
-    double hd = (double)h;
-    double lod = 0.0, hid = INFINITY;
-    double om_d = 0.0;
-    const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
-    bool okd = false, last = false;
-    for (int it = 0; it < 16; ++it) {
-        double H = kKappa * hd;
-        double iH = 1.0 / H;
-        double H2 = H * H;
-        float Hf = (float)H * 1.001f;
-        float H2f = Hf * Hf;
-        int k[3];
-        for (int a = 0; a < 3; ++a) k[a] = (int)ceil(H * g.inv_cell[a] * 1.001);
-        double sw = 0.0, sdw = 0.0;
-        for_each_candidate(g, cx, cy, cz, k, [&](int j) {
-            float dxf = fsep(xq[j], qx, hp.scale[0]);
-            float dyf = fsep(xq[n + j], qy, hp.scale[1]);
-            float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
-            if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) return;
-            double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
-            double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
-            double dz = sep_fast(xs[2 * n + j], pz, g.box[2], half[2], g.periodic);
-            double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < H2) {
-                double q = sqrt(r2) * iH;
-                double w = spline_w(q);
-                sw += w;
-                sdw += 3.0 * w + q * spline_dw(q);
+        // ---- float phase: Newton on float separations, omega summed in double
+        float lo = 0.f, hi = INFINITY;
+        const float eta = (float)hp.eta;
+        bool ok = false;
+        double sw_last = 0.0;
+        for (int it = 0; it < hp.max_iter; ++it) {
+            float H = kapf * h;
+            float iH = 1.f / H;
+            float H2 = H * H;
+            double sw = 0.0;
+            float sdw = 0.f;
+            for_each_candidate(g, pxf, pyf, pzf, H, [&](int j) {
+                float dx = fsep(xq[j], qx, hp.scale[0]);
+                float dy = fsep(xq[n + j], qy, hp.scale[1]);
+                float dz = fsep(xq[2 * n + j], qz, hp.scale[2]);
+                float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < H2) {
+                    float q = sqrtf(r2) * iH;
+                    float w = spline_w(q);
+                    sw += (double)w;
+                    sdw += 3.f * w + q * spline_dw(q);
+                }
+            });
+            sw_last = sw;
+            float om = sigf * iH * iH * iH * (float)sw;
+            float dom = -kapf * sigf * iH * iH * iH * iH * sdw;      // d omega / d h
+            float cb = cbrtf(om);
+            float f = h - eta / cb;
+            float fp = 1.f + (eta / 3.f) / (cb * om) * dom;
+            if (f < 0.f) lo = h; else hi = h;
+            float step = f / fp;
+            float hn = h - step;
+            if (!(fabsf(step) > hp.tol32 * h)) { ok = true; break; }
+            if (!(hn > lo && hn < hi) || !(fp > 0.f)) hn = isinf(hi) ? 2.f * h : 0.5f * (lo + hi);
+            if (hn > (float)hp.h_cap) hn = (float)hp.h_cap;
+            h = hn;
+        }
+        if (!ok) atomicExch(&flags[F_NOCONV], 1);
+        hd = (double)h;
+        {
+            double H = kKappa * hd;
+            om_d = kSigma / (H * H * H) * sw_last;
+        }
+
+        // ---- double phase (FP64 path): Newton on the exact separations to machine precision
+        if (hp.refine64 && ok) {
+            double lod = 0.0, hid = INFINITY;
+            const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
+            bool okd = false, last = false;
+            for (int it = 0; it < 16; ++it) {
+                double H = kKappa * hd;
+                double iH = 1.0 / H;
+                double H2 = H * H;
+                float Hf = (float)H * 1.001f;
+                float H2f = Hf * Hf;
+                double sw = 0.0, sdw = 0.0;
+                for_each_candidate(g, pxf, pyf, pzf, Hf, [&](int j) {
+                    float dxf = fsep(xq[j], qx, hp.scale[0]);
+                    float dyf = fsep(xq[n + j], qy, hp.scale[1]);
+                    float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+                    if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) return;
+                    double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
+                    double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
+                    double dz = sep_fast(xs[2 * n + j], pz, g.box[2], half[2], g.periodic);
+                    double r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < H2) {
+                        double q = sqrt(r2) * iH;
+                        double w = spline_w(q);
+                        sw += w;
+                        sdw += 3.0 * w + q * spline_dw(q);
+                    }
+                });
+                double om = kSigma * iH * iH * iH * sw;
+                double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
+                double cb = cbrt(om);
+                double f = hd - hp.eta / cb;
+                double fp = 1.0 + (hp.eta / 3.0) / (cb * om) * dom;
+                om_d = om;
+                if (last) { okd = true; break; }        // omega evaluated at the final h
+                if (f < 0.0) lod = hd; else hid = hd;
+                double step = f / fp;
+                // once the Newton step is tiny the next iterate is exact to rounding: take it and
+                // evaluate omega there once more
+                if (fabs(step) <= 1e-11 * hd) last = true;
+                double hn = hd - step;
+                if (!last && (!(hn > lod && hn < hid) || !(fp > 0.0)))
+                    hn = isinf(hid) ? 1.01 * hd : 0.5 * (lod + hid);
+                hd = hn;
             }
-        });
-        double om = kSigma * iH * iH * iH * sw;
-        double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
-        double cb = cbrt(om);
-        double f = hd - hp.eta / cb;
-        double fp = 1.0 + (hp.eta / 3.0) / (cb * om) * dom;
-        om_d = om;
-        if (last) { okd = true; break; }        // omega evaluated at the final h
-        if (f < 0.0) lod = hd; else hid = hd;
-        double step = f / fp;
-        // once the Newton step is tiny the next iterate is exact to rounding: take it and
-        // evaluate omega there once more
-        if (fabs(step) <= 1e-11 * hd) last = true;
-        double hn = hd - step;
-        if (!last && (!(hn > lod && hn < hid) || !(fp > 0.0))) hn = isinf(hid) ? 1.01 * hd : 0.5 * (lod + hid);
-        hd = hn;
+            if (!okd) atomicExch(&flags[F_NOCONV], 1);
+        }
+        h_out[p] = hd;
+        omega_out[p] = om_d;
+        double Hd = kKappa * hd;
+        H2f_out[p] = (float)(Hd * Hd);
     }
-    if (!okd) atomicExch(&flags[F_NOCONV], 1);
-    h_out[p] = hd;
-    omega_out[p] = om_d;
+    double mn = active ? hd : INFINITY, mx = active ? hd : 0.0;
+    warp_minmax(mn, mx);
+    if ((threadIdx.x & 31) == 0 && mx > 0.0) {
+        atomic_min_pos(&hminmax[0], mn);
+        atomic_max_pos(&hminmax[1], mx);
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -276,34 +353,29 @@ struct PairParams {
 
 template <bool FILL>
 __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
-                        const double* __restrict__ h, int64_t n, PairParams pp, int32_t* counts,
-                        const int64_t* __restrict__ row_off, int32_t* cols) {
+                        const double* __restrict__ h, const float* __restrict__ H2f, int64_t n, PairParams pp,
+                        int32_t* counts, const int64_t* __restrict__ row_off, int32_t* cols) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
     uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
     double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
-    double Hi = __dmul_rn(kKappa, h[p]);
-    int cx = cell_coord(px, g.inv_cell[0], g.nc[0]);
-    int cy = cell_coord(py, g.inv_cell[1], g.nc[1]);
-    int cz = cell_coord(pz, g.inv_cell[2], g.nc[2]);
-    double R = fmax(Hi, pp.Hmax) * 1.0001;
-    int k[3];
-    for (int a = 0; a < 3; ++a) k[a] = (int)ceil(R * g.inv_cell[a]);
+    const float H2i = H2f[p];
+    float R = sqrtf(fmaxf(H2i, (float)(pp.Hmax * pp.Hmax))) * 1.0001f;
     int cnt = 0;
     int64_t base = FILL ? row_off[p] : 0;
-    for_each_candidate(g, cx, cy, cz, k, [&](int j) {
+    for_each_candidate(g, (float)px, (float)py, (float)pz, R, [&](int j) {
         if (j == p) return;
-        double Hj = __dmul_rn(kKappa, h[j]);
-        double Hm = fmax(Hi, Hj);
         float dx = fsep(xq[j], qx, pp.scale[0]);
         float dy = fsep(xq[n + j], qy, pp.scale[1]);
         float dz = fsep(xq[2 * n + j], qz, pp.scale[2]);
         float r2f = dx * dx + dy * dy + dz * dz;
-        float H2f = (float)(Hm * Hm);
+        float H2m = fmaxf(H2i, H2f[j]);
         bool in;
-        if (r2f < H2f * (1.f - 1e-5f)) in = true;
-        else if (r2f > H2f * (1.f + 1e-5f)) in = false;
+        if (r2f < H2m * (1.f - 1e-5f)) in = true;
+        else if (r2f > H2m * (1.f + 1e-5f)) in = false;
         else {
+            // exact double test (no contraction), as a plain double evaluation would do it
+            double Hm = fmax(__dmul_rn(kKappa, h[p]), __dmul_rn(kKappa, h[j]));
             double ex = sep_exact(xs[j], px, g.box[0], g.periodic);
             double ey = sep_exact(xs[n + j], py, g.box[1], g.periodic);
             double ez = sep_exact(xs[2 * n + j], pz, g.box[2], g.periodic);
@@ -338,19 +410,47 @@ __device__ void sym3_eigs(double a, double b, double c, double d, double e, doub
 }
 
 template <class T>
-__global__ void k_geometry(const double* __restrict__ xs, const double* __restrict__ h,
-                           const double* __restrict__ omega, const int64_t* __restrict__ row_off,
-                           const int32_t* __restrict__ cols, int64_t n, double b0, double b1, double b2, int periodic,
-                           double* V_out, double* B_out, double* cond_out, T* invH_t, T* h_t, T* om_t, T* Bp_t,
-                           int* flags) {
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const double box[3] = {b0, b1, b2};
-    const double half[3] = {0.5 * b0, 0.5 * b1, 0.5 * b2};
+__device__ __forceinline__ void store_pos(void* pos, int64_t p, const double* xs, const uint32_t* xq, int64_t n);
+template <>
+__device__ __forceinline__ void store_pos<float>(void* pos, int64_t p, const double*, const uint32_t* xq, int64_t n) {
+    reinterpret_cast<uint4*>(pos)[p] = make_uint4(xq[p], xq[n + p], xq[2 * n + p], 0u);
+}
+template <>
+__device__ __forceinline__ void store_pos<double>(void* pos, int64_t p, const double* xs, const uint32_t*, int64_t n) {
+    double2* d = reinterpret_cast<double2*>(pos) + 2 * p;
+    d[0] = make_double2(xs[p], xs[n + p]);
+    d[1] = make_double2(xs[2 * n + p], 0.0);
+}
+
+// E_i accumulation over the pair list.  Double path: separations and weights in double.
+// Float path: separations from the fixed-point positions, weights in float and a
+// compensated (Kahan) float sum, so that E_i keeps ~1e-8 relative accuracy before its
+// inversion in double.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <class T>
+__device__ __forceinline__ void accumulate_E(const double* xs, const uint32_t* xq, const double* box, int periodic,
+                                             float s0, float s1, float s2, int64_t n, int64_t p, double H,
+                                             const int64_t* row_off, const int32_t* cols, double E[6]);
+
+template <>
+__device__ __forceinline__ void accumulate_E<double>(const double* xs, const uint32_t*, const double* box,
+                                                     int periodic, float, float, float, int64_t n, int64_t p,
+                                                     double H, const int64_t* row_off, const int32_t* cols,
+                                                     double E[6]) {
+    const double half[3] = {0.5 * box[0], 0.5 * box[1], 0.5 * box[2]};
     double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
-    double hi = h[p], H = kKappa * hi, iH = 1.0 / H, H2 = H * H;
-    double om = omega[p];
-    double e_xx = 0, e_yy = 0, e_zz = 0, e_xy = 0, e_xz = 0, e_yz = 0;
+    double iH = 1.0 / H, H2 = H * H;
+    for (int k = 0; k < 6; ++k) E[k] = 0.0;
     for (int64_t e = row_off[p]; e < row_off[p + 1]; ++e) {
         int j = cols[e];
         double dx = sep_fast(xs[j], px, box[0], half[0], periodic);
@@ -359,47 +459,98 @@ __global__ void k_geometry(const double* __restrict__ xs, const double* __restri
         double r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 < H2)) continue;
         double w = spline_w(sqrt(r2) * iH);
-        e_xx += w * dx * dx; e_yy += w * dy * dy; e_zz += w * dz * dz;
-        e_xy += w * dx * dy; e_xz += w * dx * dz; e_yz += w * dy * dz;
+        E[0] += w * dx * dx; E[1] += w * dy * dy; E[2] += w * dz * dz;
+        E[3] += w * dx * dy; E[4] += w * dx * dz; E[5] += w * dy * dz;
     }
-    double fac = kSigma * iH * iH * iH / om;   // psi = fac * w
-    e_xx *= fac; e_yy *= fac; e_zz *= fac; e_xy *= fac; e_xz *= fac; e_yz *= fac;
-    // cofactor inverse of the symmetric matrix
-    double c_xx = e_yy * e_zz - e_yz * e_yz;
-    double c_xy = e_xz * e_yz - e_xy * e_zz;
-    double c_xz = e_xy * e_yz - e_xz * e_yy;
-    double det = e_xx * c_xx + e_xy * c_xy + e_xz * c_xz;
-    double V = 1.0 / om;
-    V_out[p] = V;
-    if (!(det > 0.0) || !(om > 0.0)) {
-        atomicExch(&flags[F_GEOM], 1);
-        for (int k = 0; k < 6; ++k) B_out[k * n + p] = 0.0;
-        cond_out[p] = INFINITY;
-        return;
+}
+
+template <>
+__device__ __forceinline__ void accumulate_E<float>(const double*, const uint32_t* xq, const double*, int, float s0,
+                                                    float s1, float s2, int64_t n, int64_t p, double H,
+                                                    const int64_t* row_off, const int32_t* cols, double E[6]) {
+    uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    float iH = (float)(1.0 / H), H2 = (float)(H * H);
+    Kahan acc[6];
+    for (int64_t e = row_off[p]; e < row_off[p + 1]; ++e) {
+        int j = cols[e];
+        float dx = fsep(xq[j], qx, s0), dy = fsep(xq[n + j], qy, s1), dz = fsep(xq[2 * n + j], qz, s2);
+        float r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < H2)) continue;
+        float w = spline_w(sqrtf(r2) * iH);
+        acc[0].add(w * dx * dx); acc[1].add(w * dy * dy); acc[2].add(w * dz * dz);
+        acc[3].add(w * dx * dy); acc[4].add(w * dx * dz); acc[5].add(w * dy * dz);
     }
-    double id = 1.0 / det;
-    double B[6];
-    B[0] = c_xx * id;
-    B[1] = (e_xx * e_zz - e_xz * e_xz) * id;
-    B[2] = (e_xx * e_yy - e_xy * e_xy) * id;
-    B[3] = c_xy * id;
-    B[4] = c_xz * id;
-    B[5] = (e_xy * e_xz - e_xx * e_yz) * id;
-    double ev[3];
-    sym3_eigs(e_xx, e_yy, e_zz, e_xy, e_xz, e_yz, ev);
-    double lmin = fmin(ev[0], fmin(ev[1], ev[2])), lmax = fmax(ev[0], fmax(ev[1], ev[2]));
-    double cond = lmin > 0 ? lmax / lmin : INFINITY;
-    cond_out[p] = cond;
-    if (!(lmin > 0)) atomicExch(&flags[F_GEOM], 1);
-    if (cond > 1e10) atomicAdd(&flags[F_ILL], 1);
-    double bp = V * V * kSigma * iH * iH * iH;   // V_i psitilde_j(x_i) = Bp_i d w(q_ij)
-    for (int k = 0; k < 6; ++k) {
-        B_out[k * n + p] = B[k];
-        Bp_t[k * n + p] = (T)(bp * B[k]);
+    for (int k = 0; k < 6; ++k) E[k] = acc[k].value();
+}
+
+// Also writes the pair kernels' records: position, {1/H, h, Bp (6)} with
+// Bp = V^2 sigma / H^3 B (so that V_i psitilde_j(x_i) = Bp_i d w(q)), and omega; reduces
+// max cond_2(E_i) and min V_i into red[2], red[3].
+template <class T>
+__global__ void k_geometry(const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+                           const double* __restrict__ h, const double* __restrict__ omega,
+                           const int64_t* __restrict__ row_off, const int32_t* __restrict__ cols, int64_t n, double b0,
+                           double b1, double b2, int periodic, float s0, float s1, float s2, double* V_out,
+                           double* B_out, double* cond_out, void* pos_t, T* geo_t, T* om_t,
+                           unsigned long long* red, int* flags) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double cond = 0.0, V = INFINITY;
+    if (p < n) {
+        const double box[3] = {b0, b1, b2};
+        double hi = h[p], H = kKappa * hi, iH = 1.0 / H;
+        double om = omega[p];
+        double E[6];
+        accumulate_E<T>(xs, xq, box, periodic, s0, s1, s2, n, p, H, row_off, cols, E);
+        double fac = kSigma * iH * iH * iH / om;   // psi = fac * w
+        double e_xx = E[0] * fac, e_yy = E[1] * fac, e_zz = E[2] * fac;
+        double e_xy = E[3] * fac, e_xz = E[4] * fac, e_yz = E[5] * fac;
+        // cofactor inverse of the symmetric matrix
+        double c_xx = e_yy * e_zz - e_yz * e_yz;
+        double c_xy = e_xz * e_yz - e_xy * e_zz;
+        double c_xz = e_xy * e_yz - e_xz * e_yy;
+        double det = e_xx * c_xx + e_xy * c_xy + e_xz * c_xz;
+        V = 1.0 / om;
+        V_out[p] = V;
+        store_pos<T>(pos_t, p, xs, xq, n);
+        if (!(det > 0.0) || !(om > 0.0)) {
+            atomicExch(&flags[F_GEOM], 1);
+            for (int k = 0; k < 6; ++k) B_out[k * n + p] = 0.0;
+            for (int k = 0; k < 8; ++k) geo_t[8 * p + k] = (T)0;
+            om_t[p] = (T)0;
+            cond_out[p] = INFINITY;
+            cond = INFINITY;
+        } else {
+            double id = 1.0 / det;
+            double B[6];
+            B[0] = c_xx * id;
+            B[1] = (e_xx * e_zz - e_xz * e_xz) * id;
+            B[2] = (e_xx * e_yy - e_xy * e_xy) * id;
+            B[3] = c_xy * id;
+            B[4] = c_xz * id;
+            B[5] = (e_xy * e_xz - e_xx * e_yz) * id;
+            double ev[3];
+            sym3_eigs(e_xx, e_yy, e_zz, e_xy, e_xz, e_yz, ev);
+            double lmin = fmin(ev[0], fmin(ev[1], ev[2])), lmax = fmax(ev[0], fmax(ev[1], ev[2]));
+            cond = lmin > 0 ? lmax / lmin : INFINITY;
+            cond_out[p] = cond;
+            if (!(lmin > 0)) atomicExch(&flags[F_GEOM], 1);
+            if (cond > 1e10) atomicAdd(&flags[F_ILL], 1);
+            double bp = V * V * kSigma * iH * iH * iH;   // V_i psitilde_j(x_i) = Bp_i d w(q_ij)
+            geo_t[8 * p] = (T)iH;
+            geo_t[8 * p + 1] = (T)hi;
+            for (int k = 0; k < 6; ++k) {
+                B_out[k * n + p] = B[k];
+                geo_t[8 * p + 2 + k] = (T)(bp * B[k]);
+            }
+            om_t[p] = (T)om;
+        }
     }
-    invH_t[p] = (T)iH;
-    h_t[p] = (T)hi;
-    om_t[p] = (T)om;
+    double vmin = V, cmax = cond;
+    warp_minmax(vmin, cmax);
+    if ((threadIdx.x & 31) == 0) {
+        if (cmax > 0.0) atomic_max_pos(&red[2], cmax);
+        if (vmin < INFINITY) atomic_min_pos(&red[3], vmin);
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -452,24 +603,81 @@ struct SrcParams {
     int max_iter;
 };
 
-__global__ void k_src_h(Grid g, const double* __restrict__ xs, int64_t n, const double* __restrict__ xsrc,
-                        int64_t S, SrcParams sp, double* hs_out, double* oms_out, int* flags) {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= S) return;
-    double p[3] = {xsrc[warp], xsrc[S + warp], xsrc[2 * S + warp]};
-    int c[3];
-    for (int a = 0; a < 3; ++a) c[a] = cell_coord(p[a], g.inv_cell[a], g.nc[a]);
+// Rows of the culled walk of for_each_candidate handed out round-robin to the threads of a
+// block (thread t takes rows t, t + nt, ...).
+template <class F>
+__device__ __forceinline__ void strided_rows(const Grid& g, float px, float py, float pz, float R, int t, int nt,
+                                             F&& f) {
+    const float Rc = R * 1.0001f + 1e-6f * (g.cellf[0] + g.cellf[1] + g.cellf[2]);
+    const float R2 = Rc * Rc;
+    const float p[3] = {px, py, pz};
+    int lo[3], hi[3];
+    bool all[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (int)floorf((p[a] - Rc) * g.inv_cellf[a]);
+        hi[a] = (int)floorf((p[a] + Rc) * g.inv_cellf[a]);
+        all[a] = (hi[a] - lo[a] + 1 >= g.nc[a]);
+        if (all[a]) {
+            lo[a] = 0;
+            hi[a] = g.nc[a] - 1;
+        } else if (!g.periodic) {
+            lo[a] = max(lo[a], 0);
+            hi[a] = min(hi[a], g.nc[a] - 1);
+        }
+    }
+    const int ny = hi[1] - lo[1] + 1;
+    const int nrows = (hi[2] - lo[2] + 1) * ny;
+    for (int r = t; r < nrows; r += nt) {
+        int z = lo[2] + r / ny, y = lo[1] + r % ny;
+        float dz = all[2] ? 0.f : fmaxf(0.f, fmaxf(z * g.cellf[2] - pz, pz - (z + 1) * g.cellf[2]));
+        float dy = all[1] ? 0.f : fmaxf(0.f, fmaxf(y * g.cellf[1] - py, py - (y + 1) * g.cellf[1]));
+        float rem = R2 - dy * dy - dz * dz;
+        if (rem <= 0.f) continue;
+        int zz = wrap_cell(z, g.nc[2]), yy = wrap_cell(y, g.nc[1]);
+        int64_t base = ((int64_t)zz * g.nc[1] + yy) * g.nc[0];
+        int xa, xb;
+        if (all[0]) {
+            xa = 0;
+            xb = g.nc[0] - 1;
+        } else {
+            float w = sqrtf(rem);
+            xa = (int)floorf((px - w) * g.inv_cellf[0]);
+            xb = (int)floorf((px + w) * g.inv_cellf[0]);
+            if (!g.periodic) {
+                xa = max(xa, 0);
+                xb = min(xb, g.nc[0] - 1);
+            }
+        }
+        int sl[2], sh[2], ns = 0;
+        if (xa < 0) { sl[ns] = xa + g.nc[0]; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb; }
+        else if (xb >= g.nc[0]) { sl[ns] = xa; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb - g.nc[0]; }
+        else { sl[ns] = xa; sh[ns++] = xb; }
+        for (int sI = 0; sI < ns; ++sI) {
+            int b = g.cell_start[base + sl[sI]];
+            int e = g.cell_start[base + sh[sI] + 1];
+            for (int j = b; j < e; ++j) f(j);
+        }
+    }
+}
+
+constexpr int kSrcThreads = 128;
+
+// one block per source: Newton on h_s = eta_s omega_s(h_s)^(-1/3) over gas only (no self
+// term), omega summed over the rows of all threads in a fixed tree order
+__global__ void __launch_bounds__(kSrcThreads) k_src_h(Grid g, const double* __restrict__ xs, int64_t n,
+                                                       const double* __restrict__ xsrc, int64_t S, SrcParams sp,
+                                                       double* hs_out, double* oms_out, int* flags) {
+    const int s_id = blockIdx.x;
+    const int t = threadIdx.x;
+    __shared__ double red_w[kSrcThreads], red_dw[kSrcThreads];
+    double p[3] = {xsrc[s_id], xsrc[S + s_id], xsrc[2 * S + s_id]};
     const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
     double h = sp.h0, lo = 0.0, hi = INFINITY, om = 0.0;
     bool ok = false;
     for (int it = 0; it < sp.max_iter; ++it) {
         double H = kKappa * h, iH = 1.0 / H, H2 = H * H;
-        int k[3];
-        for (int a = 0; a < 3; ++a) k[a] = (int)ceil(H * g.inv_cell[a]);
         double sw = 0.0, sdw = 0.0;
-        warp_candidates(g, c[0], c[1], c[2], k, lane, [&](int j, bool act) {
-            if (!act) return;
+        strided_rows(g, (float)p[0], (float)p[1], (float)p[2], (float)H, t, kSrcThreads, [&](int j) {
             double dx = sep_fast(xs[j], p[0], g.box[0], half[0], g.periodic);
             double dy = sep_fast(xs[n + j], p[1], g.box[1], half[1], g.periodic);
             double dz = sep_fast(xs[2 * n + j], p[2], g.box[2], half[2], g.periodic);
@@ -481,10 +689,20 @@ __global__ void k_src_h(Grid g, const double* __restrict__ xs, int64_t n, const 
                 sdw += 3.0 * w + q * spline_dw(q);
             }
         });
-        sw = warp_sum(sw);
-        sdw = warp_sum(sdw);
+        red_w[t] = sw;
+        red_dw[t] = sdw;
+        __syncthreads();
+        for (int w = kSrcThreads / 2; w > 0; w >>= 1) {
+            if (t < w) {
+                red_w[t] += red_w[t + w];
+                red_dw[t] += red_dw[t + w];
+            }
+            __syncthreads();
+        }
+        sw = red_w[0];
+        sdw = red_dw[0];
+        __syncthreads();
         om = kSigma * iH * iH * iH * sw;
-        double hn;
         double f, fp;
         if (om > 0.0) {
             double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
@@ -498,15 +716,16 @@ __global__ void k_src_h(Grid g, const double* __restrict__ xs, int64_t n, const 
         if (f < 0.0) lo = h; else hi = h;
         double step = (om > 0.0) ? f / fp : -INFINITY;
         if (om > 0.0 && !(fabs(step) > 2e-16 * h)) { ok = true; break; }
-        hn = h - step;
+        double hn = h - step;
         if (!(hn > lo && hn < hi) || !(fp > 0.0)) hn = isinf(hi) ? 1.5 * h : 0.5 * (lo + hi);
         if (hn > sp.h_cap) hn = sp.h_cap;
+        if (hn == h) { ok = om > 0.0; break; }
         h = hn;
     }
-    if (lane == 0) {
+    if (t == 0) {
         if (!ok) atomicExch(&flags[F_SRC_NOCONV], 1);
-        hs_out[warp] = h;
-        oms_out[warp] = om;
+        hs_out[s_id] = h;
+        oms_out[s_id] = om;
     }
 }
 
@@ -623,30 +842,6 @@ __global__ void k_inj_targets(const uint64_t* __restrict__ keys, const int32_t* 
     if (e == total - 1) inj_off[head_pos[e] + head_flag[e]] = (int32_t)total;
 }
 
-__global__ void k_minmax(const double* __restrict__ v, int64_t n, double* out) {
-    // single block; out[0] = min, out[1] = max
-    __shared__ double smin[256], smax[256];
-    double mn = INFINITY, mx = -INFINITY;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        mn = fmin(mn, v[i]);
-        mx = fmax(mx, v[i]);
-    }
-    smin[threadIdx.x] = mn;
-    smax[threadIdx.x] = mx;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
-            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        out[0] = smin[0];
-        out[1] = smax[0];
-    }
-}
-
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // ------------------------------------------------------------------------------------
@@ -687,6 +882,8 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         g.nc[a] = c->nc[a];
         g.cell[a] = c->cell[a];
         g.inv_cell[a] = 1.0 / c->cell[a];
+        g.cellf[a] = (float)c->cell[a];
+        g.inv_cellf[a] = (float)(1.0 / c->cell[a]);
         g.box[a] = cfg.box[a];
     }
     g.periodic = cfg.periodic;
@@ -702,15 +899,15 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     RT_TRY(ensure(c, c->xq, 3 * n * 4, "positions"));
     RT_TRY(ensure(c, c->m_s, n * 8, "masses"));
     RT_TRY(ensure(c, c->h_d, n * 8, "h"));
+    RT_TRY(ensure(c, c->H2f, n * 4, "h"));
     RT_TRY(ensure(c, c->omega_d, n * 8, "omega"));
     RT_TRY(ensure(c, c->V_d, n * 8, "V"));
     RT_TRY(ensure(c, c->B_d, 6 * n * 8, "B"));
     RT_TRY(ensure(c, c->cond_d, n * 8, "cond"));
     size_t ts = c->fp64 ? 8 : 4;
-    RT_TRY(ensure(c, c->invH_t, n * ts, "geom"));
-    RT_TRY(ensure(c, c->h_t, n * ts, "geom"));
+    RT_TRY(ensure(c, c->pos_t, n * 32, "geom"));
+    RT_TRY(ensure(c, c->geo_t, 8 * n * ts, "geom"));
     RT_TRY(ensure(c, c->omega_t, n * ts, "geom"));
-    RT_TRY(ensure(c, c->Bp_t, 6 * n * ts, "geom"));
     RT_TRY(ensure(c, c->counts, (n + 1) * 4, "counts"));
     RT_TRY(ensure(c, c->row_off, (n + 1) * 8, "row_off"));
     RT_TRY(ensure(c, c->flags, 64, "flags"));
@@ -718,6 +915,11 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
 
     int* flags = c->flags.as<int>();
     RT_CUDA(c, cudaMemsetAsync(flags, 0, 64, st));
+    // reductions: [0] min h, [1] max h, [2] max cond, [3] min V (bit patterns of positive doubles)
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(c->red_tmp.p);
+    RT_CUDA(c, cudaMemsetAsync(red, 0, 32, st));
+    RT_CUDA(c, cudaMemsetAsync(red, 0xff, 8, st));
+    RT_CUDA(c, cudaMemsetAsync(red + 3, 0xff, 8, st));
 
     // cub scratch: radix sort of N and scan of N+1
     size_t t1 = 0, t2 = 0, t3 = 0;
@@ -747,6 +949,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
                                                   c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->m_s.as<double>(),
                                                   c->inv_perm.as<int32_t>());
     RT_CUDA(c, cudaGetLastError());
+    c->launches += 3;   // keys, cell table, gather
 
     // a2: smoothing lengths
     HParams hp;
@@ -757,14 +960,16 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     for (int a = 0; a < 3; ++a) hp.scale[a] = qscale[a];
     hp.max_iter = cfg.h_max_iter > 0 ? cfg.h_max_iter : 100;
     hp.tol32 = (float)std::max(cfg.h_tol, 2e-6);
+    hp.refine64 = c->fp64 ? 1 : 0;
     k_h_solve<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp,
-                                             c->h_d.as<double>(), c->omega_d.as<double>(), flags);
+                                             c->h_d.as<double>(), c->omega_d.as<double>(), c->H2f.as<float>(), red,
+                                             flags);
     RT_CUDA(c, cudaGetLastError());
-    k_minmax<<<1, 256, 0, st>>>(c->h_d.as<double>(), n, c->red_tmp.as<double>());
+    c->launches += 1;
     int hflags[8];
     double hmm[2];
     RT_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
-    RT_CUDA(c, cudaMemcpyAsync(hmm, c->red_tmp.p, sizeof(hmm), cudaMemcpyDeviceToHost, st));
+    RT_CUDA(c, cudaMemcpyAsync(hmm, red, sizeof(hmm), cudaMemcpyDeviceToHost, st));
     RT_CUDA(c, cudaStreamSynchronize(st));
     if (hflags[F_BADPOS]) return fail(c, RT_ERR_INVALID, "positions must be finite and inside [0, box)");
     if (hflags[F_NOCONV]) return fail(c, RT_ERR_NOCONV, "smoothing-length iteration did not converge");
@@ -778,8 +983,8 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     PairParams pp;
     for (int a = 0; a < 3; ++a) pp.scale[a] = qscale[a];
     pp.Hmax = Hmax;
-    k_pairs<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(), n,
-                                                  pp, c->counts.as<int32_t>(), nullptr, nullptr);
+    k_pairs<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(),
+                                                  c->H2f.as<float>(), n, pp, c->counts.as<int32_t>(), nullptr, nullptr);
     RT_CUDA(c, cudaMemsetAsync(c->counts.as<int32_t>() + n, 0, 4, st));
     tb = c->cub_tmp.bytes;
     RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->counts.as<int32_t>(), c->row_off.as<int64_t>(),
@@ -790,23 +995,25 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     if (P2 >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "more than 2^31 neighbour entries");
     c->n_directed = P2;
     RT_TRY(ensure(c, c->cols, std::max<int64_t>(P2, 1) * 4, "pair lists"));
-    k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(), n,
-                                                 pp, nullptr, c->row_off.as<int64_t>(), c->cols.as<int32_t>());
+    k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(),
+                                                 c->H2f.as<float>(), n, pp, nullptr, c->row_off.as<int64_t>(),
+                                                 c->cols.as<int32_t>());
     RT_CUDA(c, cudaGetLastError());
+    c->launches += 3;   // count, fill, geometry below
 
     // a4: geometry
     if (c->fp64)
         k_geometry<double><<<nblk(n, 128), 128, 0, st>>>(
-            c->xs_d.as<double>(), c->h_d.as<double>(), c->omega_d.as<double>(), c->row_off.as<int64_t>(),
-            c->cols.as<int32_t>(), n, cfg.box[0], cfg.box[1], cfg.box[2], cfg.periodic, c->V_d.as<double>(),
-            c->B_d.as<double>(), c->cond_d.as<double>(), c->invH_t.as<double>(), c->h_t.as<double>(),
-            c->omega_t.as<double>(), c->Bp_t.as<double>(), flags);
+            c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(), c->omega_d.as<double>(),
+            c->row_off.as<int64_t>(), c->cols.as<int32_t>(), n, cfg.box[0], cfg.box[1], cfg.box[2], cfg.periodic,
+            qscale[0], qscale[1], qscale[2], c->V_d.as<double>(), c->B_d.as<double>(), c->cond_d.as<double>(),
+            c->pos_t.p, c->geo_t.as<double>(), c->omega_t.as<double>(), red, flags);
     else
         k_geometry<float><<<nblk(n, 128), 128, 0, st>>>(
-            c->xs_d.as<double>(), c->h_d.as<double>(), c->omega_d.as<double>(), c->row_off.as<int64_t>(),
-            c->cols.as<int32_t>(), n, cfg.box[0], cfg.box[1], cfg.box[2], cfg.periodic, c->V_d.as<double>(),
-            c->B_d.as<double>(), c->cond_d.as<double>(), c->invH_t.as<float>(), c->h_t.as<float>(),
-            c->omega_t.as<float>(), c->Bp_t.as<float>(), flags);
+            c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(), c->omega_d.as<double>(),
+            c->row_off.as<int64_t>(), c->cols.as<int32_t>(), n, cfg.box[0], cfg.box[1], cfg.box[2], cfg.periodic,
+            qscale[0], qscale[1], qscale[2], c->V_d.as<double>(), c->B_d.as<double>(), c->cond_d.as<double>(),
+            c->pos_t.p, c->geo_t.as<float>(), c->omega_t.as<float>(), red, flags);
     RT_CUDA(c, cudaGetLastError());
 
     // a5 preparation: sources
@@ -825,8 +1032,8 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         sp.h_cap = hp.h_cap;
         sp.max_iter = std::max(hp.max_iter, 200);
         unsigned sb = nblk(S * 32, 128);
-        k_src_h<<<sb, 128, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S, sp, c->hs_d.as<double>(),
-                                     c->omegas_d.as<double>(), flags);
+        k_src_h<<<(unsigned)S, kSrcThreads, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S, sp,
+                                                     c->hs_d.as<double>(), c->omegas_d.as<double>(), flags);
         k_src_entries<false><<<sb, 128, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S,
                                                  c->hs_d.as<double>(), c->omegas_d.as<double>(),
                                                  c->src_counts.as<int32_t>(), nullptr, nullptr, nullptr, nullptr);
@@ -834,6 +1041,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         tb = c->cub_tmp.bytes;
         RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->src_counts.as<int32_t>(),
                                                  c->src_off.as<int64_t>(), (int)(S + 1), st));
+        c->launches += 2;
         int64_t NE = 0;
         RT_CUDA(c, cudaMemcpyAsync(&NE, c->src_off.as<int64_t>() + S, 8, cudaMemcpyDeviceToHost, st));
         RT_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
@@ -857,7 +1065,9 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
                                                 c->hs_d.as<double>(), c->omegas_d.as<double>(), nullptr,
                                                 c->src_off.as<int64_t>(), c->src_entry_gas.as<int32_t>(),
                                                 c->src_entry_xi.as<double>(), octw);
+        ++c->launches;
         if (NE > 0) {
+            c->launches += 3;
             k_inj_keys<<<nblk(NE, B), B, 0, st>>>(c->src_entry_gas.as<int32_t>(), c->src_off.as<int64_t>(), S, NE,
                                                    c->inj_key.as<uint64_t>(), c->inj_val.as<int32_t>());
             tb = c->cub_tmp.bytes;
@@ -890,15 +1100,11 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     c->diag.n_directed = P2;
     c->diag.n_pairs = P2 / 2;
     c->diag.n_injection = c->n_inj_entries;
-    k_minmax<<<1, 256, 0, st>>>(c->cond_d.as<double>(), n, c->red_tmp.as<double>());
-    double cmm[2];
-    RT_CUDA(c, cudaMemcpyAsync(cmm, c->red_tmp.p, sizeof(cmm), cudaMemcpyDeviceToHost, st));
-    k_minmax<<<1, 256, 0, st>>>(c->V_d.as<double>(), n, c->red_tmp.as<double>() + 2);
-    double vmm[2];
-    RT_CUDA(c, cudaMemcpyAsync(vmm, c->red_tmp.as<double>() + 2, sizeof(vmm), cudaMemcpyDeviceToHost, st));
+    double cv[2];
+    RT_CUDA(c, cudaMemcpyAsync(cv, red + 2, sizeof(cv), cudaMemcpyDeviceToHost, st));
     RT_CUDA(c, cudaStreamSynchronize(st));
-    c->diag.cond_max = cmm[1];
-    c->diag.dx_min = std::cbrt(vmm[0] / (4.0 * M_PI / 3.0));
+    c->diag.cond_max = cv[0];
+    c->diag.dx_min = std::cbrt(cv[1] / (4.0 * M_PI / 3.0));
     return RT_OK;
 }
 

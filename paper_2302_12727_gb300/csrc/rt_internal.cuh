@@ -8,6 +8,7 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "../../include/rt.h"
 
@@ -28,28 +29,23 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
-// Per-particle geometry consumed by the pair kernels, cell-sorted order.  For the double
-// path positions are doubles; for the float path positions are 32-bit fixed point in units
-// of box / 2^32, so that x_j - x_i is an exact integer difference whose wrap-around is the
-// periodic minimal image.
-template <class T>
-struct Geom {
-    const void* x;        // double[3][N] (T = double) or uint32[3][N] (T = float)
-    const T* invH;        // 1 / H_i
-    const T* h;           // h_i
-    const T* omega;       // omega_i = 1 / V_i
-    const T* Bp;          // [6][N]  V_i^2 sigma / H_i^3 * B_i  (xx, yy, zz, xy, xz, yz)
-    T scale[3];           // fixed-point unit per axis (float path)
-    double box[3];        // box (double path, minimal image)
-    int periodic;
-    int64_t n;
-};
-
 struct GraphKey {
     int n_sub, has_src, has_alpha;
     bool operator<(const GraphKey& o) const {
         return std::tie(n_sub, has_src, has_alpha) < std::tie(o.n_sub, o.has_src, o.has_alpha);
     }
+};
+
+// events recorded around one profiled launch
+struct ProfRec {
+    int kind;
+    cudaEvent_t start, stop;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;               // kernel nodes per replay
+    std::vector<ProfRec> prof;         // event nodes (profiling on)
 };
 
 }  // namespace rt
@@ -74,7 +70,8 @@ struct rt_ctx {
     rt::DevBuf keys_in, keys_out, idx_in, perm, inv_perm, cell_start, cell_end, cub_tmp;
     rt::DevBuf xs_d, xq, m_s;
     rt::DevBuf h_d, omega_d, V_d, B_d, cond_d;           // double per particle
-    rt::DevBuf invH_t, h_t, omega_t, Bp_t;              // working precision per particle
+    rt::DevBuf H2f;                                     // float (kappa h)^2, pair-search prefilter
+    rt::DevBuf pos_t, geo_t, omega_t;                   // working precision per particle (pair kernels)
     rt::DevBuf counts, row_off, cols;                   // symmetric pair lists (CSR)
     rt::DevBuf flags;                                   // int32 error flags + counters
     rt::DevBuf red_tmp;                                 // small reduction scratch (double)
@@ -85,8 +82,8 @@ struct rt_ctx {
     rt::DevBuf inj_targets, inj_off, inj_src, inj_coef, src_entry_gas, src_entry_xi;
     int64_t n_inj_entries = 0, n_inj_targets = 0;
 
-    // state (sorted order, working precision)
-    rt::DevBuf U_a, U_b, grad, alpha_s, L_dev, dt_dev, energy_part;
+    // state records (sorted order, working precision): U [N][4G] (double-buffered), grad U [N][12G]
+    rt::DevBuf U_a, U_b, grad_t, alpha_s, L_dev, dt_dev, energy_part;
     // adjoint
     rt::DevBuf ck, seg, lam_a, lam_b, gbar, lbar_part, lbar_acc;
     int64_t ck_cap = 0, seg_cap = 0;
@@ -95,7 +92,14 @@ struct rt_ctx {
     rt_diag diag{};
     int tpp = 1;   // threads per particle for pair kernels
 
-    std::map<rt::GraphKey, cudaGraphExec_t> graphs;
+    std::map<rt::GraphKey, rt::GraphEntry> graphs;
+
+    // tracing
+    int profiling = 0;
+    int64_t launches = 0;                    // own kernel launches (see rt_diag)
+    std::vector<rt::ProfRec>* prof_sink = nullptr;   // where launch helpers append records
+    std::vector<rt::ProfRec> plain_prof;     // records of the last plain step
+    const std::vector<rt::ProfRec>* last_prof = nullptr;
 };
 
 // ------------------------------------------------------------------------------------
@@ -104,6 +108,9 @@ namespace rt {
 rt_status fail(rt_ctx* c, rt_status s, const std::string& msg);
 rt_status cuda_fail(rt_ctx* c, cudaError_t e, const char* what);
 rt_status ensure(rt_ctx* c, DevBuf& b, size_t bytes, const char* what);
+// record a start event before a profiled launch (returns the index, or -1 when off)
+int prof_begin(rt_ctx* c, cudaStream_t s, int kind);
+void prof_end(rt_ctx* c, cudaStream_t s, int idx);
 }  // namespace rt
 
 #define RT_CUDA(ctx, call)                                         \
@@ -121,12 +128,15 @@ rt_status ensure(rt_ctx* c, DevBuf& b, size_t bytes, const char* what);
 // entry points of the kernel files
 namespace rt {
 rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc);
-rt_status to_sorted(rt_ctx* c, const void* U_user, void* U_sorted, int comps);
-rt_status from_sorted(rt_ctx* c, const void* U_sorted, void* U_user, int comps);
+// caller-order component-major arrays <-> sorted records (comps values at record offset off)
+rt_status state_in(rt_ctx* c, const void* U_user, void* rec, int comps, int RS, int off);
+rt_status state_out(rt_ctx* c, const void* rec, void* U_user, int comps, int RS, int off);
+// sorted double per-particle fields [comps][N] -> caller order
+rt_status field_out(rt_ctx* c, const double* src_sorted, double* dst_user, int comps);
 rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double* alpha);
 rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha);
-rt_status launch_gradient(rt_ctx* c, cudaStream_t s, const void* U, void* grad);
-rt_status launch_energy(rt_ctx* c, cudaStream_t s, const void* U_sorted, double* out_dev);
+rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec);
+rt_status launch_energy(rt_ctx* c, cudaStream_t s, const void* rec, double* out_dev);
 rt_status run_adjoint(rt_ctx* c, int n_sub, int ckpt_every, bool has_src, bool has_alpha, const void* U0_sorted,
                       const void* lam_final_sorted, void* lam0_sorted, double* dLdL_dev);
 }  // namespace rt

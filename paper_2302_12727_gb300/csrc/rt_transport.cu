@@ -3,10 +3,20 @@
 // minmod-limited face states, M1 closure and GLF flux, the explicit update, the grey sink
 // and the energy diagnostic.
 //
-// Every pair kernel runs one thread per particle over its symmetric neighbour list in
-// cell-sorted order.  The flux of a pair is evaluated by both particles with the same
-// operand order (the lower sorted index is the left state k), so the two evaluations are
-// bitwise identical and the exchange is exactly antisymmetric without atomics.
+// Layout (cell-sorted order): per particle a state record of 4G values (E, Fx, Fy, Fz per
+// group), a gradient record of 12G values (d/dx, d/dy, d/dz per component), a position
+// record (fixed-point uint4 for the float path, 4 doubles for the double path) and a
+// geometry record of 8 values {1/H, h, Bp (6)} with Bp = V^2 sigma / H^3 B so that
+// V_i psitilde_j(x_i) = Bp_i d w(q).  A neighbour's data is then a few 16-byte loads.
+//
+// Every pair kernel runs one thread per particle over its symmetric neighbour list.  Each
+// particle evaluates the flux of a pair with itself as the left state (the form of
+// Eq. transport-update-explicit).  Every operation on that path is either odd in the
+// separation d (so the other particle's evaluation, with -d, gives the exact negative) or
+// symmetric in the two particles; the three places where a fused multiply-add could break
+// that symmetry use explicitly rounded operations.  The exchange is therefore exactly
+// antisymmetric, and so exactly conservative, without atomics and without evaluating the
+// pair in a canonical orientation.
 #include "rt_internal.cuh"
 
 namespace rt {
@@ -14,15 +24,197 @@ namespace rt {
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // ------------------------------------------------------------------------------------
-// caller order <-> cell-sorted order, component-major arrays of `comps` rows
+// precision-specific primitives: IEEE in double, approximate reciprocal / square root in
+// float (relative error ~1e-7, far inside the float path's tolerance)
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float rcp_(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// explicitly rounded operations, so that the compiler cannot fuse them differently
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
+
+// cubic-spline shape without branches: (1-q)_+^3 - 4 (1/2-q)_+^3 (Eq. cubic-spline-kernel)
 template <class T>
-__global__ void k_to_sorted(const T* __restrict__ src, const int32_t* __restrict__ perm, int64_t n, int comps, T* dst) {
+__device__ __forceinline__ T spline_w_(T q) {
+    T a = fmax_(T(1) - q, T(0));
+    T b = fmax_(T(0.5) - q, T(0));
+    return a * a * a - T(4) * (b * b * b);
+}
+
+// minmod of Eq. rt-minmod as selects: both positive -> min, both negative -> max, else 0
+template <class T>
+__device__ __forceinline__ T minmod_(T a, T b) {
+    T lo = fmin_(a, b), hi = fmax_(a, b);
+    return lo > T(0) ? lo : (hi < T(0) ? hi : T(0));
+}
+
+// M1 flux of one group contracted with A, branch-free form of m1_dot (Eq. eddington-group):
+// (F . A, c^2 E [(1-chi)/2 A + b(u) u/|F|^2 (F . A) F]), zero pressure for E <= 0.
+template <class T>
+__device__ __forceinline__ void m1_dot_(T E, T Fx, T Fy, T Fz, T Ax, T Ay, T Az, T c, T& oE, T& oFx, T& oFy,
+                                        T& oFz) {
+    T FA = Fx * Ax + Fy * Ay + Fz * Az;
+    oE = FA;
+    bool pos = E > T(0);
+    T Es = pos ? E : T(1);
+    T F2 = Fx * Fx + Fy * Fy + Fz * Fz;
+    T icE = rcp_(c * Es);
+    T icE2 = icE * icE;
+    T u = F2 * icE2;
+    bool clip = u > T(1);
+    T sc = clip ? rcp_(F2) : icE2;
+    u = clip ? T(1) : u;
+    T s = sqrt_(T(4) - T(3) * u);
+    T den = rcp_(T(5) + T(2) * s);
+    T a_iso = (T(1) + s - T(2) * u) * den;
+    T b = T(6) * (T(1) + rcp_(T(4) + T(2) * s)) * den;
+    T cE = pos ? c * c * E : T(0);
+    T t = b * FA * sc;
+    oFx = cE * (a_iso * Ax + t * Fx);
+    oFy = cE * (a_iso * Ay + t * Fy);
+    oFz = cE * (a_iso * Az + t * Fz);
+}
+
+// ------------------------------------------------------------------------------------
+// positions
+template <class T>
+struct Pos;
+template <>
+struct Pos<float> {
+    uint32_t a, b, c;
+};
+template <>
+struct Pos<double> {
+    double a, b, c;
+};
+
+__device__ __forceinline__ Pos<float> load_pos(const float*, const void* P, int64_t i) {
+    uint4 v = reinterpret_cast<const uint4*>(P)[i];
+    return {v.x, v.y, v.z};
+}
+__device__ __forceinline__ Pos<double> load_pos(const double*, const void* P, int64_t i) {
+    const double2* p = reinterpret_cast<const double2*>(P) + 2 * i;
+    double2 u = p[0], v = p[1];
+    return {u.x, u.y, v.x};
+}
+
+struct SepParams {
+    float s0, s1, s2;          // float path: fixed-point unit
+    double b0, b1, b2;         // double path: box
+    int periodic;
+};
+
+__device__ __forceinline__ double wrap_d(double v, double box, int periodic) {
+    if (periodic) {
+        double h = 0.5 * box;
+        v = v > h ? v - box : (v < -h ? v + box : v);
+    }
+    return v;
+}
+
+// d = x_to - x_from
+__device__ __forceinline__ void sep(const SepParams& s, const Pos<float>& f, const Pos<float>& t, float& dx, float& dy,
+                                    float& dz) {
+    dx = (float)(int32_t)(t.a - f.a) * s.s0;
+    dy = (float)(int32_t)(t.b - f.b) * s.s1;
+    dz = (float)(int32_t)(t.c - f.c) * s.s2;
+}
+__device__ __forceinline__ void sep(const SepParams& s, const Pos<double>& f, const Pos<double>& t, double& dx,
+                                    double& dy, double& dz) {
+    dx = wrap_d(t.a - f.a, s.b0, s.periodic);
+    dy = wrap_d(t.b - f.b, s.b1, s.periodic);
+    dz = wrap_d(t.c - f.c, s.b2, s.periodic);
+}
+
+// vector loads of K consecutive values (16-byte aligned)
+template <int K>
+__device__ __forceinline__ void vload(const float* __restrict__ p, float* o) {
+    static_assert(K % 4 == 0, "K multiple of 4");
+#pragma unroll
+    for (int k = 0; k < K; k += 4) {
+        float4 v = *reinterpret_cast<const float4*>(p + k);
+        o[k] = v.x; o[k + 1] = v.y; o[k + 2] = v.z; o[k + 3] = v.w;
+    }
+}
+template <int K>
+__device__ __forceinline__ void vload(const double* __restrict__ p, double* o) {
+    static_assert(K % 2 == 0, "K even");
+#pragma unroll
+    for (int k = 0; k < K; k += 2) {
+        double2 v = *reinterpret_cast<const double2*>(p + k);
+        o[k] = v.x; o[k + 1] = v.y;
+    }
+}
+template <int K>
+__device__ __forceinline__ void vstore(float* p, const float* o) {
+#pragma unroll
+    for (int k = 0; k < K; k += 4) *reinterpret_cast<float4*>(p + k) = make_float4(o[k], o[k + 1], o[k + 2], o[k + 3]);
+}
+template <int K>
+__device__ __forceinline__ void vstore(double* p, const double* o) {
+#pragma unroll
+    for (int k = 0; k < K; k += 2) *reinterpret_cast<double2*>(p + k) = make_double2(o[k], o[k + 1]);
+}
+
+template <class T>
+struct PairArgs {
+    const void* pos;          // uint4[N] or double[4N]
+    const T* geo;             // [N][8] {1/H, h, Bp xx yy zz xy xz yz}
+    const T* omega;           // [N]
+    const int64_t* row_off;
+    const int32_t* cols;
+    SepParams sp;
+    int64_t n;
+    const T* grad;            // [N][12G]
+    int G;
+};
+
+// symmetric 3x3 (xx, yy, zz, xy, xz, yz) times vector
+template <class T>
+__device__ __forceinline__ void sym_mv(const T M[6], T x, T y, T z, T& ox, T& oy, T& oz) {
+    ox = M[0] * x + M[3] * y + M[4] * z;
+    oy = M[3] * x + M[1] * y + M[5] * z;
+    oz = M[4] * x + M[5] * y + M[2] * z;
+}
+
+// ------------------------------------------------------------------------------------
+// caller order <-> cell-sorted records
+template <class T>
+__global__ void k_state_in(const T* __restrict__ src, const int32_t* __restrict__ perm, int64_t n, int comps, int RS,
+                           int off, T* __restrict__ rec) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
     int64_t i = perm[p];
-    for (int c = 0; c < comps; ++c) dst[c * n + p] = src[c * n + i];
+    for (int c = 0; c < comps; ++c) rec[p * RS + off + c] = src[c * n + i];
 }
 
+template <class T>
+__global__ void k_state_out(const T* __restrict__ rec, const int32_t* __restrict__ inv_perm, int64_t n, int comps,
+                            int RS, int off, T* __restrict__ dst) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t p = inv_perm[i];
+    for (int c = 0; c < comps; ++c) dst[c * n + i] = rec[p * RS + off + c];
+}
+
+// plain SoA gathers (double per-particle fields)
 template <class T>
 __global__ void k_from_sorted(const T* __restrict__ src, const int32_t* __restrict__ inv_perm, int64_t n, int comps,
                               T* dst) {
@@ -42,94 +234,13 @@ __global__ void k_alpha_sorted(const double* __restrict__ alpha, const int32_t* 
 __global__ void k_set_scalar(double* dst, double v) { *dst = v; }
 
 // ------------------------------------------------------------------------------------
-// separation x_l - x_k in the working precision
-template <class T>
-struct Sep;
-
-template <>
-struct Sep<float> {
-    const uint32_t* x;
-    float s0, s1, s2;
-    int64_t n;
-    __device__ __forceinline__ void pos(int64_t i, uint32_t& a, uint32_t& b, uint32_t& c) const {
-        a = x[i];
-        b = x[n + i];
-        c = x[2 * n + i];
-    }
-};
-
-template <>
-struct Sep<double> {
-    const double* x;
-    double b0, b1, b2;
-    int periodic;
-    int64_t n;
-};
-
-__device__ __forceinline__ double wrap_d(double v, double box, int periodic) {
-    if (periodic) {
-        double h = 0.5 * box;
-        if (v > h) v -= box;
-        else if (v < -h) v += box;
-    }
-    return v;
-}
-
-template <class T>
-struct PosT;
-template <>
-struct PosT<float> { uint32_t a, b, c; };
-template <>
-struct PosT<double> { double a, b, c; };
-
-__device__ __forceinline__ void load_pos(const Sep<float>& s, int64_t i, PosT<float>& p) {
-    p.a = s.x[i]; p.b = s.x[s.n + i]; p.c = s.x[2 * s.n + i];
-}
-__device__ __forceinline__ void load_pos(const Sep<double>& s, int64_t i, PosT<double>& p) {
-    p.a = s.x[i]; p.b = s.x[s.n + i]; p.c = s.x[2 * s.n + i];
-}
-// d = x_to - x_from
-__device__ __forceinline__ void sep(const Sep<float>& s, const PosT<float>& from, const PosT<float>& to, float& dx,
-                                    float& dy, float& dz) {
-    dx = (float)(int32_t)(to.a - from.a) * s.s0;
-    dy = (float)(int32_t)(to.b - from.b) * s.s1;
-    dz = (float)(int32_t)(to.c - from.c) * s.s2;
-}
-__device__ __forceinline__ void sep(const Sep<double>& s, const PosT<double>& from, const PosT<double>& to,
-                                    double& dx, double& dy, double& dz) {
-    dx = wrap_d(to.a - from.a, s.b0, s.periodic);
-    dy = wrap_d(to.b - from.b, s.b1, s.periodic);
-    dz = wrap_d(to.c - from.c, s.b2, s.periodic);
-}
-
-template <class T>
-struct PairArgs {
-    Sep<T> sp;
-    const T* invH;
-    const T* h;
-    const T* omega;
-    const T* Bp;          // [6][N]
-    const int64_t* row_off;
-    const int32_t* cols;
-    int64_t n;
-};
-
-// symmetric 3x3 (xx, yy, zz, xy, xz, yz) times vector
-template <class T>
-__device__ __forceinline__ void sym_mv(const T M[6], T x, T y, T z, T& ox, T& oy, T& oz) {
-    ox = M[0] * x + M[3] * y + M[4] * z;
-    oy = M[3] * x + M[1] * y + M[5] * z;
-    oz = M[4] * x + M[5] * y + M[2] * z;
-}
-
-// ------------------------------------------------------------------------------------
 // a5: injection, one thread per target particle: E_g += dt * sum_e coef_e L[src_e][g]
 // (coef = xi / V_target), accumulated in double.
 template <class T>
 __global__ void k_inject(const int32_t* __restrict__ targets, const int32_t* __restrict__ off,
                          const int32_t* __restrict__ src, const double* __restrict__ coef,
                          const double* __restrict__ L, int G, const double* __restrict__ dt_dev, int64_t n_targets,
-                         int64_t n, T* U) {
+                         int RS, T* rec) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_targets) return;
     double dt = *dt_dev;
@@ -137,7 +248,7 @@ __global__ void k_inject(const int32_t* __restrict__ targets, const int32_t* __r
     for (int g = 0; g < G; ++g) {
         double acc = 0.0;
         for (int e = off[t]; e < off[t + 1]; ++e) acc += coef[e] * L[(int64_t)src[e] * G + g];
-        T* E = U + (int64_t)(4 * g) * n + p;
+        T* E = rec + p * RS + 4 * g;
         *E = (T)((double)*E + dt * acc);
     }
 }
@@ -146,52 +257,55 @@ __global__ void k_inject(const int32_t* __restrict__ targets, const int32_t* __r
 // a6: least-squares gradient (Eq. gradient) of the groups [g0, g0 + GC):
 // grad Q_i = omega_i Bp_i sum_j (Q_j - Q_i) w(r_ij / H_i) d_ij,  d_ij = x_j - x_i
 template <class T, int GC>
-__global__ void __launch_bounds__(128) k_gradient(PairArgs<T> a, const T* __restrict__ U, T* __restrict__ grad, int g0) {
+__global__ void __launch_bounds__(128) k_gradient(PairArgs<T> a, const T* __restrict__ rec, T* __restrict__ grad,
+                                                  int g0) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t n = a.n;
-    if (i >= n) return;
+    if (i >= a.n) return;
     constexpr int NC = 4 * GC;
-    PosT<T> pi;
-    load_pos(a.sp, i, pi);
-    T iH = a.invH[i];
+    const T* tag = nullptr;
+    Pos<T> pi = load_pos(tag, a.pos, i);
+    const T iH = a.geo[8 * i];
+    const int RS = 4 * a.G;
     T ui[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) ui[c] = U[(int64_t)(4 * g0 + c) * n + i];
+    vload<NC>(rec + i * RS + 4 * g0, ui);
     T acc[NC][3];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c][0] = acc[c][1] = acc[c][2] = T(0);
     const int64_t e0 = a.row_off[i], e1 = a.row_off[i + 1];
-    for (int64_t e = e0; e < e1; ++e) {
-        int j = a.cols[e];
-        PosT<T> pj;
-        load_pos(a.sp, j, pj);
-        T dx, dy, dz;
-        sep(a.sp, pi, pj, dx, dy, dz);
-        T r = sqrt(dx * dx + dy * dy + dz * dz);
-        T w = spline_w(r * iH);
-        if (w == T(0)) continue;
-        T wx = w * dx, wy = w * dy, wz = w * dz;
+    // two neighbours per iteration: both neighbours' loads are in flight together
+    for (int64_t e = e0; e < e1; e += 2) {
+        const bool two = e + 1 < e1;
+        const int j0 = a.cols[e];
+        const int j1 = two ? a.cols[e + 1] : j0;
+        Pos<T> p0 = load_pos(tag, a.pos, j0);
+        Pos<T> p1 = load_pos(tag, a.pos, j1);
+        T u0[NC], u1[NC];
+        vload<NC>(rec + (int64_t)j0 * RS + 4 * g0, u0);
+        vload<NC>(rec + (int64_t)j1 * RS + 4 * g0, u1);
+        T dx0, dy0, dz0, dx1, dy1, dz1;
+        sep(a.sp, pi, p0, dx0, dy0, dz0);
+        sep(a.sp, pi, p1, dx1, dy1, dz1);
+        T w0 = spline_w_(sqrt_(dx0 * dx0 + dy0 * dy0 + dz0 * dz0) * iH);
+        T w1 = two ? spline_w_(sqrt_(dx1 * dx1 + dy1 * dy1 + dz1 * dz1) * iH) : T(0);
+        T wx0 = w0 * dx0, wy0 = w0 * dy0, wz0 = w0 * dz0;
+        T wx1 = w1 * dx1, wy1 = w1 * dy1, wz1 = w1 * dz1;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            T dq = U[(int64_t)(4 * g0 + c) * n + j] - ui[c];
-            acc[c][0] += dq * wx;
-            acc[c][1] += dq * wy;
-            acc[c][2] += dq * wz;
+            T dq0 = u0[c] - ui[c];
+            T dq1 = u1[c] - ui[c];
+            acc[c][0] += dq0 * wx0 + dq1 * wx1;
+            acc[c][1] += dq0 * wy0 + dq1 * wy1;
+            acc[c][2] += dq0 * wz0 + dq1 * wz1;
         }
     }
     T M[6];
-    T om = a.omega[i];
+    const T om = a.omega[i];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) M[k] = om * a.Bp[k * n + i];
+    for (int k = 0; k < 6; ++k) M[k] = om * a.geo[8 * i + 2 + k];
+    T out[3 * NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        T gx, gy, gz;
-        sym_mv(M, acc[c][0], acc[c][1], acc[c][2], gx, gy, gz);
-        int64_t base = ((int64_t)(4 * g0 + c) * 3) * n + i;
-        grad[base] = gx;
-        grad[base + n] = gy;
-        grad[base + 2 * n] = gz;
-    }
+    for (int c = 0; c < NC; ++c) sym_mv(M, acc[c][0], acc[c][1], acc[c][2], out[3 * c], out[3 * c + 1], out[3 * c + 2]);
+    vstore<3 * NC>(grad + i * 12 * a.G + 12 * g0, out);
 }
 
 // ------------------------------------------------------------------------------------
@@ -205,114 +319,89 @@ struct FluxExtra {
     unsigned long long* clamp_count;
 };
 
-// Flux of pair (k, l) for one group: face states (Eq. rt-riemann-problem with
-// s = minmod(grad Q_k . d, grad Q_l . d)), M1 fluxes (Eq. eddington-group), GLF (Eq. riemann-GLF).
+// Flux of pair (k, l) for one group, k = this particle as the left state: face states
+// (Eq. rt-riemann-problem with s = minmod(grad Q_k . d, grad Q_l . d)), M1 fluxes
+// (Eq. eddington-group), GLF (Eq. riemann-GLF).  The face states use explicit fma so that
+// the evaluation by l (with -d and the roles swapped) gives exactly -phi.
 template <class T>
-__device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T gk[4][3], const T gl[4][3], T dx, T dy,
-                                          T dz, T wk, T wl, T Ax, T Ay, T Az, T An, T c, T phi[4]) {
+__device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T gk[12], const T gl[12], T dx, T dy,
+                                          T dz, T wk, T wl, T Ax, T Ay, T Az, T diss, T c, T phi[4]) {
     T L[4], R[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        T dqk = gk[q][0] * dx + gk[q][1] * dy + gk[q][2] * dz;
-        T dql = gl[q][0] * dx + gl[q][1] * dy + gl[q][2] * dz;
-        T s = minmod(dqk, dql);
-        L[q] = uk[q] + wk * s;
-        R[q] = ul[q] - wl * s;
+        T dqk = gk[3 * q] * dx + gk[3 * q + 1] * dy + gk[3 * q + 2] * dz;
+        T dql = gl[3 * q] * dx + gl[3 * q + 1] * dy + gl[3 * q + 2] * dz;
+        T s = minmod_(dqk, dql);
+        L[q] = fma_rn(wk, s, uk[q]);
+        R[q] = fma_rn(-wl, s, ul[q]);
     }
     T fL[4], fR[4];
-    m1_dot(L[0], L[1], L[2], L[3], Ax, Ay, Az, c, fL[0], fL[1], fL[2], fL[3]);
-    m1_dot(R[0], R[1], R[2], R[3], Ax, Ay, Az, c, fR[0], fR[1], fR[2], fR[3]);
-    T diss = T(0.5) * c * An;
+    m1_dot_(L[0], L[1], L[2], L[3], Ax, Ay, Az, c, fL[0], fL[1], fL[2], fL[3]);
+    m1_dot_(R[0], R[1], R[2], R[3], Ax, Ay, Az, c, fR[0], fR[1], fR[2], fR[3]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) phi[q] = T(0.5) * (fL[q] + fR[q]) - diss * (R[q] - L[q]);
 }
 
-// geometry of the pair in canonical roles: A_kl = (Bp_k w_k + Bp_l w_l) d (Eq. HopkinsAij with
-// V psitilde = Bp d w), |A|, the interface weights h_k/(h_k+h_l), h_l/(h_k+h_l)
-template <class T>
-__device__ __forceinline__ void pair_geometry(const T Bk[6], const T Bl[6], T iHk, T iHl, T hk, T hl, T dx, T dy,
-                                              T dz, T& Ax, T& Ay, T& Az, T& An, T& wk, T& wl) {
-    T r = sqrt(dx * dx + dy * dy + dz * dz);
-    T sk = spline_w(r * iHk);
-    T sl = spline_w(r * iHl);
-    T M[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) M[q] = Bk[q] * sk + Bl[q] * sl;
-    sym_mv(M, dx, dy, dz, Ax, Ay, Az);
-    An = sqrt(Ax * Ax + Ay * Ay + Az * Az);
-    T ih = T(1) / (hk + hl);
-    wk = hk * ih;
-    wl = hl * ih;
-}
-
 template <class T, int GC>
-__global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ U,
-                                              const T* __restrict__ grad, T* __restrict__ Uout, int g0) {
+__global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ rec,
+                                              T* __restrict__ out, int g0) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t n = a.n;
-    if (i >= n) return;
+    if (i >= a.n) return;
     constexpr int NC = 4 * GC;
-    PosT<T> pi;
-    load_pos(a.sp, i, pi);
-    const T iHi = a.invH[i], hi = a.h[i];
-    T Bi[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) Bi[k] = a.Bp[k * n + i];
-    T ui[NC], gi[NC][3];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        int64_t cc = 4 * g0 + c;
-        ui[c] = U[cc * n + i];
-        gi[c][0] = grad[(cc * 3) * n + i];
-        gi[c][1] = grad[(cc * 3 + 1) * n + i];
-        gi[c][2] = grad[(cc * 3 + 2) * n + i];
-    }
+    const T* tag = nullptr;
+    const int G = a.G, RS = 4 * G;
+    const Pos<T> pi = load_pos(tag, a.pos, i);
+    T gi8[8];
+    vload<8>(a.geo + 8 * i, gi8);
     T acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = T(0);
+    const T* ri = rec + i * RS;
+    const T* qi = a.grad + i * 12 * G;
     const int64_t e0 = a.row_off[i], e1 = a.row_off[i + 1];
     for (int64_t e = e0; e < e1; ++e) {
         const int j = a.cols[e];
-        const bool ik = i < j;
-        PosT<T> pj;
-        load_pos(a.sp, j, pj);
-        const T iHj = a.invH[j], hj = a.h[j];
-        T Bj[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Bj[k] = a.Bp[k * n + j];
-        // canonical roles: k = lower sorted index (left state), l = higher
+        const Pos<T> pj = load_pos(tag, a.pos, j);
+        T gj8[8];
+        vload<8>(a.geo + 8 * (int64_t)j, gj8);
         T dx, dy, dz;
-        if (ik) sep(a.sp, pi, pj, dx, dy, dz);
-        else sep(a.sp, pj, pi, dx, dy, dz);
-        T Ax, Ay, Az, An, wk, wl;
-        if (ik) pair_geometry(Bi, Bj, iHi, iHj, hi, hj, dx, dy, dz, Ax, Ay, Az, An, wk, wl);
-        else pair_geometry(Bj, Bi, iHj, iHi, hj, hi, dx, dy, dz, Ax, Ay, Az, An, wk, wl);
+        sep(a.sp, pi, pj, dx, dy, dz);              // d = x_j - x_i
+        // A_ij = (Bp_i w_i + Bp_j w_j) d  (Eq. HopkinsAij): the sum of the two products is
+        // rounded explicitly so that it is the same seen from either particle
+        T r = sqrt_(dx * dx + dy * dy + dz * dz);
+        T si = spline_w_(r * gi8[0]);
+        T sj = spline_w_(r * gj8[0]);
+        T M[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) M[q] = add_rn(mul_rn(gi8[2 + q], si), mul_rn(gj8[2 + q], sj));
+        T Ax, Ay, Az;
+        sym_mv(M, dx, dy, dz, Ax, Ay, Az);
+        T diss = T(0.5) * x.c * sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+        T ih = rcp_(gi8[1] + gj8[1]);
+        T wi = gi8[1] * ih, wj = gj8[1] * ih;
+        const T* rj = rec + (int64_t)j * RS;
+        const T* qj = a.grad + (int64_t)j * 12 * G;
 #pragma unroll
         for (int g = 0; g < GC; ++g) {
-            T uo[4], go[4][3];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                int64_t cc = 4 * (g0 + g) + q;
-                uo[q] = U[cc * n + j];
-                go[q][0] = grad[(cc * 3) * n + j];
-                go[q][1] = grad[(cc * 3 + 1) * n + j];
-                go[q][2] = grad[(cc * 3 + 2) * n + j];
-            }
+            const int gg = g0 + g;
+            T ui[4], uj[4], gri[12], grj[12];
+            vload<4>(ri + 4 * gg, ui);
+            vload<4>(rj + 4 * gg, uj);
+            vload<12>(qi + 12 * gg, gri);
+            vload<12>(qj + 12 * gg, grj);
             T phi[4];
-            if (ik) pair_flux(&ui[4 * g], uo, &gi[4 * g], go, dx, dy, dz, wk, wl, Ax, Ay, Az, An, x.c, phi);
-            else pair_flux(uo, &ui[4 * g], go, &gi[4 * g], dx, dy, dz, wk, wl, Ax, Ay, Az, An, x.c, phi);
+            pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, phi);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[4 * g + q] += ik ? phi[q] : -phi[q];
+            for (int q = 0; q < 4; ++q) acc[4 * g + q] += phi[q];
         }
     }
     // U_i(t + dt) = U_i - dt / V_i sum_l F_il . A_il, then the sink and the fix-up
     const T dt = (T)(*x.dt_dev);
     const T f = dt * a.omega[i];
     T sink = T(1);
-    if (x.alpha) {
-        sink = T(1) - x.c * x.alpha[i] * dt;
-        sink = sink > T(0) ? sink : T(0);
-    }
+    if (x.alpha) sink = fmax_(T(1) - x.c * x.alpha[i] * dt, T(0));
+    T ui[NC];
+    vload<NC>(rec + i * RS + 4 * g0, ui);
     int nclamp = 0;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -321,8 +410,9 @@ __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, con
             v = T(0);
             ++nclamp;
         }
-        Uout[(int64_t)(4 * g0 + c) * n + i] = v;
+        ui[c] = v;
     }
+    vstore<NC>(out + i * RS + 4 * g0, ui);
     if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
 }
 
@@ -331,13 +421,13 @@ __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, con
 constexpr int kEnergyBlocks = 512;
 
 template <class T>
-__global__ void k_energy_part(const T* __restrict__ U, const double* __restrict__ V, int64_t n, int G,
+__global__ void k_energy_part(const T* __restrict__ rec, int RS, const double* __restrict__ V, int64_t n, int G,
                               double* part) {
     __shared__ double sm[256];
     for (int g = 0; g < G; ++g) {
         double s = 0.0;
         for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
-            s += V[p] * (double)U[(int64_t)(4 * g) * n + p];
+            s += V[p] * (double)rec[p * RS + 4 * g];
         sm[threadIdx.x] = s;
         __syncthreads();
         for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -361,49 +451,60 @@ __global__ void k_energy_final(const double* __restrict__ part, int nb, int G, d
 template <class T>
 static PairArgs<T> pair_args(rt_ctx* c) {
     PairArgs<T> a;
-    if constexpr (sizeof(T) == 4) {
-        a.sp.x = c->xq.as<uint32_t>();
-        double units = c->cfg.periodic ? 4294967296.0 : 2147483648.0;
-        a.sp.s0 = (float)(c->cfg.box[0] / units);
-        a.sp.s1 = (float)(c->cfg.box[1] / units);
-        a.sp.s2 = (float)(c->cfg.box[2] / units);
-        a.sp.n = c->n;
-    } else {
-        a.sp.x = c->xs_d.as<double>();
-        a.sp.b0 = c->cfg.box[0];
-        a.sp.b1 = c->cfg.box[1];
-        a.sp.b2 = c->cfg.box[2];
-        a.sp.periodic = c->cfg.periodic;
-        a.sp.n = c->n;
-    }
-    a.invH = c->invH_t.as<T>();
-    a.h = c->h_t.as<T>();
+    a.pos = c->pos_t.p;
+    a.geo = c->geo_t.as<T>();
     a.omega = c->omega_t.as<T>();
-    a.Bp = c->Bp_t.as<T>();
     a.row_off = c->row_off.as<int64_t>();
     a.cols = c->cols.as<int32_t>();
+    double units = c->cfg.periodic ? 4294967296.0 : 2147483648.0;
+    a.sp.s0 = (float)(c->cfg.box[0] / units);
+    a.sp.s1 = (float)(c->cfg.box[1] / units);
+    a.sp.s2 = (float)(c->cfg.box[2] / units);
+    a.sp.b0 = c->cfg.box[0];
+    a.sp.b1 = c->cfg.box[1];
+    a.sp.b2 = c->cfg.box[2];
+    a.sp.periodic = c->cfg.periodic;
     a.n = c->n;
+    a.grad = c->grad_t.as<T>();
+    a.G = c->cfg.n_groups;
     return a;
 }
 
+// the pair kernels use no shared memory: give the whole unified L1 to the cache
 template <class T>
-static void launch_gradient_t(rt_ctx* c, cudaStream_t s, const T* U, T* grad) {
+static void set_carveouts() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    const void* fs[] = {(const void*)k_gradient<T, 1>, (const void*)k_gradient<T, 2>, (const void*)k_gradient<T, 3>,
+                        (const void*)k_gradient<T, 4>, (const void*)k_flux<T, 1>,     (const void*)k_flux<T, 2>,
+                        (const void*)k_flux<T, 3>,     (const void*)k_flux<T, 4>};
+    for (const void* f : fs) cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    (void)cudaGetLastError();
+}
+
+template <class T>
+static void launch_gradient_t(rt_ctx* c, cudaStream_t s, T* rec) {
+    set_carveouts<T>();
     PairArgs<T> a = pair_args<T>(c);
     const int G = c->cfg.n_groups;
     unsigned nb = nblk(c->n, 128);
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
+        int pr = prof_begin(c, s, RT_KERNEL_GRADIENT);
         switch (gc) {
-            case 1: k_gradient<T, 1><<<nb, 128, 0, s>>>(a, U, grad, g0); break;
-            case 2: k_gradient<T, 2><<<nb, 128, 0, s>>>(a, U, grad, g0); break;
-            case 3: k_gradient<T, 3><<<nb, 128, 0, s>>>(a, U, grad, g0); break;
-            default: k_gradient<T, 4><<<nb, 128, 0, s>>>(a, U, grad, g0); break;
+            case 1: k_gradient<T, 1><<<nb, 128, 0, s>>>(a, rec, c->grad_t.as<T>(), g0); break;
+            case 2: k_gradient<T, 2><<<nb, 128, 0, s>>>(a, rec, c->grad_t.as<T>(), g0); break;
+            case 3: k_gradient<T, 3><<<nb, 128, 0, s>>>(a, rec, c->grad_t.as<T>(), g0); break;
+            default: k_gradient<T, 4><<<nb, 128, 0, s>>>(a, rec, c->grad_t.as<T>(), g0); break;
         }
+        prof_end(c, s, pr);
+        ++c->launches;
     }
 }
 
 template <class T>
-static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* U, const T* grad, T* Uout, bool has_alpha) {
+static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool has_alpha) {
     PairArgs<T> a = pair_args<T>(c);
     FluxExtra<T> x;
     x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
@@ -415,26 +516,32 @@ static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* U, const T* grad, 
     unsigned nb = nblk(c->n, 128);
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
+        int pr = prof_begin(c, s, RT_KERNEL_FLUX);
         switch (gc) {
-            case 1: k_flux<T, 1><<<nb, 128, 0, s>>>(a, x, U, grad, Uout, g0); break;
-            case 2: k_flux<T, 2><<<nb, 128, 0, s>>>(a, x, U, grad, Uout, g0); break;
-            case 3: k_flux<T, 3><<<nb, 128, 0, s>>>(a, x, U, grad, Uout, g0); break;
-            default: k_flux<T, 4><<<nb, 128, 0, s>>>(a, x, U, grad, Uout, g0); break;
+            case 1: k_flux<T, 1><<<nb, 128, 0, s>>>(a, x, rec, out, g0); break;
+            case 2: k_flux<T, 2><<<nb, 128, 0, s>>>(a, x, rec, out, g0); break;
+            case 3: k_flux<T, 3><<<nb, 128, 0, s>>>(a, x, rec, out, g0); break;
+            default: k_flux<T, 4><<<nb, 128, 0, s>>>(a, x, rec, out, g0); break;
         }
+        prof_end(c, s, pr);
+        ++c->launches;
     }
 }
 
 template <class T>
-static void launch_inject_t(rt_ctx* c, cudaStream_t s, T* U) {
+static void launch_inject_t(rt_ctx* c, cudaStream_t s, T* rec) {
     if (c->n_inj_targets <= 0) return;
+    int pr = prof_begin(c, s, RT_KERNEL_INJECT);
     k_inject<T><<<nblk(c->n_inj_targets, 128), 128, 0, s>>>(
         c->inj_targets.as<int32_t>(), c->inj_off.as<int32_t>(), c->inj_src.as<int32_t>(), c->inj_coef.as<double>(),
-        c->L_dev.as<double>(), c->cfg.n_groups, c->dt_dev.as<double>(), c->n_inj_targets, c->n, U);
+        c->L_dev.as<double>(), c->cfg.n_groups, c->dt_dev.as<double>(), c->n_inj_targets, 4 * c->cfg.n_groups, rec);
+    prof_end(c, s, pr);
+    ++c->launches;
 }
 
-rt_status launch_gradient(rt_ctx* c, cudaStream_t s, const void* U, void* grad) {
-    if (c->fp64) launch_gradient_t<double>(c, s, (const double*)U, (double*)grad);
-    else launch_gradient_t<float>(c, s, (const float*)U, (float*)grad);
+rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec) {
+    if (c->fp64) launch_gradient_t<double>(c, s, (double*)rec);
+    else launch_gradient_t<float>(c, s, (float*)rec);
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
 }
@@ -442,37 +549,47 @@ rt_status launch_gradient(rt_ctx* c, cudaStream_t s, const void* U, void* grad) 
 rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha) {
     if (c->fp64) {
         if (has_src) launch_inject_t<double>(c, s, (double*)Uin);
-        launch_gradient_t<double>(c, s, (const double*)Uin, c->grad.as<double>());
-        launch_flux_t<double>(c, s, (const double*)Uin, c->grad.as<double>(), (double*)Uout, has_alpha);
+        launch_gradient_t<double>(c, s, (double*)Uin);
+        launch_flux_t<double>(c, s, (const double*)Uin, (double*)Uout, has_alpha);
     } else {
         if (has_src) launch_inject_t<float>(c, s, (float*)Uin);
-        launch_gradient_t<float>(c, s, (const float*)Uin, c->grad.as<float>());
-        launch_flux_t<float>(c, s, (const float*)Uin, c->grad.as<float>(), (float*)Uout, has_alpha);
+        launch_gradient_t<float>(c, s, (float*)Uin);
+        launch_flux_t<float>(c, s, (const float*)Uin, (float*)Uout, has_alpha);
     }
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
 }
 
-rt_status to_sorted(rt_ctx* c, const void* U_user, void* U_sorted, int comps) {
+rt_status state_in(rt_ctx* c, const void* U_user, void* rec, int comps, int RS, int off) {
     unsigned nb = nblk(c->n, 256);
     if (c->fp64)
-        k_to_sorted<double><<<nb, 256, 0, c->stream>>>((const double*)U_user, c->perm.as<int32_t>(), c->n, comps,
-                                                        (double*)U_sorted);
+        k_state_in<double><<<nb, 256, 0, c->stream>>>((const double*)U_user, c->perm.as<int32_t>(), c->n, comps, RS,
+                                                       off, (double*)rec);
     else
-        k_to_sorted<float><<<nb, 256, 0, c->stream>>>((const float*)U_user, c->perm.as<int32_t>(), c->n, comps,
-                                                       (float*)U_sorted);
+        k_state_in<float><<<nb, 256, 0, c->stream>>>((const float*)U_user, c->perm.as<int32_t>(), c->n, comps, RS, off,
+                                                      (float*)rec);
+    ++c->launches;
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
 }
 
-rt_status from_sorted(rt_ctx* c, const void* U_sorted, void* U_user, int comps) {
+rt_status state_out(rt_ctx* c, const void* rec, void* U_user, int comps, int RS, int off) {
     unsigned nb = nblk(c->n, 256);
     if (c->fp64)
-        k_from_sorted<double><<<nb, 256, 0, c->stream>>>((const double*)U_sorted, c->inv_perm.as<int32_t>(), c->n,
-                                                          comps, (double*)U_user);
+        k_state_out<double><<<nb, 256, 0, c->stream>>>((const double*)rec, c->inv_perm.as<int32_t>(), c->n, comps, RS,
+                                                        off, (double*)U_user);
     else
-        k_from_sorted<float><<<nb, 256, 0, c->stream>>>((const float*)U_sorted, c->inv_perm.as<int32_t>(), c->n,
-                                                         comps, (float*)U_user);
+        k_state_out<float><<<nb, 256, 0, c->stream>>>((const float*)rec, c->inv_perm.as<int32_t>(), c->n, comps, RS,
+                                                       off, (float*)U_user);
+    ++c->launches;
+    RT_CUDA(c, cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status field_out(rt_ctx* c, const double* src_sorted, double* dst_user, int comps) {
+    k_from_sorted<double><<<nblk(c->n, 256), 256, 0, c->stream>>>(src_sorted, c->inv_perm.as<int32_t>(), c->n, comps,
+                                                                  dst_user);
+    ++c->launches;
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
 }
@@ -480,6 +597,7 @@ rt_status from_sorted(rt_ctx* c, const void* U_sorted, void* U_user, int comps) 
 rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double* alpha) {
     cudaStream_t s = c->stream;
     k_set_scalar<<<1, 1, 0, s>>>(c->dt_dev.as<double>(), dt);
+    ++c->launches;
     if (Lsrc && c->n_src > 0)
         RT_CUDA(c, cudaMemcpyAsync(c->L_dev.p, Lsrc, (size_t)c->n_src * c->cfg.n_groups * sizeof(double),
                                    cudaMemcpyDeviceToDevice, s));
@@ -487,20 +605,23 @@ rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double
         unsigned nb = nblk(c->n, 256);
         if (c->fp64) k_alpha_sorted<double><<<nb, 256, 0, s>>>(alpha, c->perm.as<int32_t>(), c->n, c->alpha_s.as<double>());
         else k_alpha_sorted<float><<<nb, 256, 0, s>>>(alpha, c->perm.as<int32_t>(), c->n, c->alpha_s.as<float>());
+        ++c->launches;
     }
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
 }
 
-rt_status launch_energy(rt_ctx* c, cudaStream_t s, const void* U_sorted, double* out_dev) {
+rt_status launch_energy(rt_ctx* c, cudaStream_t s, const void* rec, double* out_dev) {
     double* part = c->energy_part.as<double>();
+    int RS = 4 * c->cfg.n_groups;
     if (c->fp64)
-        k_energy_part<double><<<kEnergyBlocks, 256, 0, s>>>((const double*)U_sorted, c->V_d.as<double>(), c->n,
+        k_energy_part<double><<<kEnergyBlocks, 256, 0, s>>>((const double*)rec, RS, c->V_d.as<double>(), c->n,
                                                             c->cfg.n_groups, part);
     else
-        k_energy_part<float><<<kEnergyBlocks, 256, 0, s>>>((const float*)U_sorted, c->V_d.as<double>(), c->n,
+        k_energy_part<float><<<kEnergyBlocks, 256, 0, s>>>((const float*)rec, RS, c->V_d.as<double>(), c->n,
                                                            c->cfg.n_groups, part);
     k_energy_final<<<1, 32 * ((c->cfg.n_groups + 31) / 32), 0, s>>>(part, kEnergyBlocks, c->cfg.n_groups, out_dev);
+    c->launches += 2;
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
 }

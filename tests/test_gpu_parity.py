@@ -1,7 +1,7 @@
 """CUDA library vs the FP64 oracle, element by element, through the C interface.
 
 Tolerances (derived from the arithmetic, see the design notes):
-  FP64 path:  |gpu - oracle| <= 1e-12 (|oracle| + 1e-6 max|oracle of that component|) per particle
+  FP64 path:  |gpu - oracle| <= 1e-12 |oracle| + 1e-14 max|oracle of that component| per element
   FP32 path:  relative L1 per component and group <= 1e-5 per step; energy drift <= 1e-6
   neighbour sets: identical except pairs whose r^2 lies within 1e-12 H^2 of the threshold
 """
@@ -23,19 +23,18 @@ def _need_gpu():
         pytest.skip("no GPU")
 
 
-def fp64_close(g, o, tol=1e-12):
-    g = np.asarray(g).reshape(o.shape[0] if o.ndim > 1 else 1, -1) if False else np.asarray(g)
-    o = np.asarray(o)
-    if o.ndim == 1:
-        scale = np.abs(o).max()
-        bad = np.abs(g - o) > tol * (np.abs(o) + 1e-6 * scale)
-        return bad.sum(), np.max(np.abs(g - o) / (np.abs(o) + 1e-6 * scale + 1e-300))
+def fp64_close(g, o, rtol=1e-12, atol_scale=1e-14):
+    """Per element: |g - o| <= rtol |o| + atol_scale * max|o of that component|.
+    The absolute part is the rounding bound of a sum of ~50 neighbour terms of the
+    component's magnitude (50 x 1.1e-16 ~ 6e-15); returns (violations, worst ratio)."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
     o2 = o.reshape(-1, o.shape[-1])
     g2 = g.reshape(o2.shape)
     scale = np.abs(o2).max(axis=1, keepdims=True)
-    den = np.abs(o2) + 1e-6 * scale + 1e-300
-    r = np.abs(g2 - o2) / den
-    return int((r > tol).sum()), float(r.max())
+    tol = rtol * np.abs(o2) + atol_scale * scale + 1e-300
+    r = np.abs(g2 - o2) / tol
+    return int((r > 1).sum()), float(r.max())
 
 
 def rel_l1(g, o):
@@ -101,7 +100,7 @@ def test_gradients_fp64(cfg1):
     ref = og.gradients(U).reshape(2, 4, 3, w.n)
     g = t.gradients(t.state(U)).cpu().numpy()
     nbad, rmax = fp64_close(g, ref)
-    assert nbad == 0, rmax
+    assert nbad == 0, f"worst error / tolerance {rmax:.3e}"
     t.close()
 
 
@@ -114,8 +113,11 @@ def test_transport_fp64_config1(cfg1, dt_reading):
     t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64")
     U = t.state(w.U0)
     t.subcycle(U, w.n_steps, dt, t.luminosities(w.Lsrc))
-    nbad, rmax = fp64_close(U.cpu().numpy(), ref)
-    assert nbad == 0, f"max rel err {rmax:.3e}"
+    # with dt = 0.9 min h / c (three times the GLF positivity bound) the state grows ~600x in
+    # ten steps and rounding differences grow with it: 100x looser there
+    rtol = 1e-12 if dt_reading == "cfl" else 1e-10
+    nbad, rmax = fp64_close(U.cpu().numpy(), ref, rtol=rtol, atol_scale=rtol * 1e-2)
+    assert nbad == 0, f"worst error / tolerance {rmax:.3e}"
     t.close()
 
 
@@ -237,3 +239,28 @@ def test_errors_are_reported():
     with pytest.raises(RTError, match="RT_ERR_STATE"):
         rt_transport_step(ctx, 0.1, U)
     rt_destroy(ctx)
+
+
+def test_kernel_times_and_launch_counts():
+    """Profiling records event pairs around every pair-kernel launch, in plain steps and in
+    graph replays, and the launch counter counts graph kernel nodes."""
+    _need_gpu()
+    from paper_2302_12727_gb300 import rt_kernel_times, rt_set_profiling
+    w = W.config1()
+    t = Transport(w.x, w.m, w.xsrc, n_groups=1, precision="fp32")
+    rt_set_profiling(t.ctx, True)
+    L = t.luminosities(w.Lsrc)
+    U = t.state(w.U0)
+    n0 = t.diagnostics()["kernel_launches"]
+    t.subcycle(U, 4, 0.01, L)
+    kt = rt_kernel_times(t.ctx)
+    assert kt["flux"][1] == 4 and kt["gradient"][1] == 4 and kt["inject"][1] == 4
+    assert kt["flux"][0] > 0 and kt["gradient"][0] > 0
+    n1 = t.diagnostics()["kernel_launches"]
+    # to_sorted, set dt, 4 x (inject, gradient, flux), from_sorted
+    assert n1 - n0 == 1 + 1 + 12 + 1
+    t.step(U, 0.01, L)
+    kt = rt_kernel_times(t.ctx)
+    assert kt["flux"][1] == 1 and kt["flux"][0] > 0
+    rt_set_profiling(t.ctx, False)
+    t.close()
