@@ -202,7 +202,7 @@ def run_ours(args):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
         kt = rt_kernel_times(T.ctx)
-        kflux_ms += kt["flux"][0]
+        kflux_ms += kt["flux"][0] + kt["flux_gather"][0]     # both passes of the pair flux
         kflux_n += kt["flux"][1]
         kgrad_ms += kt["gradient"][0]
         kgrad_n += kt["gradient"][1]
@@ -249,7 +249,7 @@ def run_ours(args):
                        "sources": w.n_src, "pairs": P, "dt": dt, "dt_rule": f"{args.cfl} * min dx / c (Eq. rt-cfl)",
                        "precision": "fp32 fluxes/gradients, fp64 h/E_i/B_i/energy" if prec == "fp32" else "fp64",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
-            "roofline": {"bound": "alu", "kernel": "k_flux", "achieved": achieved, "peak": alu_peak,
+            "roofline": {"bound": "alu", "kernel": "k_flux + k_flux_gather", "achieved": achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
                          "traffic": traffic, "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                          "flops_per_launch": flux_flops, "avg_launch_ms": flux_avg_s * 1e3,

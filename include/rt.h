@@ -99,7 +99,8 @@ typedef struct {
 } rt_diag;
 
 /* Kernel kinds reported by rt_kernel_times. */
-enum { RT_KERNEL_INJECT = 0, RT_KERNEL_GRADIENT = 1, RT_KERNEL_FLUX = 2, RT_KERNEL_KINDS = 3 };
+enum { RT_KERNEL_INJECT = 0, RT_KERNEL_GRADIENT = 1, RT_KERNEL_FLUX = 2, RT_KERNEL_FLUX_GATHER = 3,
+       RT_KERNEL_KINDS = 4 };
 
 /* Create a context for n particles and n_src sources.  cuda_stream is a cudaStream_t
  * (NULL = legacy default stream).  Allocates the per-particle workspaces.  On failure
@@ -164,7 +165,7 @@ rt_status rt_diagnostics(rt_ctx* ctx, rt_diag* out);
 
 /* Per-kernel timing (tracing aid, no counterpart in the thesis).  With on = 1, later
  * rt_transport_step / rt_subcycle calls record CUDA events around every injection,
- * gradient and flux launch (inside the captured graph as event nodes).  Changing the
+ * gradient, pair-flux and flux-gather launch (inside the captured graph as event nodes).  Changing the
  * setting discards the captured graphs. */
 rt_status rt_set_profiling(rt_ctx* ctx, int32_t on);
 

@@ -23,7 +23,7 @@ EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_t
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
             "rt_kernel_times", "rt_last_error", "rt_destroy"]
 
-RT_KERNEL_INJECT, RT_KERNEL_GRADIENT, RT_KERNEL_FLUX, RT_KERNEL_KINDS = 0, 1, 2, 3
+RT_KERNEL_INJECT, RT_KERNEL_GRADIENT, RT_KERNEL_FLUX, RT_KERNEL_FLUX_GATHER, RT_KERNEL_KINDS = 0, 1, 2, 3, 4
 
 
 class rt_config(C.Structure):
@@ -185,7 +185,7 @@ def rt_kernel_times(ctx):
     ms = (C.c_double * RT_KERNEL_KINDS)()
     nl = (C.c_int64 * RT_KERNEL_KINDS)()
     _check(ctx, load_library().rt_kernel_times(ctx, ms, nl))
-    names = ("inject", "gradient", "flux")
+    names = ("inject", "gradient", "flux", "flux_gather")
     return {names[k]: (ms[k], nl[k]) for k in range(RT_KERNEL_KINDS)}
 
 

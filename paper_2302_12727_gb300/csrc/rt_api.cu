@@ -112,6 +112,9 @@ static rt_status ensure_state(rt_ctx* c) {
     RT_TRY(ensure(c, c->L_dev, (size_t)std::max<int64_t>(c->n_src, 1) * G * 8, "luminosities"));
     RT_TRY(ensure(c, c->dt_dev, 64, "dt"));
     RT_TRY(ensure(c, c->energy_part, (size_t)G * 512 * 8 + (size_t)G * 8, "energy"));
+    // per-pair flux slots of one group chunk (at most 4 groups)
+    const int gc = G < kMaxGC ? G : kMaxGC;
+    RT_TRY(ensure(c, c->pairbuf, (size_t)std::max<int64_t>(c->n_directed / 2, 1) * 4 * gc * tsize(c), "pair fluxes"));
     return RT_OK;
 }
 
@@ -432,7 +435,8 @@ void rt_destroy(rt_ctx* c) {
     destroy_prof(c->plain_prof);
     DevBuf* bufs[] = {&c->keys_in, &c->keys_out, &c->idx_in, &c->perm, &c->inv_perm, &c->cell_start, &c->cub_tmp,
                       &c->xs_d, &c->xq, &c->m_s, &c->h_d, &c->H2f, &c->omega_d, &c->V_d, &c->B_d, &c->cond_d, &c->pos_t,
-                      &c->geo_t, &c->omega_t, &c->counts, &c->row_off, &c->cols, &c->flags, &c->red_tmp,
+                      &c->geo_t, &c->omega_t, &c->counts, &c->row_off, &c->cols, &c->cols_tmp, &c->n_low,
+                      &c->n_up, &c->up_off, &c->low_slot, &c->pair_ends, &c->pairbuf, &c->flags, &c->red_tmp,
                       &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
                       &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,
                       &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->alpha_s,

@@ -389,6 +389,51 @@ __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint32_t* _
     if (!FILL) counts[p] = cnt;
 }
 
+// Rows sorted ascending are [lower neighbours j < i | upper neighbours j > i].  Each
+// unordered pair is the upper entry of its lower particle; slot(i, j) numbers those entries.
+__global__ void k_row_split(const int64_t* __restrict__ row_off, const int32_t* __restrict__ cols, int64_t n,
+                            int32_t* n_low, int32_t* n_up) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t lo = row_off[i], hi = row_off[i + 1];
+    int64_t b = lo, e = hi;
+    while (b < e) {
+        int64_t m = (b + e) >> 1;
+        if (cols[m] < (int32_t)i) b = m + 1; else e = m;
+    }
+    n_low[i] = (int32_t)(b - lo);
+    n_up[i] = (int32_t)(hi - b);
+}
+
+// the two particles of every pair slot
+__global__ void k_pair_ends(const int64_t* __restrict__ row_off, const int32_t* __restrict__ cols,
+                            const int32_t* __restrict__ n_low, const int64_t* __restrict__ up_off, int64_t n,
+                            int2* ends) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t e0 = row_off[i] + n_low[i], e1 = row_off[i + 1], slot = up_off[i];
+    for (int64_t e = e0; e < e1; ++e, ++slot) ends[slot] = make_int2((int)i, cols[e]);
+}
+
+// for every lower entry (i, k), k < i: the slot of the pair in k's upper list
+__global__ void k_low_slots(const int64_t* __restrict__ row_off, const int32_t* __restrict__ cols,
+                            const int32_t* __restrict__ n_low, const int64_t* __restrict__ up_off, int64_t n,
+                            int32_t* low_slot) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t r0 = row_off[i];
+    int64_t lbase = r0 - up_off[i];       // lower entries before row i
+    for (int e = 0; e < n_low[i]; ++e) {
+        int k = cols[r0 + e];
+        int64_t b = row_off[k] + n_low[k], hi = row_off[k + 1], t = hi;
+        while (b < t) {
+            int64_t m = (b + t) >> 1;
+            if (cols[m] < (int32_t)i) b = m + 1; else t = m;
+        }
+        low_slot[lbase + e] = (int32_t)(up_off[k] + (b - row_off[k] - n_low[k]));
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // a4: E_i = sum_j psi_j(x_i) d d^T, B_i = E_i^-1 (double), and the per-particle factors used
 // by the pair kernels.
@@ -995,11 +1040,41 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     if (P2 >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "more than 2^31 neighbour entries");
     c->n_directed = P2;
     RT_TRY(ensure(c, c->cols, std::max<int64_t>(P2, 1) * 4, "pair lists"));
+    RT_TRY(ensure(c, c->cols_tmp, std::max<int64_t>(P2, 1) * 4, "pair lists"));
     k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(),
                                                  c->H2f.as<float>(), n, pp, nullptr, c->row_off.as<int64_t>(),
-                                                 c->cols.as<int32_t>());
+                                                 c->cols_tmp.as<int32_t>());
     RT_CUDA(c, cudaGetLastError());
     c->launches += 3;   // count, fill, geometry below
+
+    // rows in ascending order, the lower / upper split and the slots of the pairs
+    {
+        size_t need = 0;
+        cub::DeviceSegmentedSort::SortKeys(nullptr, need, c->cols_tmp.as<int32_t>(), c->cols.as<int32_t>(), (int)P2,
+                                           (int)n, c->row_off.as<int64_t>(), c->row_off.as<int64_t>() + 1, st);
+        RT_TRY(ensure(c, c->cub_tmp, need + 256, "cub scratch"));
+        tb = c->cub_tmp.bytes;
+        RT_CUDA(c, cub::DeviceSegmentedSort::SortKeys(c->cub_tmp.p, tb, c->cols_tmp.as<int32_t>(), c->cols.as<int32_t>(),
+                                                      (int)P2, (int)n, c->row_off.as<int64_t>(),
+                                                      c->row_off.as<int64_t>() + 1, st));
+    }
+    RT_TRY(ensure(c, c->n_low, (n + 1) * 4, "pair split"));
+    RT_TRY(ensure(c, c->n_up, (n + 1) * 4, "pair split"));
+    RT_TRY(ensure(c, c->up_off, (n + 1) * 8, "pair split"));
+    RT_TRY(ensure(c, c->low_slot, std::max<int64_t>(P2 / 2, 1) * 4, "pair split"));
+    k_row_split<<<nblk(n, 256), 256, 0, st>>>(c->row_off.as<int64_t>(), c->cols.as<int32_t>(), n,
+                                               c->n_low.as<int32_t>(), c->n_up.as<int32_t>());
+    RT_CUDA(c, cudaMemsetAsync(c->n_up.as<int32_t>() + n, 0, 4, st));
+    tb = c->cub_tmp.bytes;
+    RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->n_up.as<int32_t>(), c->up_off.as<int64_t>(),
+                                             (int)(n + 1), st));
+    k_low_slots<<<nblk(n, 128), 128, 0, st>>>(c->row_off.as<int64_t>(), c->cols.as<int32_t>(), c->n_low.as<int32_t>(),
+                                               c->up_off.as<int64_t>(), n, c->low_slot.as<int32_t>());
+    RT_TRY(ensure(c, c->pair_ends, std::max<int64_t>(P2 / 2, 1) * 8, "pair split"));
+    k_pair_ends<<<nblk(n, 128), 128, 0, st>>>(c->row_off.as<int64_t>(), c->cols.as<int32_t>(), c->n_low.as<int32_t>(),
+                                               c->up_off.as<int64_t>(), n, c->pair_ends.as<int2>());
+    c->launches += 3;
+    RT_CUDA(c, cudaGetLastError());
 
     // a4: geometry
     if (c->fp64)

@@ -72,7 +72,9 @@ struct rt_ctx {
     rt::DevBuf h_d, omega_d, V_d, B_d, cond_d;           // double per particle
     rt::DevBuf H2f;                                     // float (kappa h)^2, pair-search prefilter
     rt::DevBuf pos_t, geo_t, omega_t;                   // working precision per particle (pair kernels)
-    rt::DevBuf counts, row_off, cols;                   // symmetric pair lists (CSR)
+    rt::DevBuf counts, row_off, cols, cols_tmp;         // symmetric pair lists (CSR), rows ascending
+    rt::DevBuf n_low, n_up, up_off, low_slot, pair_ends; // lower / upper split, pair slots
+    rt::DevBuf pairbuf;                                 // per-pair fluxes of one group chunk
     rt::DevBuf flags;                                   // int32 error flags + counters
     rt::DevBuf red_tmp;                                 // small reduction scratch (double)
     int64_t n_directed = 0;

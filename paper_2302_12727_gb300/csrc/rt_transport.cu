@@ -9,14 +9,12 @@
 // geometry record of 8 values {1/H, h, Bp (6)} with Bp = V^2 sigma / H^3 B so that
 // V_i psitilde_j(x_i) = Bp_i d w(q).  A neighbour's data is then a few 16-byte loads.
 //
-// Every pair kernel runs one thread per particle over its symmetric neighbour list.  Each
-// particle evaluates the flux of a pair with itself as the left state (the form of
-// Eq. transport-update-explicit).  Every operation on that path is either odd in the
-// separation d (so the other particle's evaluation, with -d, gives the exact negative) or
-// symmetric in the two particles; the three places where a fused multiply-add could break
-// that symmetry use explicitly rounded operations.  The exchange is therefore exactly
-// antisymmetric, and so exactly conservative, without atomics and without evaluating the
-// pair in a canonical orientation.
+// The gradient kernel runs one thread per particle over its symmetric neighbour list.  The
+// flux of each unordered pair (k < l) is evaluated once, by one thread with k as the left
+// state, and stored in the pair's slot; a second kernel lets every particle add the fluxes
+// of its upper pairs and subtract those of its lower pairs in a fixed order.  Both particles thus
+// apply the very same Phi_kl with opposite signs: the exchange is exactly antisymmetric,
+// and so exactly conservative, deterministic, and free of atomics.
 #include "rt_internal.cuh"
 
 namespace rt {
@@ -183,6 +181,11 @@ struct PairArgs {
     SepParams sp;
     int64_t n;
     const T* grad;            // [N][12G]
+    const int32_t* n_low;     // lower neighbours per row (rows ascending)
+    const int64_t* up_off;    // first pair slot of each row
+    const int32_t* low_slot;  // slot of each lower entry's pair
+    const int2* ends;         // (k, l) of each pair slot
+    int64_t n_pairs;
     int G;
 };
 
@@ -342,60 +345,93 @@ __device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T 
     for (int q = 0; q < 4; ++q) phi[q] = T(0.5) * (fL[q] + fR[q]) - diss * (R[q] - L[q]);
 }
 
+// Pass 1 of the flux: one thread per unordered pair (k, l), k < l, evaluates Phi_kl once with
+// k as the left state and stores it in the pair's slot.
 template <class T, int GC>
 __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ rec,
-                                              T* __restrict__ out, int g0) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+                                              T* __restrict__ pairbuf, int g0) {
+    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (slot >= a.n_pairs) return;
     constexpr int NC = 4 * GC;
     const T* tag = nullptr;
     const int G = a.G, RS = 4 * G;
+    const int2 kl = a.ends[slot];
+    const int64_t i = kl.x, j = kl.y;
     const Pos<T> pi = load_pos(tag, a.pos, i);
-    T gi8[8];
+    const Pos<T> pj = load_pos(tag, a.pos, j);
+    T gi8[8], gj8[8];
     vload<8>(a.geo + 8 * i, gi8);
+    vload<8>(a.geo + 8 * j, gj8);
+    T dx, dy, dz;
+    sep(a.sp, pi, pj, dx, dy, dz);              // d = x_l - x_k
+    // A_kl = (Bp_k w_k + Bp_l w_l) d  (Eq. HopkinsAij)
+    T r = sqrt_(dx * dx + dy * dy + dz * dz);
+    T si = spline_w_(r * gi8[0]);
+    T sj = spline_w_(r * gj8[0]);
+    T M[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) M[q] = gi8[2 + q] * si + gj8[2 + q] * sj;
+    T Ax, Ay, Az;
+    sym_mv(M, dx, dy, dz, Ax, Ay, Az);
+    T diss = T(0.5) * x.c * sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+    T ih = rcp_(gi8[1] + gj8[1]);
+    T wi = gi8[1] * ih, wj = gj8[1] * ih;
+    const T* ri = rec + i * RS;
+    const T* rj = rec + j * RS;
+    const T* qi = a.grad + i * 12 * G;
+    const T* qj = a.grad + j * 12 * G;
+    T out[NC];
+#pragma unroll
+    for (int g = 0; g < GC; ++g) {
+        const int gg = g0 + g;
+        T ui[4], uj[4], gri[12], grj[12];
+        vload<4>(ri + 4 * gg, ui);
+        vload<4>(rj + 4 * gg, uj);
+        vload<12>(qi + 12 * gg, gri);
+        vload<12>(qj + 12 * gg, grj);
+        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, &out[4 * g]);
+    }
+    vstore<NC>(pairbuf + slot * NC, out);
+}
+
+// Pass 2: particle i adds the fluxes of its own upper pairs (contiguous slots) and subtracts
+// those of its lower pairs (k < i, read from k's slots), in a fixed order; then
+// U_i(t + dt) = U_i - dt / V_i sum_l F_il . A_il, the sink and the fix-up.
+template <class T, int GC>
+__global__ void __launch_bounds__(128) k_flux_gather(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ rec,
+                                                     const T* __restrict__ pairbuf, T* __restrict__ out, int g0) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    constexpr int NC = 4 * GC;
+    const int RS = 4 * a.G;
     T acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = T(0);
-    const T* ri = rec + i * RS;
-    const T* qi = a.grad + i * 12 * G;
-    const int64_t e0 = a.row_off[i], e1 = a.row_off[i + 1];
-    for (int64_t e = e0; e < e1; ++e) {
-        const int j = a.cols[e];
-        const Pos<T> pj = load_pos(tag, a.pos, j);
-        T gj8[8];
-        vload<8>(a.geo + 8 * (int64_t)j, gj8);
-        T dx, dy, dz;
-        sep(a.sp, pi, pj, dx, dy, dz);              // d = x_j - x_i
-        // A_ij = (Bp_i w_i + Bp_j w_j) d  (Eq. HopkinsAij): the sum of the two products is
-        // rounded explicitly so that it is the same seen from either particle
-        T r = sqrt_(dx * dx + dy * dy + dz * dz);
-        T si = spline_w_(r * gi8[0]);
-        T sj = spline_w_(r * gj8[0]);
-        T M[6];
+    const int64_t r0 = a.row_off[i], s0 = a.up_off[i], s1 = a.up_off[i + 1];
+    for (int64_t sl = s0; sl < s1; ++sl) {
+        T phi[NC];
+        vload<NC>(pairbuf + sl * NC, phi);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) M[q] = add_rn(mul_rn(gi8[2 + q], si), mul_rn(gj8[2 + q], sj));
-        T Ax, Ay, Az;
-        sym_mv(M, dx, dy, dz, Ax, Ay, Az);
-        T diss = T(0.5) * x.c * sqrt_(Ax * Ax + Ay * Ay + Az * Az);
-        T ih = rcp_(gi8[1] + gj8[1]);
-        T wi = gi8[1] * ih, wj = gj8[1] * ih;
-        const T* rj = rec + (int64_t)j * RS;
-        const T* qj = a.grad + (int64_t)j * 12 * G;
-#pragma unroll
-        for (int g = 0; g < GC; ++g) {
-            const int gg = g0 + g;
-            T ui[4], uj[4], gri[12], grj[12];
-            vload<4>(ri + 4 * gg, ui);
-            vload<4>(rj + 4 * gg, uj);
-            vload<12>(qi + 12 * gg, gri);
-            vload<12>(qj + 12 * gg, grj);
-            T phi[4];
-            pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, phi);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[4 * g + q] += phi[q];
-        }
+        for (int c = 0; c < NC; ++c) acc[c] += phi[c];
     }
-    // U_i(t + dt) = U_i - dt / V_i sum_l F_il . A_il, then the sink and the fix-up
+    const int nl = a.n_low[i];
+    const int32_t* ls = a.low_slot + (r0 - s0);
+    int e = 0;
+    for (; e + 4 <= nl; e += 4) {     // four loads in flight, subtracted in order
+        T p0[NC], p1[NC], p2[NC], p3[NC];
+        vload<NC>(pairbuf + (int64_t)ls[e] * NC, p0);
+        vload<NC>(pairbuf + (int64_t)ls[e + 1] * NC, p1);
+        vload<NC>(pairbuf + (int64_t)ls[e + 2] * NC, p2);
+        vload<NC>(pairbuf + (int64_t)ls[e + 3] * NC, p3);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = (((acc[c] - p0[c]) - p1[c]) - p2[c]) - p3[c];
+    }
+    for (; e < nl; ++e) {
+        T phi[NC];
+        vload<NC>(pairbuf + (int64_t)ls[e] * NC, phi);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] -= phi[c];
+    }
     const T dt = (T)(*x.dt_dev);
     const T f = dt * a.omega[i];
     T sink = T(1);
@@ -466,6 +502,11 @@ static PairArgs<T> pair_args(rt_ctx* c) {
     a.sp.periodic = c->cfg.periodic;
     a.n = c->n;
     a.grad = c->grad_t.as<T>();
+    a.n_low = c->n_low.as<int32_t>();
+    a.up_off = c->up_off.as<int64_t>();
+    a.low_slot = c->low_slot.as<int32_t>();
+    a.ends = c->pair_ends.as<int2>();
+    a.n_pairs = c->n_directed / 2;
     a.G = c->cfg.n_groups;
     return a;
 }
@@ -478,7 +519,9 @@ static void set_carveouts() {
     done = true;
     const void* fs[] = {(const void*)k_gradient<T, 1>, (const void*)k_gradient<T, 2>, (const void*)k_gradient<T, 3>,
                         (const void*)k_gradient<T, 4>, (const void*)k_flux<T, 1>,     (const void*)k_flux<T, 2>,
-                        (const void*)k_flux<T, 3>,     (const void*)k_flux<T, 4>};
+                        (const void*)k_flux<T, 3>,     (const void*)k_flux<T, 4>,
+                        (const void*)k_flux_gather<T, 1>, (const void*)k_flux_gather<T, 2>,
+                        (const void*)k_flux_gather<T, 3>, (const void*)k_flux_gather<T, 4>};
     for (const void* f : fs) cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     (void)cudaGetLastError();
 }
@@ -514,17 +557,27 @@ static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool 
     x.clamp_count = reinterpret_cast<unsigned long long*>(c->flags.as<int>() + 8);
     const int G = c->cfg.n_groups;
     unsigned nb = nblk(c->n, 128);
+    T* pb = c->pairbuf.as<T>();
+    unsigned npb = nblk(std::max<int64_t>(a.n_pairs, 1), 128);
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
         int pr = prof_begin(c, s, RT_KERNEL_FLUX);
         switch (gc) {
-            case 1: k_flux<T, 1><<<nb, 128, 0, s>>>(a, x, rec, out, g0); break;
-            case 2: k_flux<T, 2><<<nb, 128, 0, s>>>(a, x, rec, out, g0); break;
-            case 3: k_flux<T, 3><<<nb, 128, 0, s>>>(a, x, rec, out, g0); break;
-            default: k_flux<T, 4><<<nb, 128, 0, s>>>(a, x, rec, out, g0); break;
+            case 1: k_flux<T, 1><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+            case 2: k_flux<T, 2><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+            case 3: k_flux<T, 3><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+            default: k_flux<T, 4><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
         }
         prof_end(c, s, pr);
-        ++c->launches;
+        pr = prof_begin(c, s, RT_KERNEL_FLUX_GATHER);
+        switch (gc) {
+            case 1: k_flux_gather<T, 1><<<nb, 128, 0, s>>>(a, x, rec, pb, out, g0); break;
+            case 2: k_flux_gather<T, 2><<<nb, 128, 0, s>>>(a, x, rec, pb, out, g0); break;
+            case 3: k_flux_gather<T, 3><<<nb, 128, 0, s>>>(a, x, rec, pb, out, g0); break;
+            default: k_flux_gather<T, 4><<<nb, 128, 0, s>>>(a, x, rec, pb, out, g0); break;
+        }
+        prof_end(c, s, pr);
+        c->launches += 2;
     }
 }
 

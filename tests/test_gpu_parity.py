@@ -256,9 +256,10 @@ def test_kernel_times_and_launch_counts():
     kt = rt_kernel_times(t.ctx)
     assert kt["flux"][1] == 4 and kt["gradient"][1] == 4 and kt["inject"][1] == 4
     assert kt["flux"][0] > 0 and kt["gradient"][0] > 0
+    assert kt["flux_gather"][1] == 4 and kt["flux_gather"][0] > 0
     n1 = t.diagnostics()["kernel_launches"]
-    # to_sorted, set dt, 4 x (inject, gradient, flux), from_sorted
-    assert n1 - n0 == 1 + 1 + 12 + 1
+    # state in, set dt, 4 x (inject, gradient, pair flux, flux gather), state out
+    assert n1 - n0 == 1 + 1 + 16 + 1
     t.step(U, 0.01, L)
     kt = rt_kernel_times(t.ctx)
     assert kt["flux"][1] == 1 and kt["flux"][0] > 0
