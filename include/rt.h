@@ -152,6 +152,30 @@ rt_status rt_adjoint(rt_ctx* ctx, int32_t n_sub, double dt, int32_t ckpt_every, 
  * E_tot_host [G] is HOST memory; the call synchronises the stream. */
 rt_status rt_energy(rt_ctx* ctx, const void* U_dev, double* E_tot_host);
 
+/* Total radiation energy per group, sum_i V_i E_i,g, without allocating anything and
+ * without a context.  The thesis has no counterpart: this entry point exists for callers
+ * that must not allocate device memory themselves or through the library, such as a host
+ * simulation code whose memory pool owns the whole GPU and forbids other allocations, or
+ * a monitoring hook that has to leave device memory untouched.
+ *   U_dev      [G][4][N] state in caller order (double for RT_FP64, float for RT_FP32_MIXED)
+ *   V_dev      [N] particle volumes in caller order (double), e.g. from rt_particle_fields
+ *   n          number of particles (>= 1)
+ *   n_groups   G, at most RT_ENERGY_STATIC_MAX_GROUPS
+ *   precision  RT_FP64 or RT_FP32_MIXED, the element type of U_dev
+ *   cuda_stream  stream of the two kernel launches (NULL = legacy default stream)
+ *   E_tot_dev  [G] DEVICE doubles receiving the sums, written asynchronously on the stream
+ * The partial sums live in a fixed 32 KiB array in the library's device memory, held on
+ * every GPU that loads the library until the process exits.  Each call overwrites the part
+ * of it that it reads, so nothing carries over from the previous call, but calls that
+ * overlap on the GPU share the array and race: order them on one stream.  The first call
+ * on a device looks up the array's device address with that device current; make that
+ * first call before any stream capture.  Returns RT_ERR_INVALID for NULL pointers, n < 1,
+ * n_groups outside [1, RT_ENERGY_STATIC_MAX_GROUPS] or an unknown
+ * precision, RT_ERR_CUDA if a CUDA call fails; there is no context, so no message. */
+#define RT_ENERGY_STATIC_MAX_GROUPS 16
+rt_status rt_energy_static(const void* U_dev, const double* V_dev, int64_t n, int32_t n_groups, int32_t precision,
+                           void* cuda_stream, double* E_tot_dev);
+
 /* Per-particle geometry in caller order (device pointers, each may be NULL):
  * h [N], omega [N], V [N], B [N][3][3] (double). */
 rt_status rt_particle_fields(rt_ctx* ctx, double* h_dev, double* omega_dev, double* V_dev, double* B_dev);

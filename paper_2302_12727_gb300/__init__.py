@@ -21,7 +21,9 @@ _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4
 
 EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
-            "rt_kernel_times", "rt_last_error", "rt_destroy"]
+            "rt_kernel_times", "rt_energy_static", "rt_last_error", "rt_destroy"]
+
+RT_ENERGY_STATIC_MAX_GROUPS = 16
 
 RT_KERNEL_INJECT, RT_KERNEL_GRADIENT, RT_KERNEL_FLUX, RT_KERNEL_FLUX_GATHER, RT_KERNEL_KINDS = 0, 1, 2, 3, 4
 
@@ -80,6 +82,7 @@ def load_library():
     lib.rt_diagnostics.argtypes = [vp, C.POINTER(rt_diag)]
     lib.rt_set_profiling.argtypes = [vp, C.c_int32]
     lib.rt_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    lib.rt_energy_static.argtypes = [vp, vp, i64, C.c_int32, C.c_int32, vp, vp]
     lib.rt_last_error.argtypes = [vp]
     lib.rt_last_error.restype = C.c_char_p
     lib.rt_destroy.argtypes = [vp]
@@ -187,6 +190,14 @@ def rt_kernel_times(ctx):
     _check(ctx, load_library().rt_kernel_times(ctx, ms, nl))
     names = ("inject", "gradient", "flux", "flux_gather")
     return {names[k]: (ms[k], nl[k]) for k in range(RT_KERNEL_KINDS)}
+
+
+def rt_energy_static(U, V, n, n_groups, precision, E_out, stream=None):
+    """Energy per group into the device array E_out without any allocation (no context)."""
+    st = load_library().rt_energy_static(_ptr(U), _ptr(V), int(n), int(n_groups), int(precision), stream,
+                                         _ptr(E_out))
+    if st != RT_OK:
+        raise RTError(st, "rt_energy_static rejected the call")
 
 
 def rt_last_error(ctx) -> str:
