@@ -440,8 +440,8 @@ void rt_destroy(rt_ctx* c) {
                       &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
                       &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,
                       &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->alpha_s,
-                      &c->L_dev, &c->dt_dev, &c->energy_part, &c->ck, &c->seg, &c->lam_a, &c->lam_b, &c->gbar,
-                      &c->lbar_part, &c->lbar_acc};
+                      &c->L_dev, &c->dt_dev, &c->energy_part, &c->ck, &c->seg, &c->lam_a, &c->lam_b, &c->adj_w,
+                      &c->adj_x, &c->adj_ub, &c->adj_gam, &c->adj_lam};
     for (DevBuf* b : bufs) free_buf(*b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;

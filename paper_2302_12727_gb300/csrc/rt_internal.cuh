@@ -87,7 +87,7 @@ struct rt_ctx {
     // state records (sorted order, working precision): U [N][4G] (double-buffered), grad U [N][12G]
     rt::DevBuf U_a, U_b, grad_t, alpha_s, L_dev, dt_dev, energy_part;
     // adjoint
-    rt::DevBuf ck, seg, lam_a, lam_b, gbar, lbar_part, lbar_acc;
+    rt::DevBuf ck, seg, lam_a, lam_b, adj_w, adj_x, adj_ub, adj_gam, adj_lam;
     int64_t ck_cap = 0, seg_cap = 0;
 
     // diagnostics
@@ -138,6 +138,7 @@ rt_status field_out(rt_ctx* c, const double* src_sorted, double* dst_user, int c
 rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double* alpha);
 rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha);
 rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec);
+rt_status launch_inject(rt_ctx* c, cudaStream_t s, void* rec);
 rt_status launch_energy(rt_ctx* c, cudaStream_t s, const void* rec, double* out_dev);
 rt_status run_adjoint(rt_ctx* c, int n_sub, int ckpt_every, bool has_src, bool has_alpha, const void* U0_sorted,
                       const void* lam_final_sorted, void* lam0_sorted, double* dLdL_dev);

@@ -15,187 +15,11 @@
 // of its upper pairs and subtract those of its lower pairs in a fixed order.  Both particles thus
 // apply the very same Phi_kl with opposite signs: the exchange is exactly antisymmetric,
 // and so exactly conservative, deterministic, and free of atomics.
-#include "rt_internal.cuh"
+#include "rt_pair.cuh"
 
 namespace rt {
 
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
-
-// ------------------------------------------------------------------------------------
-// precision-specific primitives: IEEE in double, approximate reciprocal / square root in
-// float (relative error ~1e-7, far inside the float path's tolerance)
-__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
-__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-__device__ __forceinline__ float rcp_(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float sqrt_(float x) {
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-// explicitly rounded operations, so that the compiler cannot fuse them differently
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
-__device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
-__device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
-__device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
-
-// cubic-spline shape without branches: (1-q)_+^3 - 4 (1/2-q)_+^3 (Eq. cubic-spline-kernel)
-template <class T>
-__device__ __forceinline__ T spline_w_(T q) {
-    T a = fmax_(T(1) - q, T(0));
-    T b = fmax_(T(0.5) - q, T(0));
-    return a * a * a - T(4) * (b * b * b);
-}
-
-// minmod of Eq. rt-minmod as selects: both positive -> min, both negative -> max, else 0
-template <class T>
-__device__ __forceinline__ T minmod_(T a, T b) {
-    T lo = fmin_(a, b), hi = fmax_(a, b);
-    return lo > T(0) ? lo : (hi < T(0) ? hi : T(0));
-}
-
-// M1 flux of one group contracted with A, branch-free form of m1_dot (Eq. eddington-group):
-// (F . A, c^2 E [(1-chi)/2 A + b(u) u/|F|^2 (F . A) F]), zero pressure for E <= 0.
-template <class T>
-__device__ __forceinline__ void m1_dot_(T E, T Fx, T Fy, T Fz, T Ax, T Ay, T Az, T c, T& oE, T& oFx, T& oFy,
-                                        T& oFz) {
-    T FA = Fx * Ax + Fy * Ay + Fz * Az;
-    oE = FA;
-    bool pos = E > T(0);
-    T Es = pos ? E : T(1);
-    T F2 = Fx * Fx + Fy * Fy + Fz * Fz;
-    T icE = rcp_(c * Es);
-    T icE2 = icE * icE;
-    T u = F2 * icE2;
-    bool clip = u > T(1);
-    T sc = clip ? rcp_(F2) : icE2;
-    u = clip ? T(1) : u;
-    T s = sqrt_(T(4) - T(3) * u);
-    T den = rcp_(T(5) + T(2) * s);
-    T a_iso = (T(1) + s - T(2) * u) * den;
-    T b = T(6) * (T(1) + rcp_(T(4) + T(2) * s)) * den;
-    T cE = pos ? c * c * E : T(0);
-    T t = b * FA * sc;
-    oFx = cE * (a_iso * Ax + t * Fx);
-    oFy = cE * (a_iso * Ay + t * Fy);
-    oFz = cE * (a_iso * Az + t * Fz);
-}
-
-// ------------------------------------------------------------------------------------
-// positions
-template <class T>
-struct Pos;
-template <>
-struct Pos<float> {
-    uint32_t a, b, c;
-};
-template <>
-struct Pos<double> {
-    double a, b, c;
-};
-
-__device__ __forceinline__ Pos<float> load_pos(const float*, const void* P, int64_t i) {
-    uint4 v = reinterpret_cast<const uint4*>(P)[i];
-    return {v.x, v.y, v.z};
-}
-__device__ __forceinline__ Pos<double> load_pos(const double*, const void* P, int64_t i) {
-    const double2* p = reinterpret_cast<const double2*>(P) + 2 * i;
-    double2 u = p[0], v = p[1];
-    return {u.x, u.y, v.x};
-}
-
-struct SepParams {
-    float s0, s1, s2;          // float path: fixed-point unit
-    double b0, b1, b2;         // double path: box
-    int periodic;
-};
-
-__device__ __forceinline__ double wrap_d(double v, double box, int periodic) {
-    if (periodic) {
-        double h = 0.5 * box;
-        v = v > h ? v - box : (v < -h ? v + box : v);
-    }
-    return v;
-}
-
-// d = x_to - x_from
-__device__ __forceinline__ void sep(const SepParams& s, const Pos<float>& f, const Pos<float>& t, float& dx, float& dy,
-                                    float& dz) {
-    dx = (float)(int32_t)(t.a - f.a) * s.s0;
-    dy = (float)(int32_t)(t.b - f.b) * s.s1;
-    dz = (float)(int32_t)(t.c - f.c) * s.s2;
-}
-__device__ __forceinline__ void sep(const SepParams& s, const Pos<double>& f, const Pos<double>& t, double& dx,
-                                    double& dy, double& dz) {
-    dx = wrap_d(t.a - f.a, s.b0, s.periodic);
-    dy = wrap_d(t.b - f.b, s.b1, s.periodic);
-    dz = wrap_d(t.c - f.c, s.b2, s.periodic);
-}
-
-// vector loads of K consecutive values (16-byte aligned)
-template <int K>
-__device__ __forceinline__ void vload(const float* __restrict__ p, float* o) {
-    static_assert(K % 4 == 0, "K multiple of 4");
-#pragma unroll
-    for (int k = 0; k < K; k += 4) {
-        float4 v = *reinterpret_cast<const float4*>(p + k);
-        o[k] = v.x; o[k + 1] = v.y; o[k + 2] = v.z; o[k + 3] = v.w;
-    }
-}
-template <int K>
-__device__ __forceinline__ void vload(const double* __restrict__ p, double* o) {
-    static_assert(K % 2 == 0, "K even");
-#pragma unroll
-    for (int k = 0; k < K; k += 2) {
-        double2 v = *reinterpret_cast<const double2*>(p + k);
-        o[k] = v.x; o[k + 1] = v.y;
-    }
-}
-template <int K>
-__device__ __forceinline__ void vstore(float* p, const float* o) {
-#pragma unroll
-    for (int k = 0; k < K; k += 4) *reinterpret_cast<float4*>(p + k) = make_float4(o[k], o[k + 1], o[k + 2], o[k + 3]);
-}
-template <int K>
-__device__ __forceinline__ void vstore(double* p, const double* o) {
-#pragma unroll
-    for (int k = 0; k < K; k += 2) *reinterpret_cast<double2*>(p + k) = make_double2(o[k], o[k + 1]);
-}
-
-template <class T>
-struct PairArgs {
-    const void* pos;          // uint4[N] or double[4N]
-    const T* geo;             // [N][8] {1/H, h, Bp xx yy zz xy xz yz}
-    const T* omega;           // [N]
-    const int64_t* row_off;
-    const int32_t* cols;
-    SepParams sp;
-    int64_t n;
-    const T* grad;            // [N][12G]
-    const int32_t* n_low;     // lower neighbours per row (rows ascending)
-    const int64_t* up_off;    // first pair slot of each row
-    const int32_t* low_slot;  // slot of each lower entry's pair
-    const int2* ends;         // (k, l) of each pair slot
-    int64_t n_pairs;
-    int G;
-};
-
-// symmetric 3x3 (xx, yy, zz, xy, xz, yz) times vector
-template <class T>
-__device__ __forceinline__ void sym_mv(const T M[6], T x, T y, T z, T& ox, T& oy, T& oz) {
-    ox = M[0] * x + M[3] * y + M[4] * z;
-    oy = M[3] * x + M[1] * y + M[5] * z;
-    oz = M[4] * x + M[5] * y + M[2] * z;
-}
 
 // ------------------------------------------------------------------------------------
 // caller order <-> cell-sorted records
@@ -313,37 +137,6 @@ __global__ void __launch_bounds__(128) k_gradient(PairArgs<T> a, const T* __rest
 
 // ------------------------------------------------------------------------------------
 // a7 + a8: pair fluxes, explicit update, grey sink, optional fix-up, groups [g0, g0 + GC).
-template <class T>
-struct FluxExtra {
-    const T* alpha;                 // sorted, or null
-    const double* dt_dev;
-    T c;
-    int clamp;
-    unsigned long long* clamp_count;
-};
-
-// Flux of pair (k, l) for one group, k = this particle as the left state: face states
-// (Eq. rt-riemann-problem with s = minmod(grad Q_k . d, grad Q_l . d)), M1 fluxes
-// (Eq. eddington-group), GLF (Eq. riemann-GLF).  The face states use explicit fma so that
-// the evaluation by l (with -d and the roles swapped) gives exactly -phi.
-template <class T>
-__device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T gk[12], const T gl[12], T dx, T dy,
-                                          T dz, T wk, T wl, T Ax, T Ay, T Az, T diss, T c, T phi[4]) {
-    T L[4], R[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        T dqk = gk[3 * q] * dx + gk[3 * q + 1] * dy + gk[3 * q + 2] * dz;
-        T dql = gl[3 * q] * dx + gl[3 * q + 1] * dy + gl[3 * q + 2] * dz;
-        T s = minmod_(dqk, dql);
-        L[q] = fma_rn(wk, s, uk[q]);
-        R[q] = fma_rn(-wl, s, ul[q]);
-    }
-    T fL[4], fR[4];
-    m1_dot_(L[0], L[1], L[2], L[3], Ax, Ay, Az, c, fL[0], fL[1], fL[2], fL[3]);
-    m1_dot_(R[0], R[1], R[2], R[3], Ax, Ay, Az, c, fR[0], fR[1], fR[2], fR[3]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) phi[q] = T(0.5) * (fL[q] + fR[q]) - diss * (R[q] - L[q]);
-}
 
 // Pass 1 of the flux: one thread per unordered pair (k, l), k < l, evaluates Phi_kl once with
 // k as the left state and stores it in the pair's slot.
@@ -484,33 +277,6 @@ __global__ void k_energy_final(const double* __restrict__ part, int nb, int G, d
 }
 
 // ------------------------------------------------------------------------------------
-template <class T>
-static PairArgs<T> pair_args(rt_ctx* c) {
-    PairArgs<T> a;
-    a.pos = c->pos_t.p;
-    a.geo = c->geo_t.as<T>();
-    a.omega = c->omega_t.as<T>();
-    a.row_off = c->row_off.as<int64_t>();
-    a.cols = c->cols.as<int32_t>();
-    double units = c->cfg.periodic ? 4294967296.0 : 2147483648.0;
-    a.sp.s0 = (float)(c->cfg.box[0] / units);
-    a.sp.s1 = (float)(c->cfg.box[1] / units);
-    a.sp.s2 = (float)(c->cfg.box[2] / units);
-    a.sp.b0 = c->cfg.box[0];
-    a.sp.b1 = c->cfg.box[1];
-    a.sp.b2 = c->cfg.box[2];
-    a.sp.periodic = c->cfg.periodic;
-    a.n = c->n;
-    a.grad = c->grad_t.as<T>();
-    a.n_low = c->n_low.as<int32_t>();
-    a.up_off = c->up_off.as<int64_t>();
-    a.low_slot = c->low_slot.as<int32_t>();
-    a.ends = c->pair_ends.as<int2>();
-    a.n_pairs = c->n_directed / 2;
-    a.G = c->cfg.n_groups;
-    return a;
-}
-
 // the pair kernels use no shared memory: give the whole unified L1 to the cache
 template <class T>
 static void set_carveouts() {
@@ -590,6 +356,13 @@ static void launch_inject_t(rt_ctx* c, cudaStream_t s, T* rec) {
         c->L_dev.as<double>(), c->cfg.n_groups, c->dt_dev.as<double>(), c->n_inj_targets, 4 * c->cfg.n_groups, rec);
     prof_end(c, s, pr);
     ++c->launches;
+}
+
+rt_status launch_inject(rt_ctx* c, cudaStream_t s, void* rec) {
+    if (c->fp64) launch_inject_t<double>(c, s, (double*)rec);
+    else launch_inject_t<float>(c, s, (float*)rec);
+    RT_CUDA(c, cudaGetLastError());
+    return RT_OK;
 }
 
 rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec) {
