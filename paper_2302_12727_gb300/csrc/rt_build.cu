@@ -220,8 +220,8 @@ struct HParams {
 __device__ __forceinline__ float fsep(uint32_t a, uint32_t b, float scale) { return (float)(int32_t)(a - b) * scale; }
 
 __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
-                          HParams hp, double* h_out, double* omega_out, float* H2f_out, unsigned long long* hminmax,
-                          int* flags) {
+                          HParams hp, const double* __restrict__ h_prev, const int32_t* __restrict__ perm,
+                          double* h_out, double* omega_out, float* H2f_out, unsigned long long* hminmax, int* flags) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double hd = 0.0, om_d = 0.0;
     bool active = p < n;
@@ -232,11 +232,18 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
         double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
         float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
 
-        // first guess from the particle count of the surrounding 27 cells
-        int cnt = count_27(g, cell_coord(px, g.inv_cell[0], g.nc[0]), cell_coord(py, g.inv_cell[1], g.nc[1]),
-                           cell_coord(pz, g.inv_cell[2], g.nc[2]));
-        double vol27 = 27.0 * g.cell[0] * g.cell[1] * g.cell[2];
-        float h = cnt > 1 ? (float)(hp.eta * cbrt(vol27 / (double)cnt)) : (float)hp.h0;
+        // first guess: the particle's h of the previous call (particles move little between
+        // calls), else the particle count of the surrounding 27 cells
+        float h;
+        if (h_prev) {
+            h = (float)h_prev[perm[p]];
+        } else {
+            int cnt = count_27(g, cell_coord(px, g.inv_cell[0], g.nc[0]), cell_coord(py, g.inv_cell[1], g.nc[1]),
+                               cell_coord(pz, g.inv_cell[2], g.nc[2]));
+            double vol27 = 27.0 * g.cell[0] * g.cell[1] * g.cell[2];
+            h = cnt > 1 ? (float)(hp.eta * cbrt(vol27 / (double)cnt)) : (float)hp.h0;
+        }
+        if (!(h > 0.f) || !(h < (float)hp.h_cap)) h = (float)hp.h0;
 
         // ---- float phase: Newton on float separations, omega summed in double
         float lo = 0.f, hi = INFINITY;
@@ -960,6 +967,8 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
 
     int* flags = c->flags.as<int>();
     RT_CUDA(c, cudaMemsetAsync(flags, 0, 64, st));
+    const bool warm = c->has_h_prev;
+    c->has_h_prev = false;       // set again only when this call succeeds
     // reductions: [0] min h, [1] max h, [2] max cond, [3] min V (bit patterns of positive doubles)
     unsigned long long* red = reinterpret_cast<unsigned long long*>(c->red_tmp.p);
     RT_CUDA(c, cudaMemsetAsync(red, 0, 32, st));
@@ -1007,6 +1016,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     hp.tol32 = (float)std::max(cfg.h_tol, 2e-6);
     hp.refine64 = c->fp64 ? 1 : 0;
     k_h_solve<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp,
+                                             warm ? c->h_prev.as<double>() : nullptr, c->perm.as<int32_t>(),
                                              c->h_d.as<double>(), c->omega_d.as<double>(), c->H2f.as<float>(), red,
                                              flags);
     RT_CUDA(c, cudaGetLastError());
@@ -1180,6 +1190,10 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     RT_CUDA(c, cudaStreamSynchronize(st));
     c->diag.cond_max = cv[0];
     c->diag.dx_min = std::cbrt(cv[1] / (4.0 * M_PI / 3.0));
+    // keep h in caller order as the first guess of the next call
+    RT_TRY(ensure(c, c->h_prev, n * 8, "h"));
+    RT_TRY(field_out(c, c->h_d.as<double>(), c->h_prev.as<double>(), 1));
+    c->has_h_prev = true;
     return RT_OK;
 }
 

@@ -71,6 +71,8 @@ struct rt_ctx {
     rt::DevBuf xs_d, xq, m_s;
     rt::DevBuf h_d, omega_d, V_d, B_d, cond_d;           // double per particle
     rt::DevBuf H2f;                                     // float (kappa h)^2, pair-search prefilter
+    rt::DevBuf h_prev;                                  // h of the last call, caller order (first guess)
+    bool has_h_prev = false;
     rt::DevBuf pos_t, geo_t, omega_t;                   // working precision per particle (pair kernels)
     rt::DevBuf counts, row_off, cols, cols_tmp;         // symmetric pair lists (CSR), rows ascending
     rt::DevBuf n_low, n_up, up_off, low_slot, pair_ends; // lower / upper split, pair slots
