@@ -143,6 +143,22 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(t, ws, device):
+    """The slowest rank's time (all ranks get it)."""
+    if ws == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(units_per_rank, ws, t_max):
+    """Whole-job throughput of independent replicas: every rank's units over the slowest time."""
+    return units_per_rank * ws / t_max
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -214,13 +230,9 @@ def run_ours(args):
     clocks = sampler.stop()
     launches = T.diagnostics()["kernel_launches"] - launches0
     # U.copy_ and flush.fill_ are torch's kernels, outside the per-step events
-    t_total = sum(times) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = max_over_ranks(sum(times) / 1e3, ws, dev)
     units_rank = P * G * n_sub * args.steps
-    value = units_rank * ws / t_total
+    value = job_value(units_rank, ws, t_total)
     ms_step = t_total / args.steps * 1e3
 
     out = None

@@ -98,7 +98,7 @@ def lognormal_field_particles(n: int, grid: int, sigma_ln: float, rng: np.random
     nz = k2 > 0
     amp[nz] = k2[nz] ** (-0.5)          # sqrt(P(k)) with P ~ k^-2
     noise = rng.standard_normal(k2.shape) + 1j * rng.standard_normal(k2.shape)
-    delta = np.fft.irfftn(noise * amp, s=(grid, grid, grid))
+    delta = np.fft.irfftn(noise * amp, s=(grid, grid, grid), axes=(0, 1, 2))
     delta *= sigma_ln / delta.std()
     rho = np.exp(delta - 0.5 * sigma_ln ** 2).ravel()
     counts = rng.multinomial(n, rho / rho.sum())

@@ -265,3 +265,63 @@ def test_kernel_times_and_launch_counts():
     assert kt["flux"][1] == 1 and kt["flux"][0] > 0
     rt_set_profiling(t.ctx, False)
     t.close()
+
+
+def test_failures_are_reported_not_raised_on_the_gpu():
+    """Host-made faults come back as status codes: NaN position, a flat (coplanar) particle
+    set whose E_i is singular, an iteration cap too small for the h solve, bad arguments."""
+    _need_gpu()
+    from paper_2302_12727_gb300 import make_config, rt_create, rt_destroy, rt_subcycle
+    rng = np.random.default_rng(3)
+    x = W.jittered_lattice(8, 0.2, rng)
+    x[1, 7] = np.nan
+    with pytest.raises(RTError, match="RT_ERR_INVALID"):
+        Transport(x, None, None, n_groups=1)
+    # all particles in the plane z = 0.5: E_i has no zz component
+    g = (np.arange(24) + 0.5) / 24
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    flat = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, 0.5)])
+    with pytest.raises(RTError, match="RT_ERR_GEOMETRY"):
+        Transport(flat, None, None, n_groups=1)
+    with pytest.raises(RTError, match="RT_ERR_NOCONV"):
+        Transport(W.jittered_lattice(8, 0.2, rng), None, None, n_groups=1, h_max_iter=1)
+    with pytest.raises(RTError, match="RT_ERR_INVALID"):
+        rt_create(make_config(0), 100, 0)
+    t = Transport(W.jittered_lattice(8, 0.2, rng), None, None, n_groups=1)
+    U = t.state(np.ones((1, 4, t.n)))
+    with pytest.raises(RTError, match="RT_ERR_INVALID"):
+        rt_subcycle(t.ctx, 2, -1.0, U)
+    # the context stays usable after a rejected call
+    t.subcycle(U, 2, 0.001)
+    assert np.isfinite(U.cpu().numpy()).all()
+    t.close()
+
+
+@pytest.mark.parametrize("cfg", [2, 4])
+def test_full_size_per_step_parity(cfg):
+    """The benchmark workload (config 2, 262,144 particles, 3 groups, source, beam, grey sink)
+    and config 4 (2,097,152 particles, lognormal density, 4 groups, 64 sources), every
+    particle: the FP32 path's error of one step from the oracle's state, over the first
+    steps, relative L1 <= 1e-5 per component and group."""
+    _need_gpu()
+    w = W.CONFIGS[cfg]()
+    nsteps = 2 if cfg == 2 else 1
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
+    dt = cfl_dt(o)
+    alpha = w.kappa * w.m * o.omega if w.kappa else None
+    t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp32", c_red=w.c_red)
+    L = t.luminosities(w.Lsrc)
+    al = t.alpha(alpha)
+    Uo = w.U0.copy()
+    for k in range(nsteps):
+        Ug = t.state(Uo)
+        t.step(Ug, dt, L, al)
+        Uo, _ = o.run(Uo, 1, dt, w.Lsrc, alpha)
+        err = rel_l1(Ug.cpu().numpy().astype(np.float64), Uo)
+        nz = np.abs(Uo.reshape(-1, w.n)).sum(1) > 0
+        assert err[nz].max() <= 1e-5, (k, err)
+    # energy of one graph-replayed run against the oracle's
+    Ug = t.state(w.U0)
+    t.subcycle(Ug, nsteps, dt, L, al)
+    np.testing.assert_allclose(t.energy(Ug), o.energy(Uo), rtol=1e-6)
+    t.close()
