@@ -96,6 +96,10 @@ typedef struct {
     int64_t kernel_launches;  /* cumulative launches of the library's own kernels (graph
                                  replays count every kernel node; library sorts and scans
                                  that the build calls are not counted) */
+    int32_t pair_build;       /* pair-list build of the last rt_neighbours: 0 = every particle
+                                 searched to max(H_i, H_max); 1 = own supports, then sorted and
+                                 de-duplicated with their transposes (chosen when the h range is
+                                 wide); both give the same lists */
 } rt_diag;
 
 /* Kernel kinds reported by rt_kernel_times. */

@@ -39,7 +39,8 @@ class rt_diag(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("n_directed", C.c_int64), ("n_injection", C.c_int64),
                 ("n_ill_conditioned", C.c_int64), ("cond_max", C.c_double), ("h_min", C.c_double),
                 ("h_max", C.c_double), ("dx_min", C.c_double), ("clamp_events", C.c_int64),
-                ("grid", C.c_int32 * 3), ("threads_per_particle", C.c_int32), ("kernel_launches", C.c_int64)]
+                ("grid", C.c_int32 * 3), ("threads_per_particle", C.c_int32), ("kernel_launches", C.c_int64),
+                ("pair_build", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -276,10 +276,18 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
             float fp = 1.f + (eta / 3.f) / (cb * om) * dom;
             if (f < 0.f) lo = h; else hi = h;
             float step = f / fp;
+            // converged: residual at the rounding floor, a tiny Newton step, or a collapsed
+            // bracket (where f' is small, rounding alone keeps the step above tolerance)
+            if (fabsf(f) <= 1e-6f * h || (fp > 0.f && fabsf(step) <= hp.tol32 * h) ||
+                (hi - lo) <= hp.tol32 * h) {
+                ok = true;
+                break;
+            }
             float hn = h - step;
-            if (!(fabsf(step) > hp.tol32 * h)) { ok = true; break; }
-            if (!(hn > lo && hn < hi) || !(fp > 0.f)) hn = isinf(hi) ? 2.f * h : 0.5f * (lo + hi);
+            // safeguarded Newton; plain bisection of the bracket after 24 Newton steps
+            if (it >= 24 || !(hn > lo && hn < hi) || !(fp > 0.f)) hn = isinf(hi) ? 2.f * h : 0.5f * (lo + hi);
             if (hn > (float)hp.h_cap) hn = (float)hp.h_cap;
+            if (hn == h) break;       // no progress possible: reported as not converged
             h = hn;
         }
         if (!ok) atomicExch(&flags[F_NOCONV], 1);
@@ -294,7 +302,7 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
             double lod = 0.0, hid = INFINITY;
             const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
             bool okd = false, last = false;
-            for (int it = 0; it < 16; ++it) {
+            for (int it = 0; it < 60; ++it) {
                 double H = kKappa * hd;
                 double iH = 1.0 / H;
                 double H2 = H * H;
@@ -327,10 +335,12 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
                 if (f < 0.0) lod = hd; else hid = hd;
                 double step = f / fp;
                 // once the Newton step is tiny the next iterate is exact to rounding: take it and
-                // evaluate omega there once more
-                if (fabs(step) <= 1e-11 * hd) last = true;
+                // evaluate omega there once more; a residual at the rounding floor or a
+                // collapsed bracket ends the iteration at the current h
+                if (fabs(f) <= 1e-15 * hd || (hid - lod) <= 1e-14 * hd) { okd = true; break; }
+                if (fp > 0.0 && fabs(step) <= 1e-11 * hd) last = true;
                 double hn = hd - step;
-                if (!last && (!(hn > lod && hn < hid) || !(fp > 0.0)))
+                if (!last && (it >= 12 || !(hn > lod && hn < hid) || !(fp > 0.0)))
                     hn = isinf(hid) ? 1.01 * hd : 0.5 * (lod + hid);
                 hd = hn;
             }
@@ -343,9 +353,13 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
     }
     double mn = active ? hd : INFINITY, mx = active ? hd : 0.0;
     warp_minmax(mn, mx);
+    // sum of H^3 (only steers the choice of the pair-search method, never a result)
+    double h3 = active ? (kKappa * hd) * (kKappa * hd) * (kKappa * hd) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) h3 += __shfl_xor_sync(0xffffffffu, h3, o);
     if ((threadIdx.x & 31) == 0 && mx > 0.0) {
         atomic_min_pos(&hminmax[0], mn);
         atomic_max_pos(&hminmax[1], mx);
+        atomicAdd(reinterpret_cast<double*>(&hminmax[4]), h3);
     }
 }
 
@@ -439,6 +453,58 @@ __global__ void k_low_slots(const int64_t* __restrict__ row_off, const int32_t* 
         }
         low_slot[lbase + e] = (int32_t)(up_off[k] + (b - row_off[k] - n_low[k]));
     }
+}
+
+// Pair search for strongly varying h: each particle lists only { j : r_ij < H_i } (its own
+// support) and emits the entry and its transpose as 64-bit keys (row << 32 | col); sorting
+// and removing duplicates gives the same symmetric lists, rows ascending, without any
+// particle searching out to the largest H of the set.
+template <bool FILL>
+__global__ void k_pairs_gather(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+                               const double* __restrict__ h, const float* __restrict__ H2f, int64_t n, PairParams pp,
+                               int32_t* counts, const int64_t* __restrict__ off, uint64_t* keys) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+    const float H2i = H2f[p];
+    int cnt = 0;
+    int64_t base = FILL ? off[p] : 0;
+    for_each_candidate(g, (float)px, (float)py, (float)pz, sqrtf(H2i) * 1.0001f, [&](int j) {
+        if (j == p) return;
+        float dx = fsep(xq[j], qx, pp.scale[0]);
+        float dy = fsep(xq[n + j], qy, pp.scale[1]);
+        float dz = fsep(xq[2 * n + j], qz, pp.scale[2]);
+        float r2f = dx * dx + dy * dy + dz * dz;
+        bool in;
+        if (r2f < H2i * (1.f - 1e-5f)) in = true;
+        else if (r2f > H2i * (1.f + 1e-5f)) in = false;
+        else {
+            double Hi = __dmul_rn(kKappa, h[p]);
+            double ex = sep_exact(xs[j], px, g.box[0], g.periodic);
+            double ey = sep_exact(xs[n + j], py, g.box[1], g.periodic);
+            double ez = sep_exact(xs[2 * n + j], pz, g.box[2], g.periodic);
+            in = norm2_exact(ex, ey, ez) < __dmul_rn(Hi, Hi);
+        }
+        if (in) {
+            if (FILL) {
+                keys[2 * (base + cnt)] = ((uint64_t)p << 32) | (uint32_t)j;
+                keys[2 * (base + cnt) + 1] = ((uint64_t)(uint32_t)j << 32) | (uint64_t)p;
+            }
+            ++cnt;
+        }
+    });
+    if (!FILL) counts[p] = cnt;
+}
+
+// unique sorted keys -> columns, and the number of entries of every row
+__global__ void k_keys_to_csr(const uint64_t* __restrict__ ukeys, const int64_t* __restrict__ nuniq, int32_t* cols,
+                              int32_t* counts) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= *nuniq) return;
+    uint64_t k = ukeys[e];
+    cols[e] = (int32_t)(uint32_t)(k & 0xffffffffu);
+    atomicAdd(&counts[(int64_t)(k >> 32)], 1);
 }
 
 // ------------------------------------------------------------------------------------
@@ -971,7 +1037,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     c->has_h_prev = false;       // set again only when this call succeeds
     // reductions: [0] min h, [1] max h, [2] max cond, [3] min V (bit patterns of positive doubles)
     unsigned long long* red = reinterpret_cast<unsigned long long*>(c->red_tmp.p);
-    RT_CUDA(c, cudaMemsetAsync(red, 0, 32, st));
+    RT_CUDA(c, cudaMemsetAsync(red, 0, 40, st));
     RT_CUDA(c, cudaMemsetAsync(red, 0xff, 8, st));
     RT_CUDA(c, cudaMemsetAsync(red + 3, 0xff, 8, st));
 
@@ -1038,27 +1104,34 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     PairParams pp;
     for (int a = 0; a < 3; ++a) pp.scale[a] = qscale[a];
     pp.Hmax = Hmax;
-    k_pairs<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(),
-                                                  c->H2f.as<float>(), n, pp, c->counts.as<int32_t>(), nullptr, nullptr);
-    RT_CUDA(c, cudaMemsetAsync(c->counts.as<int32_t>() + n, 0, 4, st));
-    tb = c->cub_tmp.bytes;
-    RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->counts.as<int32_t>(), c->row_off.as<int64_t>(),
-                                             (int)(n + 1), st));
-    int64_t P2 = 0;
-    RT_CUDA(c, cudaMemcpyAsync(&P2, c->row_off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st));
+    // Searching every particle out to max(H_i, H_max) visits H_max^3 / <H^3> times the volume
+    // of its own support; above a ratio of 12 the sort-based build is cheaper.
+    double sumH3 = 0.0;
+    RT_CUDA(c, cudaMemcpyAsync(&sumH3, red + 4, 8, cudaMemcpyDeviceToHost, st));
     RT_CUDA(c, cudaStreamSynchronize(st));
-    if (P2 >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "more than 2^31 neighbour entries");
-    c->n_directed = P2;
-    RT_TRY(ensure(c, c->cols, std::max<int64_t>(P2, 1) * 4, "pair lists"));
-    RT_TRY(ensure(c, c->cols_tmp, std::max<int64_t>(P2, 1) * 4, "pair lists"));
-    k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(),
-                                                 c->H2f.as<float>(), n, pp, nullptr, c->row_off.as<int64_t>(),
-                                                 c->cols_tmp.as<int32_t>());
-    RT_CUDA(c, cudaGetLastError());
-    c->launches += 3;   // count, fill, geometry below
-
-    // rows in ascending order, the lower / upper split and the slots of the pairs
-    {
+    const double vol_ratio = Hmax * Hmax * Hmax / std::max(sumH3 / (double)n, 1e-300);
+    const bool sorted_build = vol_ratio > 12.0;
+    c->diag.pair_build = sorted_build ? 1 : 0;
+    int64_t P2 = 0;
+    if (!sorted_build) {
+        k_pairs<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
+                                                      c->h_d.as<double>(), c->H2f.as<float>(), n, pp,
+                                                      c->counts.as<int32_t>(), nullptr, nullptr);
+        RT_CUDA(c, cudaMemsetAsync(c->counts.as<int32_t>() + n, 0, 4, st));
+        tb = c->cub_tmp.bytes;
+        RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->counts.as<int32_t>(), c->row_off.as<int64_t>(),
+                                                 (int)(n + 1), st));
+        RT_CUDA(c, cudaMemcpyAsync(&P2, c->row_off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st));
+        RT_CUDA(c, cudaStreamSynchronize(st));
+        if (P2 >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "more than 2^31 neighbour entries");
+        RT_TRY(ensure(c, c->cols, std::max<int64_t>(P2, 1) * 4, "pair lists"));
+        RT_TRY(ensure(c, c->cols_tmp, std::max<int64_t>(P2, 1) * 4, "pair lists"));
+        k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
+                                                     c->h_d.as<double>(), c->H2f.as<float>(), n, pp, nullptr,
+                                                     c->row_off.as<int64_t>(), c->cols_tmp.as<int32_t>());
+        RT_CUDA(c, cudaGetLastError());
+        c->launches += 2;
+        // rows in ascending order
         size_t need = 0;
         cub::DeviceSegmentedSort::SortKeys(nullptr, need, c->cols_tmp.as<int32_t>(), c->cols.as<int32_t>(), (int)P2,
                                            (int)n, c->row_off.as<int64_t>(), c->row_off.as<int64_t>() + 1, st);
@@ -1067,7 +1140,62 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         RT_CUDA(c, cub::DeviceSegmentedSort::SortKeys(c->cub_tmp.p, tb, c->cols_tmp.as<int32_t>(), c->cols.as<int32_t>(),
                                                       (int)P2, (int)n, c->row_off.as<int64_t>(),
                                                       c->row_off.as<int64_t>() + 1, st));
+    } else {
+        int64_t* goff = c->row_off.as<int64_t>();      // gather offsets first, CSR offsets after
+        k_pairs_gather<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
+                                                             c->h_d.as<double>(), c->H2f.as<float>(), n, pp,
+                                                             c->counts.as<int32_t>(), nullptr, nullptr);
+        RT_CUDA(c, cudaMemsetAsync(c->counts.as<int32_t>() + n, 0, 4, st));
+        tb = c->cub_tmp.bytes;
+        RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->counts.as<int32_t>(), goff, (int)(n + 1), st));
+        int64_t Mg = 0;
+        RT_CUDA(c, cudaMemcpyAsync(&Mg, goff + n, 8, cudaMemcpyDeviceToHost, st));
+        RT_CUDA(c, cudaStreamSynchronize(st));
+        if (2 * Mg >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "more than 2^31 neighbour entries");
+        const int64_t K = std::max<int64_t>(2 * Mg, 1);
+        RT_TRY(ensure(c, c->pkeys, K * 8, "pair keys"));
+        RT_TRY(ensure(c, c->pkeys_alt, K * 8, "pair keys"));
+        k_pairs_gather<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
+                                                            c->h_d.as<double>(), c->H2f.as<float>(), n, pp, nullptr,
+                                                            goff, c->pkeys.as<uint64_t>());
+        c->launches += 2;
+        int key_bits = 32 + c->key_bits;
+        {
+            int nb = 1;
+            while (((int64_t)1 << nb) < n) ++nb;
+            key_bits = 32 + nb;
+        }
+        size_t need = 0;
+        cub::DeviceRadixSort::SortKeys(nullptr, need, c->pkeys.as<uint64_t>(), c->pkeys_alt.as<uint64_t>(), (int)K, 0,
+                                       key_bits, st);
+        size_t need2 = 0;
+        cub::DeviceSelect::Unique(nullptr, need2, c->pkeys_alt.as<uint64_t>(), c->pkeys.as<uint64_t>(),
+                                  (int64_t*)nullptr, (int)K, st);
+        RT_TRY(ensure(c, c->cub_tmp, std::max(need, need2) + 256, "cub scratch"));
+        tb = c->cub_tmp.bytes;
+        RT_CUDA(c, cub::DeviceRadixSort::SortKeys(c->cub_tmp.p, tb, c->pkeys.as<uint64_t>(), c->pkeys_alt.as<uint64_t>(),
+                                                  (int)K, 0, key_bits, st));
+        int64_t* nuniq = reinterpret_cast<int64_t*>(red + 5);
+        tb = c->cub_tmp.bytes;
+        RT_CUDA(c, cub::DeviceSelect::Unique(c->cub_tmp.p, tb, c->pkeys_alt.as<uint64_t>(), c->pkeys.as<uint64_t>(),
+                                             nuniq, (int)K, st));
+        RT_CUDA(c, cudaMemcpyAsync(&P2, nuniq, 8, cudaMemcpyDeviceToHost, st));
+        RT_CUDA(c, cudaStreamSynchronize(st));
+        RT_TRY(ensure(c, c->cols, std::max<int64_t>(P2, 1) * 4, "pair lists"));
+        RT_CUDA(c, cudaMemsetAsync(c->counts.as<int32_t>(), 0, (n + 1) * 4, st));
+        k_keys_to_csr<<<nblk(std::max<int64_t>(P2, 1), 256), 256, 0, st>>>(c->pkeys.as<uint64_t>(), nuniq,
+                                                                            c->cols.as<int32_t>(),
+                                                                            c->counts.as<int32_t>());
+        tb = c->cub_tmp.bytes;
+        RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->counts.as<int32_t>(), c->row_off.as<int64_t>(),
+                                                 (int)(n + 1), st));
+        ++c->launches;
+        RT_CUDA(c, cudaGetLastError());
     }
+    c->n_directed = P2;
+    c->launches += 1;   // geometry below
+
+    // the lower / upper split and the slots of the pairs
     RT_TRY(ensure(c, c->n_low, (n + 1) * 4, "pair split"));
     RT_TRY(ensure(c, c->n_up, (n + 1) * 4, "pair split"));
     RT_TRY(ensure(c, c->up_off, (n + 1) * 8, "pair split"));

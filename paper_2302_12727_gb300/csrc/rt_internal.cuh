@@ -75,6 +75,7 @@ struct rt_ctx {
     bool has_h_prev = false;
     rt::DevBuf pos_t, geo_t, omega_t;                   // working precision per particle (pair kernels)
     rt::DevBuf counts, row_off, cols, cols_tmp;         // symmetric pair lists (CSR), rows ascending
+    rt::DevBuf pkeys, pkeys_alt;                        // (row, col) keys of the sort-based build
     rt::DevBuf n_low, n_up, up_off, low_slot, pair_ends; // lower / upper split, pair slots
     rt::DevBuf pairbuf;                                 // per-pair fluxes of one group chunk
     rt::DevBuf flags;                                   // int32 error flags + counters
