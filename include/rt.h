@@ -79,7 +79,12 @@ typedef struct {
     double h_tol;            /* relative tolerance of the smoothing-length iteration (<= 1e-6;
                                 the FP64 path always refines to machine precision) */
     int32_t h_max_iter;      /* iteration cap of that solve; exceeding it gives RT_ERR_NOCONV */
-    uint64_t device_wait_budget_cycles;  /* reserved: bound for device-side waits */
+    uint64_t device_wait_budget_cycles;  /* bound, in SM clock cycles, of every device-side wait
+                                            (the copy waits of flux_variant 2, rt_tuning); 0 means
+                                            4e9 (about two seconds).  A wait that runs out skips
+                                            its pairs and sets a flag that rt_energy reports as
+                                            RT_ERR_TIMEOUT (and rt_diag.wait_timeouts) until the
+                                            next rt_neighbours */
 } rt_config;
 
 typedef struct {
@@ -100,7 +105,29 @@ typedef struct {
                                  searched to max(H_i, H_max); 1 = own supports, then sorted and
                                  de-duplicated with their transposes (chosen when the h range is
                                  wide); both give the same lists */
+    int32_t wait_timeouts;    /* 1 if a device-side wait ran out since the last rt_neighbours */
 } rt_diag;
+
+/* Launch variants of the float (RT_FP32_MIXED) pair kernels.  The paper has no counterpart:
+ * they choose how the GPU threads map onto the pair loops of Eq. gradient and
+ * Eq. transport-update-explicit, never what is computed.  Every variant gives bitwise the
+ * same fluxes and the same order of accumulation; the double path ignores them.
+ *   flux_variant      0: one thread per pair slot loading both particles' records directly;
+ *                     1: the same, with the neighbour records of each warp staged through
+ *                        shared memory by cooperative asynchronous copies;
+ *                     2: the same, with the neighbour rows of each warp fetched into shared
+ *                        memory by tensor-memory-accelerator row gathers (default; falls back
+ *                        to 0 where the driver offers no tensor-map encoder).
+ *   gather_variant    0: one thread per particle;
+ *                     1: one thread per (particle, group) (default).
+ *   gradient_variant  0: one thread per particle;
+ *                     1: one thread per (particle, group) (default).
+ * Changing the variants drops the context's captured sub-cycle graphs. */
+typedef struct {
+    int32_t flux_variant;
+    int32_t gather_variant;
+    int32_t gradient_variant;
+} rt_tuning;
 
 /* Kernel kinds reported by rt_kernel_times. */
 enum { RT_KERNEL_INJECT = 0, RT_KERNEL_GRADIENT = 1, RT_KERNEL_FLUX = 2, RT_KERNEL_FLUX_GATHER = 3,
@@ -202,6 +229,12 @@ rt_status rt_set_profiling(rt_ctx* ctx, int32_t on);
  * recent rt_transport_step or rt_subcycle call made with profiling on; zeros if none.
  * Synchronises the stream. */
 rt_status rt_kernel_times(rt_ctx* ctx, double* ms_host, int64_t* launches_host);
+
+/* Set (rt_set_tuning) or read (rt_get_tuning) the launch variants of the float pair kernels
+ * (host struct, copied).  RT_ERR_INVALID for a variant outside the values listed above; the
+ * context is unchanged then.  Valid before or after rt_neighbours. */
+rt_status rt_set_tuning(rt_ctx* ctx, const rt_tuning* tuning);
+rt_status rt_get_tuning(const rt_ctx* ctx, rt_tuning* tuning);
 
 /* Message of the last failure ("" if none).  Valid until the next call on ctx. */
 const char* rt_last_error(const rt_ctx* ctx);

@@ -21,7 +21,8 @@ _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4
 
 EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
-            "rt_kernel_times", "rt_energy_static", "rt_last_error", "rt_destroy"]
+            "rt_kernel_times", "rt_set_tuning", "rt_get_tuning", "rt_energy_static", "rt_last_error",
+            "rt_destroy"]
 
 RT_ENERGY_STATIC_MAX_GROUPS = 16
 
@@ -40,12 +41,16 @@ class rt_diag(C.Structure):
                 ("n_ill_conditioned", C.c_int64), ("cond_max", C.c_double), ("h_min", C.c_double),
                 ("h_max", C.c_double), ("dx_min", C.c_double), ("clamp_events", C.c_int64),
                 ("grid", C.c_int32 * 3), ("threads_per_particle", C.c_int32), ("kernel_launches", C.c_int64),
-                ("pair_build", C.c_int32)]
+                ("pair_build", C.c_int32), ("wait_timeouts", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["grid"] = list(self.grid)
         return d
+
+
+class rt_tuning(C.Structure):
+    _fields_ = [("flux_variant", C.c_int32), ("gather_variant", C.c_int32), ("gradient_variant", C.c_int32)]
 
 
 class RTError(RuntimeError):
@@ -83,6 +88,8 @@ def load_library():
     lib.rt_diagnostics.argtypes = [vp, C.POINTER(rt_diag)]
     lib.rt_set_profiling.argtypes = [vp, C.c_int32]
     lib.rt_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    lib.rt_set_tuning.argtypes = [vp, C.POINTER(rt_tuning)]
+    lib.rt_get_tuning.argtypes = [vp, C.POINTER(rt_tuning)]
     lib.rt_energy_static.argtypes = [vp, vp, i64, C.c_int32, C.c_int32, vp, vp]
     lib.rt_last_error.argtypes = [vp]
     lib.rt_last_error.restype = C.c_char_p
@@ -191,6 +198,19 @@ def rt_kernel_times(ctx):
     _check(ctx, load_library().rt_kernel_times(ctx, ms, nl))
     names = ("inject", "gradient", "flux", "flux_gather")
     return {names[k]: (ms[k], nl[k]) for k in range(RT_KERNEL_KINDS)}
+
+
+def rt_set_tuning(ctx, flux_variant: int = 2, gather_variant: int = 1, gradient_variant: int = 1):
+    """Launch variants of the float pair kernels (see rt.h); same results for every choice."""
+    t = rt_tuning(int(flux_variant), int(gather_variant), int(gradient_variant))
+    _check(ctx, load_library().rt_set_tuning(ctx, C.byref(t)))
+
+
+def rt_get_tuning(ctx) -> dict:
+    t = rt_tuning()
+    _check(ctx, load_library().rt_get_tuning(ctx, C.byref(t)))
+    return {"flux_variant": t.flux_variant, "gather_variant": t.gather_variant,
+            "gradient_variant": t.gradient_variant}
 
 
 def rt_energy_static(U, V, n, n_groups, precision, E_out, stream=None):

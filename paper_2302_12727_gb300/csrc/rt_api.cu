@@ -115,6 +115,7 @@ static rt_status ensure_state(rt_ctx* c) {
     // per-pair flux slots of one group chunk (at most 4 groups)
     const int gc = G < kMaxGC ? G : kMaxGC;
     RT_TRY(ensure(c, c->pairbuf, (size_t)std::max<int64_t>(c->n_directed / 2, 1) * 4 * gc * tsize(c), "pair fluxes"));
+    if (!c->fp64 && G <= kMaxGC) RT_TRY(ensure(c, c->frec, (size_t)(12 + 16 * G) * n * 4, "packed flux rows"));
     return RT_OK;
 }
 
@@ -299,7 +300,12 @@ rt_status rt_energy(rt_ctx* c, const void* U, double* E_host) {
     double* out = c->energy_part.as<double>() + (size_t)G * 512;
     RT_TRY(launch_energy(c, c->stream, c->U_a.p, out));
     RT_CUDA(c, cudaMemcpyAsync(E_host, out, G * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    int timed_out = 0;
+    RT_CUDA(c, cudaMemcpyAsync(&timed_out, c->flags.as<int>() + F_TIMEOUT, sizeof(int), cudaMemcpyDeviceToHost,
+                               c->stream));
     RT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (timed_out)
+        return fail(c, RT_ERR_TIMEOUT, "a device-side wait of the pair kernel ran out since the last rt_neighbours");
     return RT_OK;
 }
 
@@ -381,11 +387,15 @@ rt_status rt_diagnostics(rt_ctx* c, rt_diag* out) {
     if (!c || !out) return RT_ERR_INVALID;
     c->err.clear();
     unsigned long long cl = 0;
+    int timed_out = 0;
     if (c->flags.p) {
-        RT_CUDA(c, cudaMemcpyAsync(&cl, c->flags.as<int>() + 8, 8, cudaMemcpyDeviceToHost, c->stream));
+        RT_CUDA(c, cudaMemcpyAsync(&cl, c->flags.as<int>() + F_CLAMP, 8, cudaMemcpyDeviceToHost, c->stream));
+        RT_CUDA(c, cudaMemcpyAsync(&timed_out, c->flags.as<int>() + F_TIMEOUT, sizeof(int), cudaMemcpyDeviceToHost,
+                                   c->stream));
         RT_CUDA(c, cudaStreamSynchronize(c->stream));
     }
     c->diag.clamp_events = (int64_t)cl;
+    c->diag.wait_timeouts = timed_out;
     c->diag.threads_per_particle = c->tpp;
     c->diag.kernel_launches = c->launches;
     *out = c->diag;
@@ -425,6 +435,28 @@ rt_status rt_kernel_times(rt_ctx* c, double* ms, int64_t* launches) {
     return RT_OK;
 }
 
+rt_status rt_set_tuning(rt_ctx* c, const rt_tuning* t) {
+    if (!c) return RT_ERR_INVALID;
+    c->err.clear();
+    if (!t) return fail(c, RT_ERR_INVALID, "rt_set_tuning: NULL tuning");
+    if (t->flux_variant < 0 || t->flux_variant > 2 || t->gather_variant < 0 || t->gather_variant > 1 ||
+        t->gradient_variant < 0 || t->gradient_variant > 1)
+        return fail(c, RT_ERR_INVALID, "rt_set_tuning: flux_variant must be 0, 1 or 2, the others 0 or 1");
+    if (t->flux_variant != c->tune.flux_variant || t->gather_variant != c->tune.gather_variant ||
+        t->gradient_variant != c->tune.gradient_variant) {
+        RT_CUDA(c, cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+        c->tune = *t;
+    }
+    return RT_OK;
+}
+
+rt_status rt_get_tuning(const rt_ctx* c, rt_tuning* t) {
+    if (!c || !t) return RT_ERR_INVALID;
+    *t = c->tune;
+    return RT_OK;
+}
+
 const char* rt_last_error(const rt_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
 
 void rt_destroy(rt_ctx* c) {
@@ -439,7 +471,7 @@ void rt_destroy(rt_ctx* c) {
                       &c->n_up, &c->up_off, &c->low_slot, &c->pair_ends, &c->pairbuf, &c->flags, &c->red_tmp,
                       &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
                       &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,
-                      &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->alpha_s,
+                      &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->frec, &c->alpha_s,
                       &c->L_dev, &c->dt_dev, &c->energy_part, &c->ck, &c->seg, &c->lam_a, &c->lam_b, &c->adj_w,
                       &c->adj_x, &c->adj_ub, &c->adj_gam, &c->adj_lam};
     for (DevBuf* b : bufs) free_buf(*b);

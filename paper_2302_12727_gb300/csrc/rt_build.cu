@@ -15,7 +15,6 @@
 
 namespace rt {
 
-enum FlagSlot { F_BADPOS = 0, F_NOCONV = 1, F_GEOM = 2, F_ILL = 3, F_SRC_NOCONV = 4, F_NSLOTS = 8 };
 
 struct Grid {
     int nc[3];

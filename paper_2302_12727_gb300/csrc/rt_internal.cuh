@@ -2,6 +2,7 @@
 // buffers, and the per-pair device arithmetic shared by the forward and adjoint kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,6 +19,10 @@ namespace rt {
 constexpr double kKappa = 1.825742;
 // sigma = 16 / pi, Eq. cubic-spline-kernel in 3D.
 constexpr double kSigma = 5.0929581789406507446;   // 16 / pi
+// int slots of the context's 64-byte flag buffer (cleared by every rt_neighbours): error
+// flags of the build, the clamp counter (64-bit, slots 8-9) and the device-wait time-out flag
+enum FlagSlot { F_BADPOS = 0, F_NOCONV = 1, F_GEOM = 2, F_ILL = 3, F_SRC_NOCONV = 4, F_NSLOTS = 8, F_CLAMP = 8,
+                F_TIMEOUT = 12 };
 constexpr int kMaxGC = 4;                          // groups handled by one pair-kernel launch
 
 // ------------------------------------------------------------------------------------
@@ -89,6 +94,10 @@ struct rt_ctx {
 
     // state records (sorted order, working precision): U [N][4G] (double-buffered), grad U [N][12G]
     rt::DevBuf U_a, U_b, grad_t, alpha_s, L_dev, dt_dev, energy_part;
+    rt::DevBuf frec;                                    // packed float flux-input rows (G <= 4)
+    CUtensorMap rows_map{};                             // tensor map of frec (tile::gather4)
+    const void* rows_map_for = nullptr;
+    int64_t rows_map_n = 0;
     // adjoint
     rt::DevBuf ck, seg, lam_a, lam_b, adj_w, adj_x, adj_ub, adj_gam, adj_lam;
     int64_t ck_cap = 0, seg_cap = 0;
@@ -96,6 +105,8 @@ struct rt_ctx {
     // diagnostics
     rt_diag diag{};
     int tpp = 1;   // threads per particle for pair kernels
+    // launch variants of the float pair kernels (rt_set_tuning); the double path has one
+    rt_tuning tune{2, 1, 1};
 
     std::map<rt::GraphKey, rt::GraphEntry> graphs;
 

@@ -142,6 +142,51 @@ __device__ __forceinline__ void vload(const double* __restrict__ p, double* o) {
         o[k] = v.x; o[k + 1] = v.y;
     }
 }
+// 16-byte asynchronous global -> shared copy (cached in L1), and the wait for all of a
+// thread's outstanding copies
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// ------------------------------------------------------------------------------------
+// TMA row gathers (cp.async.bulk.tensor, tile::gather4) completing on an mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// waits for phase `parity` of the barrier to complete; false once `budget` clock cycles
+// have passed without completion.  Each try_wait may suspend the thread for up to 0.1 ms
+// (woken early when the phase completes), so waiting warps issue almost no instructions.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long budget) {
+    const unsigned long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar), "r"(parity), "r"(100000u)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+// four rows (r0..r3) of a 2-D row-major tensor, columns [col, col + box width), into
+// consecutive rows at dst; the tensor map's box is one row high
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void* tmap, int col, int r0, int r1, int r2, int r3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+        : "memory");
+}
+
 template <int K>
 __device__ __forceinline__ void vstore(float* p, const float* o) {
 #pragma unroll
@@ -169,6 +214,11 @@ struct PairArgs {
     const int2* ends;         // (k, l) of each pair slot
     int64_t n_pairs;
     int G;
+    // packed flux-input rows [N][RW], RW = 12 + 16G: {pos (4 words), geo (8), U (4G), grad U
+    // (12G)}; when set, the gradient kernels write U, grad U and the static part there
+    // (instead of grad) for the tensor-memory-accelerator flux pass
+    T* frec;
+    int RW;
 };
 
 // symmetric 3x3 (xx, yy, zz, xy, xz, yz) times vector
@@ -236,6 +286,8 @@ inline PairArgs<T> pair_args(rt_ctx* c) {
     a.ends = c->pair_ends.as<int2>();
     a.n_pairs = c->n_directed / 2;
     a.G = c->cfg.n_groups;
+    a.frec = nullptr;
+    a.RW = 12 + 16 * a.G;
     return a;
 }
 

@@ -15,6 +15,9 @@
 // of its upper pairs and subtract those of its lower pairs in a fixed order.  Both particles thus
 // apply the very same Phi_kl with opposite signs: the exchange is exactly antisymmetric,
 // and so exactly conservative, deterministic, and free of atomics.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "rt_pair.cuh"
 
 namespace rt {
@@ -80,6 +83,17 @@ __global__ void k_inject(const int32_t* __restrict__ targets, const int32_t* __r
     }
 }
 
+// position and geometry words of particle i's packed flux row
+template <class T>
+__device__ __forceinline__ void packed_static(const PairArgs<T>& a, int64_t i, T* row) {
+    if constexpr (std::is_same<T, float>::value) {
+        *reinterpret_cast<uint4*>(row) = reinterpret_cast<const uint4*>(a.pos)[i];
+        float g8[8];
+        vload<8>(a.geo + 8 * i, g8);
+        vstore<8>(row + 4, g8);
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // a6: least-squares gradient (Eq. gradient) of the groups [g0, g0 + GC):
 // grad Q_i = omega_i Bp_i sum_j (Q_j - Q_i) w(r_ij / H_i) d_ij,  d_ij = x_j - x_i
@@ -132,7 +146,78 @@ __global__ void __launch_bounds__(128) k_gradient(PairArgs<T> a, const T* __rest
     T out[3 * NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) sym_mv(M, acc[c][0], acc[c][1], acc[c][2], out[3 * c], out[3 * c + 1], out[3 * c + 2]);
-    vstore<3 * NC>(grad + i * 12 * a.G + 12 * g0, out);
+    if (a.frec) {
+        T* row = a.frec + i * a.RW;
+        vstore<3 * NC>(row + 12 + 4 * a.G + 12 * g0, out);
+        vstore<NC>(row + 12 + 4 * g0, ui);
+        if (g0 == 0) packed_static(a, i, row);
+    } else {
+        vstore<3 * NC>(grad + i * 12 * a.G + 12 * g0, out);
+    }
+}
+
+// Float gradient with one thread per (particle, group): the GC lanes of a particle read the
+// same neighbour position and neighbouring 16-byte pieces of the same state record, so a
+// warp request touches about 32 / GC records instead of 32.  Same neighbour pairing and
+// order of accumulation as k_gradient.
+template <int GC>
+__global__ void __launch_bounds__(256) k_gradient_g(PairArgs<float> a, const float* __restrict__ rec,
+                                                    float* __restrict__ grad, int g0) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = t / GC;
+    if (i >= a.n) return;
+    const int g = (int)(t - i * GC);
+    const float* tag = nullptr;
+    const Pos<float> pi = load_pos(tag, a.pos, i);
+    const float iH = a.geo[8 * i];
+    const int RS = 4 * a.G;
+    const int off = 4 * (g0 + g);
+    float ui[4];
+    vload<4>(rec + i * RS + off, ui);
+    float acc[4][3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c][0] = acc[c][1] = acc[c][2] = 0.f;
+    const int64_t e0 = a.row_off[i], e1 = a.row_off[i + 1];
+    for (int64_t e = e0; e < e1; e += 2) {
+        const bool two = e + 1 < e1;
+        const int j0 = a.cols[e];
+        const int j1 = two ? a.cols[e + 1] : j0;
+        Pos<float> p0 = load_pos(tag, a.pos, j0);
+        Pos<float> p1 = load_pos(tag, a.pos, j1);
+        float u0[4], u1[4];
+        vload<4>(rec + (int64_t)j0 * RS + off, u0);
+        vload<4>(rec + (int64_t)j1 * RS + off, u1);
+        float dx0, dy0, dz0, dx1, dy1, dz1;
+        sep(a.sp, pi, p0, dx0, dy0, dz0);
+        sep(a.sp, pi, p1, dx1, dy1, dz1);
+        float w0 = spline_w_(sqrt_(dx0 * dx0 + dy0 * dy0 + dz0 * dz0) * iH);
+        float w1 = two ? spline_w_(sqrt_(dx1 * dx1 + dy1 * dy1 + dz1 * dz1) * iH) : 0.f;
+        float wx0 = w0 * dx0, wy0 = w0 * dy0, wz0 = w0 * dz0;
+        float wx1 = w1 * dx1, wy1 = w1 * dy1, wz1 = w1 * dz1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float dq0 = u0[c] - ui[c];
+            float dq1 = u1[c] - ui[c];
+            acc[c][0] += dq0 * wx0 + dq1 * wx1;
+            acc[c][1] += dq0 * wy0 + dq1 * wy1;
+            acc[c][2] += dq0 * wz0 + dq1 * wz1;
+        }
+    }
+    float M[6];
+    const float om = a.omega[i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) M[k] = om * a.geo[8 * i + 2 + k];
+    float out[12];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sym_mv(M, acc[c][0], acc[c][1], acc[c][2], out[3 * c], out[3 * c + 1], out[3 * c + 2]);
+    if (a.frec) {
+        float* row = a.frec + i * a.RW;
+        vstore<12>(row + 12 + 4 * a.G + 12 * (g0 + g), out);
+        vstore<4>(row + 12 + off, ui);
+        if (g0 + g == 0) packed_static(a, i, row);
+    } else {
+        vstore<12>(grad + i * 12 * a.G + 12 * (g0 + g), out);
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -245,6 +330,252 @@ __global__ void __launch_bounds__(128) k_flux_gather(PairArgs<T> a, FluxExtra<T>
     if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
 }
 
+// Float pass 1 with the neighbour records staged through shared memory.  One thread per
+// pair slot as in k_flux, but the 32 l-records a warp needs (position, geometry, state and
+// gradient of the launched groups) are first copied by the whole warp, one array at a time,
+// so that each 16-byte request of the warp covers a few consecutive records instead of 32
+// scattered ones; the per-pair loads of the direct kernel saturate the L1 data pipe.  The
+// k side needs no staging: consecutive slots mostly share k, so its loads are broadcasts.
+// The arithmetic is the same as k_flux's.
+template <int GC>
+struct Staged {
+    static constexpr int RW = 12 + 16 * GC;   // words per staged record: pos 4, geo 8, state 4GC, grad 12GC
+    static constexpr int WARPS = 4;
+    static constexpr size_t bytes = (size_t)WARPS * 32 * RW * sizeof(float);
+};
+
+template <int GC>
+__global__ void __launch_bounds__(128) k_flux_staged(PairArgs<float> a, FluxExtra<float> x,
+                                                     const float* __restrict__ rec, float* __restrict__ pairbuf,
+                                                     int g0) {
+    constexpr int NC = 4 * GC, RW = Staged<GC>::RW;
+    // RW / 4 is odd for every GC, so the lanes' 16-byte reads of their own records are free
+    // of bank conflicts
+    __shared__ __align__(16) float st[Staged<GC>::WARPS * 32 * RW];
+    const int lane = threadIdx.x & 31;
+    float* ws = st + (threadIdx.x >> 5) * 32 * RW;
+    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool act = slot < a.n_pairs;
+    // lanes past the last slot stage particle 0 (always present) and store nothing
+    const int2 kl = act ? a.ends[slot] : make_int2(0, 0);
+    const int G = a.G, RS = 4 * G;
+    const unsigned FULL = 0xffffffffu;
+    cp_async16(ws + lane * RW, reinterpret_cast<const uint4*>(a.pos) + kl.y);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int t = m * 32 + lane, r = t >> 1, q = t & 1;
+        const int64_t l = __shfl_sync(FULL, kl.y, r);
+        cp_async16(ws + r * RW + 4 + 4 * q, a.geo + 8 * l + 4 * q);
+    }
+#pragma unroll
+    for (int m = 0; m < GC; ++m) {
+        const int t = m * 32 + lane, r = t / GC, q = t - r * GC;
+        const int64_t l = __shfl_sync(FULL, kl.y, r);
+        cp_async16(ws + r * RW + 12 + 4 * q, rec + l * RS + 4 * g0 + 4 * q);
+    }
+#pragma unroll
+    for (int m = 0; m < 3 * GC; ++m) {
+        const int t = m * 32 + lane, r = t / (3 * GC), q = t - r * (3 * GC);
+        const int64_t l = __shfl_sync(FULL, kl.y, r);
+        cp_async16(ws + r * RW + 12 + 4 * GC + 4 * q, a.grad + l * 12 * G + 12 * g0 + 4 * q);
+    }
+    const float* tag = nullptr;
+    const int64_t i = kl.x;
+    const Pos<float> pi = load_pos(tag, a.pos, i);
+    float gi8[8], gj8[8];
+    vload<8>(a.geo + 8 * i, gi8);
+    cp_async_wait_all();
+    __syncwarp();
+    const float* mine = ws + lane * RW;
+    const uint4 pv = *reinterpret_cast<const uint4*>(mine);
+    const Pos<float> pj = {pv.x, pv.y, pv.z};
+    vload<8>(mine + 4, gj8);
+    float dx, dy, dz;
+    sep(a.sp, pi, pj, dx, dy, dz);
+    float r = sqrt_(dx * dx + dy * dy + dz * dz);
+    float si = spline_w_(r * gi8[0]);
+    float sj = spline_w_(r * gj8[0]);
+    float M[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) M[q] = gi8[2 + q] * si + gj8[2 + q] * sj;
+    float Ax, Ay, Az;
+    sym_mv(M, dx, dy, dz, Ax, Ay, Az);
+    float diss = 0.5f * x.c * sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+    float ih = rcp_(gi8[1] + gj8[1]);
+    float wi = gi8[1] * ih, wj = gj8[1] * ih;
+    const float* ri = rec + i * RS;
+    const float* qi = a.grad + i * 12 * G;
+    float out[NC];
+#pragma unroll
+    for (int g = 0; g < GC; ++g) {
+        const int gg = g0 + g;
+        float ui[4], uj[4], gri[12], grj[12];
+        vload<4>(ri + 4 * gg, ui);
+        vload<4>(mine + 12 + 4 * g, uj);
+        vload<12>(qi + 12 * gg, gri);
+        vload<12>(mine + 12 + 4 * GC + 12 * g, grj);
+        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, &out[4 * g]);
+    }
+    if (act) vstore<NC>(pairbuf + slot * NC, out);
+}
+
+// Float pass 1 with the neighbour rows fetched by the tensor memory accelerator.  The
+// gradient pass has packed each particle's flux inputs (position, geometry, state and
+// gradient) into one row; each warp gathers the rows of its 32 l-particles into shared
+// memory with eight tile::gather4 copies (four rows each).  The copies bypass the
+// load/store pipeline whose wavefronts bound the direct kernel; the k side is loaded
+// directly (mostly broadcasts).  Same arithmetic as k_flux.  A copy that does not complete
+// within the wait budget sets err_flag, and the warp returns without storing.
+template <int G>
+struct PackedRows {
+    static constexpr int RW = 12 + 16 * G;              // words per row
+    static constexpr int SLOT = (4 * RW + 31) / 32 * 32; // four rows, padded to 128 bytes
+    static constexpr int WF = 8 * SLOT;                 // floats per warp
+    static constexpr uint32_t bytes = 32u * RW * 4u;    // bytes gathered per warp
+};
+
+template <int G>
+__global__ void __launch_bounds__(128) k_flux_tma(PairArgs<float> a, FluxExtra<float> x,
+                                                  float* __restrict__ pairbuf,
+                                                  const __grid_constant__ CUtensorMap rows, int* err_flag,
+                                                  unsigned long long budget) {
+    using R = PackedRows<G>;
+    constexpr int NC = 4 * G, RW = R::RW;
+    __shared__ __align__(128) float sm[4 * R::WF];
+    __shared__ __align__(8) uint64_t bar[4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* ws = sm + wid * R::WF;
+    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool act = slot < a.n_pairs;
+    // lanes past the last slot gather particle 0 (always present) and store nothing
+    const int2 kl = act ? a.ends[slot] : make_int2(0, 0);
+    const uint32_t mb = smem_u32(&bar[wid]);
+    if (lane == 0) {
+        mbar_init(mb, 1);
+        mbar_expect_tx(mb, R::bytes);
+    }
+    __syncwarp();
+    const unsigned FULL = 0xffffffffu;
+    const int q = lane & 7;
+    const int r0 = __shfl_sync(FULL, kl.y, 4 * q), r1 = __shfl_sync(FULL, kl.y, 4 * q + 1);
+    const int r2 = __shfl_sync(FULL, kl.y, 4 * q + 2), r3 = __shfl_sync(FULL, kl.y, 4 * q + 3);
+    if (lane < 8) tma_gather4(smem_u32(ws + q * R::SLOT), &rows, 0, r0, r1, r2, r3, mb);
+    const int64_t i = kl.x;
+    const float* rk = a.frec + i * RW;
+    const uint4 pkv = *reinterpret_cast<const uint4*>(rk);
+    const Pos<float> pi = {pkv.x, pkv.y, pkv.z};
+    float gi8[8], gj8[8];
+    vload<8>(rk + 4, gi8);
+    if (!mbar_wait(mb, 0, budget)) {
+        atomicExch(err_flag, 1);
+        mbar_wait(mb, 0, budget);     // let copies still in flight land before the block exits
+        return;
+    }
+    // this lane's row: slot lane / 4, row lane % 4 within it
+    const float* rl = ws + (lane >> 2) * R::SLOT + (lane & 3) * RW;
+    const uint4 pv = *reinterpret_cast<const uint4*>(rl);
+    const Pos<float> pj = {pv.x, pv.y, pv.z};
+    vload<8>(rl + 4, gj8);
+    float dx, dy, dz;
+    sep(a.sp, pi, pj, dx, dy, dz);
+    float r = sqrt_(dx * dx + dy * dy + dz * dz);
+    float si = spline_w_(r * gi8[0]);
+    float sj = spline_w_(r * gj8[0]);
+    float M[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) M[k] = gi8[2 + k] * si + gj8[2 + k] * sj;
+    float Ax, Ay, Az;
+    sym_mv(M, dx, dy, dz, Ax, Ay, Az);
+    float diss = 0.5f * x.c * sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+    float ih = rcp_(gi8[1] + gj8[1]);
+    float wi = gi8[1] * ih, wj = gj8[1] * ih;
+    float out[NC];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        float ui[4], uj[4], gri[12], grj[12];
+        vload<4>(rk + 12 + 4 * g, ui);
+        vload<4>(rl + 12 + 4 * g, uj);
+        vload<12>(rk + 12 + 4 * G + 12 * g, gri);
+        vload<12>(rl + 12 + 4 * G + 12 * g, grj);
+        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, &out[4 * g]);
+    }
+    if (act) vstore<NC>(pairbuf + slot * NC, out);
+}
+
+// Float pass 2 with one thread per (particle, group): the lanes of one particle read the
+// 16-byte pieces of a slot that lie side by side, so a warp request touches about 32 / GC
+// slots instead of 32.  Same order of additions and subtractions as k_flux_gather.
+template <int GC>
+__global__ void __launch_bounds__(256) k_flux_gather_g(PairArgs<float> a, FluxExtra<float> x,
+                                                       const float* __restrict__ rec,
+                                                       const float* __restrict__ pairbuf, float* __restrict__ out,
+                                                       int g0) {
+    // blocks run from the last particles to the first: the pair pass wrote the slots in
+    // ascending order, so the most recent (still L2-resident) slots are read first
+    const int64_t t = (gridDim.x - 1 - blockIdx.x) * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = t / GC;
+    if (i >= a.n) return;
+    const int g = (int)(t - i * GC);
+    constexpr int NC = 4 * GC;
+    const int RS = 4 * a.G;
+    const float* pb = pairbuf + 4 * g;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t r0 = a.row_off[i], s0 = a.up_off[i], s1 = a.up_off[i + 1];
+    int64_t sl = s0;
+    for (; sl + 4 <= s1; sl += 4) {   // four loads in flight, added in order
+        float p0[4], p1[4], p2[4], p3[4];
+        vload<4>(pb + sl * NC, p0);
+        vload<4>(pb + (sl + 1) * NC, p1);
+        vload<4>(pb + (sl + 2) * NC, p2);
+        vload<4>(pb + (sl + 3) * NC, p3);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = (((acc[c] + p0[c]) + p1[c]) + p2[c]) + p3[c];
+    }
+    for (; sl < s1; ++sl) {
+        float phi[4];
+        vload<4>(pb + sl * NC, phi);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += phi[c];
+    }
+    const int nl = a.n_low[i];
+    const int32_t* ls = a.low_slot + (r0 - s0);
+    int e = 0;
+    for (; e + 4 <= nl; e += 4) {
+        float p0[4], p1[4], p2[4], p3[4];
+        vload<4>(pb + (int64_t)ls[e] * NC, p0);
+        vload<4>(pb + (int64_t)ls[e + 1] * NC, p1);
+        vload<4>(pb + (int64_t)ls[e + 2] * NC, p2);
+        vload<4>(pb + (int64_t)ls[e + 3] * NC, p3);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = (((acc[c] - p0[c]) - p1[c]) - p2[c]) - p3[c];
+    }
+    for (; e < nl; ++e) {
+        float phi[4];
+        vload<4>(pb + (int64_t)ls[e] * NC, phi);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] -= phi[c];
+    }
+    const float dt = (float)(*x.dt_dev);
+    const float f = dt * a.omega[i];
+    float sink = 1.f;
+    if (x.alpha) sink = fmax_(1.f - x.c * x.alpha[i] * dt, 0.f);
+    float ui[4];
+    const int64_t o = i * RS + 4 * (g0 + g);
+    vload<4>(rec + o, ui);
+    int nclamp = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float v = (ui[c] - f * acc[c]) * sink;
+        if (x.clamp && c == 0 && v < 0.f) {
+            v = 0.f;
+            ++nclamp;
+        }
+        ui[c] = v;
+    }
+    vstore<4>(out + o, ui);
+    if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
+}
+
 // ------------------------------------------------------------------------------------
 // a10: energy per group, sum_i V_i E_i,g in double; fixed grid and tree order.
 constexpr int kEnergyBlocks = 512;
@@ -293,14 +624,30 @@ static void set_carveouts() {
 }
 
 template <class T>
-static void launch_gradient_t(rt_ctx* c, cudaStream_t s, T* rec) {
+static void launch_gradient_t(rt_ctx* c, cudaStream_t s, T* rec, bool packed = false) {
     set_carveouts<T>();
     PairArgs<T> a = pair_args<T>(c);
+    if (packed) a.frec = c->frec.as<T>();
     const int G = c->cfg.n_groups;
     unsigned nb = nblk(c->n, 128);
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
         int pr = prof_begin(c, s, RT_KERNEL_GRADIENT);
+        if constexpr (std::is_same<T, float>::value) {
+            if (c->tune.gradient_variant == 1) {
+                unsigned nbg = nblk(c->n * gc, 256);
+                float* gr = c->grad_t.as<float>();
+                switch (gc) {
+                    case 1: k_gradient_g<1><<<nbg, 256, 0, s>>>(a, rec, gr, g0); break;
+                    case 2: k_gradient_g<2><<<nbg, 256, 0, s>>>(a, rec, gr, g0); break;
+                    case 3: k_gradient_g<3><<<nbg, 256, 0, s>>>(a, rec, gr, g0); break;
+                    default: k_gradient_g<4><<<nbg, 256, 0, s>>>(a, rec, gr, g0); break;
+                }
+                prof_end(c, s, pr);
+                ++c->launches;
+                continue;
+            }
+        }
         switch (gc) {
             case 1: k_gradient<T, 1><<<nb, 128, 0, s>>>(a, rec, c->grad_t.as<T>(), g0); break;
             case 2: k_gradient<T, 2><<<nb, 128, 0, s>>>(a, rec, c->grad_t.as<T>(), g0); break;
@@ -312,21 +659,105 @@ static void launch_gradient_t(rt_ctx* c, cudaStream_t s, T* rec) {
     }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        (void)cudaGetLastError();
+    }
+    return fn;
+}
+
+// tensor map of the packed rows [n][12 + 16G] floats, box of one whole row (for
+// tile::gather4); encoded again whenever the buffer or its shape changes
+static bool packed_rows_map(rt_ctx* c) {
+    const int RW = 12 + 16 * c->cfg.n_groups;
+    if (c->rows_map_for == c->frec.p && c->rows_map_n == c->n) return true;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !c->frec.p) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)RW, (cuuint64_t)c->n};
+    cuuint64_t strides[1] = {(cuuint64_t)RW * 4};
+    cuuint32_t box[2] = {(cuuint32_t)RW, 1};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&c->rows_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->frec.p, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    c->rows_map_for = c->frec.p;
+    c->rows_map_n = c->n;
+    return true;
+}
+
+// float pass 1 and 2 in the variants chosen by the context's tuning
+template <int GC>
+static void flux_float(rt_ctx* c, cudaStream_t s, const PairArgs<float>& a, const FluxExtra<float>& x,
+                       const float* rec, float* pb, float* out, int g0) {
+    static bool attr = false;
+    if (!attr) {
+        attr = true;
+        cudaFuncSetAttribute((const void*)k_flux_staged<GC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute((const void*)k_flux_gather_g<GC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        cudaFuncSetAttribute((const void*)k_flux_tma<GC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        (void)cudaGetLastError();
+    }
+    unsigned npb = nblk(std::max<int64_t>(a.n_pairs, 1), 128);
+    int variant = c->tune.flux_variant;
+    if (variant == 2 && !a.frec) variant = 0;
+    int pr = prof_begin(c, s, RT_KERNEL_FLUX);
+    if (variant == 2) {
+        unsigned long long budget = c->cfg.device_wait_budget_cycles ? c->cfg.device_wait_budget_cycles
+                                                                     : 4000000000ull;
+        k_flux_tma<GC><<<npb, 128, 0, s>>>(a, x, pb, c->rows_map, c->flags.as<int>() + F_TIMEOUT, budget);
+    } else if (variant == 1) {
+        k_flux_staged<GC><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);
+    } else {
+        k_flux<float, GC><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);
+    }
+    prof_end(c, s, pr);
+    pr = prof_begin(c, s, RT_KERNEL_FLUX_GATHER);
+    if (c->tune.gather_variant == 1)
+        k_flux_gather_g<GC><<<nblk(c->n * GC, 256), 256, 0, s>>>(a, x, rec, pb, out, g0);
+    else
+        k_flux_gather<float, GC><<<nblk(c->n, 128), 128, 0, s>>>(a, x, rec, pb, out, g0);
+    prof_end(c, s, pr);
+    c->launches += 2;
+}
+
 template <class T>
-static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool has_alpha) {
+static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool has_alpha, bool packed = false) {
     PairArgs<T> a = pair_args<T>(c);
+    if (packed) a.frec = c->frec.as<T>();
     FluxExtra<T> x;
     x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
     x.dt_dev = c->dt_dev.as<double>();
     x.c = (T)c->cfg.c_red;
     x.clamp = c->cfg.clamp_negative;
-    x.clamp_count = reinterpret_cast<unsigned long long*>(c->flags.as<int>() + 8);
+    x.clamp_count = reinterpret_cast<unsigned long long*>(c->flags.as<int>() + F_CLAMP);
     const int G = c->cfg.n_groups;
     unsigned nb = nblk(c->n, 128);
     T* pb = c->pairbuf.as<T>();
     unsigned npb = nblk(std::max<int64_t>(a.n_pairs, 1), 128);
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
+        if constexpr (std::is_same<T, float>::value) {
+            switch (gc) {
+                case 1: flux_float<1>(c, s, a, x, rec, pb, out, g0); break;
+                case 2: flux_float<2>(c, s, a, x, rec, pb, out, g0); break;
+                case 3: flux_float<3>(c, s, a, x, rec, pb, out, g0); break;
+                default: flux_float<4>(c, s, a, x, rec, pb, out, g0); break;
+            }
+            continue;
+        }
         int pr = prof_begin(c, s, RT_KERNEL_FLUX);
         switch (gc) {
             case 1: k_flux<T, 1><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
@@ -379,8 +810,10 @@ rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has
         launch_flux_t<double>(c, s, (const double*)Uin, (double*)Uout, has_alpha);
     } else {
         if (has_src) launch_inject_t<float>(c, s, (float*)Uin);
-        launch_gradient_t<float>(c, s, (float*)Uin);
-        launch_flux_t<float>(c, s, (const float*)Uin, (float*)Uout, has_alpha);
+        // packed rows for the tensor-memory-accelerator pair pass (one group chunk only)
+        const bool packed = c->tune.flux_variant == 2 && c->cfg.n_groups <= kMaxGC && packed_rows_map(c);
+        launch_gradient_t<float>(c, s, (float*)Uin, packed);
+        launch_flux_t<float>(c, s, (const float*)Uin, (float*)Uout, has_alpha, packed);
     }
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;

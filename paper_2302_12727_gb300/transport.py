@@ -12,8 +12,8 @@ import numpy as np
 import torch
 
 from . import (RT_FP32_MIXED, RT_FP64, make_config, rt_adjoint, rt_create, rt_destroy, rt_diagnostics, rt_energy,
-               rt_gradients, rt_neighbours, rt_pairs, rt_particle_fields, rt_set_stream, rt_subcycle,
-               rt_transport_step)
+               rt_get_tuning, rt_gradients, rt_neighbours, rt_pairs, rt_particle_fields, rt_set_stream,
+               rt_set_tuning, rt_subcycle, rt_transport_step)
 
 
 def _dev(a, dtype, device):
@@ -126,6 +126,12 @@ class Transport:
     def diagnostics(self):
         self._sync_stream()
         return rt_diagnostics(self.ctx)
+
+    def set_tuning(self, flux_variant=2, gather_variant=1, gradient_variant=1):
+        rt_set_tuning(self.ctx, flux_variant, gather_variant, gradient_variant)
+
+    def tuning(self):
+        return rt_get_tuning(self.ctx)
 
     def close(self):
         if self.ctx:

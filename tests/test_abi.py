@@ -37,12 +37,12 @@ def test_library_is_sm103a_only():
 def test_config_struct_layout_matches_header(tmp_path):
     """ctypes mirrors of rt_config / rt_diag have the C compiler's size and field offsets."""
     import subprocess
-    from paper_2302_12727_gb300 import rt_config, rt_diag
+    from paper_2302_12727_gb300 import rt_config, rt_diag, rt_tuning
     src = tmp_path / "layout.c"
     fields_c = [f for f, _ in rt_config._fields_]
     fields_d = [f for f, _ in rt_diag._fields_]
     body = ['#include <stdio.h>', '#include <stddef.h>', '#include "rt.h"', "int main(void) {",
-            'printf("%zu %zu\\n", sizeof(rt_config), sizeof(rt_diag));']
+            'printf("%zu %zu %zu\\n", sizeof(rt_config), sizeof(rt_diag), sizeof(rt_tuning));']
     for f in fields_c:
         body.append(f'printf("%zu\\n", offsetof(rt_config, {f}));')
     for f in fields_d:
@@ -54,6 +54,7 @@ def test_config_struct_layout_matches_header(tmp_path):
     out = subprocess.check_output([str(exe)]).decode().split()
     vals = [int(v) for v in out]
     assert vals[0] == ctypes.sizeof(rt_config) and vals[1] == ctypes.sizeof(rt_diag)
-    offs = vals[2:]
+    assert vals[2] == ctypes.sizeof(rt_tuning)
+    offs = vals[3:]
     want = [getattr(rt_config, f).offset for f in fields_c] + [getattr(rt_diag, f).offset for f in fields_d]
     assert offs == want

@@ -359,3 +359,45 @@ def test_sorted_pair_build_on_clustered_particles():
     nbad, rmax = fp64_close(U.cpu().numpy(), ref)
     assert nbad == 0, rmax
     t.close()
+
+
+@pytest.mark.parametrize("G", [3, 5])
+def test_launch_variants_give_identical_results(G):
+    """Every (flux, gather) launch variant of the float pair kernels computes the same fluxes
+    and accumulates them in the same order: results bitwise equal, plain steps and graphs.
+    G = 5 runs two group chunks (4 + 1) per pass."""
+    _need_gpu()
+    from paper_2302_12727_gb300 import RTError as Err
+    w = W.config2(24)
+    rng = np.random.default_rng(31)
+    U0 = np.zeros((G, 4, w.n))
+    U0[:, 0] = rng.uniform(0.1, 1.0, size=(G, w.n))
+    U0[:, 1:] = 0.5 * U0[:, :1] * rng.uniform(-1, 1, size=(G, 3, w.n)) / np.sqrt(3)
+    Ls = rng.uniform(0.5, 2.0, size=(1, G))
+    t = Transport(w.x, w.m, w.xsrc, n_groups=G, precision="fp32", c_red=w.c_red, clamp_negative=True)
+    dt = 0.9 * t.diagnostics()["dx_min"]
+    L = t.luminosities(Ls)
+    al = t.alpha(0.1 * t.fields()["omega"] * torch.as_tensor(w.m, device="cuda"))
+    outs = {}
+    default = t.tuning()
+    for fv in (0, 1, 2):
+        for gv in (0, 1):
+            for rv in (0, 1):
+                t.set_tuning(fv, gv, rv)
+                assert t.tuning() == {"flux_variant": fv, "gather_variant": gv, "gradient_variant": rv}
+                U = t.state(U0)
+                t.subcycle(U, 4, dt, L, al)
+                U2 = t.state(U0)
+                for _ in range(4):
+                    t.step(U2, dt, L, al)
+                assert torch.equal(U, U2)
+                outs[(fv, gv, rv)] = U
+    ref = outs[(0, 0, 0)]
+    for k, v in outs.items():
+        assert torch.equal(v, ref), k
+    t.set_tuning(**default)
+    with pytest.raises(Err):
+        t.set_tuning(3, 0, 0)
+    assert t.tuning() == default
+    assert t.diagnostics()["wait_timeouts"] == 0
+    t.close()
