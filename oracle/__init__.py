@@ -16,6 +16,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import m1_eigen
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rt_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
@@ -39,7 +41,7 @@ class _Cfg(C.Structure):
     _fields_ = [("n_groups", C.c_int32), ("c_red", C.c_double), ("eta_res", C.c_double),
                 ("eta_res_star", C.c_double), ("box", C.c_double * 3), ("periodic", C.c_int32),
                 ("clamp_negative", C.c_int32), ("h_tol", C.c_double), ("h_max_iter", C.c_int32),
-                ("brute_force", C.c_int32)]
+                ("brute_force", C.c_int32), ("riemann", C.c_int32)]
 
 
 _lib = None
@@ -79,6 +81,9 @@ def _load():
         lib.orc_face_states.argtypes = [dp, dp, dp, dp, dp, C.c_double, C.c_double, dp, dp]
         lib.orc_glf_flux.argtypes = [dp, dp, dp, C.c_double, dp]
         lib.orc_get_psi.argtypes = [vp, dp, dp]
+        lib.orc_set_wave_table.argtypes = [vp, dp, dp, C.c_int, C.c_int]
+        lib.orc_hll_flux.argtypes = [vp, dp, dp, dp, dp]
+        lib.orc_wave_speeds.argtypes = [vp, dp, dp, dp, dp]
         _lib = lib
     return _lib
 
@@ -112,7 +117,9 @@ class Oracle:
 
     def __init__(self, x, m, xsrc=None, *, n_groups=1, c_red=1.0, eta_res=1.2348, eta_res_star=1.2348,
                  box=(1.0, 1.0, 1.0), periodic=True, clamp_negative=False, h_tol=1e-15, h_max_iter=200,
-                 brute_force=False):
+                 brute_force=False, riemann="glf", wave_table=None):
+        """riemann: "glf" (Eq. riemann-GLF) or "hll" (Eq. riemann-HLL); for HLL the wave-speed
+        table (lmax, lmin) over (f, theta) defaults to m1_eigen.default_table()."""
         lib = _load()
         self.lib = lib
         self.x = _c(x)
@@ -122,8 +129,10 @@ class Oracle:
         self.n_src = self.xsrc.shape[1]
         self.G = n_groups
         self.c_red = c_red
+        if riemann not in ("glf", "hll"):
+            raise ValueError("riemann must be 'glf' or 'hll'")
         cfg = _Cfg(n_groups, c_red, eta_res, eta_res_star, (C.c_double * 3)(*box), int(periodic),
-                   int(clamp_negative), h_tol, h_max_iter, int(brute_force))
+                   int(clamp_negative), h_tol, h_max_iter, int(brute_force), int(riemann == "hll"))
         st = C.c_int(0)
         self._p = lib.orc_create(C.byref(cfg), self.n, _dp(self.x), _dp(self.m), self.n_src,
                                  _dp(self.xsrc) if self.n_src else _dp(np.zeros(3)), C.byref(st))
@@ -132,6 +141,23 @@ class Oracle:
             self._p = None
             raise OracleError(f"oracle build failed with status {st.value}")
         self._cache = {}
+        if riemann == "hll" or wave_table is not None:
+            self.set_wave_table(*(wave_table if wave_table is not None else m1_eigen.default_table()))
+
+    def set_wave_table(self, lmax, lmin):
+        lmax, lmin = _c(lmax), _c(lmin)
+        self._wt = (lmax, lmin)
+        self.lib.orc_set_wave_table(self._p, _dp(lmax), _dp(lmin), lmax.shape[0], lmax.shape[1])
+
+    def hll_flux(self, uL, uR, A):
+        phi = np.empty(4)
+        self.lib.orc_hll_flux(self._p, _dp(_c(uL)), _dp(_c(uR)), _dp(_c(A)), _dp(phi))
+        return phi
+
+    def wave_speeds(self, u, A):
+        a, b = C.c_double(0), C.c_double(0)
+        self.lib.orc_wave_speeds(self._p, _dp(_c(u)), _dp(_c(A)), C.byref(a), C.byref(b))
+        return a.value, b.value
 
     def __del__(self):
         if getattr(self, "_p", None):

@@ -20,6 +20,8 @@
 //   minmod limiter                        Eq. rt-minmod
 //   M1 closure, Eddington tensor          Eqs. eddington-group (pressure-tensor-group-*)
 //   GLF Riemann flux                      Eq. riemann-GLF
+//   HLL Riemann flux, wave speeds         Eq. riemann-HLL (eigenvalue table supplied by the caller,
+//                                         built in m1_eigen.py from the M1 flux Jacobian)
 //   explicit update                       Eq. transport-update-explicit
 //   injection weights xi, octant mu_a     Sec. "Weights For Distribution Of Energy Density",
 //                                         Eq. isotropy-correction-with-zero
@@ -43,6 +45,9 @@
 //   * M1: f^2 is clamped to <= 1 inside chi; F = 0 gives D = I/3; E <= 0 gives zero pressure.
 //   * grey sink: U <- U * max(0, 1 - c alpha_i dt), alpha_i supplied per particle.
 //   * optional negative-energy fix-up: E <- max(E, 0) after the sink (counted).
+//   * HLL: l+ = max(0, lmax_L, lmax_R), l- = min(0, lmin_L, lmin_R) over both face states;
+//     speeds from the (f, theta) table by bilinear interpolation; E <= 0 gives [-c, c];
+//     F = 0 gives theta = 0; l+ = l- = 0 gives the central flux.
 //
 // Parity unpinned (no closed form or paper value reaches them beyond this code itself):
 //   the exact value of h where neighbour sets are irregular, B_i of ill-conditioned
@@ -75,6 +80,7 @@ struct Config {
     double h_tol;
     int32_t h_max_iter;
     int32_t brute_force;      // 1: O(N^2) neighbour search, 0: cell list
+    int32_t riemann;          // 0: GLF (Eq. riemann-GLF), 1: HLL (Eq. riemann-HLL)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -343,6 +349,9 @@ struct Model {
     std::vector<double> octw;     // 8 per source (w_a)
     long n_ill = 0;
     double cond_max = 0;
+    // HLL wave-speed table over (f, theta) (units of c), given by the caller
+    int wnf = 0, wnth = 0;
+    std::vector<double> wmax, wmin;
 
     double H(long i) const { return kHoverh * h[i]; }
 };
@@ -583,6 +592,67 @@ static void glf_flux(const T uL[4], const T uR[4], const double A[3], double c, 
     for (int q = 0; q < 4; ++q) phi[q] = T(0.5) * (fL[q] + fR[q]) - T(0.5 * c * Anorm) * (uR[q] - uL[q]);
 }
 
+// HLL wave speeds of one face state through A (Eq. riemann-HLL): the largest and smallest
+// eigenvalue of the M1 flux Jacobian along n = A/|A|, looked up in the (f, theta) table
+// with bilinear interpolation; f = |F|/(cE) clipped to 1, cos theta = F . n / |F| (theta = 0
+// for F = 0).  A state with E <= 0 has no closure; it gets the whole light cone [-c, c].
+// The speeds are taken at the state's values (not differentiated).
+static void wave_speeds(const Model& M, const double u[4], const double A[3], double c, double& lmax,
+                        double& lmin) {
+    if (!(u[0] > 0.0)) {
+        lmax = c;
+        lmin = -c;
+        return;
+    }
+    double Fn = std::sqrt(u[1] * u[1] + u[2] * u[2] + u[3] * u[3]);
+    double f = std::min(Fn / (c * u[0]), 1.0);
+    double ct = 1.0;
+    if (Fn > 0.0) {
+        double An = std::sqrt(norm2(A));
+        ct = (u[1] * A[0] + u[2] * A[1] + u[3] * A[2]) / (Fn * An);
+        ct = std::max(-1.0, std::min(1.0, ct));
+    }
+    double theta = std::acos(ct);
+    double x = f * (M.wnf - 1), y = theta / M_PI * (M.wnth - 1);
+    int i = std::min((int)x, M.wnf - 2), j = std::min((int)y, M.wnth - 2);
+    double t = x - i, s = y - j;
+    auto at = [&](const std::vector<double>& T, int a, int b) { return T[(size_t)a * M.wnth + b]; };
+    auto lerp2 = [&](const std::vector<double>& T) {
+        return (1 - t) * (1 - s) * at(T, i, j) + t * (1 - s) * at(T, i + 1, j) + (1 - t) * s * at(T, i, j + 1) +
+               t * s * at(T, i + 1, j + 1);
+    };
+    lmax = c * lerp2(M.wmax);
+    lmin = c * lerp2(M.wmin);
+}
+
+// HLL flux through A, Eq. riemann-HLL, with the M1 flux contracted with A in place of F and
+// |A| on the jump term:  (l+ F_L.A - l- F_R.A + l+ l- |A| (U_R - U_L)) / (l+ - l-),
+// l+ = max(0, lmax_L, lmax_R), l- = min(0, lmin_L, lmin_R).  With l+ = l- = 0 (both states
+// free-streaming exactly along the surface) the central flux 1/2 (F_L + F_R).A is taken.
+template <class T>
+static void hll_flux(const Model& M, const T uL[4], const T uR[4], const double A[3], double c, T phi[4]) {
+    T fL[4], fR[4];
+    m1_flux_dot(uL, A, c, fL);
+    m1_flux_dot(uR, A, c, fR);
+    double vL[4], vR[4];
+    for (int q = 0; q < 4; ++q) {
+        vL[q] = val(uL[q]);
+        vR[q] = val(uR[q]);
+    }
+    double xL, nL, xR, nR;
+    wave_speeds(M, vL, A, c, xL, nL);
+    wave_speeds(M, vR, A, c, xR, nR);
+    double lp = std::max(0.0, std::max(xL, xR));
+    double lm = std::min(0.0, std::min(nL, nR));
+    if (lp - lm > 0.0) {
+        double An = std::sqrt(norm2(A));
+        for (int q = 0; q < 4; ++q)
+            phi[q] = (T(lp) * fL[q] - T(lm) * fR[q] + T(lp * lm * An) * (uR[q] - uL[q])) / T(lp - lm);
+    } else {
+        for (int q = 0; q < 4; ++q) phi[q] = T(0.5) * (fL[q] + fR[q]);
+    }
+}
+
 struct StepStats { long clamped = 0; };
 
 // One time step: injection -> transport -> grey sink (-> optional fix-up).
@@ -628,7 +698,10 @@ static void step(const Model& M, double dt, std::vector<T>& U, const std::vector
                 }
                 T uL[4], uR[4];
                 face_states(uk, ul, gk, gl, d, M.h[k], M.h[l], uL, uR);
-                glf_flux(uL, uR, A, c, phi);
+                if (M.cfg.riemann == 1)
+                    hll_flux(M, uL, uR, A, c, phi);
+                else
+                    glf_flux(uL, uR, A, c, phi);
                 for (int q = 0; q < 4; ++q) acc[4 * g + q] += phi[q];
             }
         }
@@ -671,6 +744,7 @@ struct orc_config {
     double h_tol;
     int32_t h_max_iter;
     int32_t brute_force;
+    int32_t riemann;
 };
 
 void* orc_create(const orc_config* cfg, long n, const double* x, const double* m, long n_src, const double* xsrc,
@@ -686,6 +760,7 @@ void* orc_create(const orc_config* cfg, long n, const double* x, const double* m
     M->cfg.h_tol = cfg->h_tol;
     M->cfg.h_max_iter = cfg->h_max_iter;
     M->cfg.brute_force = cfg->brute_force;
+    M->cfg.riemann = cfg->riemann;
     M->P.n = n;
     for (int a = 0; a < 3; ++a) M->P.box[a] = cfg->box[a];
     M->P.periodic = cfg->periodic != 0;
@@ -889,6 +964,26 @@ void orc_get_psi(void* p, double* psi, double* psi_self) {
 }
 
 double orc_minmod(double a, double b) { return minmod<double>(a, b); }
+
+// HLL wave-speed table (units of c): lmax, lmin [nf][nth] over f = i/(nf-1), theta = j pi/(nth-1)
+void orc_set_wave_table(void* p, const double* lmax, const double* lmin, int nf, int nth) {
+    Model* M = (Model*)p;
+    M->wnf = nf;
+    M->wnth = nth;
+    M->wmax.assign(lmax, lmax + (size_t)nf * nth);
+    M->wmin.assign(lmin, lmin + (size_t)nf * nth);
+}
+
+// HLL flux of one pair and group (uses the model's table and c)
+void orc_hll_flux(void* p, const double* uL, const double* uR, const double* A, double* phi) {
+    Model* M = (Model*)p;
+    hll_flux<double>(*M, uL, uR, A, M->cfg.c_red, phi);
+}
+
+void orc_wave_speeds(void* p, const double* u, const double* A, double* lmax, double* lmin) {
+    Model* M = (Model*)p;
+    wave_speeds(*M, u, A, M->cfg.c_red, *lmax, *lmin);
+}
 
 int orc_num_threads() {
 #ifdef _OPENMP

@@ -390,3 +390,103 @@ def test_plane_wave_converges():
     slope = np.polyfit(np.log(1.0 / np.array(sizes)), np.log(errs), 1)[0]
     assert errs[0] > errs[1] > errs[2]
     assert slope > 1.0, (errs, slope)
+
+
+# ----------------------------------------------------------------------------------------
+# HLL (Eq. riemann-HLL): the wave-speed table and the flux
+
+def _chi_1d(f):
+    """M1 closure chi(f) and d chi / df in closed form (the Eddington factor of Eq. eddington)."""
+    s = math.sqrt(4.0 - 3.0 * f * f)
+    chi = (3.0 + 4.0 * f * f) / (5.0 + 2.0 * s)
+    ds = -3.0 * f / s
+    dchi = (8.0 * f * (5.0 + 2.0 * s) - (3.0 + 4.0 * f * f) * 2.0 * ds) / (5.0 + 2.0 * s) ** 2
+    return chi, dchi
+
+
+def test_wave_table_closed_forms():
+    """f = 0: the Jacobian is [[0, n^T], [n/3, 0]], eigenvalues +-1/sqrt(3) at every angle.
+    theta = 0 (flux along n): the system reduces to the 1-D pair (E, F_n) with P = chi(f) E,
+    whose Jacobian [[0, 1], [chi - f chi', chi']] has eigenvalues
+    (chi' +- sqrt(chi'^2 - 4 (f chi' - chi))) / 2 -- the extremes of the 3-D table there.
+    theta = pi mirrors it: l(f, pi) = -l(f, 0) with max and min swapped."""
+    from oracle import m1_eigen
+    lmax, lmin = m1_eigen.default_table()
+    np.testing.assert_allclose(lmax[0], 1 / math.sqrt(3), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(lmin[0], -1 / math.sqrt(3), rtol=0, atol=1e-14)
+    nf = lmax.shape[0]
+    for i in range(1, nf - 1):
+        f = i / (nf - 1)
+        chi, dchi = _chi_1d(f)
+        root = math.sqrt(dchi * dchi - 4.0 * (f * dchi - chi))
+        assert lmax[i, 0] == pytest.approx((dchi + root) / 2, abs=1e-13)
+        assert lmin[i, 0] == pytest.approx((dchi - root) / 2, abs=1e-13)
+        assert lmax[i, -1] == pytest.approx(-(dchi - root) / 2, abs=1e-13)
+        assert lmin[i, -1] == pytest.approx(-(dchi + root) / 2, abs=1e-13)
+
+
+def test_wave_table_symmetry_and_free_streaming_limit():
+    """Reversing n maps theta to pi - theta and the eigenvalues to their negatives:
+    lmin(f, theta) = -lmax(f, pi - theta).  As f -> 1 all four eigenvalues merge at
+    cos(theta) (free streaming), at the rate ~ sqrt(1 - f) of a coalescing root; the table's
+    f = 1 row is that limit.  All speeds lie within the light cone."""
+    from oracle import m1_eigen
+    lmax, lmin = m1_eigen.default_table()
+    np.testing.assert_allclose(lmin, -lmax[:, ::-1], rtol=0, atol=1e-12)
+    th = np.linspace(0, np.pi, lmax.shape[1])
+    np.testing.assert_allclose(lmax[-1], np.cos(th), rtol=0, atol=1e-15)
+    for f in (1 - 1e-4, 1 - 1e-6):
+        for t in th[::5]:
+            a, b = m1_eigen.eigen_extremes(f, t)
+            assert abs(a - math.cos(t)) <= 1.5 * math.sqrt(1 - f)
+            assert abs(b - math.cos(t)) <= 1.5 * math.sqrt(1 - f)
+    assert np.all(lmax <= 1 + 1e-12) and np.all(lmin >= -1 - 1e-12) and np.all(lmin <= lmax + 1e-12)
+
+
+def _hll_oracle(table=None):
+    w = W.config1()
+    return oracle.Oracle(w.x, w.m, None, n_groups=1, c_red=1.7, riemann="hll", wave_table=table)
+
+
+def test_hll_limits():
+    """Eq. riemann-HLL: with speeds -c and +c it is the GLF flux (the paper's remark); with
+    equal states it is the exact flux F(U) . A (consistency); with both states streaming
+    along n (f = 1, theta = 0, so l- = 0) it is the upwind flux F(U_L) . A."""
+    rng = np.random.default_rng(41)
+    nf = nth = 101
+    o1 = _hll_oracle((np.ones((nf, nth)), -np.ones((nf, nth))))
+    o = _hll_oracle()
+    c = 1.7
+    for _ in range(20):
+        A = rng.normal(size=3) * 1e-2
+        uL = np.r_[rng.uniform(0.1, 2), rng.normal(size=3) * 0.3]
+        uR = np.r_[rng.uniform(0.1, 2), rng.normal(size=3) * 0.3]
+        np.testing.assert_allclose(o1.hll_flux(uL, uR, A), oracle.glf_flux(uL, uR, A, c), rtol=1e-14, atol=1e-18)
+        np.testing.assert_allclose(o.hll_flux(uL, uL, A), oracle.m1_flux(uL, A, c), rtol=1e-14, atol=1e-18)
+        n = A / np.linalg.norm(A)
+        sL = np.r_[1.3, c * 1.3 * n]
+        sR = np.r_[0.4, c * 0.4 * n]
+        # theta = acos(1 - rounding) ~ 1e-8: the interpolated cos(theta) is c to ~1e-10
+        assert o.wave_speeds(sL, A) == pytest.approx((c, c), rel=1e-9)
+        np.testing.assert_allclose(o.hll_flux(sL, sR, A), oracle.m1_flux(sL, A, c), rtol=1e-13, atol=1e-18)
+        # E <= 0: the whole light cone
+        assert o.wave_speeds(np.r_[-1.0, 0.1, 0, 0], A) == (c, -c)
+
+
+def test_hll_transport_conserves_energy_and_is_antisymmetric():
+    """With HLL fluxes the exchange between two particles is still antisymmetric, so
+    sum_i V_i E_i is constant without sources or sinks (Eq. transport-update-explicit)."""
+    rng = np.random.default_rng(42)
+    x = W.jittered_lattice(10, 0.25, rng)
+    n = x.shape[1]
+    o = oracle.Oracle(x, np.full(n, 1.0 / n), None, n_groups=2, riemann="hll")
+    U0 = np.zeros((2, 4, n))
+    U0[:, 0] = rng.uniform(0.5, 2.0, size=(2, n))
+    U0[:, 1:] = 0.6 * U0[:, :1] * rng.uniform(-1, 1, size=(2, 3, n)) / math.sqrt(3)
+    dt = 0.6 * ((o.V / (4 * math.pi / 3)) ** (1 / 3)).min()
+    U, _ = o.run(U0, 5, dt)
+    np.testing.assert_allclose(o.energy(U), o.energy(U0), rtol=1e-13)
+    # HLL is not GLF on the same input
+    og = oracle.Oracle(x, np.full(n, 1.0 / n), None, n_groups=2)
+    Ug, _ = og.run(U0, 5, dt)
+    assert np.abs(Ug - U).max() > 1e-6
