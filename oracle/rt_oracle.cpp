@@ -46,8 +46,8 @@
 //   * grey sink: U <- U * max(0, 1 - c alpha_i dt), alpha_i supplied per particle.
 //   * optional negative-energy fix-up: E <- max(E, 0) after the sink (counted).
 //   * HLL: l+ = max(0, lmax_L, lmax_R), l- = min(0, lmin_L, lmin_R) over both face states;
-//     speeds from the (f, theta) table by bilinear interpolation; E <= 0 gives [-c, c];
-//     F = 0 gives theta = 0; l+ = l- = 0 gives the central flux.
+//     speeds from the (f, theta) table by bilinear interpolation, theta = atan2(|F x A|, F . A)
+//     (0 for F = 0); E <= 0 gives [-c, c]; l+ = l- = 0 gives the central flux.
 //
 // Parity unpinned (no closed form or paper value reaches them beyond this code itself):
 //   the exact value of h where neighbour sets are irregular, B_i of ill-conditioned
@@ -594,8 +594,10 @@ static void glf_flux(const T uL[4], const T uR[4], const double A[3], double c, 
 
 // HLL wave speeds of one face state through A (Eq. riemann-HLL): the largest and smallest
 // eigenvalue of the M1 flux Jacobian along n = A/|A|, looked up in the (f, theta) table
-// with bilinear interpolation; f = |F|/(cE) clipped to 1, cos theta = F . n / |F| (theta = 0
-// for F = 0).  A state with E <= 0 has no closure; it gets the whole light cone [-c, c].
+// with bilinear interpolation; f = |F|/(cE) clipped to 1, theta the angle between F and A,
+// taken as atan2(|F x A|, F . A) (well conditioned at theta = 0 and pi, where acos of the
+// normalised dot product is not).  A state with E <= 0 has no closure; it gets the whole
+// light cone [-c, c].
 // The speeds are taken at the state's values (not differentiated).
 static void wave_speeds(const Model& M, const double u[4], const double A[3], double c, double& lmax,
                         double& lmin) {
@@ -606,13 +608,8 @@ static void wave_speeds(const Model& M, const double u[4], const double A[3], do
     }
     double Fn = std::sqrt(u[1] * u[1] + u[2] * u[2] + u[3] * u[3]);
     double f = std::min(Fn / (c * u[0]), 1.0);
-    double ct = 1.0;
-    if (Fn > 0.0) {
-        double An = std::sqrt(norm2(A));
-        ct = (u[1] * A[0] + u[2] * A[1] + u[3] * A[2]) / (Fn * An);
-        ct = std::max(-1.0, std::min(1.0, ct));
-    }
-    double theta = std::acos(ct);
+    double cx = u[2] * A[2] - u[3] * A[1], cy = u[3] * A[0] - u[1] * A[2], cz = u[1] * A[1] - u[2] * A[0];
+    double theta = std::atan2(std::sqrt(cx * cx + cy * cy + cz * cz), u[1] * A[0] + u[2] * A[1] + u[3] * A[2]);
     double x = f * (M.wnf - 1), y = theta / M_PI * (M.wnth - 1);
     int i = std::min((int)x, M.wnf - 2), j = std::min((int)y, M.wnth - 2);
     double t = x - i, s = y - j;
