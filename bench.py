@@ -173,7 +173,7 @@ def run_ours(args):
     w = workload(args.config)
     G, n_sub, n = w.n_groups, w.n_steps, w.n
     prec = args.precision
-    T = Transport(w.x, w.m, w.xsrc, n_groups=G, c_red=w.c_red, precision=prec, device=dev)
+    T = Transport(w.x, w.m, w.xsrc, n_groups=G, c_red=w.c_red, precision=prec, device=dev, riemann=args.riemann)
     if args.tuning:
         T.set_tuning(*(int(v) for v in args.tuning.split(",")))
     diag = T.diagnostics()
@@ -268,7 +268,7 @@ def run_ours(args):
                        "sources": w.n_src, "pairs": P, "dt": dt, "dt_rule": f"{args.cfl} * min dx / c (Eq. rt-cfl)",
                        "precision": "fp32 fluxes/gradients, fp64 h/E_i/B_i/energy" if prec == "fp32" else "fp64",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
-                       "tuning": T.tuning()},
+                       "tuning": T.tuning(), "riemann": args.riemann},
             "roofline": {"bound": "alu", "kernel": "flux stage (pair flux + gather)",
                          "achieved": achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
@@ -341,7 +341,7 @@ def run_fp64_plain(w, args, dev, ms_fp32, P):
     import torch
     from paper_2302_12727_gb300 import Transport
     G, n_sub = w.n_groups, w.n_steps
-    T = Transport(w.x, w.m, w.xsrc, n_groups=G, c_red=w.c_red, precision="fp64", device=dev)
+    T = Transport(w.x, w.m, w.xsrc, n_groups=G, c_red=w.c_red, precision="fp64", device=dev, riemann=args.riemann)
     d = T.diagnostics()
     dt = args.cfl * d["dx_min"] / w.c_red
     alpha = None
@@ -369,10 +369,10 @@ def run_fp64_plain(w, args, dev, ms_fp32, P):
             "speedup_of_fp32_graph": ms / ms_fp32}
 
 
-def oracle_step_times(w, P, n_src_steps=2):
+def oracle_step_times(w, P, n_src_steps=2, riemann="glf"):
     import oracle
     o_t0 = time.perf_counter()
-    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red, riemann=riemann)
     t_build = time.perf_counter() - o_t0
     dx = (o.V / (4 * np.pi / 3)) ** (1 / 3)
     dt = 0.9 * dx.min() / w.c_red
@@ -384,7 +384,7 @@ def oracle_step_times(w, P, n_src_steps=2):
 
 
 def cpu_baseline(w, args, P):
-    t_build, t_step, cores = oracle_step_times(w, P)
+    t_build, t_step, cores = oracle_step_times(w, P, 2, args.riemann)
     T = t_build + w.n_steps * t_step
     return {"value": P * w.n_groups * w.n_steps / T, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"full {w.n}-particle set: oracle build ({t_build:.2f} s) + 2 of the {w.n_steps} steps "
@@ -403,7 +403,7 @@ def run_reference(args):
     del o
     times = []
     for k in range(args.warmup + args.steps):
-        t_build, t_step, cores = oracle_step_times(w, P, 1)
+        t_build, t_step, cores = oracle_step_times(w, P, 1, args.riemann)
         if k >= args.warmup:
             times.append(t_build + w.n_steps * t_step)
     T = sum(times) / len(times)
@@ -412,7 +412,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": T * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": w.name, "particles": w.n, "groups": w.n_groups, "sub_cycles": w.n_steps,
-                      "pairs": P},
+                      "pairs": P, "riemann": args.riemann},
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"each step: oracle build + 1 of the {w.n_steps} sub-cycle steps timed on the "
                                       f"full {w.n}-particle set, the step time extrapolated to {w.n_steps} sub-cycles"},
@@ -432,6 +432,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
+    ap.add_argument("--riemann", default="glf", choices=["glf", "hll"],
+                    help="pair-flux Riemann solver (Eq. riemann-GLF or Eq. riemann-HLL)")
     ap.add_argument("--tuning", default="", help="flux,gather,gradient variants of the float pair kernels")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -46,6 +46,14 @@ extern "C" {
 
 typedef struct rt_ctx rt_ctx;
 
+/* Riemann solvers of the pair flux (rt_config.riemann_solver). */
+enum { RT_RIEMANN_GLF = 0, RT_RIEMANN_HLL = 1 };
+
+/* Size of the HLL wave-speed table: RT_WAVE_NF values of f = i / (RT_WAVE_NF - 1) by
+ * RT_WAVE_NTH values of theta = j pi / (RT_WAVE_NTH - 1). */
+#define RT_WAVE_NF 101
+#define RT_WAVE_NTH 101
+
 typedef enum {
     RT_OK = 0,
     RT_ERR_INVALID = 1,   /* bad argument or configuration */
@@ -85,6 +93,9 @@ typedef struct {
                                             its pairs and sets a flag that rt_energy reports as
                                             RT_ERR_TIMEOUT (and rt_diag.wait_timeouts) until the
                                             next rt_neighbours */
+    int32_t riemann_solver;  /* RT_RIEMANN_GLF (Eq. riemann-GLF) or RT_RIEMANN_HLL (Eq. riemann-HLL:
+                                wave speeds from the library's M1 eigenvalue table, see
+                                rt_wave_table); rt_adjoint supports GLF only */
 } rt_config;
 
 typedef struct {
@@ -229,6 +240,17 @@ rt_status rt_set_profiling(rt_ctx* ctx, int32_t on);
  * recent rt_transport_step or rt_subcycle call made with profiling on; zeros if none.
  * Synchronises the stream. */
 rt_status rt_kernel_times(rt_ctx* ctx, double* ms_host, int64_t* launches_host);
+
+/* HLL wave speeds (Eq. riemann-HLL): the largest (lmax_host) and smallest (lmin_host)
+ * eigenvalue, in units of c, of the Jacobian of the M1 flux along a unit normal n, for a
+ * state of reduced flux f = |F| / (cE) at angle theta between F and n; row-major host
+ * arrays [RT_WAVE_NF][RT_WAVE_NTH] over the grid above.  The flux transport kernels
+ * interpolate this table bilinearly.  The library derives it on the host, without a context
+ * or a GPU: the Jacobian analytically (the F component normal to the (n, F) plane decouples
+ * with eigenvalue b(f) f cos theta), the remaining 3 x 3 block's characteristic cubic solved
+ * in extended precision and polished by Newton steps; at f = 1 (free streaming) every
+ * eigenvalue equals cos theta.  RT_ERR_INVALID for NULL arrays. */
+rt_status rt_wave_table(double* lmax_host, double* lmin_host);
 
 /* Set (rt_set_tuning) or read (rt_get_tuning) the launch variants of the float pair kernels
  * (host struct, copied).  RT_ERR_INVALID for a variant outside the values listed above; the

@@ -21,19 +21,22 @@ _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4
 
 EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
-            "rt_kernel_times", "rt_set_tuning", "rt_get_tuning", "rt_energy_static", "rt_last_error",
-            "rt_destroy"]
+            "rt_kernel_times", "rt_set_tuning", "rt_get_tuning", "rt_wave_table", "rt_energy_static",
+            "rt_last_error", "rt_destroy"]
 
 RT_ENERGY_STATIC_MAX_GROUPS = 16
 
 RT_KERNEL_INJECT, RT_KERNEL_GRADIENT, RT_KERNEL_FLUX, RT_KERNEL_FLUX_GATHER, RT_KERNEL_KINDS = 0, 1, 2, 3, 4
+RT_RIEMANN_GLF, RT_RIEMANN_HLL = 0, 1
+RT_WAVE_NF, RT_WAVE_NTH = 101, 101
 
 
 class rt_config(C.Structure):
     _fields_ = [("n_groups", C.c_int32), ("c_red", C.c_double), ("eta_res", C.c_double),
                 ("eta_res_star", C.c_double), ("box", C.c_double * 3), ("periodic", C.c_int32),
                 ("precision", C.c_int32), ("clamp_negative", C.c_int32), ("limiter_variant", C.c_int32),
-                ("h_tol", C.c_double), ("h_max_iter", C.c_int32), ("device_wait_budget_cycles", C.c_uint64)]
+                ("h_tol", C.c_double), ("h_max_iter", C.c_int32), ("device_wait_budget_cycles", C.c_uint64),
+                ("riemann_solver", C.c_int32)]
 
 
 class rt_diag(C.Structure):
@@ -88,6 +91,7 @@ def load_library():
     lib.rt_diagnostics.argtypes = [vp, C.POINTER(rt_diag)]
     lib.rt_set_profiling.argtypes = [vp, C.c_int32]
     lib.rt_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    lib.rt_wave_table.argtypes = [dp, dp]
     lib.rt_set_tuning.argtypes = [vp, C.POINTER(rt_tuning)]
     lib.rt_get_tuning.argtypes = [vp, C.POINTER(rt_tuning)]
     lib.rt_energy_static.argtypes = [vp, vp, i64, C.c_int32, C.c_int32, vp, vp]
@@ -124,9 +128,13 @@ def _check(ctx, status):
 
 
 def make_config(n_groups=1, c_red=1.0, eta_res=1.2348, eta_res_star=1.2348, box=(1.0, 1.0, 1.0), periodic=True,
-                precision=RT_FP32_MIXED, clamp_negative=False, h_tol=1e-6, h_max_iter=100) -> rt_config:
+                precision=RT_FP32_MIXED, clamp_negative=False, h_tol=1e-6, h_max_iter=100,
+                riemann="glf") -> rt_config:
+    if riemann not in ("glf", "hll"):
+        raise ValueError("riemann must be 'glf' or 'hll'")
     return rt_config(n_groups, c_red, eta_res, eta_res_star, (C.c_double * 3)(*box), int(periodic), precision,
-                     int(clamp_negative), 0, h_tol, h_max_iter, 0)
+                     int(clamp_negative), 0, h_tol, h_max_iter, 0,
+                     RT_RIEMANN_HLL if riemann == "hll" else RT_RIEMANN_GLF)
 
 
 def rt_create(cfg: rt_config, n: int, n_src: int, stream=None):
@@ -211,6 +219,18 @@ def rt_get_tuning(ctx) -> dict:
     _check(ctx, load_library().rt_get_tuning(ctx, C.byref(t)))
     return {"flux_variant": t.flux_variant, "gather_variant": t.gather_variant,
             "gradient_variant": t.gradient_variant}
+
+
+def rt_wave_table():
+    """The library's HLL wave-speed table (lmax, lmin), [RT_WAVE_NF, RT_WAVE_NTH] in units of c
+    (host computation, no context or GPU)."""
+    import numpy as np
+    lmax = np.empty((RT_WAVE_NF, RT_WAVE_NTH))
+    lmin = np.empty((RT_WAVE_NF, RT_WAVE_NTH))
+    st = load_library().rt_wave_table(lmax.ctypes.data, lmin.ctypes.data)
+    if st != RT_OK:
+        raise RTError(st, "rt_wave_table")
+    return lmax, lmin
 
 
 def rt_energy_static(U, V, n, n_groups, precision, E_out, stream=None):

@@ -146,6 +146,8 @@ rt_status rt_create(const rt_config* cfg, int64_t n, int64_t n_src, void* cuda_s
     if (cfg->precision != RT_FP64 && cfg->precision != RT_FP32_MIXED)
         return fail(c, RT_ERR_INVALID, "precision must be RT_FP64 or RT_FP32_MIXED");
     if (cfg->limiter_variant != 0) return fail(c, RT_ERR_INVALID, "limiter_variant must be 0 (minmod)");
+    if (cfg->riemann_solver != RT_RIEMANN_GLF && cfg->riemann_solver != RT_RIEMANN_HLL)
+        return fail(c, RT_ERR_INVALID, "riemann_solver must be RT_RIEMANN_GLF or RT_RIEMANN_HLL");
     if (cfg->h_tol < 0.0 || cfg->h_tol > 1e-3) return fail(c, RT_ERR_INVALID, "h_tol must be in [0, 1e-3]");
     c->fp64 = cfg->precision == RT_FP64;
     RT_CUDA(c, cudaGetDevice(&c->device));
@@ -154,6 +156,22 @@ rt_status rt_create(const rt_config* cfg, int64_t n, int64_t n_src, void* cuda_s
     RT_TRY(ensure(c, c->flags, 64, "flags"));
     RT_CUDA(c, cudaMemset(c->flags.p, 0, 64));
     RT_TRY(ensure_state(c));
+    if (cfg->riemann_solver == RT_RIEMANN_HLL) {
+        // the wave-speed table, interleaved (lmax, lmin) per node, in working precision
+        const int nodes = RT_WAVE_NF * RT_WAVE_NTH;
+        std::vector<double> lmax(nodes), lmin(nodes);
+        build_wave_table(lmax.data(), lmin.data());
+        RT_TRY(ensure(c, c->wave_t, (size_t)2 * nodes * tsize(c), "wave-speed table"));
+        if (c->fp64) {
+            std::vector<double> t(2 * nodes);
+            for (int k = 0; k < nodes; ++k) t[2 * k] = lmax[k], t[2 * k + 1] = lmin[k];
+            RT_CUDA(c, cudaMemcpy(c->wave_t.p, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> t(2 * nodes);
+            for (int k = 0; k < nodes; ++k) t[2 * k] = (float)lmax[k], t[2 * k + 1] = (float)lmin[k];
+            RT_CUDA(c, cudaMemcpy(c->wave_t.p, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    }
     return RT_OK;
 }
 
@@ -276,6 +294,8 @@ rt_status rt_adjoint(rt_ctx* c, int32_t n_sub, double dt, int32_t ckpt_every, co
     if (!U0 || !dLdU_final || !dLdU0) return fail(c, RT_ERR_INVALID, "NULL array");
     if (n_sub < 1 || n_sub > 100000) return fail(c, RT_ERR_INVALID, "n_sub must be in [1, 100000]");
     if (ckpt_every < 1) return fail(c, RT_ERR_INVALID, "ckpt_every must be >= 1");
+    if (c->cfg.riemann_solver != RT_RIEMANN_GLF)
+        return fail(c, RT_ERR_INVALID, "rt_adjoint differentiates the GLF flux only (riemann_solver = RT_RIEMANN_GLF)");
     if (!std::isfinite(dt) || dt < 0) return fail(c, RT_ERR_INVALID, "dt must be finite and >= 0");
     const int G = c->cfg.n_groups;
     bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
@@ -471,7 +491,7 @@ void rt_destroy(rt_ctx* c) {
                       &c->n_up, &c->up_off, &c->low_slot, &c->pair_ends, &c->pairbuf, &c->flags, &c->red_tmp,
                       &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
                       &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,
-                      &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->frec, &c->alpha_s,
+                      &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->frec, &c->wave_t, &c->alpha_s,
                       &c->L_dev, &c->dt_dev, &c->energy_part, &c->ck, &c->seg, &c->lam_a, &c->lam_b, &c->adj_w,
                       &c->adj_x, &c->adj_ub, &c->adj_gam, &c->adj_lam};
     for (DevBuf* b : bufs) free_buf(*b);

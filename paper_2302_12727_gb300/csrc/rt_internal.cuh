@@ -95,6 +95,7 @@ struct rt_ctx {
     // state records (sorted order, working precision): U [N][4G] (double-buffered), grad U [N][12G]
     rt::DevBuf U_a, U_b, grad_t, alpha_s, L_dev, dt_dev, energy_part;
     rt::DevBuf frec;                                    // packed float flux-input rows (G <= 4)
+    rt::DevBuf wave_t;                                  // HLL wave-speed table, working precision
     CUtensorMap rows_map{};                             // tensor map of frec (tile::gather4)
     const void* rows_map_for = nullptr;
     int64_t rows_map_n = 0;
@@ -124,6 +125,8 @@ namespace rt {
 rt_status fail(rt_ctx* c, rt_status s, const std::string& msg);
 rt_status cuda_fail(rt_ctx* c, cudaError_t e, const char* what);
 rt_status ensure(rt_ctx* c, DevBuf& b, size_t bytes, const char* what);
+// HLL wave speeds over (f, theta), [RT_WAVE_NF][RT_WAVE_NTH] each (rt_hll.cu)
+void build_wave_table(double* lmax, double* lmin);
 // record a start event before a profiled launch (returns the index, or -1 when off)
 int prof_begin(rt_ctx* c, cudaStream_t s, int kind);
 void prof_end(rt_ctx* c, cudaStream_t s, int idx);

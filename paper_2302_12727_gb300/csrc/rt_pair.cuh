@@ -229,13 +229,54 @@ __device__ __forceinline__ void sym_mv(const T M[6], T x, T y, T z, T& ox, T& oy
     oz = M[4] * x + M[5] * y + M[2] * z;
 }
 
+// HLL wave speeds of one face state through A (Eq. riemann-HLL): the largest and smallest
+// eigenvalue of the M1 flux Jacobian along n = A/|A|, bilinear in the (f, theta) table of
+// rt_wave_table (interleaved (lmax, lmin) per node, units of c); f = |F|/(cE) clipped to 1,
+// theta = atan2(|F x A|, F . A) (well conditioned at 0 and pi; 0 for F = 0).  A state with
+// E <= 0 has no closure and gets the whole light cone [-c, c].
+template <class T>
+struct Pair2;
+template <>
+struct Pair2<float> {
+    typedef float2 type;
+};
+template <>
+struct Pair2<double> {
+    typedef double2 type;
+};
+
+template <class T>
+__device__ __forceinline__ void wave_speeds_(const T* __restrict__ tab, T E, T Fx, T Fy, T Fz, T Ax, T Ay, T Az,
+                                             T c, T& lmax, T& lmin) {
+    if (!(E > T(0))) {
+        lmax = c;
+        lmin = -c;
+        return;
+    }
+    const T Fn = sqrt_(Fx * Fx + Fy * Fy + Fz * Fz);
+    const T f = fmin_(Fn / (c * E), T(1));
+    const T cx = Fy * Az - Fz * Ay, cy = Fz * Ax - Fx * Az, cz = Fx * Ay - Fy * Ax;
+    const T th = atan2(sqrt_(cx * cx + cy * cy + cz * cz), Fx * Ax + Fy * Ay + Fz * Az);
+    const T x = f * T(RT_WAVE_NF - 1), y = th / T(3.14159265358979323846) * T(RT_WAVE_NTH - 1);
+    const int i = min((int)x, RT_WAVE_NF - 2), j = min((int)y, RT_WAVE_NTH - 2);
+    const T t = x - T(i), s = y - T(j);
+    typedef typename Pair2<T>::type V;
+    const V* tv = reinterpret_cast<const V*>(tab);
+    const V a = tv[i * RT_WAVE_NTH + j], b = tv[(i + 1) * RT_WAVE_NTH + j];
+    const V d = tv[i * RT_WAVE_NTH + j + 1], e = tv[(i + 1) * RT_WAVE_NTH + j + 1];
+    const T w00 = (T(1) - t) * (T(1) - s), w10 = t * (T(1) - s), w01 = (T(1) - t) * s, w11 = t * s;
+    lmax = c * (w00 * a.x + w10 * b.x + w01 * d.x + w11 * e.x);
+    lmin = c * (w00 * a.y + w10 * b.y + w01 * d.y + w11 * e.y);
+}
+
 // Flux of pair (k, l) for one group, k = this particle as the left state: face states
 // (Eq. rt-riemann-problem with s = minmod(grad Q_k . d, grad Q_l . d)), M1 fluxes
 // (Eq. eddington-group), GLF (Eq. riemann-GLF).  The face states use explicit fma so that
 // the evaluation by l (with -d and the roles swapped) gives exactly -phi.
 template <class T>
 __device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T gk[12], const T gl[12], T dx, T dy,
-                                          T dz, T wk, T wl, T Ax, T Ay, T Az, T diss, T c, T phi[4]) {
+                                          T dz, T wk, T wl, T Ax, T Ay, T Az, T diss, T c, const T* wave, T An,
+                                          T phi[4]) {
     T L[4], R[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -248,6 +289,24 @@ __device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T 
     T fL[4], fR[4];
     m1_dot_(L[0], L[1], L[2], L[3], Ax, Ay, Az, c, fL[0], fL[1], fL[2], fL[3]);
     m1_dot_(R[0], R[1], R[2], R[3], Ax, Ay, Az, c, fR[0], fR[1], fR[2], fR[3]);
+    if (wave) {
+        // HLL (Eq. riemann-HLL): (l+ F_L.A - l- F_R.A + l+ l- |A| (U_R - U_L)) / (l+ - l-),
+        // l+ = max(0, lmax_L, lmax_R), l- = min(0, lmin_L, lmin_R); central flux if l+ = l-
+        T xL, nL, xR, nR;
+        wave_speeds_(wave, L[0], L[1], L[2], L[3], Ax, Ay, Az, c, xL, nL);
+        wave_speeds_(wave, R[0], R[1], R[2], R[3], Ax, Ay, Az, c, xR, nR);
+        const T lp = fmax_(T(0), fmax_(xL, xR)), lm = fmin_(T(0), fmin_(nL, nR));
+        const T den = lp - lm;
+        if (den > T(0)) {
+            const T jm = lp * lm * An;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) phi[q] = (lp * fL[q] - lm * fR[q] + jm * (R[q] - L[q])) / den;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) phi[q] = T(0.5) * (fL[q] + fR[q]);
+        }
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) phi[q] = T(0.5) * (fL[q] + fR[q]) - diss * (R[q] - L[q]);
 }
@@ -255,6 +314,7 @@ __device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T 
 // update parameters of the flux stage
 template <class T>
 struct FluxExtra {
+    const T* wave;                  // HLL wave-speed table (interleaved), or null for GLF
     const T* alpha;                 // sorted, or null
     const double* dt_dev;
     T c;

@@ -251,7 +251,8 @@ __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, con
     for (int q = 0; q < 6; ++q) M[q] = gi8[2 + q] * si + gj8[2 + q] * sj;
     T Ax, Ay, Az;
     sym_mv(M, dx, dy, dz, Ax, Ay, Az);
-    T diss = T(0.5) * x.c * sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+    T An = sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+    T diss = T(0.5) * x.c * An;
     T ih = rcp_(gi8[1] + gj8[1]);
     T wi = gi8[1] * ih, wj = gj8[1] * ih;
     const T* ri = rec + i * RS;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, con
         vload<4>(rj + 4 * gg, uj);
         vload<12>(qi + 12 * gg, gri);
         vload<12>(qj + 12 * gg, grj);
-        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, &out[4 * g]);
+        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
     }
     vstore<NC>(pairbuf + slot * NC, out);
 }
@@ -400,7 +401,8 @@ __global__ void __launch_bounds__(128) k_flux_staged(PairArgs<float> a, FluxExtr
     for (int q = 0; q < 6; ++q) M[q] = gi8[2 + q] * si + gj8[2 + q] * sj;
     float Ax, Ay, Az;
     sym_mv(M, dx, dy, dz, Ax, Ay, Az);
-    float diss = 0.5f * x.c * sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+    float An = sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+    float diss = 0.5f * x.c * An;
     float ih = rcp_(gi8[1] + gj8[1]);
     float wi = gi8[1] * ih, wj = gj8[1] * ih;
     const float* ri = rec + i * RS;
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(128) k_flux_staged(PairArgs<float> a, FluxExtr
         vload<4>(mine + 12 + 4 * g, uj);
         vload<12>(qi + 12 * gg, gri);
         vload<12>(mine + 12 + 4 * GC + 12 * g, grj);
-        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, &out[4 * g]);
+        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
     }
     if (act) vstore<NC>(pairbuf + slot * NC, out);
 }
@@ -486,7 +488,8 @@ __global__ void __launch_bounds__(128) k_flux_tma(PairArgs<float> a, FluxExtra<f
     for (int k = 0; k < 6; ++k) M[k] = gi8[2 + k] * si + gj8[2 + k] * sj;
     float Ax, Ay, Az;
     sym_mv(M, dx, dy, dz, Ax, Ay, Az);
-    float diss = 0.5f * x.c * sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+    float An = sqrt_(Ax * Ax + Ay * Ay + Az * Az);
+    float diss = 0.5f * x.c * An;
     float ih = rcp_(gi8[1] + gj8[1]);
     float wi = gi8[1] * ih, wj = gj8[1] * ih;
     float out[NC];
@@ -497,7 +500,7 @@ __global__ void __launch_bounds__(128) k_flux_tma(PairArgs<float> a, FluxExtra<f
         vload<4>(rl + 12 + 4 * g, uj);
         vload<12>(rk + 12 + 4 * G + 12 * g, gri);
         vload<12>(rl + 12 + 4 * G + 12 * g, grj);
-        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, &out[4 * g]);
+        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
     }
     if (act) vstore<NC>(pairbuf + slot * NC, out);
 }
@@ -738,6 +741,7 @@ static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool 
     PairArgs<T> a = pair_args<T>(c);
     if (packed) a.frec = c->frec.as<T>();
     FluxExtra<T> x;
+    x.wave = c->cfg.riemann_solver == RT_RIEMANN_HLL ? c->wave_t.as<T>() : nullptr;
     x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
     x.dt_dev = c->dt_dev.as<double>();
     x.c = (T)c->cfg.c_red;

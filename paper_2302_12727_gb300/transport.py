@@ -33,7 +33,7 @@ class Transport:
 
     def __init__(self, x, m=None, xsrc=None, *, n_groups=1, c_red=1.0, eta_res=1.2348, eta_res_star=None,
                  box=(1.0, 1.0, 1.0), periodic=True, precision="fp32", clamp_negative=False, h_tol=1e-6,
-                 h_max_iter=100, device="cuda:0"):
+                 h_max_iter=100, device="cuda:0", riemann="glf"):
         self.device = torch.device(device)
         self.x = _dev(x, torch.float64, self.device)
         self.n = int(self.x.shape[1])
@@ -46,7 +46,7 @@ class Transport:
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.cfg = make_config(self.G, c_red, eta_res, eta_res if eta_res_star is None else eta_res_star, box,
                                periodic, RT_FP64 if precision == "fp64" else RT_FP32_MIXED, clamp_negative, h_tol,
-                               h_max_iter)
+                               h_max_iter, riemann)
         self.c_red = c_red
         self.ctx = None
         with torch.cuda.device(self.device):
