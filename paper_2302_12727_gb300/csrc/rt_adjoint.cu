@@ -1,5 +1,5 @@
 // Reverse-mode derivative of n sub-cycles of the transport step (no counterpart in the
-// thesis; SURVEY row a11).  Given lambda = dL/dU(final) it returns dL/dU0 and dL/dL_src.
+// thesis).  Given lambda = dL/dU(final) it returns dL/dU0 and dL/dL_src.
 //
 // One forward step is  U_inj = U + inj(L);  g = grad(U_inj);  Phi_kl = flux(U_inj, g);
 // U~_i = U_inj,i - dt omega_i (sum_{k=i} Phi - sum_{l=i} Phi);  U'_i = U~_i sink_i.
