@@ -258,6 +258,23 @@ rt_status rt_wave_table(double* lmax_host, double* lmin_host);
 rt_status rt_set_tuning(rt_ctx* ctx, const rt_tuning* tuning);
 rt_status rt_get_tuning(const rt_ctx* ctx, rt_tuning* tuning);
 
+/* Number of launch-variant combinations rt_autotune tries: candidate k is
+ * {flux_variant k / 4, gather_variant (k / 2) % 2, gradient_variant k % 2}. */
+#define RT_TUNE_CANDIDATES 12
+
+/* Autotuner (no paper counterpart): times n_sub plain transport steps of every candidate
+ * launch-variant combination on the caller's state U_dev (4G x N, caller order, element
+ * type per precision; read only) with luminosities Lsrc_dev (S x G or NULL) and absorption
+ * alpha_dev (N or NULL), on the context's stream with CUDA events, keeping the fastest of
+ * `repeats` repetitions (after one warm-up) per candidate; then adopts the fastest candidate
+ * (as rt_set_tuning, dropping captured graphs) and returns it in *best (host struct).
+ * ms_out (host, RT_TUNE_CANDIDATES doubles, may be NULL) receives each candidate's time.
+ * The double path has one variant: every entry repeats the first.  Synchronises the
+ * stream; uses the context's state buffers, so it must not overlap other calls on the
+ * context.  RT_ERR_INVALID for n_sub outside [1, 1000] or repeats outside [1, 100]. */
+rt_status rt_autotune(rt_ctx* ctx, const void* U_dev, double dt, int32_t n_sub, const double* Lsrc_dev,
+                      const double* alpha_dev, int32_t repeats, rt_tuning* best, double* ms_out);
+
 /* Message of the last failure ("" if none).  Valid until the next call on ctx. */
 const char* rt_last_error(const rt_ctx* ctx);
 

@@ -21,14 +21,15 @@ _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4
 
 EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
-            "rt_kernel_times", "rt_set_tuning", "rt_get_tuning", "rt_wave_table", "rt_energy_static",
-            "rt_last_error", "rt_destroy"]
+            "rt_kernel_times", "rt_set_tuning", "rt_get_tuning", "rt_autotune", "rt_wave_table",
+            "rt_energy_static", "rt_last_error", "rt_destroy"]
 
 RT_ENERGY_STATIC_MAX_GROUPS = 16
 
 RT_KERNEL_INJECT, RT_KERNEL_GRADIENT, RT_KERNEL_FLUX, RT_KERNEL_FLUX_GATHER, RT_KERNEL_KINDS = 0, 1, 2, 3, 4
 RT_RIEMANN_GLF, RT_RIEMANN_HLL = 0, 1
 RT_WAVE_NF, RT_WAVE_NTH = 101, 101
+RT_TUNE_CANDIDATES = 12
 
 
 class rt_config(C.Structure):
@@ -94,6 +95,8 @@ def load_library():
     lib.rt_wave_table.argtypes = [dp, dp]
     lib.rt_set_tuning.argtypes = [vp, C.POINTER(rt_tuning)]
     lib.rt_get_tuning.argtypes = [vp, C.POINTER(rt_tuning)]
+    lib.rt_autotune.argtypes = [vp, dp, C.c_double, C.c_int32, dp, dp, C.c_int32, C.POINTER(rt_tuning),
+                                C.POINTER(C.c_double)]
     lib.rt_energy_static.argtypes = [vp, vp, i64, C.c_int32, C.c_int32, vp, vp]
     lib.rt_last_error.argtypes = [vp]
     lib.rt_last_error.restype = C.c_char_p
@@ -219,6 +222,17 @@ def rt_get_tuning(ctx) -> dict:
     _check(ctx, load_library().rt_get_tuning(ctx, C.byref(t)))
     return {"flux_variant": t.flux_variant, "gather_variant": t.gather_variant,
             "gradient_variant": t.gradient_variant}
+
+
+def rt_autotune(ctx, U, dt, n_sub, Lsrc=None, alpha=None, repeats=3):
+    """Times every launch-variant candidate on U and adopts the fastest:
+    returns ({flux_variant, gather_variant, gradient_variant}, [ms per candidate])."""
+    t = rt_tuning()
+    ms = (C.c_double * RT_TUNE_CANDIDATES)()
+    _check(ctx, load_library().rt_autotune(ctx, _ptr(U), float(dt), int(n_sub), _ptr(Lsrc), _ptr(alpha),
+                                           int(repeats), C.byref(t), ms))
+    return ({"flux_variant": t.flux_variant, "gather_variant": t.gather_variant,
+             "gradient_variant": t.gradient_variant}, list(ms))
 
 
 def rt_wave_table():

@@ -1,0 +1,74 @@
+"""Driver of the library's autotuner with a JSON cache.
+
+``rt_autotune`` times every launch-variant combination of the float pair kernels (the
+``rt_tuning`` space: pair-flux variant, gather variant, gradient variant; all give the same
+result bits) on the caller's workload and adopts the fastest.  This module keys the
+outcome by the workload's shape -- particles N, groups G, pairs P, Riemann solver and
+precision -- and stores it in a JSON file, so that later runs of the same shape apply the
+cached choice without timing again.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import rt_autotune, rt_diagnostics, rt_set_tuning
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tune_cache.json")
+
+
+def shape_key(n: int, G: int, pairs: int, riemann: str, precision: str) -> str:
+    return f"N={n};G={G};P={pairs};riemann={riemann};precision={precision}"
+
+
+def load_cache(path: str) -> dict:
+    if not os.path.exists(path):
+        return {}
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def store_cache(path: str, cache: dict) -> None:
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def lookup_or_tune(key: str, tune, apply, cache_path: str = DEFAULT_CACHE, retune: bool = False) -> dict:
+    """Apply the cached tuning for `key`, or call `tune()` -> (tuning, ms list), cache it and
+    apply it.  Returns the cache entry ({"tuning": ..., "ms": ..., "source": ...})."""
+    cache = load_cache(cache_path)
+    entry = cache.get(key)
+    if entry is not None and not retune:
+        apply(entry["tuning"])
+        return dict(entry, source="cache")
+    tuning, ms = tune()
+    entry = {"tuning": tuning, "ms": ms}
+    cache[key] = entry
+    store_cache(cache_path, cache)
+    apply(tuning)
+    return dict(entry, source="measured")
+
+
+def autotune(transport, U, dt, n_sub, L=None, alpha=None, repeats=3, cache_path: str = DEFAULT_CACHE,
+             retune: bool = False) -> dict:
+    """Tune a ``Transport`` on the device state U (torch tensor [G, 4, N])."""
+    d = rt_diagnostics(transport.ctx)
+    key = shape_key(transport.n, transport.G, d["n_pairs"], transport.riemann, transport.precision)
+
+    def tune():
+        transport._sync_stream()
+        return rt_autotune(transport.ctx, U, dt, n_sub, L, alpha, repeats)
+
+    def apply(t):
+        rt_set_tuning(transport.ctx, t["flux_variant"], t["gather_variant"], t["gradient_variant"])
+
+    out = lookup_or_tune(key, tune, apply, cache_path, retune)
+    out["key"] = key
+    return out

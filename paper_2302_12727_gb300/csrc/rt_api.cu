@@ -471,6 +471,68 @@ rt_status rt_set_tuning(rt_ctx* c, const rt_tuning* t) {
     return RT_OK;
 }
 
+rt_status rt_autotune(rt_ctx* c, const void* U, double dt, int32_t n_sub, const double* Lsrc, const double* alpha,
+                      int32_t repeats, rt_tuning* best, double* ms_out) {
+    RT_TRY(check_ready(c));
+    if (!U || !best) return fail(c, RT_ERR_INVALID, "rt_autotune: NULL U or best");
+    if (n_sub < 1 || n_sub > 1000) return fail(c, RT_ERR_INVALID, "rt_autotune: n_sub must be in [1, 1000]");
+    if (repeats < 1 || repeats > 100) return fail(c, RT_ERR_INVALID, "rt_autotune: repeats must be in [1, 100]");
+    if (!std::isfinite(dt) || dt < 0) return fail(c, RT_ERR_INVALID, "dt must be finite and >= 0");
+    const int G = c->cfg.n_groups;
+    const bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
+    const bool has_alpha = alpha != nullptr;
+    RT_TRY(set_step_inputs(c, dt, Lsrc, alpha));
+    const rt_tuning saved = c->tune;
+    int best_k = -1;
+    double best_ms = 0.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rt_status st = RT_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        st = fail(c, RT_ERR_CUDA, "rt_autotune: cudaEventCreate failed");
+    }
+    for (int k = 0; k < RT_TUNE_CANDIDATES && st == RT_OK; ++k) {
+        // candidate k: flux variant k / 4, gather variant (k / 2) % 2, gradient variant k % 2
+        c->tune = rt_tuning{k / 4, (k / 2) % 2, k % 2};
+        if (c->fp64 && k > 0) {       // the double path has one variant
+            if (ms_out) ms_out[k] = ms_out[0];
+            continue;
+        }
+        double kbest = 0.0;
+        for (int r = 0; r <= repeats && st == RT_OK; ++r) {   // r = 0 warms up
+            st = state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0);
+            if (st != RT_OK) break;
+            void* a = c->U_a.p;
+            void* b = c->U_b.p;
+            if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(c, RT_ERR_CUDA, "cudaEventRecord");
+            for (int i = 0; i < n_sub && st == RT_OK; ++i) {
+                st = launch_step(c, c->stream, a, b, has_src, has_alpha);
+                std::swap(a, b);
+            }
+            if (st != RT_OK) break;
+            float t = 0.f;
+            if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+                st = fail(c, RT_ERR_CUDA, "rt_autotune: event timing failed");
+                break;
+            }
+            if (r == 1 || (r > 1 && t < kbest)) kbest = t;
+        }
+        if (st != RT_OK) break;
+        if (ms_out) ms_out[k] = kbest;
+        if (best_k < 0 || kbest < best_ms) {
+            best_k = k;
+            best_ms = kbest;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c->tune = saved;
+    if (st != RT_OK) return st;
+    const rt_tuning win = c->fp64 ? saved : rt_tuning{best_k / 4, (best_k / 2) % 2, best_k % 2};
+    *best = win;
+    return rt_set_tuning(c, &win);
+}
+
 rt_status rt_get_tuning(const rt_ctx* c, rt_tuning* t) {
     if (!c || !t) return RT_ERR_INVALID;
     *t = c->tune;

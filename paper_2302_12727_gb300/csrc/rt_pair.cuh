@@ -273,7 +273,7 @@ __device__ __forceinline__ void wave_speeds_(const T* __restrict__ tab, T E, T F
 // (Eq. rt-riemann-problem with s = minmod(grad Q_k . d, grad Q_l . d)), M1 fluxes
 // (Eq. eddington-group), GLF (Eq. riemann-GLF).  The face states use explicit fma so that
 // the evaluation by l (with -d and the roles swapped) gives exactly -phi.
-template <class T>
+template <bool HLL, class T>
 __device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T gk[12], const T gl[12], T dx, T dy,
                                           T dz, T wk, T wl, T Ax, T Ay, T Az, T diss, T c, const T* wave, T An,
                                           T phi[4]) {
@@ -289,7 +289,7 @@ __device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T 
     T fL[4], fR[4];
     m1_dot_(L[0], L[1], L[2], L[3], Ax, Ay, Az, c, fL[0], fL[1], fL[2], fL[3]);
     m1_dot_(R[0], R[1], R[2], R[3], Ax, Ay, Az, c, fR[0], fR[1], fR[2], fR[3]);
-    if (wave) {
+    if constexpr (HLL) {
         // HLL (Eq. riemann-HLL): (l+ F_L.A - l- F_R.A + l+ l- |A| (U_R - U_L)) / (l+ - l-),
         // l+ = max(0, lmax_L, lmax_R), l- = min(0, lmin_L, lmin_R); central flux if l+ = l-
         T xL, nL, xR, nR;
@@ -314,7 +314,7 @@ __device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T 
 // update parameters of the flux stage
 template <class T>
 struct FluxExtra {
-    const T* wave;                  // HLL wave-speed table (interleaved), or null for GLF
+    const T* wave;                  // HLL wave-speed table (interleaved); unused by the GLF kernels
     const T* alpha;                 // sorted, or null
     const double* dt_dev;
     T c;

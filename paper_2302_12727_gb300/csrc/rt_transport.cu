@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) k_gradient_g(PairArgs<float> a, const flo
 
 // Pass 1 of the flux: one thread per unordered pair (k, l), k < l, evaluates Phi_kl once with
 // k as the left state and stores it in the pair's slot.
-template <class T, int GC>
+template <class T, int GC, bool HLL>
 __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ rec,
                                               T* __restrict__ pairbuf, int g0) {
     const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, con
         vload<4>(rj + 4 * gg, uj);
         vload<12>(qi + 12 * gg, gri);
         vload<12>(qj + 12 * gg, grj);
-        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
+        pair_flux<HLL>(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
     }
     vstore<NC>(pairbuf + slot * NC, out);
 }
@@ -345,7 +345,7 @@ struct Staged {
     static constexpr size_t bytes = (size_t)WARPS * 32 * RW * sizeof(float);
 };
 
-template <int GC>
+template <int GC, bool HLL>
 __global__ void __launch_bounds__(128) k_flux_staged(PairArgs<float> a, FluxExtra<float> x,
                                                      const float* __restrict__ rec, float* __restrict__ pairbuf,
                                                      int g0) {
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(128) k_flux_staged(PairArgs<float> a, FluxExtr
         vload<4>(mine + 12 + 4 * g, uj);
         vload<12>(qi + 12 * gg, gri);
         vload<12>(mine + 12 + 4 * GC + 12 * g, grj);
-        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
+        pair_flux<HLL>(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
     }
     if (act) vstore<NC>(pairbuf + slot * NC, out);
 }
@@ -436,7 +436,7 @@ struct PackedRows {
     static constexpr uint32_t bytes = 32u * RW * 4u;    // bytes gathered per warp
 };
 
-template <int G>
+template <int G, bool HLL>
 __global__ void __launch_bounds__(128) k_flux_tma(PairArgs<float> a, FluxExtra<float> x,
                                                   float* __restrict__ pairbuf,
                                                   const __grid_constant__ CUtensorMap rows, int* err_flag,
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(128) k_flux_tma(PairArgs<float> a, FluxExtra<f
         vload<4>(rl + 12 + 4 * g, uj);
         vload<12>(rk + 12 + 4 * G + 12 * g, gri);
         vload<12>(rl + 12 + 4 * G + 12 * g, grj);
-        pair_flux(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
+        pair_flux<HLL>(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
     }
     if (act) vstore<NC>(pairbuf + slot * NC, out);
 }
@@ -618,8 +618,11 @@ static void set_carveouts() {
     if (done) return;
     done = true;
     const void* fs[] = {(const void*)k_gradient<T, 1>, (const void*)k_gradient<T, 2>, (const void*)k_gradient<T, 3>,
-                        (const void*)k_gradient<T, 4>, (const void*)k_flux<T, 1>,     (const void*)k_flux<T, 2>,
-                        (const void*)k_flux<T, 3>,     (const void*)k_flux<T, 4>,
+                        (const void*)k_gradient<T, 4>, (const void*)k_flux<T, 1, false>,
+                        (const void*)k_flux<T, 2, false>, (const void*)k_flux<T, 3, false>,
+                        (const void*)k_flux<T, 4, false>, (const void*)k_flux<T, 1, true>,
+                        (const void*)k_flux<T, 2, true>, (const void*)k_flux<T, 3, true>,
+                        (const void*)k_flux<T, 4, true>,
                         (const void*)k_flux_gather<T, 1>, (const void*)k_flux_gather<T, 2>,
                         (const void*)k_flux_gather<T, 3>, (const void*)k_flux_gather<T, 4>};
     for (const void* f : fs) cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
@@ -700,16 +703,16 @@ static bool packed_rows_map(rt_ctx* c) {
 }
 
 // float pass 1 and 2 in the variants chosen by the context's tuning
-template <int GC>
+template <int GC, bool HLL>
 static void flux_float(rt_ctx* c, cudaStream_t s, const PairArgs<float>& a, const FluxExtra<float>& x,
                        const float* rec, float* pb, float* out, int g0) {
     static bool attr = false;
     if (!attr) {
         attr = true;
-        cudaFuncSetAttribute((const void*)k_flux_staged<GC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute((const void*)k_flux_staged<GC, HLL>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         cudaFuncSetAttribute((const void*)k_flux_gather_g<GC>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        cudaFuncSetAttribute((const void*)k_flux_tma<GC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute((const void*)k_flux_tma<GC, HLL>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         (void)cudaGetLastError();
     }
@@ -720,11 +723,11 @@ static void flux_float(rt_ctx* c, cudaStream_t s, const PairArgs<float>& a, cons
     if (variant == 2) {
         unsigned long long budget = c->cfg.device_wait_budget_cycles ? c->cfg.device_wait_budget_cycles
                                                                      : 4000000000ull;
-        k_flux_tma<GC><<<npb, 128, 0, s>>>(a, x, pb, c->rows_map, c->flags.as<int>() + F_TIMEOUT, budget);
+        k_flux_tma<GC, HLL><<<npb, 128, 0, s>>>(a, x, pb, c->rows_map, c->flags.as<int>() + F_TIMEOUT, budget);
     } else if (variant == 1) {
-        k_flux_staged<GC><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);
+        k_flux_staged<GC, HLL><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);
     } else {
-        k_flux<float, GC><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);
+        k_flux<float, GC, HLL><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);
     }
     prof_end(c, s, pr);
     pr = prof_begin(c, s, RT_KERNEL_FLUX_GATHER);
@@ -741,7 +744,8 @@ static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool 
     PairArgs<T> a = pair_args<T>(c);
     if (packed) a.frec = c->frec.as<T>();
     FluxExtra<T> x;
-    x.wave = c->cfg.riemann_solver == RT_RIEMANN_HLL ? c->wave_t.as<T>() : nullptr;
+    const bool hll = c->cfg.riemann_solver == RT_RIEMANN_HLL;
+    x.wave = hll ? c->wave_t.as<T>() : nullptr;
     x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
     x.dt_dev = c->dt_dev.as<double>();
     x.c = (T)c->cfg.c_red;
@@ -754,20 +758,38 @@ static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool 
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
         if constexpr (std::is_same<T, float>::value) {
-            switch (gc) {
-                case 1: flux_float<1>(c, s, a, x, rec, pb, out, g0); break;
-                case 2: flux_float<2>(c, s, a, x, rec, pb, out, g0); break;
-                case 3: flux_float<3>(c, s, a, x, rec, pb, out, g0); break;
-                default: flux_float<4>(c, s, a, x, rec, pb, out, g0); break;
+            if (hll) {
+                switch (gc) {
+                    case 1: flux_float<1, true>(c, s, a, x, rec, pb, out, g0); break;
+                    case 2: flux_float<2, true>(c, s, a, x, rec, pb, out, g0); break;
+                    case 3: flux_float<3, true>(c, s, a, x, rec, pb, out, g0); break;
+                    default: flux_float<4, true>(c, s, a, x, rec, pb, out, g0); break;
+                }
+            } else {
+                switch (gc) {
+                    case 1: flux_float<1, false>(c, s, a, x, rec, pb, out, g0); break;
+                    case 2: flux_float<2, false>(c, s, a, x, rec, pb, out, g0); break;
+                    case 3: flux_float<3, false>(c, s, a, x, rec, pb, out, g0); break;
+                    default: flux_float<4, false>(c, s, a, x, rec, pb, out, g0); break;
+                }
             }
             continue;
         }
         int pr = prof_begin(c, s, RT_KERNEL_FLUX);
-        switch (gc) {
-            case 1: k_flux<T, 1><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
-            case 2: k_flux<T, 2><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
-            case 3: k_flux<T, 3><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
-            default: k_flux<T, 4><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+        if (hll) {
+            switch (gc) {
+                case 1: k_flux<T, 1, true><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+                case 2: k_flux<T, 2, true><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+                case 3: k_flux<T, 3, true><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+                default: k_flux<T, 4, true><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+            }
+        } else {
+            switch (gc) {
+                case 1: k_flux<T, 1, false><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+                case 2: k_flux<T, 2, false><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+                case 3: k_flux<T, 3, false><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+                default: k_flux<T, 4, false><<<npb, 128, 0, s>>>(a, x, rec, pb, g0); break;
+            }
         }
         prof_end(c, s, pr);
         pr = prof_begin(c, s, RT_KERNEL_FLUX_GATHER);

@@ -43,6 +43,7 @@ class Transport:
         self.n_src = int(self.xsrc.shape[1])
         self.G = int(n_groups)
         self.precision = precision
+        self.riemann = riemann
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.cfg = make_config(self.G, c_red, eta_res, eta_res if eta_res_star is None else eta_res_star, box,
                                periodic, RT_FP64 if precision == "fp64" else RT_FP32_MIXED, clamp_negative, h_tol,

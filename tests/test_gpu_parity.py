@@ -401,3 +401,34 @@ def test_launch_variants_give_identical_results(G):
     assert t.tuning() == default
     assert t.diagnostics()["wait_timeouts"] == 0
     t.close()
+
+
+def test_autotune_adopts_a_candidate_with_identical_results(tmp_path):
+    """rt_autotune times all launch-variant candidates, adopts the fastest, and the result of
+    a sub-cycle run is unchanged (all candidates compute the same bits)."""
+    _need_gpu()
+    from paper_2302_12727_gb300 import RT_TUNE_CANDIDATES, rt_autotune
+    from paper_2302_12727_gb300.autotune import autotune
+    w = W.config2(24)
+    for prec in ("fp32", "fp64"):
+        t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision=prec, c_red=w.c_red)
+        dt = 0.9 * t.diagnostics()["dx_min"]
+        L = t.luminosities(w.Lsrc)
+        U0 = t.state(w.U0)
+        ref = U0.clone()
+        t.subcycle(ref, 4, dt, L)
+        best, ms = rt_autotune(t.ctx, U0, dt, 3, L, None, 2)
+        assert len(ms) == RT_TUNE_CANDIDATES and all(m > 0 for m in ms)
+        assert t.tuning() == best
+        if prec == "fp32":
+            k = 4 * best["flux_variant"] + 2 * best["gather_variant"] + best["gradient_variant"]
+            assert ms[k] == min(ms)
+        U = U0.clone()
+        t.subcycle(U, 4, dt, L)
+        assert torch.equal(U, ref)
+        # the driver: measured once, then served from its cache
+        path = str(tmp_path / f"cache_{prec}.json")
+        e1 = autotune(t, U0, dt, 3, L, cache_path=path)
+        e2 = autotune(t, U0, dt, 3, L, cache_path=path)
+        assert e1["source"] == "measured" and e2["source"] == "cache" and e2["tuning"] == e1["tuning"]
+        t.close()
