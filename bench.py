@@ -119,14 +119,14 @@ class ClockSampler:
 
 
 def flux_traffic_from_profile(G):
-    """DRAM bytes of one flux stage (pair pass + gather) from the committed ncu summary, if
-    it was taken on the current source of the kernels (else None)."""
+    """DRAM bytes of one pair-pass launch from the committed ncu summary, if it was taken on
+    the current source of the kernels (else None)."""
     path = os.path.join(ROOT, "profiles", "k_flux_poisson-sine-64^3-G3.md")
     csrc = os.path.join(ROOT, "paper_2302_12727_gb300", "csrc")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m = re.search(r"pair_pass_dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"source_sha1:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
@@ -249,14 +249,19 @@ def run_ours(args):
     out = None
     if rank == 0:
         hbm_gbs, sm_max_mhz, peak_kind = measured_peaks()
-        # per sub-cycle: the flux stage is one pair-flux launch and one gather launch per group chunk
+        # per sub-cycle: one pair-pass launch and one gather launch per group chunk (G <= 4: one)
         n_sc = args.steps * n_sub
         flux_avg_s = kflux_ms / n_sc / 1e3
         grad_avg_s = kgrad_ms / n_sc / 1e3
+        pair_avg_s = kpair_ms / kflux_n / 1e3 if kflux_n else None    # one launch of the pair pass
         alu_peak = 152 * 128 * 2 * 2070e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x max clock
         flux_flops = P * flux_flops_per_pair(G)
-        achieved = flux_flops / flux_avg_s / 1e12 if kflux_n else None
-        traffic = flux_traffic_from_profile(G) if (args.config == 2 and prec == "fp32") else None
+        achieved = flux_flops / pair_avg_s / 1e12 if kflux_n else None
+        tune = T.tuning()
+        default_shape = (args.config == 2 and prec == "fp32" and args.riemann == "glf"
+                         and tune == {"flux_variant": 2, "gather_variant": 1, "gradient_variant": 1})
+        traffic = flux_traffic_from_profile(G) if default_shape else None
+        pair_kernel = {0: "k_flux", 1: "k_flux_staged", 2: "k_flux_tma"}[tune["flux_variant"]]
         sub_s = (kflux_ms + kgrad_ms) / 1e3 / args.steps
         out = {
             "metric": METRIC,
@@ -276,13 +281,16 @@ def run_ours(args):
                        "precision": "fp32 fluxes/gradients, fp64 h/E_i/B_i/energy" if prec == "fp32" else "fp64",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
                        "tuning": T.tuning(), "tuning_source": tune_info.get("source"), "riemann": args.riemann},
-            "roofline": {"bound": "alu", "kernel": "flux stage (pair flux + gather)",
+            "roofline": {"bound": "alu", "kernel": f"{pair_kernel} (pair pass)",
                          "achieved": achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
                          "traffic": traffic, "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                         "flops_per_subcycle": flux_flops, "avg_subcycle_ms": flux_avg_s * 1e3,
-                         "hbm_frac_of_" + peak_kind: (flux_bytes_per_particle(G) * n / flux_avg_s / 1e9) / hbm_gbs
-                         if kflux_n else None},
+                         "flops_per_launch": flux_flops, "avg_launch_ms": pair_avg_s * 1e3 if pair_avg_s else None,
+                         "hbm_frac_of_" + peak_kind: (flux_bytes_per_particle(G) * n / pair_avg_s / 1e9) / hbm_gbs
+                         if kflux_n else None,
+                         "traffic_note": "ncu DRAM read + write of one pair-pass launch (cold cache), from "
+                                         "profiles/k_flux_poisson-sine-64^3-G3.md; null unless the kernel "
+                                         "sources and the launch variants match that capture"},
             "kernels": {"flux_stage_ms_per_subcycle": flux_avg_s * 1e3, "gradient_ms_per_subcycle": grad_avg_s * 1e3,
                         "pair_flux_ms_per_subcycle": kpair_ms / n_sc, "gather_ms_per_subcycle": kgath_ms / n_sc,
                         "flux_launches": kflux_n, "gradient_launches": kgrad_n},
