@@ -432,3 +432,32 @@ def test_autotune_adopts_a_candidate_with_identical_results(tmp_path):
         e2 = autotune(t, U0, dt, 3, L, cache_path=path)
         assert e1["source"] == "measured" and e2["source"] == "cache" and e2["tuning"] == e1["tuning"]
         t.close()
+
+
+def test_point_source_steady_state_on_gpu():
+    """The oracle's inverse-square steady state (absorbing outer shell, see the oracle pin of
+    the same name) reached by the FP32 graph path: 60 sub-cycles, then E against the
+    oracle's and E 4 pi r^2 c / L within +-20% of 1 for r in [0.1, 0.3]."""
+    _need_gpu()
+    rng = np.random.default_rng(7)
+    x = W.jittered_lattice(24, 0.2, rng)
+    n = x.shape[1]
+    xs = np.array([[0.5], [0.5], [0.5]])
+    o = oracle.Oracle(x, np.full(n, 1.0 / n), xs, n_groups=1, c_red=1.0)
+    d = x - 0.5
+    r = np.sqrt((d ** 2).sum(0))
+    dt = cfl_dt(o)
+    alpha = np.where(r > 0.4, 1.0 / dt, 0.0)
+    U0 = np.zeros((1, 4, n))
+    U0[0, 0] = 1e-10
+    ref, _ = o.run(U0, 60, dt, np.ones((1, 1)), alpha)
+    t = Transport(x, None, xs, n_groups=1, precision="fp32")
+    U = t.state(U0)
+    t.subcycle(U, 60, dt, t.luminosities(np.ones((1, 1))), t.alpha(alpha))
+    Ug = U.cpu().numpy().astype(np.float64)
+    assert rel_l1(Ug, ref).max() <= 1e-4
+    E = Ug[0, 0]
+    for a, b in ((0.1, 0.15), (0.15, 0.2), (0.2, 0.25), (0.25, 0.3)):
+        m = (r >= a) & (r < b)
+        assert 0.8 <= (4 * np.pi * r[m] ** 2 * E[m]).mean() <= 1.2
+    t.close()

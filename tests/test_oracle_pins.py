@@ -490,3 +490,36 @@ def test_hll_transport_conserves_energy_and_is_antisymmetric():
     og = oracle.Oracle(x, np.full(n, 1.0 / n), None, n_groups=2)
     Ug, _ = og.run(U0, 5, dt)
     assert np.abs(Ug - U).max() > 1e-6
+
+
+def test_point_source_steady_state_falls_off_as_inverse_square():
+    """An isotropic point source of luminosity L radiates, in the optically thin limit
+    |F| = cE (Sec. "Injecting Photon Fluxes From Radiative Sources"), so in a steady state
+    the energy through every sphere is L and E = L / (4 pi r^2 c).  The periodic box gets an
+    outer shell (r > 0.4) that removes all radiation each step, standing in for the
+    boundary particles of the thesis's tests that swallow escaping radiation.  Loose
+    physics check (+-20%, GLF diffusion and the discrete source smear the profile) between
+    r = 0.1 (~4 smoothing lengths) and 0.3, after the light front has crossed the shell."""
+    rng = np.random.default_rng(7)
+    x = W.jittered_lattice(24, 0.2, rng)
+    n = x.shape[1]
+    o = oracle.Oracle(x, np.full(n, 1.0 / n), np.array([[0.5], [0.5], [0.5]]), n_groups=1, c_red=1.0)
+    d = x - 0.5
+    r = np.sqrt((d ** 2).sum(0))
+    dt = 0.9 * ((o.V / (4 * math.pi / 3)) ** (1 / 3)).min()
+    alpha = np.where(r > 0.4, 1.0 / dt, 0.0)        # c alpha dt = 1 in the shell
+    U0 = np.zeros((1, 4, n))
+    U0[0, 0] = 1e-10
+    U, _ = o.run(U0, 60, dt, np.ones((1, 1)), alpha)
+    U2, _ = o.run(U, 10, dt, np.ones((1, 1)), alpha)
+    sel = (r > 0.1) & (r < 0.3)
+    np.testing.assert_allclose(U2[0, 0, sel], U[0, 0, sel], rtol=1e-3)   # steady
+    E = U[0, 0]
+    Fr = (U[0, 1:] * d).sum(0) / np.maximum(r, 1e-12)
+    for a, b in ((0.1, 0.15), (0.15, 0.2), (0.2, 0.25), (0.25, 0.3)):
+        m = (r >= a) & (r < b)
+        assert 0.8 <= (4 * math.pi * r[m] ** 2 * E[m]).mean() <= 1.2, (a, b)
+        assert 0.8 <= (4 * math.pi * r[m] ** 2 * Fr[m]).mean() <= 1.2, (a, b)
+    # the energy density follows r^-2: log-log slope over the window
+    slope = np.polyfit(np.log(r[sel]), np.log(E[sel]), 1)[0]
+    assert -2.3 <= slope <= -1.7, slope
