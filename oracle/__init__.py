@@ -82,6 +82,7 @@ def _load():
         lib.orc_glf_flux.argtypes = [dp, dp, dp, C.c_double, dp]
         lib.orc_get_psi.argtypes = [vp, dp, dp]
         lib.orc_set_wave_table.argtypes = [vp, dp, dp, C.c_int, C.c_int]
+        lib.orc_drift.argtypes = [vp, dp, dp, C.c_double, dp]
         lib.orc_hll_flux.argtypes = [vp, dp, dp, dp, dp]
         lib.orc_wave_speeds.argtypes = [vp, dp, dp, dp, dp]
         _lib = lib
@@ -261,6 +262,14 @@ class Oracle:
         self.lib.orc_jvp(self._p, int(n_sub), float(dt), _dp(U0), _dp(dU0), _dp(L) if L.size else z,
                          _dp(dL) if dL.size else z, _dp(a), _dp(U), _dp(dU))
         return U, dU
+
+    def drift(self, U, v, dt_drift):
+        """Drift-corrected state U + grad U . (v dt_drift) (Sec. "Dealing With Particle Drifts");
+        v is [3, N]; the gradients are those of this (old) particle set."""
+        U = _c(U).reshape(self.G, 4, self.n)
+        out = np.empty_like(U)
+        self.lib.orc_drift(self._p, _dp(U), _dp(_c(v)), float(dt_drift), _dp(out))
+        return out
 
     def energy(self, U):
         U = _c(U)

@@ -27,6 +27,7 @@
 //                                         Eq. isotropy-correction-with-zero
 //   photon removal (grey)                 Sec. "Third step: Thermochemistry" (forward Euler)
 //   operator order inject->transport->sink  Sec. "One RT Time Step: Outline"
+//   drift correction U + grad U . dx      Sec. "Dealing With Particle Drifts"
 //
 // Readings where the thesis is silent or inconsistent (each is listed in the design notes):
 //   * update sign: U_k(t+dt) = U_k - dt/V_k sum_l F_kl . A_kl (the RT chapter's form; the
@@ -898,6 +899,22 @@ void orc_jvp(void* p, int n_sub, double dt, const double* U0, const double* dU0,
         U[k] = u[k].v;
         dU[k] = u[k].d;
     }
+}
+
+// Drift correction (Sec. "Dealing With Particle Drifts"): a particle moved by dx = v dt_drift
+// takes the state extrapolated with its gradient (Eq. gradient) at the old position,
+// U_i + grad U_i . dx_i, for every component.  U, Uout: [G][4][N]; v: [3][N].
+void orc_drift(void* p, const double* U, const double* v, double dt_drift, double* Uout) {
+    Model* M = (Model*)p;
+    size_t n = M->P.n, C = 4 * M->cfg.n_groups;
+    std::vector<double> u(U, U + C * n), g;
+    gradients(*M, u, g);
+    for (size_t cc = 0; cc < C; ++cc)
+        for (size_t i = 0; i < n; ++i) {
+            double du = 0.0;
+            for (int a = 0; a < 3; ++a) du += g[(cc * 3 + a) * n + i] * (v[a * n + i] * dt_drift);
+            Uout[cc * n + i] = u[cc * n + i] + du;
+        }
 }
 
 // total radiation energy per group, sum_i V_i E_i,g
