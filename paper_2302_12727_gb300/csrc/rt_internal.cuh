@@ -195,45 +195,5 @@ __device__ __forceinline__ T spline_dw(T q) {
 template <class T>
 __device__ __forceinline__ T fast_rcp(T x) { return T(1) / x; }
 
-// Minmod of Eq. rt-minmod with sign tests (no product, so nothing underflows).
-template <class T>
-__device__ __forceinline__ T minmod(T a, T b) {
-    bool same = (a > T(0) && b > T(0)) || (a < T(0) && b < T(0));
-    if (!same) return T(0);
-    return (fabs(a) < fabs(b)) ? a : b;
-}
-
-// M1 flux of one group state contracted with A (Eq. eddington-group, flux tensor of
-// Eq. rt-meshless): out = (F . A, c^2 E D A) with D A = (1-chi)/2 A + (3chi-1)/2 (n.A) n.
-// Written without n = F/|F|: (3chi-1)/2 n n^T = b(u) u / |F|^2 F F^T, u = min(f^2, 1),
-// b(u) = (3chi-1)/(2u) = 6 (1 + 1/(4+2s)) / (5+2s), s = sqrt(4-3u), which is finite at u = 0.
-template <class T>
-__device__ __forceinline__ void m1_dot(T E, T Fx, T Fy, T Fz, T Ax, T Ay, T Az, T c, T& oE, T& oFx, T& oFy,
-                                       T& oFz) {
-    T FA = Fx * Ax + Fy * Ay + Fz * Az;
-    oE = FA;
-    if (!(E > T(0))) {
-        oFx = oFy = oFz = T(0);
-        return;
-    }
-    T F2 = Fx * Fx + Fy * Fy + Fz * Fz;
-    T icE = T(1) / (c * E);
-    T icE2 = icE * icE;
-    T u = F2 * icE2;
-    T sc = icE2;                         // u / |F|^2
-    if (u > T(1)) {
-        u = T(1);
-        sc = T(1) / F2;
-    }
-    T s = sqrt(T(4) - T(3) * u);
-    T den = T(1) / (T(5) + T(2) * s);
-    T a_iso = (T(1) + s - T(2) * u) * den;            // (1 - chi) / 2
-    T b = T(6) * (T(1) + T(1) / (T(4) + T(2) * s)) * den;
-    T cE = c * c * E;
-    T t = b * FA * sc;
-    oFx = cE * (a_iso * Ax + t * Fx);
-    oFy = cE * (a_iso * Ay + t * Fy);
-    oFz = cE * (a_iso * Az + t * Fz);
-}
 
 }  // namespace rt

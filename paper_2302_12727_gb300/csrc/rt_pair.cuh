@@ -45,28 +45,45 @@ __device__ __forceinline__ T minmod_(T a, T b) {
     return lo > T(0) ? lo : (hi < T(0) ? hi : T(0));
 }
 
-// M1 flux of one group contracted with A, branch-free form of m1_dot (Eq. eddington-group):
-// (F . A, c^2 E [(1-chi)/2 A + b(u) u/|F|^2 (F . A) F]), zero pressure for E <= 0.
+// smallest normal number: a product or reciprocal below it is flushed by the approximate
+// float instructions, so states below it are treated as vacuum
+template <class T>
+__device__ __forceinline__ T tiny_();
+template <>
+__device__ __forceinline__ float tiny_<float>() { return 1.17549435e-38f; }
+template <>
+__device__ __forceinline__ double tiny_<double>() { return 2.2250738585072014e-308; }
+__device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rsqrt_(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// M1 flux of one group contracted with A, in branch-free form (Eq. eddington-group):
+// (F . A, c^2 E [(1 - chi)/2 A + (3 chi - 1)/2 (n . A) n]), n = F/|F|, f = |F|/(cE) clipped
+// to 1.  The factors are bounded for every state: (1 - chi)/2 = (1 + s - 2u)/(5 + 2s) and
+// (3 chi - 1)/2 = 3u/(2 + s) with u = f^2, s = sqrt(4 - 3u), and the direction enters as
+// F/|F|, so no (cE)^-2 can overflow.  cE not a normal number (E <= 0 included) gives zero
+// pressure; F not normal gives the isotropic closure.
 template <class T>
 __device__ __forceinline__ void m1_dot_(T E, T Fx, T Fy, T Fz, T Ax, T Ay, T Az, T c, T& oE, T& oFx, T& oFy,
                                         T& oFz) {
-    T FA = Fx * Ax + Fy * Ay + Fz * Az;
+    const T FA = Fx * Ax + Fy * Ay + Fz * Az;
     oE = FA;
-    bool pos = E > T(0);
-    T Es = pos ? E : T(1);
-    T F2 = Fx * Fx + Fy * Fy + Fz * Fz;
-    T icE = rcp_(c * Es);
-    T icE2 = icE * icE;
-    T u = F2 * icE2;
-    bool clip = u > T(1);
-    T sc = clip ? rcp_(F2) : icE2;
-    u = clip ? T(1) : u;
-    T s = sqrt_(T(4) - T(3) * u);
-    T den = rcp_(T(5) + T(2) * s);
-    T a_iso = (T(1) + s - T(2) * u) * den;
-    T b = T(6) * (T(1) + rcp_(T(4) + T(2) * s)) * den;
-    T cE = pos ? c * c * E : T(0);
-    T t = b * FA * sc;
+    const T cE1 = c * E;
+    const bool pos = cE1 > tiny_<T>();
+    const T F2 = Fx * Fx + Fy * Fy + Fz * Fz;
+    const bool dir = F2 > tiny_<T>();
+    const T iFn = rsqrt_(dir ? F2 : T(1));
+    const T icE = rcp_(pos ? cE1 : T(1));
+    const T f = dir ? fmin_(F2 * iFn * icE, T(1)) : T(0);
+    const T u = f * f;
+    const T s = sqrt_(T(4) - T(3) * u);
+    const T a_iso = (T(1) + s - T(2) * u) * rcp_(T(5) + T(2) * s);
+    const T a_dir = T(3) * u * rcp_(T(2) + s);
+    const T cE = pos ? c * cE1 : T(0);
+    const T t = ((a_dir * FA) * iFn) * iFn;
     oFx = cE * (a_iso * Ax + t * Fx);
     oFy = cE * (a_iso * Ay + t * Fy);
     oFz = cE * (a_iso * Az + t * Fz);
