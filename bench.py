@@ -197,15 +197,43 @@ def run_ours(args):
     rt_set_profiling(T.ctx, True)
     stream = torch.cuda.current_stream(dev)
 
+    # moving particles (--drift V): seeded directions at speed V c; every step searches
+    # neighbours at the moved positions, sub-cycles, then applies the drift correction
+    # U += grad U . v dt_hydro (dt_hydro = n_sub dt) before the particles move on
+    drift_ev = []
+    if args.drift > 0:
+        rs = np.random.default_rng(12727 + 100 + args.config)
+        dirs = rs.standard_normal((3, n))
+        dirs /= np.linalg.norm(dirs, axis=0, keepdims=True)
+        vnp = args.drift * w.c_red * dirs
+        vel = torch.as_tensor(vnp, device=dev)
+        dt_h = n_sub * dt
+        xs = [torch.as_tensor(np.mod(w.x + k * dt_h * vnp, 1.0), device=dev)
+              for k in range(args.warmup + args.steps)]
+    counter = [0]
+
     def step():
-        T.rebuild()
+        k = counter[0]
+        counter[0] += 1
+        if args.drift > 0:
+            T.rebuild(xs[k])
+        else:
+            T.rebuild()
         T.subcycle(U, n_sub, dt, L, alpha)
+        if args.drift > 0:
+            d0 = torch.cuda.Event(enable_timing=True)
+            d1 = torch.cuda.Event(enable_timing=True)
+            d0.record(stream)
+            T.drift(U, vel, dt_h)
+            d1.record(stream)
+            drift_ev.append((d0, d1))
         return T.energy(U)
 
     for _ in range(args.warmup):
         U.copy_(U0)
         step()
     torch.cuda.synchronize()
+    drift_ev.clear()
 
     kflux_ms, kflux_n, kgrad_ms, kgrad_n, kpair_ms, kgath_ms = 0.0, 0, 0.0, 0, 0.0, 0.0
     times = []
@@ -280,7 +308,8 @@ def run_ours(args):
                        "sources": w.n_src, "pairs": P, "dt": dt, "dt_rule": f"{args.cfl} * min dx / c (Eq. rt-cfl)",
                        "precision": "fp32 fluxes/gradients, fp64 h/E_i/B_i/energy" if prec == "fp32" else "fp64",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
-                       "tuning": T.tuning(), "tuning_source": tune_info.get("source"), "riemann": args.riemann},
+                       "tuning": T.tuning(), "tuning_source": tune_info.get("source"), "riemann": args.riemann,
+                       "drift_speed_over_c": args.drift},
             "roofline": {"bound": "alu", "kernel": f"{pair_kernel} (pair pass)",
                          "achieved": achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
@@ -298,6 +327,9 @@ def run_ours(args):
                               "note": "gradient + flux kernel time only (events around each launch)",
                               "hbm_frac_of_" + peak_kind: sub_bytes_per_particle(G) * n * n_sub / sub_s / 1e9 / hbm_gbs
                               if sub_s > 0 else None},
+            "drift": ({"ms_per_step": sum(a.elapsed_time(b) for a, b in drift_ev) / len(drift_ev),
+                       "note": "rt_drift (gradients + correction) per step, CUDA events; the step also "
+                               "re-searches neighbours at the moved positions"} if drift_ev else None),
             "gpu_launches": int(launches),
             "clocks": clocks,
             "wall_s_timed": wall,
@@ -451,6 +483,8 @@ def main():
                     help="pair-flux Riemann solver (Eq. riemann-GLF or Eq. riemann-HLL)")
     ap.add_argument("--tuning", default="", help="flux,gather,gradient variants of the float pair kernels")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch variants")
+    ap.add_argument("--drift", type=float, default=0.0,
+                    help="move the particles at this fraction of c (drift correction + new neighbours every step)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -192,6 +192,17 @@ rt_status rt_adjoint(rt_ctx* ctx, int32_t n_sub, double dt, int32_t ckpt_every, 
 
 /* Total radiation energy per group, sum_i V_i E_i,g, summed in double in a fixed order.
  * E_tot_host [G] is HOST memory; the call synchronises the stream. */
+/* Drift correction (Sec. "Dealing With Particle Drifts"): particles that the hydrodynamics
+ * moves by dx_i = v_i dt_drift take the state extrapolated with their least-squares
+ * gradient (Eq. gradient) at the old position, U_i <- U_i + grad U_i . dx_i, for every
+ * component of every group.  U_dev (4G x N, caller order, element type per precision) is
+ * read and overwritten; v_dev (3 x N doubles, caller order, component-major) is read only.
+ * The gradients are those of the current (old) particle set, so call rt_drift before
+ * rt_neighbours with the moved positions.  Like the thesis's scheme it does not conserve
+ * the total energy exactly.  RT_ERR_STATE before rt_neighbours; RT_ERR_INVALID for NULL
+ * arrays or a non-finite dt_drift. */
+rt_status rt_drift(rt_ctx* ctx, void* U_dev, const double* v_dev, double dt_drift);
+
 rt_status rt_energy(rt_ctx* ctx, const void* U_dev, double* E_tot_host);
 
 /* Total radiation energy per group, sum_i V_i E_i,g, without allocating anything and

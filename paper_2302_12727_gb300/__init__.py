@@ -20,6 +20,7 @@ _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4
            5: "RT_ERR_GEOMETRY", 6: "RT_ERR_TIMEOUT", 7: "RT_ERR_STATE"}
 
 EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
+            "rt_drift",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
             "rt_kernel_times", "rt_set_tuning", "rt_get_tuning", "rt_autotune", "rt_wave_table",
             "rt_energy_static", "rt_last_error", "rt_destroy"]
@@ -87,6 +88,7 @@ def load_library():
     lib.rt_subcycle.argtypes = [vp, C.c_int32, C.c_double, dp, dp, dp]
     lib.rt_adjoint.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, dp, dp, dp, dp, dp, dp]
     lib.rt_energy.argtypes = [vp, dp, C.POINTER(C.c_double)]
+    lib.rt_drift.argtypes = [vp, dp, dp, C.c_double]
     lib.rt_particle_fields.argtypes = [vp, dp, dp, dp, dp]
     lib.rt_pairs.argtypes = [vp, dp, dp]
     lib.rt_diagnostics.argtypes = [vp, C.POINTER(rt_diag)]
@@ -196,6 +198,11 @@ def rt_diagnostics(ctx) -> dict:
     d = rt_diag()
     _check(ctx, load_library().rt_diagnostics(ctx, C.byref(d)))
     return d.as_dict()
+
+
+def rt_drift(ctx, U, v, dt_drift):
+    """U += grad U . (v dt_drift) in place (Sec. "Dealing With Particle Drifts")."""
+    _check(ctx, load_library().rt_drift(ctx, _ptr(U), _ptr(v), float(dt_drift)))
 
 
 def rt_set_profiling(ctx, on: bool):

@@ -216,6 +216,18 @@ rt_status rt_gradients(rt_ctx* c, const void* U, void* gradU) {
     return RT_OK;
 }
 
+rt_status rt_drift(rt_ctx* c, void* U, const double* v, double dt_drift) {
+    RT_TRY(check_ready(c));
+    if (!U || !v) return fail(c, RT_ERR_INVALID, "NULL array");
+    if (!std::isfinite(dt_drift)) return fail(c, RT_ERR_INVALID, "dt_drift must be finite");
+    const int G = c->cfg.n_groups;
+    RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
+    RT_TRY(launch_gradient(c, c->stream, c->U_a.p));
+    RT_TRY(launch_drift(c, c->stream, c->U_a.p, v, dt_drift));
+    RT_TRY(state_out(c, c->U_a.p, U, 4 * G, 4 * G, 0));
+    return RT_OK;
+}
+
 rt_status rt_transport_step(rt_ctx* c, double dt, void* U, const double* Lsrc, const double* alpha) {
     RT_TRY(check_ready(c));
     if (!U) return fail(c, RT_ERR_INVALID, "U_dev is NULL");

@@ -155,6 +155,8 @@ rt_status field_out(rt_ctx* c, const double* src_sorted, double* dst_user, int c
 rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double* alpha);
 rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha);
 rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec);
+// rec += grad_t . (v dt) per component (needs launch_gradient on rec first)
+rt_status launch_drift(rt_ctx* c, cudaStream_t s, void* rec, const double* v, double dt);
 rt_status launch_inject(rt_ctx* c, cudaStream_t s, void* rec);
 rt_status launch_energy(rt_ctx* c, cudaStream_t s, const void* rec, double* out_dev);
 rt_status run_adjoint(rt_ctx* c, int n_sub, int ckpt_every, bool has_src, bool has_alpha, const void* U0_sorted,

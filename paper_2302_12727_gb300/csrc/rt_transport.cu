@@ -580,6 +580,34 @@ __global__ void __launch_bounds__(256) k_flux_gather_g(PairArgs<float> a, FluxEx
 }
 
 // ------------------------------------------------------------------------------------
+// Drift correction (Sec. "Dealing With Particle Drifts"): U_i += grad U_i . (v_i dt_drift)
+// for every component, on the sorted records; v in caller order (SoA doubles).
+template <class T>
+__global__ void k_drift(T* __restrict__ rec, const T* __restrict__ grad, const double* __restrict__ v,
+                        const int32_t* __restrict__ perm, int64_t n, int G, double dt) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t i = perm[p];
+    const T dx = (T)(v[i] * dt), dy = (T)(v[n + i] * dt), dz = (T)(v[2 * n + i] * dt);
+    T* u = rec + p * 4 * G;
+    const T* g = grad + p * 12 * G;
+    for (int c = 0; c < 4 * G; ++c) u[c] += g[3 * c] * dx + g[3 * c + 1] * dy + g[3 * c + 2] * dz;
+}
+
+rt_status launch_drift(rt_ctx* c, cudaStream_t s, void* rec, const double* v, double dt) {
+    unsigned nb = nblk(c->n, 256);
+    if (c->fp64)
+        k_drift<double><<<nb, 256, 0, s>>>((double*)rec, c->grad_t.as<double>(), v, c->perm.as<int32_t>(), c->n,
+                                           c->cfg.n_groups, dt);
+    else
+        k_drift<float><<<nb, 256, 0, s>>>((float*)rec, c->grad_t.as<float>(), v, c->perm.as<int32_t>(), c->n,
+                                          c->cfg.n_groups, dt);
+    ++c->launches;
+    RT_CUDA(c, cudaGetLastError());
+    return RT_OK;
+}
+
+// ------------------------------------------------------------------------------------
 // a10: energy per group, sum_i V_i E_i,g in double; fixed grid and tree order.
 constexpr int kEnergyBlocks = 512;
 

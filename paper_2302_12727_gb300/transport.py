@@ -11,8 +11,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (RT_FP32_MIXED, RT_FP64, make_config, rt_adjoint, rt_create, rt_destroy, rt_diagnostics, rt_energy,
-               rt_get_tuning, rt_gradients, rt_neighbours, rt_pairs, rt_particle_fields, rt_set_stream,
+from . import (RT_FP32_MIXED, RT_FP64, make_config, rt_adjoint, rt_create, rt_destroy, rt_diagnostics, rt_drift,
+               rt_energy, rt_get_tuning, rt_gradients, rt_neighbours, rt_pairs, rt_particle_fields, rt_set_stream,
                rt_set_tuning, rt_subcycle, rt_transport_step)
 
 
@@ -104,6 +104,12 @@ class Transport:
             L is not None and self.n_src) else None
         rt_adjoint(self.ctx, n_sub, dt, ckpt_every, U0, L, alpha, lam_final, lam0, dL)
         return lam0, dL
+
+    def drift(self, U, v, dt_drift):
+        """In place: U += grad U . (v dt_drift) on the current particle set (then call
+        rebuild with the moved positions).  v: [3, N] float64 (numpy or tensor)."""
+        self._sync_stream()
+        rt_drift(self.ctx, U, _dev(v, torch.float64, self.device), dt_drift)
 
     def energy(self, U):
         self._sync_stream()
