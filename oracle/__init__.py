@@ -83,6 +83,8 @@ def _load():
         lib.orc_get_psi.argtypes = [vp, dp, dp]
         lib.orc_set_wave_table.argtypes = [vp, dp, dp, C.c_int, C.c_int]
         lib.orc_drift.argtypes = [vp, dp, dp, C.c_double, dp]
+        lib.orc_run_groups.restype = C.c_long
+        lib.orc_run_groups.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp]
         lib.orc_hll_flux.argtypes = [vp, dp, dp, dp, dp]
         lib.orc_wave_speeds.argtypes = [vp, dp, dp, dp, dp]
         _lib = lib
@@ -241,10 +243,16 @@ class Oracle:
         self.lib.orc_gradients(self._p, _dp(U), _dp(g))
         return g
 
-    def run(self, U0, n_sub, dt, L=None, alpha=None):
-        """n_sub steps (inject -> transport -> sink); returns (U, clamp_count)."""
+    def run(self, U0, n_sub, dt, L=None, alpha=None, alpha_groups=None):
+        """n_sub steps (inject -> transport -> sink); returns (U, clamp_count).  alpha [N] is a
+        grey absorption; alpha_groups [G, N] one per group (photo-ionisation sink)."""
         U = _c(U0).copy().reshape(self.G, 4, self.n)
         L = _c(np.zeros((self.n_src, self.G)) if L is None else L).reshape(self.n_src, self.G)
+        if alpha_groups is not None:
+            ag = _c(alpha_groups).reshape(self.G, self.n)
+            nclamp = self.lib.orc_run_groups(self._p, int(n_sub), float(dt), _dp(U),
+                                             _dp(L) if L.size else _dp(np.zeros(1)), _dp(ag))
+            return U, nclamp
         a = None if alpha is None else _c(alpha)
         nclamp = self.lib.orc_run(self._p, int(n_sub), float(dt), _dp(U), _dp(L) if L.size else _dp(np.zeros(1)),
                                   _dp(a))

@@ -26,6 +26,7 @@
 //   injection weights xi, octant mu_a     Sec. "Weights For Distribution Of Energy Density",
 //                                         Eq. isotropy-correction-with-zero
 //   photon removal (grey)                 Sec. "Third step: Thermochemistry" (forward Euler)
+//   photon removal per group              Eqs. dEdt-group, dFdt-group (alpha_g = sum_j n_j sigma^N_gj)
 //   operator order inject->transport->sink  Sec. "One RT Time Step: Outline"
 //   drift correction U + grad U . dx      Sec. "Dealing With Particle Drifts"
 //
@@ -657,7 +658,7 @@ struct StepStats { long clamped = 0; };
 // U: [G][4][N] in/out, L: [S][G], alpha: [N] or null.
 template <class T>
 static void step(const Model& M, double dt, std::vector<T>& U, const std::vector<T>& L, const double* alpha,
-                 StepStats* st) {
+                 StepStats* st, const double* alpha_g = nullptr) {
     const long n = M.P.n;
     const int G = M.cfg.n_groups;
     const int C = 4 * G;
@@ -707,12 +708,16 @@ static void step(const Model& M, double dt, std::vector<T>& U, const std::vector
             Unew[(size_t)cc * n + k] = U[(size_t)cc * n + k] - T(dt / M.V[k]) * acc[cc];   // Eq. transport-update-explicit
     }
 
-    // 4. grey sink (forward Euler, clamped at zero) and optional fix-up
+    // 4. sink (forward Euler, clamped at zero): grey alpha_i, or per group alpha_g,i =
+    //    sum_j n_j sigma^N_gj (Eqs. dEdt-group, dFdt-group); then the optional fix-up
     long clamped = 0;
     for (long i = 0; i < n; ++i) {
         double fac = 1.0;
         if (alpha) fac = std::max(0.0, 1.0 - c * alpha[i] * dt);
-        for (int cc = 0; cc < C; ++cc) Unew[(size_t)cc * n + i] *= T(fac);
+        for (int cc = 0; cc < C; ++cc) {
+            double f = alpha_g ? std::max(0.0, 1.0 - c * alpha_g[(size_t)(cc / 4) * n + i] * dt) : fac;
+            Unew[(size_t)cc * n + i] *= T(f);
+        }
         if (M.cfg.clamp_negative)
             for (int g = 0; g < G; ++g) {
                 T& E = Unew[(size_t)(4 * g) * n + i];
@@ -882,6 +887,18 @@ long orc_run(void* p, int n_sub, double dt, double* U, const double* L, const do
     std::vector<double> l(L, L + (size_t)M->n_src * M->cfg.n_groups);
     StepStats st;
     for (int k = 0; k < n_sub; ++k) step(*M, dt, u, l, alpha, &st);
+    std::memcpy(U, u.data(), C * n * sizeof(double));
+    return st.clamped;
+}
+
+// as orc_run, with the photo-ionisation sink per group: alpha_g [G][N]
+long orc_run_groups(void* p, int n_sub, double dt, double* U, const double* L, const double* alpha_g) {
+    Model* M = (Model*)p;
+    size_t n = M->P.n, C = 4 * M->cfg.n_groups;
+    std::vector<double> u(U, U + C * n);
+    std::vector<double> l(L, L + (size_t)M->n_src * M->cfg.n_groups);
+    StepStats st;
+    for (int k = 0; k < n_sub; ++k) step(*M, dt, u, l, nullptr, &st, alpha_g);
     std::memcpy(U, u.data(), C * n * sizeof(double));
     return st.clamped;
 }

@@ -580,3 +580,90 @@ def test_drift_corrected_run_follows_the_static_one():
     e_static, e_corr, e_raw = run("static"), run("corrected"), run("uncorrected")
     assert e_corr <= 1.25 * e_static, (e_static, e_corr)
     assert e_raw >= 2.0 * e_static, (e_static, e_raw)
+
+
+# ----------------------------------------------------------------------------------------
+# Photo-ionisation sink (Eqs. sigma-parametrizaiton, sigma_N, sigma_E, dEdt-group, dFdt-group;
+# Appendix "Converting Photon Number Emission Rates to Photon Energy Emission Rates")
+
+L_SUN = 3.826e33   # erg/s; the thesis prints luminosities in L_sun without its value
+
+
+def _golden_luminosities():
+    import os
+    txt = open(os.path.join(os.path.dirname(__file__), "golden", "iliev2_group_luminosities.txt")).read()
+    T = Nd = None
+    sets, edges = [], None
+    for line in txt.splitlines():
+        if line.startswith("#") or not line.strip():
+            continue
+        if line.startswith("T_bb"):
+            T = float(line.split()[1])
+        elif line.startswith("Ndot"):
+            Nd = float(line.split()[1])
+        elif line.startswith("edges:"):
+            edges = [math.inf if v == "inf" else float(v) for v in line.split()[1:]]
+        elif line.startswith("L:"):
+            sets.append((edges, [float(v) for v in line.split()[1:]]))
+    return T, Nd, sets
+
+
+def test_group_luminosities_match_the_thesis():
+    """The thesis's Iliev-2 group luminosities (1, 3 and 10 groups, 4 digits) from
+    Ndot = 5e48 photons/s of a 1e5 K blackbody, in L_sun = 3.826e33 erg/s."""
+    from oracle import photo
+    T, Nd, sets = _golden_luminosities()
+    assert len(sets) == 3
+    for edges, want in sets:
+        got = photo.number_to_luminosity(T, Nd, edges) / L_SUN
+        np.testing.assert_allclose(got, want, rtol=6e-4)
+    # the groups partition the spectrum: their luminosities add up to the one-group value
+    one = photo.number_to_luminosity(T, Nd, [3.288e15, math.inf])[0]
+    for edges, _ in sets:
+        assert photo.number_to_luminosity(T, Nd, edges).sum() == pytest.approx(one, rel=1e-10)
+
+
+def test_cross_sections_and_group_averages():
+    """sigma(H0) at its 13.6 eV threshold is the hydrogen ground-state value 6.30e-18 cm^2
+    (within the 1% of the fit); every cross section vanishes below its threshold.  A
+    group's mean photon energy lies inside the group, and for a narrow group the averaged
+    cross sections tend to the cross section at its centre."""
+    from oracle import photo
+    assert photo.cross_section("HI", 13.60) == pytest.approx(6.30e-18, rel=0.01)
+    for s, e in photo.E_ION.items():
+        assert photo.cross_section(s, e * 0.999) == 0.0 and photo.cross_section(s, e * 1.001) > 0.0
+    h, ev = photo.H_PLANCK, photo.EV
+    edges = [3.288e15, 5.945e15, 13.157e15, 20e15]
+    eps, sN, sE = photo.group_averages(1e5, edges)
+    for i in range(3):
+        assert h * edges[i] < eps[i] < h * edges[i + 1]
+    nu0 = 8e15
+    for w in (1e-3, 1e-5):
+        eps, sN, sE = photo.group_averages(1e5, [nu0 * (1 - w), nu0 * (1 + w)])
+        for j, s in enumerate(photo.SPECIES):
+            want = photo.cross_section(s, h * nu0 / ev)
+            assert sN[0, j] == pytest.approx(want, rel=3 * w, abs=1e-30)
+            assert sE[0, j] == pytest.approx(want, rel=3 * w, abs=1e-30)
+        assert eps[0] == pytest.approx(h * nu0, rel=w)
+
+
+def test_group_sink_without_transport_and_grey_equivalence():
+    """With the group sink alone (no neighbours' fluxes: a uniform state, F = 0, on the
+    perfect lattice, where the E rows are stationary), E_g(t + dt) = E_g (1 - c alpha_g dt).
+    Equal alpha in every group reproduces the grey sink exactly."""
+    x = W.perfect_lattice(10)
+    n = x.shape[1]
+    o = oracle.Oracle(x, np.full(n, 1.0 / n), None, n_groups=3, c_red=1.5)
+    rng = np.random.default_rng(71)
+    ag = rng.uniform(0.0, 2.0, size=(3, n))
+    U0 = np.zeros((3, 4, n))
+    U0[:, 0] = 1.3
+    dt = 0.05
+    U, _ = o.run(U0, 1, dt, alpha_groups=ag)
+    np.testing.assert_allclose(U[:, 0], 1.3 * np.maximum(0, 1 - 1.5 * ag * dt), rtol=1e-14)
+    a1 = rng.uniform(0.0, 2.0, size=n)
+    U0[:, 1:] = rng.normal(size=(3, 3, n)) * 0.1
+    U0[:, 0] = rng.uniform(0.5, 2.0, size=(3, n))
+    Ua, _ = o.run(U0, 2, dt, alpha=a1)
+    Ub, _ = o.run(U0, 2, dt, alpha_groups=np.tile(a1, (3, 1)))
+    np.testing.assert_array_equal(Ua, Ub)
