@@ -181,6 +181,22 @@ def run_ours(args):
     if w.kappa:
         f = T.fields()
         alpha = (w.kappa * torch.as_tensor(w.m, device=dev) * f["omega"]).contiguous()
+    if args.photo:
+        # photo-ionisation sink per group instead of the grey kappa: H0, He0, He+ densities
+        # tracing the density with an ionised fraction varying along x; sigma^N of a 1e5 K
+        # blackbody in groups split at the three thresholds (library host helper), scaled so
+        # that H0 in group 1 gives alpha = kappa rho
+        from paper_2302_12727_gb300 import rt_blackbody_groups
+        if G != 3:
+            raise SystemExit("--photo needs 3 groups")
+        rho = w.m * T.fields()["omega"].cpu().numpy()
+        xi = 0.5 * (1 + np.sin(2 * np.pi * w.x[0]))
+        n_sp = np.stack([rho * (1 - xi), 0.08 * rho * (1 - xi), 0.08 * rho * xi])
+        edges = [13.60 * 1.602176634e-12 / 6.62607015e-27, 24.59 * 1.602176634e-12 / 6.62607015e-27,
+                 54.42 * 1.602176634e-12 / 6.62607015e-27, math.inf]
+        _, sN, _ = rt_blackbody_groups(1e5, edges)
+        T.set_absorbers(n_sp, (w.kappa or 0.1) * sN / sN[0, 0])
+        alpha = None
     L = T.luminosities(w.Lsrc)
     U0 = T.state(w.U0)
     U = U0.clone()
@@ -309,7 +325,8 @@ def run_ours(args):
                        "precision": "fp32 fluxes/gradients, fp64 h/E_i/B_i/energy" if prec == "fp32" else "fp64",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
                        "tuning": T.tuning(), "tuning_source": tune_info.get("source"), "riemann": args.riemann,
-                       "drift_speed_over_c": args.drift},
+                       "drift_speed_over_c": args.drift,
+                       "sink": "photo-ionisation per group" if args.photo else ("grey" if alpha is not None else "none")},
             "roofline": {"bound": "alu", "kernel": f"{pair_kernel} (pair pass)",
                          "achieved": achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
@@ -483,6 +500,8 @@ def main():
                     help="pair-flux Riemann solver (Eq. riemann-GLF or Eq. riemann-HLL)")
     ap.add_argument("--tuning", default="", help="flux,gather,gradient variants of the float pair kernels")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch variants")
+    ap.add_argument("--photo", action="store_true",
+                    help="per-group photo-ionisation sink (rt_set_absorbers) instead of the grey kappa")
     ap.add_argument("--drift", type=float, default=0.0,
                     help="move the particles at this fraction of c (drift correction + new neighbours every step)")
     args = ap.parse_args()

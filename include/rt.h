@@ -263,6 +263,38 @@ rt_status rt_kernel_times(rt_ctx* ctx, double* ms_host, int64_t* launches_host);
  * eigenvalue equals cos theta.  RT_ERR_INVALID for NULL arrays. */
 rt_status rt_wave_table(double* lmax_host, double* lmin_host);
 
+/* Photo-ionisation sink of the photon groups (Eqs. dEdt-group, dFdt-group): every group
+ * loses energy and flux at the rate c n_j sigma^N_gj summed over the absorbing species j.
+ * rt_set_absorbers computes, on the context's stream, alpha_g = sum_j sigma_host[g][j]
+ * n_dev[j] per particle from the caller's species number densities n_dev (n_species x N
+ * doubles, caller order, read during the call) and cross sections sigma_host (host, G x
+ * n_species doubles, in units consistent with n, c and dt).  From then on rt_transport_step,
+ * rt_subcycle and rt_autotune called with alpha_dev == NULL apply the forward-Euler sink
+ * U_g <- U_g max(0, 1 - c alpha_g dt) per group (a non-NULL alpha_dev applies its grey sink
+ * instead); n_dev == NULL clears the absorbers.  rt_adjoint refuses contexts with absorbers
+ * unless a grey alpha_dev is given.  Synchronises the stream.  RT_ERR_INVALID for
+ * n_species outside [1, 8] or negative or non-finite cross sections. */
+rt_status rt_set_absorbers(rt_ctx* ctx, int32_t n_species, const double* n_dev, const double* sigma_host);
+
+/* Host helpers of the photo-ionisation sink (no context or GPU), CGS units, frequencies in
+ * Hz.  Species j: 0 = H0, 1 = He0, 2 = He+.
+ * rt_cross_section: sigma_j(E) in cm^2 at photon energy E_eV (eV), the fit of
+ *   Eq. sigma-parametrizaiton with the parameters of Table tab:cross-sections, zero below the
+ *   ionisation energy of the species (Eqs. nuIonHI, nuIonHeI, nuIonHeII).
+ * rt_blackbody_groups: for a blackbody of temperature T_bb (Eq. blackbody) and groups
+ *   [nu_edges[g], nu_edges[g+1]) (n_groups + 1 ascending edges; the last may be +inf), the
+ *   mean photon energy eps_mean[g] (erg) and the number- and energy-weighted cross
+ *   sections sigma_N[g][j], sigma_E[g][j] (cm^2, Eqs. sigma_N, sigma_E; host arrays G, G x 3).
+ * rt_photon_number_to_luminosity: the group luminosities L_out[g] (erg/s) of a source
+ *   emitting Ndot photons/s above nu_edges[0] with that spectrum (Appendix "Converting
+ *   Photon Number Emission Rates to Photon Energy Emission Rates").
+ * RT_ERR_INVALID for NULL arrays, non-positive temperatures or unordered edges. */
+rt_status rt_cross_section(int32_t species, double E_eV, double* sigma_out);
+rt_status rt_blackbody_groups(double T_bb, int32_t n_groups, const double* nu_edges, double* eps_mean,
+                              double* sigma_N, double* sigma_E);
+rt_status rt_photon_number_to_luminosity(double T_bb, double Ndot, int32_t n_groups, const double* nu_edges,
+                                         double* L_out);
+
 /* Set (rt_set_tuning) or read (rt_get_tuning) the launch variants of the float pair kernels
  * (host struct, copied).  RT_ERR_INVALID for a variant outside the values listed above; the
  * context is unchanged then.  Valid before or after rt_neighbours. */

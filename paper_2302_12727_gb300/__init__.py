@@ -20,7 +20,8 @@ _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4
            5: "RT_ERR_GEOMETRY", 6: "RT_ERR_TIMEOUT", 7: "RT_ERR_STATE"}
 
 EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
-            "rt_drift",
+            "rt_drift", "rt_set_absorbers", "rt_cross_section", "rt_blackbody_groups",
+            "rt_photon_number_to_luminosity",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
             "rt_kernel_times", "rt_set_tuning", "rt_get_tuning", "rt_autotune", "rt_wave_table",
             "rt_energy_static", "rt_last_error", "rt_destroy"]
@@ -89,6 +90,10 @@ def load_library():
     lib.rt_adjoint.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, dp, dp, dp, dp, dp, dp]
     lib.rt_energy.argtypes = [vp, dp, C.POINTER(C.c_double)]
     lib.rt_drift.argtypes = [vp, dp, dp, C.c_double]
+    lib.rt_set_absorbers.argtypes = [vp, C.c_int32, dp, dp]
+    lib.rt_cross_section.argtypes = [C.c_int32, C.c_double, dp]
+    lib.rt_blackbody_groups.argtypes = [C.c_double, C.c_int32, dp, dp, dp, dp]
+    lib.rt_photon_number_to_luminosity.argtypes = [C.c_double, C.c_double, C.c_int32, dp, dp]
     lib.rt_particle_fields.argtypes = [vp, dp, dp, dp, dp]
     lib.rt_pairs.argtypes = [vp, dp, dp]
     lib.rt_diagnostics.argtypes = [vp, C.POINTER(rt_diag)]
@@ -203,6 +208,48 @@ def rt_diagnostics(ctx) -> dict:
 def rt_drift(ctx, U, v, dt_drift):
     """U += grad U . (v dt_drift) in place (Sec. "Dealing With Particle Drifts")."""
     _check(ctx, load_library().rt_drift(ctx, _ptr(U), _ptr(v), float(dt_drift)))
+
+
+def rt_set_absorbers(ctx, n_species, sigma):
+    """Photo-ionisation sink per group: n_species [J, N] device densities (or None to clear),
+    sigma [G, J] cross sections (host)."""
+    import numpy as np
+    if n_species is None:
+        _check(ctx, load_library().rt_set_absorbers(ctx, 0, None, None))
+        return
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    _check(ctx, load_library().rt_set_absorbers(ctx, int(sig.shape[1]), _ptr(n_species), sig.ctypes.data))
+
+
+def rt_cross_section(species: int, E_eV: float) -> float:
+    out = C.c_double()
+    if load_library().rt_cross_section(int(species), float(E_eV), C.addressof(out)) != RT_OK:
+        raise RTError(1, "rt_cross_section: species must be 0, 1 or 2")
+    return out.value
+
+
+def rt_blackbody_groups(T_bb: float, nu_edges):
+    """(eps_mean [G] erg, sigma_N [G, 3], sigma_E [G, 3] cm^2) for a blackbody spectrum."""
+    import numpy as np
+    e = np.ascontiguousarray(nu_edges, dtype=np.float64)
+    G = e.size - 1
+    eps, sN, sE = np.empty(G), np.empty((G, 3)), np.empty((G, 3))
+    st = load_library().rt_blackbody_groups(float(T_bb), G, e.ctypes.data, eps.ctypes.data, sN.ctypes.data,
+                                            sE.ctypes.data)
+    if st != RT_OK:
+        raise RTError(st, "rt_blackbody_groups")
+    return eps, sN, sE
+
+
+def rt_photon_number_to_luminosity(T_bb: float, Ndot: float, nu_edges):
+    import numpy as np
+    e = np.ascontiguousarray(nu_edges, dtype=np.float64)
+    L = np.empty(e.size - 1)
+    st = load_library().rt_photon_number_to_luminosity(float(T_bb), float(Ndot), e.size - 1, e.ctypes.data,
+                                                       L.ctypes.data)
+    if st != RT_OK:
+        raise RTError(st, "rt_photon_number_to_luminosity")
+    return L
 
 
 def rt_set_profiling(ctx, on: bool):

@@ -259,7 +259,7 @@ rt_status rt_subcycle(rt_ctx* c, int32_t n_sub, double dt, void* U, const double
     bool has_alpha = alpha != nullptr;
     RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
     RT_TRY(set_step_inputs(c, dt, Lsrc, alpha));
-    GraphKey key{n_sub, has_src ? 1 : 0, has_alpha ? 1 : 0};
+    GraphKey key{n_sub, has_src ? 1 : 0, has_alpha ? 1 : (c->has_alpha_g ? 2 : 0)};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         GraphEntry entry;
@@ -308,6 +308,8 @@ rt_status rt_adjoint(rt_ctx* c, int32_t n_sub, double dt, int32_t ckpt_every, co
     if (ckpt_every < 1) return fail(c, RT_ERR_INVALID, "ckpt_every must be >= 1");
     if (c->cfg.riemann_solver != RT_RIEMANN_GLF)
         return fail(c, RT_ERR_INVALID, "rt_adjoint differentiates the GLF flux only (riemann_solver = RT_RIEMANN_GLF)");
+    if (c->has_alpha_g && !alpha)
+        return fail(c, RT_ERR_INVALID, "rt_adjoint differentiates the grey sink only (clear the absorbers)");
     if (!std::isfinite(dt) || dt < 0) return fail(c, RT_ERR_INVALID, "dt must be finite and >= 0");
     const int G = c->cfg.n_groups;
     bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
@@ -565,7 +567,8 @@ void rt_destroy(rt_ctx* c) {
                       &c->n_up, &c->up_off, &c->low_slot, &c->pair_ends, &c->pairbuf, &c->flags, &c->red_tmp,
                       &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
                       &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,
-                      &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->frec, &c->wave_t, &c->alpha_s,
+                      &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->frec, &c->wave_t, &c->alpha_g_c, &c->alpha_g_s,
+                      &c->sigma_d, &c->alpha_s,
                       &c->L_dev, &c->dt_dev, &c->energy_part, &c->ck, &c->seg, &c->lam_a, &c->lam_b, &c->adj_w,
                       &c->adj_x, &c->adj_ub, &c->adj_gam, &c->adj_lam};
     for (DevBuf* b : bufs) free_buf(*b);

@@ -35,7 +35,7 @@ struct DevBuf {
 };
 
 struct GraphKey {
-    int n_sub, has_src, has_alpha;
+    int n_sub, has_src, has_alpha;   // has_alpha: 0 none, 1 grey, 2 per group
     bool operator<(const GraphKey& o) const {
         return std::tie(n_sub, has_src, has_alpha) < std::tie(o.n_sub, o.has_src, o.has_alpha);
     }
@@ -96,6 +96,11 @@ struct rt_ctx {
     rt::DevBuf U_a, U_b, grad_t, alpha_s, L_dev, dt_dev, energy_part;
     rt::DevBuf frec;                                    // packed float flux-input rows (G <= 4)
     rt::DevBuf wave_t;                                  // HLL wave-speed table, working precision
+    // photo-ionisation sink per group (rt_set_absorbers): alpha in caller order [G][N]
+    // (double), its sorted working-precision copy [N][G], the cross sections
+    rt::DevBuf alpha_g_c, alpha_g_s, sigma_d;
+    bool has_alpha_g = false;
+    bool step_alpha_g = false;                          // the current call applies it
     CUtensorMap rows_map{};                             // tensor map of frec (tile::gather4)
     const void* rows_map_for = nullptr;
     int64_t rows_map_n = 0;

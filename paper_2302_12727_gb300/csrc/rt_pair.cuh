@@ -333,6 +333,7 @@ template <class T>
 struct FluxExtra {
     const T* wave;                  // HLL wave-speed table (interleaved); unused by the GLF kernels
     const T* alpha;                 // sorted, or null
+    const T* alpha_g;               // sorted per-group absorption [N][G], or null
     const double* dt_dev;
     T c;
     int clamp;

@@ -61,6 +61,16 @@ __global__ void k_alpha_sorted(const double* __restrict__ alpha, const int32_t* 
     out[p] = (T)alpha[perm[p]];
 }
 
+// per-group absorption [G][N] (caller order) -> [N][G] sorted, working precision
+template <class T>
+__global__ void k_alpha_g_sorted(const double* __restrict__ ag, const int32_t* __restrict__ perm, int64_t n, int G,
+                                 T* out) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t i = perm[p];
+    for (int g = 0; g < G; ++g) out[p * G + g] = (T)ag[(int64_t)g * n + i];
+}
+
 __global__ void k_set_scalar(double* dst, double v) { *dst = v; }
 
 // ------------------------------------------------------------------------------------
@@ -320,7 +330,8 @@ __global__ void __launch_bounds__(128) k_flux_gather(PairArgs<T> a, FluxExtra<T>
     int nclamp = 0;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        T v = (ui[c] - f * acc[c]) * sink;
+        const T sk = x.alpha_g ? fmax_(T(1) - x.c * x.alpha_g[i * a.G + g0 + c / 4] * dt, T(0)) : sink;
+        T v = (ui[c] - f * acc[c]) * sk;
         if (x.clamp && (c & 3) == 0 && v < T(0)) {
             v = T(0);
             ++nclamp;
@@ -562,6 +573,7 @@ __global__ void __launch_bounds__(256) k_flux_gather_g(PairArgs<float> a, FluxEx
     const float f = dt * a.omega[i];
     float sink = 1.f;
     if (x.alpha) sink = fmax_(1.f - x.c * x.alpha[i] * dt, 0.f);
+    if (x.alpha_g) sink = fmax_(1.f - x.c * x.alpha_g[i * a.G + g0 + g] * dt, 0.f);
     float ui[4];
     const int64_t o = i * RS + 4 * (g0 + g);
     vload<4>(rec + o, ui);
@@ -775,6 +787,7 @@ static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool 
     const bool hll = c->cfg.riemann_solver == RT_RIEMANN_HLL;
     x.wave = hll ? c->wave_t.as<T>() : nullptr;
     x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
+    x.alpha_g = c->step_alpha_g ? c->alpha_g_s.as<T>() : nullptr;
     x.dt_dev = c->dt_dev.as<double>();
     x.c = (T)c->cfg.c_red;
     x.clamp = c->cfg.clamp_negative;
@@ -918,6 +931,19 @@ rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double
         unsigned nb = nblk(c->n, 256);
         if (c->fp64) k_alpha_sorted<double><<<nb, 256, 0, s>>>(alpha, c->perm.as<int32_t>(), c->n, c->alpha_s.as<double>());
         else k_alpha_sorted<float><<<nb, 256, 0, s>>>(alpha, c->perm.as<int32_t>(), c->n, c->alpha_s.as<float>());
+        ++c->launches;
+    }
+    // the photo-ionisation sink per group applies when no grey alpha is given
+    c->step_alpha_g = !alpha && c->has_alpha_g;
+    if (c->step_alpha_g) {
+        unsigned nb = nblk(c->n, 256);
+        const int G = c->cfg.n_groups;
+        if (c->fp64)
+            k_alpha_g_sorted<double><<<nb, 256, 0, s>>>(c->alpha_g_c.as<double>(), c->perm.as<int32_t>(), c->n, G,
+                                                        c->alpha_g_s.as<double>());
+        else
+            k_alpha_g_sorted<float><<<nb, 256, 0, s>>>(c->alpha_g_c.as<double>(), c->perm.as<int32_t>(), c->n, G,
+                                                       c->alpha_g_s.as<float>());
         ++c->launches;
     }
     RT_CUDA(c, cudaGetLastError());

@@ -105,6 +105,14 @@ class Transport:
         rt_adjoint(self.ctx, n_sub, dt, ckpt_every, U0, L, alpha, lam_final, lam0, dL)
         return lam0, dL
 
+    def set_absorbers(self, n_species, sigma):
+        """Photo-ionisation sink per group (rt_set_absorbers): n_species [J, N] float64
+        number densities, sigma [G, J] cross sections; None clears."""
+        from . import rt_set_absorbers
+        self._sync_stream()
+        nd = None if n_species is None else _dev(n_species, torch.float64, self.device)
+        rt_set_absorbers(self.ctx, nd, sigma)
+
     def drift(self, U, v, dt_drift):
         """In place: U += grad U . (v dt_drift) on the current particle set (then call
         rebuild with the moved positions).  v: [3, N] float64 (numpy or tensor)."""
