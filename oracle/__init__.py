@@ -83,6 +83,9 @@ def _load():
         lib.orc_get_psi.argtypes = [vp, dp, dp]
         lib.orc_set_wave_table.argtypes = [vp, dp, dp, C.c_int, C.c_int]
         lib.orc_drift.argtypes = [vp, dp, dp, C.c_double, dp]
+        lib.orc_step_bins.restype = C.c_long
+        lib.orc_step_bins.argtypes = [vp, C.c_double, ip, C.c_int, dp, dp, dp]
+        lib.orc_cfl_bins.argtypes = [vp, C.c_double, C.c_double, C.c_int, ip]
         lib.orc_run_groups.restype = C.c_long
         lib.orc_run_groups.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp]
         lib.orc_hll_flux.argtypes = [vp, dp, dp, dp, dp]
@@ -270,6 +273,23 @@ class Oracle:
         self.lib.orc_jvp(self._p, int(n_sub), float(dt), _dp(U0), _dp(dU0), _dp(L) if L.size else z,
                          _dp(dL) if dL.size else z, _dp(a), _dp(U), _dp(dU))
         return U, dU
+
+    def step_bins(self, U0, dt_min, bins, L=None, alpha=None, limit=True):
+        """One hydro step with individual time bins (see rt_oracle.cpp): returns
+        (U, bins after the limiter, clamp count)."""
+        U = _c(U0).copy().reshape(self.G, 4, self.n)
+        L = _c(np.zeros((self.n_src, self.G)) if L is None else L).reshape(self.n_src, self.G)
+        b = np.ascontiguousarray(bins, dtype=np.int32).copy()
+        a = None if alpha is None else _c(alpha)
+        ip = C.POINTER(C.c_int32)
+        nclamp = self.lib.orc_step_bins(self._p, float(dt_min), b.ctypes.data_as(ip), int(limit), _dp(U),
+                                        _dp(L) if L.size else _dp(np.zeros(1)), _dp(a))
+        return U, b, nclamp
+
+    def cfl_bins(self, cfl, dt_min, max_bin):
+        b = np.empty(self.n, dtype=np.int32)
+        self.lib.orc_cfl_bins(self._p, float(cfl), float(dt_min), int(max_bin), b.ctypes.data_as(C.POINTER(C.c_int32)))
+        return b
 
     def drift(self, U, v, dt_drift):
         """Drift-corrected state U + grad U . (v dt_drift) (Sec. "Dealing With Particle Drifts");

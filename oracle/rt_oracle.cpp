@@ -29,6 +29,8 @@
 //   photon removal per group              Eqs. dEdt-group, dFdt-group (alpha_g = sum_j n_j sigma^N_gj)
 //   operator order inject->transport->sink  Sec. "One RT Time Step: Outline"
 //   drift correction U + grad U . dx      Sec. "Dealing With Particle Drifts"
+//   individual time bins, min(dt_k, dt_l)  Sec. "Individual Timstepping", Eq. transport-update-explicit
+//   factor-4 time-step limiter             Sec. "Dynamic Sub-Cycling"
 //
 // Readings where the thesis is silent or inconsistent (each is listed in the design notes):
 //   * update sign: U_k(t+dt) = U_k - dt/V_k sum_l F_kl . A_kl (the RT chapter's form; the
@@ -654,6 +656,110 @@ static void hll_flux(const Model& M, const T uL[4], const T uR[4], const double 
 
 struct StepStats { long clamped = 0; };
 
+// Individual time bins (Sec. "Individual Timstepping"; Eqs. meshless-explicit-individual-
+// timesteps and transport-update-explicit): particle i advances in steps of
+// dt_i = 2^b_i dt_min over a hydro step of 2^B min-steps.  At min-step s a particle starts
+// a step when s mod 2^b_i = 0: it receives its injection for dt_i and a new gradient.  Every
+// pair with a starting member exchanges the time-integrated flux
+// min(dt_k, dt_l) F_kl . A_kl into both particles' accumulators (k as the left state from
+// k's side); a particle applies its accumulator, then its sink over dt_i, when its step ends
+// (at min-step s when (s + 1) mod 2^b_i = 0).  Until then its state stays as it was.
+// U: [G][4][N]; bins [N]; alpha [N] or null.
+template <class T>
+static void step_bins(const Model& M, double dt_min, int B, const int* bins, std::vector<T>& U,
+                      const std::vector<T>& L, const double* alpha, StepStats* st) {
+    const long n = M.P.n;
+    const int G = M.cfg.n_groups;
+    const int C = 4 * G;
+    const double c = M.cfg.c_red;
+    std::vector<T> acc((size_t)C * n, T(0.0)), grad, g_now;
+    std::vector<char> start(n);
+    for (long s = 0; s < (1L << B); ++s) {
+        for (long i = 0; i < n; ++i) start[i] = (s % (1L << bins[i])) == 0;
+        // injection of the starting particles over their own step
+        for (long q = 0; q < M.n_src; ++q)
+            for (const Target& t : M.inj[q])
+                if (start[t.g]) {
+                    const double dti = std::ldexp(dt_min, bins[t.g]);
+                    for (int g = 0; g < G; ++g)
+                        U[(size_t)(4 * g) * n + t.g] += T(t.xi * dti / M.V[t.g]) * L[(size_t)q * G + g];
+                }
+        // new gradients of the starting particles; the others keep theirs
+        gradients(M, U, g_now);
+        if (s == 0) grad = g_now;
+        for (long i = 0; i < n; ++i)
+            if (start[i])
+                for (int cc = 0; cc < C; ++cc)
+                    for (int a = 0; a < 3; ++a) grad[((size_t)cc * 3 + a) * n + i] = g_now[((size_t)cc * 3 + a) * n + i];
+        // exchanges of the pairs with a starting member
+#pragma omp parallel for schedule(dynamic, 64)
+        for (long k = 0; k < n; ++k) {
+            for (long l : M.nbr[k]) {
+                if (!start[k] && !start[l]) continue;
+                const double w = std::ldexp(1.0, std::min(bins[k], bins[l]));   // min(dt_k, dt_l) / dt_min
+                double d[3];
+                M.P.sep(k, l, d);
+                double A[3];
+                surface(M, k, l, d, A);
+                for (int g = 0; g < G; ++g) {
+                    T uk[4], ul[4], gk[4][3], gl[4][3], phi[4];
+                    for (int q = 0; q < 4; ++q) {
+                        const int cc = 4 * g + q;
+                        uk[q] = U[(size_t)cc * n + k];
+                        ul[q] = U[(size_t)cc * n + l];
+                        for (int a = 0; a < 3; ++a) {
+                            gk[q][a] = grad[((size_t)cc * 3 + a) * n + k];
+                            gl[q][a] = grad[((size_t)cc * 3 + a) * n + l];
+                        }
+                    }
+                    T uL[4], uR[4];
+                    face_states(uk, ul, gk, gl, d, M.h[k], M.h[l], uL, uR);
+                    if (M.cfg.riemann == 1)
+                        hll_flux(M, uL, uR, A, c, phi);
+                    else
+                        glf_flux(uL, uR, A, c, phi);
+                    for (int q = 0; q < 4; ++q) acc[(size_t)(4 * g + q) * n + k] += T(w) * phi[q];
+                }
+            }
+        }
+        // particles whose step ends now: update, sink over their step, fix-up
+        for (long i = 0; i < n; ++i) {
+            if (((s + 1) % (1L << bins[i])) != 0) continue;
+            const double dti = std::ldexp(dt_min, bins[i]);
+            const double fac = alpha ? std::max(0.0, 1.0 - c * alpha[i] * dti) : 1.0;
+            for (int cc = 0; cc < C; ++cc) {
+                T& u = U[(size_t)cc * n + i];
+                u = (u - T(dt_min / M.V[i]) * acc[(size_t)cc * n + i]) * T(fac);
+                acc[(size_t)cc * n + i] = T(0.0);
+            }
+            if (M.cfg.clamp_negative)
+                for (int g = 0; g < G; ++g) {
+                    T& E = U[(size_t)(4 * g) * n + i];
+                    if (val(E) < 0.0) {
+                        E = T(0.0);
+                        if (st) st->clamped++;
+                    }
+                }
+        }
+    }
+}
+
+// Time-step limiter (Sec. "Dynamic Sub-Cycling"): interacting particles differ by at most
+// a factor 4 in time step, i.e. 2 bins: b_i <- min(b_i, min_j b_j + 2) until nothing changes.
+static void limit_bins(const Model& M, std::vector<int>& b) {
+    for (bool changed = true; changed;) {
+        changed = false;
+        std::vector<int> nb = b;
+        for (long i = 0; i < M.P.n; ++i)
+            for (long j : M.nbr[i])
+                if (b[j] + 2 < nb[i]) {
+                    nb[i] = b[j] + 2;
+                    changed = true;
+                }
+        b.swap(nb);
+    }
+}
+
 // One time step: injection -> transport -> grey sink (-> optional fix-up).
 // U: [G][4][N] in/out, L: [S][G], alpha: [N] or null.
 template <class T>
@@ -901,6 +1007,36 @@ long orc_run_groups(void* p, int n_sub, double dt, double* U, const double* L, c
     for (int k = 0; k < n_sub; ++k) step(*M, dt, u, l, nullptr, &st, alpha_g);
     std::memcpy(U, u.data(), C * n * sizeof(double));
     return st.clamped;
+}
+
+// one hydro step with individual time bins; bins [N] in/out (limited in place when
+// `limit`); returns the clamp count
+long orc_step_bins(void* p, double dt_min, int* bins, int limit, double* U, const double* L, const double* alpha) {
+    Model* M = (Model*)p;
+    size_t n = M->P.n, C = 4 * M->cfg.n_groups;
+    std::vector<int> b(bins, bins + n);
+    if (limit) limit_bins(*M, b);
+    int B = 0;
+    for (int v : b) B = std::max(B, v);
+    std::copy(b.begin(), b.end(), bins);
+    std::vector<double> u(U, U + C * n);
+    std::vector<double> l(L, L + (size_t)M->n_src * M->cfg.n_groups);
+    StepStats st;
+    step_bins(*M, dt_min, B, b.data(), u, l, alpha, &st);
+    std::memcpy(U, u.data(), C * n * sizeof(double));
+    return st.clamped;
+}
+
+// bins from each particle's CFL step (Eq. rt-cfl): the largest b <= max_bin with
+// 2^b dt_min <= cfl dx_i / c, dx_i = (V_i / (4 pi / 3))^(1/3)
+void orc_cfl_bins(void* p, double cfl, double dt_min, int max_bin, int* bins) {
+    Model* M = (Model*)p;
+    for (long i = 0; i < M->P.n; ++i) {
+        const double lim = cfl * std::cbrt(M->V[i] / (4.0 * M_PI / 3.0)) / M->cfg.c_red;
+        int b = 0;
+        while (b < max_bin && std::ldexp(dt_min, b + 1) <= lim) ++b;
+        bins[i] = b;
+    }
 }
 
 // forward-mode derivative of n_sub steps along (dU0, dL): returns U and dU

@@ -667,3 +667,75 @@ def test_group_sink_without_transport_and_grey_equivalence():
     Ua, _ = o.run(U0, 2, dt, alpha=a1)
     Ub, _ = o.run(U0, 2, dt, alpha_groups=np.tile(a1, (3, 1)))
     np.testing.assert_array_equal(Ua, Ub)
+
+
+# ----------------------------------------------------------------------------------------
+# Individual time bins (Sec. "Individual Timstepping", Eq. transport-update-explicit with
+# min(dt_k, dt_l); the factor-4 limiter of Sec. "Dynamic Sub-Cycling")
+
+def _bins_setup(G=2, seed=81, n_side=10):
+    rng = np.random.default_rng(seed)
+    x = W.jittered_lattice(n_side, 0.25, rng)
+    n = x.shape[1]
+    o = oracle.Oracle(x, np.full(n, 1.0 / n), np.array([[0.5], [0.5], [0.5]]), n_groups=G)
+    U0 = np.zeros((G, 4, n))
+    U0[:, 0] = rng.uniform(0.5, 2.0, size=(G, n))
+    U0[:, 1:] = 0.4 * U0[:, :1] * rng.uniform(-1, 1, size=(G, 3, n)) / math.sqrt(3)
+    dt = 0.3 * ((o.V / (4 * math.pi / 3)) ** (1 / 3)).min()
+    return rng, x, o, U0, dt
+
+
+def test_time_bins_reduce_to_uniform_steps():
+    """Bins all 0 are the uniform step; bins all 1 with dt_min = dt / 2 are one uniform step
+    of dt (every exchange is 2 Phi dt_min) -- both bitwise."""
+    rng, x, o, U0, dt = _bins_setup()
+    L = rng.uniform(0.5, 1.5, size=(1, 2))
+    a = rng.uniform(0, 2, size=x.shape[1])
+    ref, _ = o.run(U0, 1, dt, L, a)
+    U, b, _ = o.step_bins(U0, dt, np.zeros(x.shape[1], np.int32), L, a)
+    np.testing.assert_array_equal(U, ref)
+    U, b, _ = o.step_bins(U0, dt / 2, np.ones(x.shape[1], np.int32), L, a)
+    np.testing.assert_array_equal(U, ref)
+
+
+def test_time_bin_limiter_and_conservation():
+    """After the limiter, neighbours differ by at most 2 bins and every bin is the largest
+    such value not above the given one: b_i = min_j (b0_j + 2 d_ij) over graph distances
+    d_ij (breadth-first search).  The min(dt_k, dt_l) exchange conserves sum_i V_i E_i
+    exactly (to rounding) with mixed bins, no sources and no sinks."""
+    rng, x, o, U0, dt = _bins_setup()
+    n = x.shape[1]
+    b0 = rng.integers(0, 5, size=n).astype(np.int32)
+    U, b, _ = o.step_bins(U0, dt / 4, b0)
+    off, cols = o.pairs()
+    for i in range(n):
+        nb = cols[off[i]:off[i + 1]]
+        assert np.all(np.abs(b[nb] - b[i]) <= 2)
+    # minimal change: multi-source BFS of b0 + 2 d
+    import heapq
+    best = b0.astype(np.int64).copy()
+    pq = [(int(best[i]), i) for i in range(n)]
+    heapq.heapify(pq)
+    while pq:
+        v, i = heapq.heappop(pq)
+        if v > best[i]:
+            continue
+        for j in cols[off[i]:off[i + 1]]:
+            if v + 2 < best[j]:
+                best[j] = v + 2
+                heapq.heappush(pq, (v + 2, j))
+    np.testing.assert_array_equal(b, best)
+    assert len(set(b.tolist())) >= 3
+    E0, E1 = o.energy(U0), o.energy(U)
+    np.testing.assert_allclose(E1, E0, rtol=1e-13)
+
+
+def test_cfl_bins():
+    """The bin of each particle is the largest b <= max_bin with 2^b dt_min <= cfl dx_i / c."""
+    rng, x, o, U0, dt = _bins_setup()
+    dx = (o.V / (4 * math.pi / 3)) ** (1 / 3)
+    dt_min = 0.9 * dx.min() / 4.3   # off the power-of-two boundaries
+    b = o.cfl_bins(0.9, dt_min, 3)
+    lim = 0.9 * dx
+    assert np.all(dt_min * 2.0 ** b <= lim)
+    assert np.all((b == 3) | (dt_min * 2.0 ** (b + 1) > lim))
