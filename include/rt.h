@@ -192,6 +192,33 @@ rt_status rt_adjoint(rt_ctx* ctx, int32_t n_sub, double dt, int32_t ckpt_every, 
 
 /* Total radiation energy per group, sum_i V_i E_i,g, summed in double in a fixed order.
  * E_tot_host [G] is HOST memory; the call synchronises the stream. */
+/* Individual time bins (Part II Sec. "Individual Timstepping", Eq. transport-update-explicit
+ * with min(dt_k, dt_l); Part III Sec. "Dynamic Sub-Cycling").  Particle i advances in steps
+ * dt_i = 2^b_i dt_min; a hydro step is 2^B min-steps, B = max_i b_i.  At min-step s particle i
+ * starts a step when s mod 2^b_i = 0: it takes its injection over dt_i and a new gradient
+ * (the others keep theirs); every pair with a starting member exchanges the time-integrated
+ * flux min(dt_k, dt_l) F_kl . A_kl into both particles' accumulators; at the end of its
+ * step particle i applies U_i - acc_i / V_i, then its sink over dt_i (grey or per group)
+ * and the fix-up.  The exchange is antisymmetric, so the total energy is conserved.
+ *
+ * rt_set_time_bins: bins from bins_dev (N int32, caller order, clipped to [0, max_bin]) or,
+ *   with bins_dev == NULL, from each particle's CFL step (Eq. rt-cfl): the largest
+ *   b <= max_bin with 2^b dt_min <= cfl dx_i / c, dx_i = (V_i / (4 pi / 3))^(1/3); then, if
+ *   `limit`, the limiter lowers them until neighbours differ by at most 2 bins (a factor 4
+ *   in time step).  Call after rt_neighbours (which discards the bins).  Synchronises.
+ * rt_get_time_bins: the bins in use (bins_dev: N int32, caller order, may be NULL) and B.
+ * rt_step_bins: one hydro step (2^B min-steps, plain launches) on U_dev (4G x N, caller
+ *   order, in/out) with luminosities Lsrc_dev (S x G or NULL) and grey absorption alpha_dev
+ *   (N or NULL; the per-group absorbers of rt_set_absorbers apply when NULL).  Every bin 0
+ *   gives one rt_transport_step of dt_min.
+ * RT_ERR_STATE before rt_neighbours or without bins; RT_ERR_INVALID for a non-positive
+ * dt_min, max_bin outside [0, RT_MAX_TIME_BIN] or a missing cfl. */
+#define RT_MAX_TIME_BIN 20
+rt_status rt_set_time_bins(rt_ctx* ctx, const int32_t* bins_dev, double dt_min, double cfl, int32_t max_bin,
+                           int32_t limit);
+rt_status rt_get_time_bins(rt_ctx* ctx, int32_t* bins_dev, int32_t* max_bin_host);
+rt_status rt_step_bins(rt_ctx* ctx, void* U_dev, const double* Lsrc_dev, const double* alpha_dev);
+
 /* Drift correction (Sec. "Dealing With Particle Drifts"): particles that the hydrodynamics
  * moves by dx_i = v_i dt_drift take the state extrapolated with their least-squares
  * gradient (Eq. gradient) at the old position, U_i <- U_i + grad U_i . dx_i, for every

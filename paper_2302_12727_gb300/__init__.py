@@ -20,7 +20,7 @@ _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4
            5: "RT_ERR_GEOMETRY", 6: "RT_ERR_TIMEOUT", 7: "RT_ERR_STATE"}
 
 EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
-            "rt_drift", "rt_set_absorbers", "rt_cross_section", "rt_blackbody_groups",
+            "rt_drift", "rt_set_time_bins", "rt_get_time_bins", "rt_step_bins", "rt_set_absorbers", "rt_cross_section", "rt_blackbody_groups",
             "rt_photon_number_to_luminosity",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
             "rt_kernel_times", "rt_set_tuning", "rt_get_tuning", "rt_autotune", "rt_wave_table",
@@ -90,6 +90,9 @@ def load_library():
     lib.rt_adjoint.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, dp, dp, dp, dp, dp, dp]
     lib.rt_energy.argtypes = [vp, dp, C.POINTER(C.c_double)]
     lib.rt_drift.argtypes = [vp, dp, dp, C.c_double]
+    lib.rt_set_time_bins.argtypes = [vp, vp, C.c_double, C.c_double, C.c_int32, C.c_int32]
+    lib.rt_get_time_bins.argtypes = [vp, vp, C.POINTER(C.c_int32)]
+    lib.rt_step_bins.argtypes = [vp, dp, dp, dp]
     lib.rt_set_absorbers.argtypes = [vp, C.c_int32, dp, dp]
     lib.rt_cross_section.argtypes = [C.c_int32, C.c_double, dp]
     lib.rt_blackbody_groups.argtypes = [C.c_double, C.c_int32, dp, dp, dp, dp]
@@ -250,6 +253,23 @@ def rt_photon_number_to_luminosity(T_bb: float, Ndot: float, nu_edges):
     if st != RT_OK:
         raise RTError(st, "rt_photon_number_to_luminosity")
     return L
+
+
+def rt_set_time_bins(ctx, bins=None, dt_min=1.0, cfl=0.0, max_bin=20, limit=True):
+    """Time bins from `bins` (device int32 [N]) or from the CFL step (bins None)."""
+    _check(ctx, load_library().rt_set_time_bins(ctx, _ptr(bins), float(dt_min), float(cfl), int(max_bin),
+                                                1 if limit else 0))
+
+
+def rt_get_time_bins(ctx, bins_out=None) -> int:
+    """Writes the bins in use into bins_out (device int32 [N], optional); returns B."""
+    mx = C.c_int32(0)
+    _check(ctx, load_library().rt_get_time_bins(ctx, _ptr(bins_out), C.byref(mx)))
+    return mx.value
+
+
+def rt_step_bins(ctx, U, Lsrc=None, alpha=None):
+    _check(ctx, load_library().rt_step_bins(ctx, _ptr(U), _ptr(Lsrc), _ptr(alpha)))
 
 
 def rt_set_profiling(ctx, on: bool):

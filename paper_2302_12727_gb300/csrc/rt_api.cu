@@ -188,6 +188,7 @@ rt_status rt_neighbours(rt_ctx* c, const double* x, const double* m, const doubl
     if (c->n_src > 0 && !xsrc) return fail(c, RT_ERR_INVALID, "xsrc_dev is NULL with n_src > 0");
     RT_CUDA(c, cudaSetDevice(c->device));
     c->built = false;
+    c->has_bins = false;   // bins live in the sorted order and depend on the pair lists
     int64_t gen0 = g_generation;
     int64_t targets0 = c->n_inj_targets;
     rt_status s = build_neighbours(c, x, m, xsrc);
@@ -213,6 +214,25 @@ rt_status rt_gradients(rt_ctx* c, const void* U, void* gradU) {
     RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
     RT_TRY(launch_gradient(c, c->stream, c->U_a.p));
     RT_TRY(state_out(c, c->grad_t.p, gradU, 12 * G, 12 * G, 0));
+    return RT_OK;
+}
+
+rt_status rt_step_bins(rt_ctx* c, void* U, const double* Lsrc, const double* alpha) {
+    RT_TRY(check_ready(c));
+    if (!U) return fail(c, RT_ERR_INVALID, "U_dev is NULL");
+    if (!c->has_bins) return fail(c, RT_ERR_STATE, "rt_set_time_bins has not been called since rt_neighbours");
+    const int G = c->cfg.n_groups;
+    const bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
+    RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
+    RT_TRY(set_step_inputs(c, c->dt_min, Lsrc, alpha));
+    RT_CUDA(c, cudaMemsetAsync(c->acc_t.p, 0, (size_t)4 * G * c->n * (c->fp64 ? 8 : 4), c->stream));
+    void* a = c->U_a.p;
+    void* b = c->U_b.p;
+    for (int s = 0; s < (1 << c->bins_max); ++s) {
+        RT_TRY(launch_step_bins(c, c->stream, s, a, b, has_src, alpha != nullptr));
+        std::swap(a, b);
+    }
+    RT_TRY(state_out(c, a, U, 4 * G, 4 * G, 0));
     return RT_OK;
 }
 
@@ -568,7 +588,7 @@ void rt_destroy(rt_ctx* c) {
                       &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
                       &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,
                       &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->frec, &c->wave_t, &c->alpha_g_c, &c->alpha_g_s,
-                      &c->sigma_d, &c->alpha_s,
+                      &c->sigma_d, &c->bins_s, &c->bins_tmp, &c->acc_t, &c->alpha_s,
                       &c->L_dev, &c->dt_dev, &c->energy_part, &c->ck, &c->seg, &c->lam_a, &c->lam_b, &c->adj_w,
                       &c->adj_x, &c->adj_ub, &c->adj_gam, &c->adj_lam};
     for (DevBuf* b : bufs) free_buf(*b);

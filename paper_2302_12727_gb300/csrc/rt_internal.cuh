@@ -22,7 +22,7 @@ constexpr double kSigma = 5.0929581789406507446;   // 16 / pi
 // int slots of the context's 64-byte flag buffer (cleared by every rt_neighbours): error
 // flags of the build, the clamp counter (64-bit, slots 8-9) and the device-wait time-out flag
 enum FlagSlot { F_BADPOS = 0, F_NOCONV = 1, F_GEOM = 2, F_ILL = 3, F_SRC_NOCONV = 4, F_NSLOTS = 8, F_CLAMP = 8,
-                F_TIMEOUT = 12 };
+                F_TIMEOUT = 12, F_SCRATCH = 13 };
 constexpr int kMaxGC = 4;                          // groups handled by one pair-kernel launch
 
 // ------------------------------------------------------------------------------------
@@ -101,6 +101,11 @@ struct rt_ctx {
     rt::DevBuf alpha_g_c, alpha_g_s, sigma_d;
     bool has_alpha_g = false;
     bool step_alpha_g = false;                          // the current call applies it
+    // individual time bins (rt_set_time_bins): sorted int8 bins, flux accumulators [N][4G]
+    rt::DevBuf bins_s, bins_tmp, acc_t;
+    bool has_bins = false;
+    int bins_max = 0;
+    double dt_min = 0.0;
     CUtensorMap rows_map{};                             // tensor map of frec (tile::gather4)
     const void* rows_map_for = nullptr;
     int64_t rows_map_n = 0;
@@ -160,6 +165,8 @@ rt_status field_out(rt_ctx* c, const double* src_sorted, double* dst_user, int c
 rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double* alpha);
 rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha);
 rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec);
+// one min-step `step` of a hydro step with individual time bins (c->bins_s, c->acc_t)
+rt_status launch_step_bins(rt_ctx* c, cudaStream_t s, int step, void* Uin, void* Uout, bool has_src, bool has_alpha);
 // rec += grad_t . (v dt) per component (needs launch_gradient on rec first)
 rt_status launch_drift(rt_ctx* c, cudaStream_t s, void* rec, const double* v, double dt);
 rt_status launch_inject(rt_ctx* c, cudaStream_t s, void* rec);

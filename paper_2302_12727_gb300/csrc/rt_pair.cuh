@@ -236,6 +236,9 @@ struct PairArgs {
     // (instead of grad) for the tensor-memory-accelerator flux pass
     T* frec;
     int RW;
+    // individual time bins (bins mode only): sorted bin per particle and the min-step index
+    const int8_t* bins;
+    int s;
 };
 
 // symmetric 3x3 (xx, yy, zz, xy, xz, yz) times vector
@@ -334,6 +337,7 @@ struct FluxExtra {
     const T* wave;                  // HLL wave-speed table (interleaved); unused by the GLF kernels
     const T* alpha;                 // sorted, or null
     const T* alpha_g;               // sorted per-group absorption [N][G], or null
+    T* acc;                         // bins mode: per-particle flux accumulators [N][4G]
     const double* dt_dev;
     T c;
     int clamp;
@@ -366,6 +370,8 @@ inline PairArgs<T> pair_args(rt_ctx* c) {
     a.G = c->cfg.n_groups;
     a.frec = nullptr;
     a.RW = 12 + 16 * a.G;
+    a.bins = nullptr;
+    a.s = 0;
     return a;
 }
 

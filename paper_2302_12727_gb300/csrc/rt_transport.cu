@@ -80,11 +80,16 @@ template <class T>
 __global__ void k_inject(const int32_t* __restrict__ targets, const int32_t* __restrict__ off,
                          const int32_t* __restrict__ src, const double* __restrict__ coef,
                          const double* __restrict__ L, int G, const double* __restrict__ dt_dev, int64_t n_targets,
-                         int RS, T* rec) {
+                         int RS, T* rec, const int8_t* __restrict__ bins, int s) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_targets) return;
     double dt = *dt_dev;
     int64_t p = targets[t];
+    if (bins) {   // time bins: only particles starting a step, for their own step
+        const int b = bins[p];
+        if (s & ((1 << b) - 1)) return;
+        dt = ldexp(dt, b);
+    }
     for (int g = 0; g < G; ++g) {
         double acc = 0.0;
         for (int e = off[t]; e < off[t + 1]; ++e) acc += coef[e] * L[(int64_t)src[e] * G + g];
@@ -107,11 +112,14 @@ __device__ __forceinline__ void packed_static(const PairArgs<T>& a, int64_t i, T
 // ------------------------------------------------------------------------------------
 // a6: least-squares gradient (Eq. gradient) of the groups [g0, g0 + GC):
 // grad Q_i = omega_i Bp_i sum_j (Q_j - Q_i) w(r_ij / H_i) d_ij,  d_ij = x_j - x_i
-template <class T, int GC>
+template <class T, int GC, bool BINS = false>
 __global__ void __launch_bounds__(128) k_gradient(PairArgs<T> a, const T* __restrict__ rec, T* __restrict__ grad,
                                                   int g0) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    if constexpr (BINS) {   // time bins: only particles starting a step take a new gradient
+        if (a.s & ((1 << a.bins[i]) - 1)) return;
+    }
     constexpr int NC = 4 * GC;
     const T* tag = nullptr;
     Pos<T> pi = load_pos(tag, a.pos, i);
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(256) k_gradient_g(PairArgs<float> a, const flo
 
 // Pass 1 of the flux: one thread per unordered pair (k, l), k < l, evaluates Phi_kl once with
 // k as the left state and stores it in the pair's slot.
-template <class T, int GC, bool HLL>
+template <class T, int GC, bool HLL, bool BINS = false>
 __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ rec,
                                               T* __restrict__ pairbuf, int g0) {
     const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -245,6 +253,12 @@ __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, con
     const int G = a.G, RS = 4 * G;
     const int2 kl = a.ends[slot];
     const int64_t i = kl.x, j = kl.y;
+    T wgt = T(1);
+    if constexpr (BINS) {   // time bins: pairs with a starting member, weighted by min(dt_k, dt_l)
+        const int bk = a.bins[i], bl = a.bins[j];
+        if ((a.s & ((1 << bk) - 1)) && (a.s & ((1 << bl) - 1))) return;
+        wgt = T(1 << min(bk, bl));
+    }
     const Pos<T> pi = load_pos(tag, a.pos, i);
     const Pos<T> pj = load_pos(tag, a.pos, j);
     T gi8[8], gj8[8];
@@ -280,19 +294,91 @@ __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, con
         vload<12>(qj + 12 * gg, grj);
         pair_flux<HLL>(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
     }
+    if constexpr (BINS) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c] *= wgt;
+    }
     vstore<NC>(pairbuf + slot * NC, out);
+}
+
+// Pass 2 with individual time bins: particle i adds to its accumulator the slots of the pairs
+// that interacted at min-step s (all of them if i starts a step, else those whose partner
+// starts one), in the same order as the uniform gather; at the end of its own step
+// ((s + 1) mod 2^b_i = 0) it applies U_i - dt_min / V_i acc_i, the sink over its step
+// dt_min 2^b_i and the fix-up, and clears the accumulator; otherwise its state is copied.
+template <class T, int GC>
+__device__ __forceinline__ void gather_bins(const PairArgs<T>& a, const FluxExtra<T>& x, const T* __restrict__ rec,
+                                            const T* __restrict__ pairbuf, T* __restrict__ out, int g0, int64_t i) {
+    constexpr int NC = 4 * GC;
+    const int RS = 4 * a.G;
+    const int bi = a.bins[i];
+    const int mask = (1 << bi) - 1;
+    const bool start_i = !(a.s & mask);
+    T* accp = x.acc + i * RS + 4 * g0;
+    T acc[NC];
+    vload<NC>(accp, acc);
+    const int64_t r0 = a.row_off[i], s0 = a.up_off[i], s1 = a.up_off[i + 1];
+    const int nl = a.n_low[i];
+    for (int64_t sl = s0; sl < s1; ++sl) {
+        const int l = a.cols[r0 + nl + (sl - s0)];
+        if (!start_i && (a.s & ((1 << a.bins[l]) - 1))) continue;
+        T phi[NC];
+        vload<NC>(pairbuf + sl * NC, phi);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] += phi[c];
+    }
+    const int32_t* ls = a.low_slot + (r0 - s0);
+    for (int e = 0; e < nl; ++e) {
+        const int k = a.cols[r0 + e];
+        if (!start_i && (a.s & ((1 << a.bins[k]) - 1))) continue;
+        T phi[NC];
+        vload<NC>(pairbuf + (int64_t)ls[e] * NC, phi);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] -= phi[c];
+    }
+    T ui[NC];
+    vload<NC>(rec + i * RS + 4 * g0, ui);
+    if ((a.s + 1) & mask) {   // the step of i goes on
+        vstore<NC>(accp, acc);
+        vstore<NC>(out + i * RS + 4 * g0, ui);
+        return;
+    }
+    const T dt = (T)(*x.dt_dev);
+    const T dti = (T)ldexp(*x.dt_dev, bi);
+    const T f = dt * a.omega[i];
+    T sink = T(1);
+    if (x.alpha) sink = fmax_(T(1) - x.c * x.alpha[i] * dti, T(0));
+    int nclamp = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const T sk = x.alpha_g ? fmax_(T(1) - x.c * x.alpha_g[i * a.G + g0 + c / 4] * dti, T(0)) : sink;
+        T v = (ui[c] - f * acc[c]) * sk;
+        if (x.clamp && (c & 3) == 0 && v < T(0)) {
+            v = T(0);
+            ++nclamp;
+        }
+        ui[c] = v;
+        acc[c] = T(0);
+    }
+    vstore<NC>(accp, acc);
+    vstore<NC>(out + i * RS + 4 * g0, ui);
+    if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
 }
 
 // Pass 2: particle i adds the fluxes of its own upper pairs (contiguous slots) and subtracts
 // those of its lower pairs (k < i, read from k's slots), in a fixed order; then
 // U_i(t + dt) = U_i - dt / V_i sum_l F_il . A_il, the sink and the fix-up.
-template <class T, int GC>
+template <class T, int GC, bool BINS = false>
 __global__ void __launch_bounds__(128) k_flux_gather(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ rec,
                                                      const T* __restrict__ pairbuf, T* __restrict__ out, int g0) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     constexpr int NC = 4 * GC;
     const int RS = 4 * a.G;
+    if constexpr (BINS) {
+        gather_bins<T, GC>(a, x, rec, pairbuf, out, g0, i);
+        return;
+    }
     T acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = T(0);
@@ -788,6 +874,7 @@ static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool 
     x.wave = hll ? c->wave_t.as<T>() : nullptr;
     x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
     x.alpha_g = c->step_alpha_g ? c->alpha_g_s.as<T>() : nullptr;
+    x.acc = nullptr;
     x.dt_dev = c->dt_dev.as<double>();
     x.c = (T)c->cfg.c_red;
     x.clamp = c->cfg.clamp_negative;
@@ -846,12 +933,13 @@ static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool 
 }
 
 template <class T>
-static void launch_inject_t(rt_ctx* c, cudaStream_t s, T* rec) {
+static void launch_inject_t(rt_ctx* c, cudaStream_t s, T* rec, const int8_t* bins = nullptr, int step = 0) {
     if (c->n_inj_targets <= 0) return;
     int pr = prof_begin(c, s, RT_KERNEL_INJECT);
     k_inject<T><<<nblk(c->n_inj_targets, 128), 128, 0, s>>>(
         c->inj_targets.as<int32_t>(), c->inj_off.as<int32_t>(), c->inj_src.as<int32_t>(), c->inj_coef.as<double>(),
-        c->L_dev.as<double>(), c->cfg.n_groups, c->dt_dev.as<double>(), c->n_inj_targets, 4 * c->cfg.n_groups, rec);
+        c->L_dev.as<double>(), c->cfg.n_groups, c->dt_dev.as<double>(), c->n_inj_targets, 4 * c->cfg.n_groups, rec,
+        bins, step);
     prof_end(c, s, pr);
     ++c->launches;
 }
@@ -866,6 +954,69 @@ rt_status launch_inject(rt_ctx* c, cudaStream_t s, void* rec) {
 rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec) {
     if (c->fp64) launch_gradient_t<double>(c, s, (double*)rec);
     else launch_gradient_t<float>(c, s, (float*)rec);
+    RT_CUDA(c, cudaGetLastError());
+    return RT_OK;
+}
+
+// one min-step of a hydro step with individual time bins: injection, gradients, pair fluxes
+// and the gather in their bins forms (direct and per-particle kernels)
+template <class T>
+static void launch_step_bins_t(rt_ctx* c, cudaStream_t s, int step, T* rec, T* out, bool has_src, bool has_alpha) {
+    set_carveouts<T>();
+    const int8_t* bins = c->bins_s.as<int8_t>();
+    if (has_src) launch_inject_t<T>(c, s, rec, bins, step);
+    PairArgs<T> a = pair_args<T>(c);
+    a.bins = bins;
+    a.s = step;
+    FluxExtra<T> x;
+    const bool hll = c->cfg.riemann_solver == RT_RIEMANN_HLL;
+    x.wave = hll ? c->wave_t.as<T>() : nullptr;
+    x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
+    x.alpha_g = c->step_alpha_g ? c->alpha_g_s.as<T>() : nullptr;
+    x.acc = c->acc_t.as<T>();
+    x.dt_dev = c->dt_dev.as<double>();
+    x.c = (T)c->cfg.c_red;
+    x.clamp = c->cfg.clamp_negative;
+    x.clamp_count = reinterpret_cast<unsigned long long*>(c->flags.as<int>() + F_CLAMP);
+    const int G = c->cfg.n_groups;
+    unsigned nb = nblk(c->n, 128);
+    unsigned npb = nblk(std::max<int64_t>(a.n_pairs, 1), 128);
+    T* pb = c->pairbuf.as<T>();
+    T* gr = c->grad_t.as<T>();
+    for (int g0 = 0; g0 < G; g0 += kMaxGC) {
+        const int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
+        switch (gc) {
+            case 1: k_gradient<T, 1, true><<<nb, 128, 0, s>>>(a, rec, gr, g0); break;
+            case 2: k_gradient<T, 2, true><<<nb, 128, 0, s>>>(a, rec, gr, g0); break;
+            case 3: k_gradient<T, 3, true><<<nb, 128, 0, s>>>(a, rec, gr, g0); break;
+            default: k_gradient<T, 4, true><<<nb, 128, 0, s>>>(a, rec, gr, g0); break;
+        }
+        ++c->launches;
+    }
+    for (int g0 = 0; g0 < G; g0 += kMaxGC) {
+        const int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
+#define RT_BINS_FLUX(GC_)                                                                    \
+    if (hll)                                                                                 \
+        k_flux<T, GC_, true, true><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);                   \
+    else                                                                                     \
+        k_flux<T, GC_, false, true><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);                  \
+    k_flux_gather<T, GC_, true><<<nb, 128, 0, s>>>(a, x, rec, pb, out, g0);
+        switch (gc) {
+            case 1: RT_BINS_FLUX(1) break;
+            case 2: RT_BINS_FLUX(2) break;
+            case 3: RT_BINS_FLUX(3) break;
+            default: RT_BINS_FLUX(4) break;
+        }
+#undef RT_BINS_FLUX
+        c->launches += 2;
+    }
+}
+
+rt_status launch_step_bins(rt_ctx* c, cudaStream_t s, int step, void* Uin, void* Uout, bool has_src, bool has_alpha) {
+    if (c->fp64)
+        launch_step_bins_t<double>(c, s, step, (double*)Uin, (double*)Uout, has_src, has_alpha);
+    else
+        launch_step_bins_t<float>(c, s, step, (float*)Uin, (float*)Uout, has_src, has_alpha);
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
 }

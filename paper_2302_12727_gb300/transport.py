@@ -105,6 +105,23 @@ class Transport:
         rt_adjoint(self.ctx, n_sub, dt, ckpt_every, U0, L, alpha, lam_final, lam0, dL)
         return lam0, dL
 
+    def set_time_bins(self, bins=None, dt_min=1.0, cfl=0.0, max_bin=20, limit=True):
+        """Individual time bins (rt_set_time_bins); returns the bins in use [N] (int32 tensor)
+        and B.  bins: int array [N] or None for the CFL rule."""
+        from . import rt_get_time_bins, rt_set_time_bins
+        self._sync_stream()
+        b = None if bins is None else _dev(bins, torch.int32, self.device)
+        rt_set_time_bins(self.ctx, b, dt_min, cfl, max_bin, limit)
+        out = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        B = rt_get_time_bins(self.ctx, out)
+        return out, B
+
+    def step_bins(self, U, L=None, alpha=None):
+        """One hydro step with individual time bins, in place."""
+        from . import rt_step_bins
+        self._sync_stream()
+        rt_step_bins(self.ctx, U, L, alpha)
+
     def set_absorbers(self, n_species, sigma):
         """Photo-ionisation sink per group (rt_set_absorbers): n_species [J, N] float64
         number densities, sigma [G, J] cross sections; None clears."""
