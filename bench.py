@@ -227,6 +227,22 @@ def run_ours(args):
         xs = [torch.as_tensor(np.mod(w.x + k * dt_h * vnp, 1.0), device=dev)
               for k in range(args.warmup + args.steps)]
     counter = [0]
+    bins_info = None
+    if args.bins >= 0:
+        # individual time bins from each particle's CFL step: dt_min = cfl min dx / c, bins up
+        # to args.bins; one hydro step = 2^B min-steps.  Interactions actually evaluated: per
+        # min-step s, the pairs with a starting member (s mod 2^b = 0), times G
+        bsel, B = T.set_time_bins(None, dt_min=dt, cfl=args.cfl, max_bin=args.bins)
+        bh = bsel.cpu().numpy()
+        off, cols = T.pairs()
+        off, cols = off.cpu().numpy(), cols.cpu().numpy()
+        rows = np.repeat(np.arange(n), np.diff(off))
+        up = cols > rows
+        bk, bl = bh[rows[up]], bh[cols[up]]
+        evals = sum(int(np.count_nonzero(((s_ % (1 << bk)) == 0) | ((s_ % (1 << bl)) == 0)))
+                    for s_ in range(1 << B))
+        bins_info = {"max_bin": int(B), "min_steps": 1 << B, "pair_evaluations": evals,
+                     "histogram": np.bincount(bh, minlength=B + 1).tolist()}
 
     def step():
         k = counter[0]
@@ -235,6 +251,10 @@ def run_ours(args):
             T.rebuild(xs[k])
         else:
             T.rebuild()
+        if args.bins >= 0:
+            T.set_time_bins(None, dt_min=dt, cfl=args.cfl, max_bin=args.bins)
+            T.step_bins(U, L, alpha)
+            return T.energy(U)
         T.subcycle(U, n_sub, dt, L, alpha)
         if args.drift > 0:
             d0 = torch.cuda.Event(enable_timing=True)
@@ -287,6 +307,8 @@ def run_ours(args):
     # U.copy_ and flush.fill_ are torch's kernels, outside the per-step events
     t_total = max_over_ranks(sum(times) / 1e3, ws, dev)
     units_rank = P * G * n_sub * args.steps
+    if bins_info:
+        units_rank = bins_info["pair_evaluations"] * G * args.steps
     value = job_value(units_rank, ws, t_total)
     ms_step = t_total / args.steps * 1e3
 
@@ -344,6 +366,10 @@ def run_ours(args):
                               "note": "gradient + flux kernel time only (events around each launch)",
                               "hbm_frac_of_" + peak_kind: sub_bytes_per_particle(G) * n * n_sub / sub_s / 1e9 / hbm_gbs
                               if sub_s > 0 else None},
+            "time_bins": (dict(bins_info, uniform_equivalent_value=P * G * bins_info["min_steps"] * args.steps / t_total,
+                               note="value counts the pair evaluations of the min-steps; uniform_equivalent_value "
+                                    "the P G 2^B a uniform dt_min scheme needs for the same hydro step")
+                          if bins_info else None),
             "drift": ({"ms_per_step": sum(a.elapsed_time(b) for a, b in drift_ev) / len(drift_ev),
                        "note": "rt_drift (gradients + correction) per step, CUDA events; the step also "
                                "re-searches neighbours at the moved positions"} if drift_ev else None),
@@ -500,6 +526,8 @@ def main():
                     help="pair-flux Riemann solver (Eq. riemann-GLF or Eq. riemann-HLL)")
     ap.add_argument("--tuning", default="", help="flux,gather,gradient variants of the float pair kernels")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch variants")
+    ap.add_argument("--bins", type=int, default=-1,
+                    help="individual time bins from the CFL step, up to this bin (one hydro step per step)")
     ap.add_argument("--photo", action="store_true",
                     help="per-group photo-ionisation sink (rt_set_absorbers) instead of the grey kappa")
     ap.add_argument("--drift", type=float, default=0.0,

@@ -226,13 +226,9 @@ rt_status rt_step_bins(rt_ctx* c, void* U, const double* Lsrc, const double* alp
     RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
     RT_TRY(set_step_inputs(c, c->dt_min, Lsrc, alpha));
     RT_CUDA(c, cudaMemsetAsync(c->acc_t.p, 0, (size_t)4 * G * c->n * (c->fp64 ? 8 : 4), c->stream));
-    void* a = c->U_a.p;
-    void* b = c->U_b.p;
-    for (int s = 0; s < (1 << c->bins_max); ++s) {
-        RT_TRY(launch_step_bins(c, c->stream, s, a, b, has_src, alpha != nullptr));
-        std::swap(a, b);
-    }
-    RT_TRY(state_out(c, a, U, 4 * G, 4 * G, 0));
+    for (int s = 0; s < (1 << c->bins_max); ++s)
+        RT_TRY(launch_step_bins(c, c->stream, s, c->U_a.p, has_src, alpha != nullptr));
+    RT_TRY(state_out(c, c->U_a.p, U, 4 * G, 4 * G, 0));
     return RT_OK;
 }
 
@@ -588,7 +584,8 @@ void rt_destroy(rt_ctx* c) {
                       &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
                       &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,
                       &c->inj_coef, &c->src_entry_gas, &c->src_entry_xi, &c->U_a, &c->U_b, &c->grad_t, &c->frec, &c->wave_t, &c->alpha_g_c, &c->alpha_g_s,
-                      &c->sigma_d, &c->bins_s, &c->bins_tmp, &c->acc_t, &c->alpha_s,
+                      &c->sigma_d, &c->bins_s, &c->bins_tmp, &c->acc_t, &c->bins_nmin, &c->order_b, &c->order_m,
+                      &c->order_q, &c->bin_keys, &c->bin_keys2, &c->bin_vals, &c->bin_cub, &c->bin_hist, &c->alpha_s,
                       &c->L_dev, &c->dt_dev, &c->energy_part, &c->ck, &c->seg, &c->lam_a, &c->lam_b, &c->adj_w,
                       &c->adj_x, &c->adj_ub, &c->adj_gam, &c->adj_lam};
     for (DevBuf* b : bufs) free_buf(*b);

@@ -11,6 +11,8 @@
 // them until interacting particles differ by at most two bins.
 #include <cmath>
 
+#include <cub/cub.cuh>
+
 #include "rt_internal.cuh"
 
 namespace rt {
@@ -60,6 +62,78 @@ __global__ void k_bins_out(const int8_t* __restrict__ b, const int32_t* __restri
 }
 
 static unsigned nb256(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+// min over a particle's own bin and its neighbours' bins
+__global__ void k_bins_nmin(const int8_t* __restrict__ b, const int64_t* __restrict__ row_off,
+                            const int32_t* __restrict__ cols, int64_t n, int8_t* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int v = b[i];
+    for (int64_t e = row_off[i]; e < row_off[i + 1]; ++e) v = b[cols[e]] < v ? b[cols[e]] : v;
+    out[i] = (int8_t)v;
+}
+
+// sort keys: a per-particle bin array, or the level min(b_k, b_l) of every pair slot
+// (counts per level: a shared histogram per block, added to the global one once per level)
+__device__ __forceinline__ void hist_flush(unsigned* sh, unsigned long long* hist) {
+    __syncthreads();
+    if (threadIdx.x < 32 && sh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], (unsigned long long)sh[threadIdx.x]);
+}
+
+__global__ void k_keys_particles(const int8_t* __restrict__ v, int64_t n, uint32_t* __restrict__ keys,
+                                 int32_t* __restrict__ vals, unsigned long long* hist) {
+    __shared__ unsigned sh[32];
+    if (threadIdx.x < 32) sh[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        keys[i] = (uint32_t)v[i];
+        vals[i] = (int32_t)i;
+        atomicAdd(&sh[v[i]], 1u);
+    }
+    hist_flush(sh, hist);
+}
+
+__global__ void k_keys_slots(const int8_t* __restrict__ b, const int2* __restrict__ ends, int64_t np,
+                             uint32_t* __restrict__ keys, int32_t* __restrict__ vals, unsigned long long* hist) {
+    __shared__ unsigned sh[32];
+    if (threadIdx.x < 32) sh[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < np) {
+        const int2 kl = ends[t];
+        const int q = b[kl.x] < b[kl.y] ? b[kl.x] : b[kl.y];
+        keys[t] = (uint32_t)q;
+        vals[t] = (int32_t)t;
+        atomicAdd(&sh[q], 1u);
+    }
+    hist_flush(sh, hist);
+}
+
+// stable order of `count` entries by their key (< 32), and the cumulative counts per level
+static rt_status level_order(rt_ctx* c, int64_t count, DevBuf& order, unsigned long long* hist_dev, int B,
+                             std::vector<int64_t>& cum) {
+    cudaStream_t s = c->stream;
+    size_t tb = 0;
+    RT_CUDA(c, cub::DeviceRadixSort::SortPairs(nullptr, tb, (const uint32_t*)nullptr, (uint32_t*)nullptr,
+                                               (const int32_t*)nullptr, (int32_t*)nullptr, (int)count, 0, 5, s));
+    RT_TRY(ensure(c, c->bin_cub, tb + 256, "time-bin sort scratch"));
+    RT_TRY(ensure(c, order, (size_t)std::max<int64_t>(count, 1) * 4, "time-bin order"));
+    tb = c->bin_cub.bytes;
+    RT_CUDA(c, cub::DeviceRadixSort::SortPairs(c->bin_cub.p, tb, c->bin_keys.as<uint32_t>(),
+                                               c->bin_keys2.as<uint32_t>(), c->bin_vals.as<int32_t>(),
+                                               order.as<int32_t>(), (int)count, 0, 5, s));
+    unsigned long long h[32];
+    RT_CUDA(c, cudaMemcpyAsync(h, hist_dev, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(c, cudaStreamSynchronize(s));
+    cum.assign(B + 1, 0);
+    int64_t run = 0;
+    for (int q = 0; q <= B; ++q) {
+        run += (int64_t)h[q];
+        cum[q] = run;
+    }
+    return RT_OK;
+}
 
 }  // namespace rt
 
@@ -111,6 +185,35 @@ rt_status rt_set_time_bins(rt_ctx* c, const int32_t* bins_dev, double dt_min, do
     RT_CUDA(c, cudaGetLastError());
     c->bins_max = mx;
     c->dt_min = dt_min;
+    // active-set orders (see rt_internal.cuh)
+    const int64_t np = c->n_directed / 2;
+    const int64_t m = std::max<int64_t>(std::max<int64_t>(np, n), 1);
+    RT_TRY(ensure(c, c->bins_nmin, (size_t)n, "time bins"));
+    RT_TRY(ensure(c, c->bin_keys, (size_t)m * 4, "time-bin keys"));
+    RT_TRY(ensure(c, c->bin_keys2, (size_t)m * 4, "time-bin keys"));
+    RT_TRY(ensure(c, c->bin_vals, (size_t)m * 4, "time-bin keys"));
+    RT_TRY(ensure(c, c->bin_hist, 3 * 32 * 8, "time-bin counts"));
+    RT_CUDA(c, cudaMemsetAsync(c->bin_hist.p, 0, 3 * 32 * 8, s));
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(c->bin_hist.p);
+    k_bins_nmin<<<nb256(n), 256, 0, s>>>(c->bins_s.as<int8_t>(), c->row_off.as<int64_t>(), c->cols.as<int32_t>(), n,
+                                         c->bins_nmin.as<int8_t>());
+    k_keys_particles<<<nb256(n), 256, 0, s>>>(c->bins_s.as<int8_t>(), n, c->bin_keys.as<uint32_t>(),
+                                              c->bin_vals.as<int32_t>(), hist);
+    c->launches += 2;
+    RT_TRY(level_order(c, n, c->order_b, hist, mx, c->cum_b));
+    k_keys_particles<<<nb256(n), 256, 0, s>>>(c->bins_nmin.as<int8_t>(), n, c->bin_keys.as<uint32_t>(),
+                                              c->bin_vals.as<int32_t>(), hist + 32);
+    ++c->launches;
+    RT_TRY(level_order(c, n, c->order_m, hist + 32, mx, c->cum_m));
+    if (np > 0) {
+        k_keys_slots<<<nb256(np), 256, 0, s>>>(c->bins_s.as<int8_t>(), c->pair_ends.as<int2>(), np,
+                                               c->bin_keys.as<uint32_t>(), c->bin_vals.as<int32_t>(), hist + 64);
+        ++c->launches;
+        RT_TRY(level_order(c, np, c->order_q, hist + 64, mx, c->cum_q));
+    } else {
+        c->cum_q.assign(mx + 1, 0);
+    }
+    RT_CUDA(c, cudaGetLastError());
     c->has_bins = true;
     return RT_OK;
 }

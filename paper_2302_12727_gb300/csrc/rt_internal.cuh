@@ -106,6 +106,12 @@ struct rt_ctx {
     bool has_bins = false;
     int bins_max = 0;
     double dt_min = 0.0;
+    // active sets: a particle starts at min-step s iff b <= ctz(s) (all at s = 0), touches a
+    // starting partner iff nmin <= ctz(s), a pair interacts iff min(b_k, b_l) <= ctz(s); the
+    // particles ordered by b and by nmin and the pair slots by level make every active set a
+    // prefix (cum_*[level] = entries with a key <= level)
+    rt::DevBuf bins_nmin, order_b, order_m, order_q, bin_keys, bin_keys2, bin_vals, bin_cub, bin_hist;
+    std::vector<int64_t> cum_b, cum_m, cum_q;
     CUtensorMap rows_map{};                             // tensor map of frec (tile::gather4)
     const void* rows_map_for = nullptr;
     int64_t rows_map_n = 0;
@@ -166,7 +172,7 @@ rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double
 rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha);
 rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec);
 // one min-step `step` of a hydro step with individual time bins (c->bins_s, c->acc_t)
-rt_status launch_step_bins(rt_ctx* c, cudaStream_t s, int step, void* Uin, void* Uout, bool has_src, bool has_alpha);
+rt_status launch_step_bins(rt_ctx* c, cudaStream_t s, int step, void* U, bool has_src, bool has_alpha);
 // rec += grad_t . (v dt) per component (needs launch_gradient on rec first)
 rt_status launch_drift(rt_ctx* c, cudaStream_t s, void* rec, const double* v, double dt);
 rt_status launch_inject(rt_ctx* c, cudaStream_t s, void* rec);

@@ -239,6 +239,10 @@ struct PairArgs {
     // individual time bins (bins mode only): sorted bin per particle and the min-step index
     const int8_t* bins;
     int s;
+    const int32_t* order;     // the active set of this launch (particles or pair slots)
+    int64_t count;
+    const int8_t* nmin;       // min bin over each particle and its neighbours
+    int tz;                   // interaction level of min-step s
 };
 
 // symmetric 3x3 (xx, yy, zz, xy, xz, yz) times vector
@@ -372,6 +376,10 @@ inline PairArgs<T> pair_args(rt_ctx* c) {
     a.RW = 12 + 16 * a.G;
     a.bins = nullptr;
     a.s = 0;
+    a.order = nullptr;
+    a.count = 0;
+    a.nmin = nullptr;
+    a.tz = 0;
     return a;
 }
 

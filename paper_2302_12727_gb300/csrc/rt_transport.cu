@@ -116,9 +116,11 @@ template <class T, int GC, bool BINS = false>
 __global__ void __launch_bounds__(128) k_gradient(PairArgs<T> a, const T* __restrict__ rec, T* __restrict__ grad,
                                                   int g0) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    if constexpr (BINS) {   // time bins: only particles starting a step take a new gradient
-        if (a.s & ((1 << a.bins[i]) - 1)) return;
+    if constexpr (BINS) {   // time bins: the particles starting a step (an ordered prefix)
+        if (i >= a.count) return;
+        i = a.order[i];
+    } else {
+        if (i >= a.n) return;
     }
     constexpr int NC = 4 * GC;
     const T* tag = nullptr;
@@ -246,19 +248,20 @@ __global__ void __launch_bounds__(256) k_gradient_g(PairArgs<float> a, const flo
 template <class T, int GC, bool HLL, bool BINS = false>
 __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ rec,
                                               T* __restrict__ pairbuf, int g0) {
-    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (slot >= a.n_pairs) return;
+    int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if constexpr (BINS) {   // time bins: the pairs with a starting member (an ordered prefix)
+        if (slot >= a.count) return;
+        slot = a.order[slot];
+    } else {
+        if (slot >= a.n_pairs) return;
+    }
     constexpr int NC = 4 * GC;
     const T* tag = nullptr;
     const int G = a.G, RS = 4 * G;
     const int2 kl = a.ends[slot];
     const int64_t i = kl.x, j = kl.y;
     T wgt = T(1);
-    if constexpr (BINS) {   // time bins: pairs with a starting member, weighted by min(dt_k, dt_l)
-        const int bk = a.bins[i], bl = a.bins[j];
-        if ((a.s & ((1 << bk) - 1)) && (a.s & ((1 << bl) - 1))) return;
-        wgt = T(1 << min(bk, bl));
-    }
+    if constexpr (BINS) wgt = T(1 << min(a.bins[i], a.bins[j]));   // min(dt_k, dt_l) / dt_min
     const Pos<T> pi = load_pos(tag, a.pos, i);
     const Pos<T> pj = load_pos(tag, a.pos, j);
     T gi8[8], gj8[8];
@@ -305,7 +308,8 @@ __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, con
 // that interacted at min-step s (all of them if i starts a step, else those whose partner
 // starts one), in the same order as the uniform gather; at the end of its own step
 // ((s + 1) mod 2^b_i = 0) it applies U_i - dt_min / V_i acc_i, the sink over its step
-// dt_min 2^b_i and the fix-up, and clears the accumulator; otherwise its state is copied.
+// dt_min 2^b_i and the fix-up, and clears the accumulator.  The states are updated in place
+// (this pass runs after the pair pass, and each particle writes only its own record).
 template <class T, int GC>
 __device__ __forceinline__ void gather_bins(const PairArgs<T>& a, const FluxExtra<T>& x, const T* __restrict__ rec,
                                             const T* __restrict__ pairbuf, T* __restrict__ out, int g0, int64_t i) {
@@ -336,13 +340,12 @@ __device__ __forceinline__ void gather_bins(const PairArgs<T>& a, const FluxExtr
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] -= phi[c];
     }
-    T ui[NC];
-    vload<NC>(rec + i * RS + 4 * g0, ui);
-    if ((a.s + 1) & mask) {   // the step of i goes on
+    if ((a.s + 1) & mask) {   // the step of i goes on (the state is updated in place)
         vstore<NC>(accp, acc);
-        vstore<NC>(out + i * RS + 4 * g0, ui);
         return;
     }
+    T ui[NC];
+    vload<NC>(rec + i * RS + 4 * g0, ui);
     const T dt = (T)(*x.dt_dev);
     const T dti = (T)ldexp(*x.dt_dev, bi);
     const T f = dt * a.omega[i];
@@ -365,6 +368,43 @@ __device__ __forceinline__ void gather_bins(const PairArgs<T>& a, const FluxExtr
     if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
 }
 
+// particles whose step ends at min-step s without any interaction at s (no starting partner,
+// nmin > tz): apply the accumulator, the sink over the step and the fix-up, in place
+template <class T, int GC>
+__global__ void k_finalize_bins(PairArgs<T> a, FluxExtra<T> x, T* __restrict__ rec, int g0) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= a.count) return;
+    const int64_t i = a.order[t];
+    if (a.nmin[i] <= a.tz) return;       // finalised by the gather of this min-step
+    constexpr int NC = 4 * GC;
+    const int RS = 4 * a.G;
+    T* accp = x.acc + i * RS + 4 * g0;
+    T acc[NC], ui[NC];
+    vload<NC>(accp, acc);
+    vload<NC>(rec + i * RS + 4 * g0, ui);
+    const int bi = a.bins[i];
+    const T dt = (T)(*x.dt_dev);
+    const T dti = (T)ldexp(*x.dt_dev, bi);
+    const T f = dt * a.omega[i];
+    T sink = T(1);
+    if (x.alpha) sink = fmax_(T(1) - x.c * x.alpha[i] * dti, T(0));
+    int nclamp = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const T sk = x.alpha_g ? fmax_(T(1) - x.c * x.alpha_g[i * a.G + g0 + c / 4] * dti, T(0)) : sink;
+        T v = (ui[c] - f * acc[c]) * sk;
+        if (x.clamp && (c & 3) == 0 && v < T(0)) {
+            v = T(0);
+            ++nclamp;
+        }
+        ui[c] = v;
+        acc[c] = T(0);
+    }
+    vstore<NC>(accp, acc);
+    vstore<NC>(rec + i * RS + 4 * g0, ui);
+    if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
+}
+
 // Pass 2: particle i adds the fluxes of its own upper pairs (contiguous slots) and subtracts
 // those of its lower pairs (k < i, read from k's slots), in a fixed order; then
 // U_i(t + dt) = U_i - dt / V_i sum_l F_il . A_il, the sink and the fix-up.
@@ -372,13 +412,13 @@ template <class T, int GC, bool BINS = false>
 __global__ void __launch_bounds__(128) k_flux_gather(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ rec,
                                                      const T* __restrict__ pairbuf, T* __restrict__ out, int g0) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if constexpr (BINS) {   // the particles with a starting partner or themselves starting
+        if (i < a.count) gather_bins<T, GC>(a, x, rec, pairbuf, out, g0, a.order[i]);
+        return;
+    }
     if (i >= a.n) return;
     constexpr int NC = 4 * GC;
     const int RS = 4 * a.G;
-    if constexpr (BINS) {
-        gather_bins<T, GC>(a, x, rec, pairbuf, out, g0, i);
-        return;
-    }
     T acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = T(0);
@@ -958,16 +998,23 @@ rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec) {
     return RT_OK;
 }
 
-// one min-step of a hydro step with individual time bins: injection, gradients, pair fluxes
-// and the gather in their bins forms (direct and per-particle kernels)
+// one min-step of a hydro step with individual time bins, on the active sets only: the
+// injection and gradients of the starting particles, the pair fluxes of the pairs with a
+// starting member, the gather of the particles they touch (finalising those whose step ends
+// now), and the finalisation of the other particles whose step ends now.  In place.
 template <class T>
-static void launch_step_bins_t(rt_ctx* c, cudaStream_t s, int step, T* rec, T* out, bool has_src, bool has_alpha) {
+static void launch_step_bins_t(rt_ctx* c, cudaStream_t s, int step, T* rec, bool has_src, bool has_alpha) {
     set_carveouts<T>();
     const int8_t* bins = c->bins_s.as<int8_t>();
     if (has_src) launch_inject_t<T>(c, s, rec, bins, step);
+    const int B = c->bins_max;
+    const int tz = step == 0 ? B : __builtin_ctz((unsigned)step);
+    const int tz1 = __builtin_ctz((unsigned)(step + 1)) < B ? __builtin_ctz((unsigned)(step + 1)) : B;
     PairArgs<T> a = pair_args<T>(c);
     a.bins = bins;
     a.s = step;
+    a.nmin = c->bins_nmin.as<int8_t>();
+    a.tz = tz;
     FluxExtra<T> x;
     const bool hll = c->cfg.riemann_solver == RT_RIEMANN_HLL;
     x.wave = hll ? c->wave_t.as<T>() : nullptr;
@@ -979,28 +1026,49 @@ static void launch_step_bins_t(rt_ctx* c, cudaStream_t s, int step, T* rec, T* o
     x.clamp = c->cfg.clamp_negative;
     x.clamp_count = reinterpret_cast<unsigned long long*>(c->flags.as<int>() + F_CLAMP);
     const int G = c->cfg.n_groups;
-    unsigned nb = nblk(c->n, 128);
-    unsigned npb = nblk(std::max<int64_t>(a.n_pairs, 1), 128);
     T* pb = c->pairbuf.as<T>();
     T* gr = c->grad_t.as<T>();
+    const int64_t n_start = c->cum_b[tz], n_touch = c->cum_m[tz], n_pairs = c->cum_q[tz], n_end = c->cum_b[tz1];
+    PairArgs<T> ag = a, af = a, ah = a, ae = a;
+    ag.order = c->order_b.as<int32_t>();
+    ag.count = n_start;
+    af.order = c->order_q.as<int32_t>();
+    af.count = n_pairs;
+    ah.order = c->order_m.as<int32_t>();
+    ah.count = n_touch;
+    ae.order = c->order_b.as<int32_t>();
+    ae.count = n_end;
+    const unsigned nbg = nblk(std::max<int64_t>(n_start, 1), 128), nbf = nblk(std::max<int64_t>(n_pairs, 1), 128);
+    const unsigned nbh = nblk(std::max<int64_t>(n_touch, 1), 128), nbe = nblk(std::max<int64_t>(n_end, 1), 128);
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         const int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
+        if (n_start == 0) break;
         switch (gc) {
-            case 1: k_gradient<T, 1, true><<<nb, 128, 0, s>>>(a, rec, gr, g0); break;
-            case 2: k_gradient<T, 2, true><<<nb, 128, 0, s>>>(a, rec, gr, g0); break;
-            case 3: k_gradient<T, 3, true><<<nb, 128, 0, s>>>(a, rec, gr, g0); break;
-            default: k_gradient<T, 4, true><<<nb, 128, 0, s>>>(a, rec, gr, g0); break;
+            case 1: k_gradient<T, 1, true><<<nbg, 128, 0, s>>>(ag, rec, gr, g0); break;
+            case 2: k_gradient<T, 2, true><<<nbg, 128, 0, s>>>(ag, rec, gr, g0); break;
+            case 3: k_gradient<T, 3, true><<<nbg, 128, 0, s>>>(ag, rec, gr, g0); break;
+            default: k_gradient<T, 4, true><<<nbg, 128, 0, s>>>(ag, rec, gr, g0); break;
         }
         ++c->launches;
     }
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         const int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
 #define RT_BINS_FLUX(GC_)                                                                    \
-    if (hll)                                                                                 \
-        k_flux<T, GC_, true, true><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);                   \
-    else                                                                                     \
-        k_flux<T, GC_, false, true><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);                  \
-    k_flux_gather<T, GC_, true><<<nb, 128, 0, s>>>(a, x, rec, pb, out, g0);
+    if (n_pairs > 0) {                                                                       \
+        if (hll)                                                                             \
+            k_flux<T, GC_, true, true><<<nbf, 128, 0, s>>>(af, x, rec, pb, g0);              \
+        else                                                                                 \
+            k_flux<T, GC_, false, true><<<nbf, 128, 0, s>>>(af, x, rec, pb, g0);             \
+        ++c->launches;                                                                       \
+    }                                                                                        \
+    if (n_touch > 0) {                                                                       \
+        k_flux_gather<T, GC_, true><<<nbh, 128, 0, s>>>(ah, x, rec, pb, rec, g0);            \
+        ++c->launches;                                                                       \
+    }                                                                                        \
+    if (n_end > 0) {                                                                         \
+        k_finalize_bins<T, GC_><<<nbe, 128, 0, s>>>(ae, x, rec, g0);                         \
+        ++c->launches;                                                                       \
+    }
         switch (gc) {
             case 1: RT_BINS_FLUX(1) break;
             case 2: RT_BINS_FLUX(2) break;
@@ -1008,15 +1076,14 @@ static void launch_step_bins_t(rt_ctx* c, cudaStream_t s, int step, T* rec, T* o
             default: RT_BINS_FLUX(4) break;
         }
 #undef RT_BINS_FLUX
-        c->launches += 2;
     }
 }
 
-rt_status launch_step_bins(rt_ctx* c, cudaStream_t s, int step, void* Uin, void* Uout, bool has_src, bool has_alpha) {
+rt_status launch_step_bins(rt_ctx* c, cudaStream_t s, int step, void* U, bool has_src, bool has_alpha) {
     if (c->fp64)
-        launch_step_bins_t<double>(c, s, step, (double*)Uin, (double*)Uout, has_src, has_alpha);
+        launch_step_bins_t<double>(c, s, step, (double*)U, has_src, has_alpha);
     else
-        launch_step_bins_t<float>(c, s, step, (float*)Uin, (float*)Uout, has_src, has_alpha);
+        launch_step_bins_t<float>(c, s, step, (float*)U, has_src, has_alpha);
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
 }
