@@ -522,3 +522,39 @@ def test_drift_correction_against_oracle():
         oo = oracle.Oracle(xo, m, None)
         t.rebuild(xo)
     t.close()
+
+
+def test_edge_cases():
+    """Five groups (two launch chunks of the pair kernels: 4 + 1) against the oracle in FP64
+    and FP32; dt = 0 and zero sub-cycles leave the state bitwise unchanged."""
+    _need_gpu()
+    rng = np.random.default_rng(101)
+    x = W.jittered_lattice(10, 0.25, rng)
+    n = x.shape[1]
+    G = 5
+    xs = np.array([[0.3], [0.6], [0.5]])
+    U0 = np.zeros((G, 4, n))
+    U0[:, 0] = rng.uniform(0.5, 2.0, size=(G, n))
+    U0[:, 1:] = 0.4 * U0[:, :1] * rng.uniform(-1, 1, size=(G, 3, n)) / np.sqrt(3)
+    Ls = rng.uniform(0.5, 2.0, size=(1, G))
+    a = rng.uniform(0.0, 1.0, size=n)
+    o = oracle.Oracle(x, np.full(n, 1.0 / n), xs, n_groups=G)
+    dt = cfl_dt(o, 0.6)
+    ref, _ = o.run(U0, 3, dt, Ls, a)
+    for prec in ("fp64", "fp32"):
+        t = Transport(x, None, xs, n_groups=G, precision=prec)
+        L, al = t.luminosities(Ls), t.alpha(a)
+        U = t.state(U0)
+        t.subcycle(U, 3, dt, L, al)
+        Ug = U.cpu().numpy().astype(np.float64)
+        if prec == "fp64":
+            nbad, rmax = fp64_close(Ug, ref)
+            assert nbad == 0, rmax
+        else:
+            assert rel_l1(Ug, ref).max() <= 5e-5
+        V = t.state(U0)
+        t.subcycle(V, 0, dt, L, al)
+        assert torch.equal(V, t.state(U0))
+        t.step(V, 0.0, L, al)
+        assert torch.equal(V, t.state(U0))
+        t.close()
