@@ -109,3 +109,31 @@ def test_mixed_bins_conserve_energy_and_cfl_bins():
     with pytest.raises(RTError):
         t.step_bins(t.state(U0))      # rt_neighbours discards the bins
     t.close()
+
+
+def test_bins_with_hll_and_group_sink():
+    """Time bins with the HLL flux against the oracle (FP64 per element); with absorbers of
+    equal alpha in every group, bitwise the grey sink's run."""
+    _need_gpu()
+    rng, x, xs, U0, o, dt, Ls, a = setup(seed=93)
+    n = x.shape[1]
+    b0 = rng.integers(0, 3, size=n).astype(np.int32)
+    oh = oracle.Oracle(x, np.full(n, 1.0 / n), xs, n_groups=2, riemann="hll")
+    ref, bo, _ = oh.step_bins(U0, dt / 4, b0, Ls, a)
+    t = Transport(x, None, xs, n_groups=2, precision="fp64", riemann="hll")
+    t.set_time_bins(b0, dt_min=dt / 4)
+    U = t.state(U0)
+    t.step_bins(U, t.luminosities(Ls), t.alpha(a))
+    nbad, rmax = fp64_close(U.cpu().numpy(), ref)
+    assert nbad == 0, rmax
+    t.close()
+    t = Transport(x, None, xs, n_groups=2, precision="fp32")
+    L = t.luminosities(Ls)
+    t.set_time_bins(b0, dt_min=dt / 4)
+    grey = t.state(U0)
+    t.step_bins(grey, L, t.alpha(a))
+    t.set_absorbers(a[None, :], np.ones((2, 1)))
+    grp = t.state(U0)
+    t.step_bins(grp, L)
+    assert torch.equal(grp, grey)
+    t.close()
