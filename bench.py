@@ -118,6 +118,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_sha1(csrc):
+    """sha1 of rt_transport.cu followed by rt_pair.cuh with // comments and blank lines
+    removed: the code the counters were taken on, whatever its comments say."""
+    lines = []
+    for f in ("rt_transport.cu", "rt_pair.cuh"):
+        for line in open(os.path.join(csrc, f)).read().splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code.strip():
+                lines.append(code)
+    return hashlib.sha1("\n".join(lines).encode()).hexdigest()
+
+
 def flux_traffic_from_profile(G):
     """DRAM bytes of one pair-pass launch from the committed ncu summary, if it was taken on
     the current source of the kernels (else None)."""
@@ -130,8 +142,7 @@ def flux_traffic_from_profile(G):
     h = re.search(r"source_sha1:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
-    blob = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("rt_transport.cu", "rt_pair.cuh"))
-    cur = hashlib.sha1(blob).hexdigest()
+    cur = kernel_source_sha1(csrc)
     return float(m.group(1)) if h.group(1) == cur else None
 
 

@@ -108,7 +108,8 @@ typedef struct {
     double dx_min;            /* min_i (V_i / (4 pi / 3))^(1/3), the cell size of Eq. rt-cfl */
     int64_t clamp_events;     /* cumulative count of E < 0 fix-ups */
     int32_t grid[3];          /* cell-list dimensions used by rt_neighbours */
-    int32_t threads_per_particle;  /* launch shape picked for the pair kernels */
+    int32_t threads_per_particle;  /* threads per particle of the float gradient kernel (G,
+                                      at most 4, in gradient_variant 1; else 1) */
     int64_t kernel_launches;  /* cumulative launches of the library's own kernels (graph
                                  replays count every kernel node; library sorts and scans
                                  that the build calls are not counted) */

@@ -446,7 +446,9 @@ rt_status rt_diagnostics(rt_ctx* c, rt_diag* out) {
     }
     c->diag.clamp_events = (int64_t)cl;
     c->diag.wait_timeouts = timed_out;
-    c->diag.threads_per_particle = c->tpp;
+    // the float gradient and gather run one thread per (particle, group) in variant 1
+    const int gc = c->cfg.n_groups < kMaxGC ? c->cfg.n_groups : kMaxGC;
+    c->diag.threads_per_particle = (!c->fp64 && c->tune.gradient_variant == 1) ? gc : 1;
     c->diag.kernel_launches = c->launches;
     *out = c->diag;
     return RT_OK;

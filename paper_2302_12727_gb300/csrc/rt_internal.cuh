@@ -121,7 +121,6 @@ struct rt_ctx {
 
     // diagnostics
     rt_diag diag{};
-    int tpp = 1;   // threads per particle for pair kernels
     // launch variants of the float pair kernels (rt_set_tuning); the double path has one
     rt_tuning tune{2, 1, 1};
 

@@ -9,12 +9,16 @@
 // geometry record of 8 values {1/H, h, Bp (6)} with Bp = V^2 sigma / H^3 B so that
 // V_i psitilde_j(x_i) = Bp_i d w(q).  A neighbour's data is then a few 16-byte loads.
 //
-// The gradient kernel runs one thread per particle over its symmetric neighbour list.  The
-// flux of each unordered pair (k < l) is evaluated once, by one thread with k as the left
-// state, and stored in the pair's slot; a second kernel lets every particle add the fluxes
-// of its upper pairs and subtract those of its lower pairs in a fixed order.  Both particles thus
-// apply the very same Phi_kl with opposite signs: the exchange is exactly antisymmetric,
-// and so exactly conservative, deterministic, and free of atomics.
+// The gradient kernels run one thread per particle (or per particle and group) over its
+// symmetric neighbour list.  The flux of each unordered pair (k < l) is evaluated once, by
+// one thread with k as the left state, and stored in the pair's slot (three launch variants:
+// direct loads, cp.async staging, or TMA row gathers of packed flux rows that the gradient
+// pass writes); a gather kernel lets every particle add the fluxes of its upper pairs and
+// subtract those of its lower pairs in a fixed order.  Both particles thus apply the very
+// same Phi_kl with opposite signs: the exchange is exactly antisymmetric, and so exactly
+// conservative, deterministic, and free of atomics.  With individual time bins the same
+// kernels run on the active sets of each min-step (BINS instantiations) and the fluxes are
+// weighted by min(dt_k, dt_l) and accumulated until each particle's step ends.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
