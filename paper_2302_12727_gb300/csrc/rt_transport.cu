@@ -666,14 +666,14 @@ __global__ void __launch_bounds__(256) k_flux_gather_g(PairArgs<float> a, FluxEx
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     const int64_t r0 = a.row_off[i], s0 = a.up_off[i], s1 = a.up_off[i + 1];
     int64_t sl = s0;
-    for (; sl + 4 <= s1; sl += 4) {   // four loads in flight, added in order
-        float p0[4], p1[4], p2[4], p3[4];
-        vload<4>(pb + sl * NC, p0);
-        vload<4>(pb + (sl + 1) * NC, p1);
-        vload<4>(pb + (sl + 2) * NC, p2);
-        vload<4>(pb + (sl + 3) * NC, p3);
+    for (; sl + 8 <= s1; sl += 8) {   // eight loads in flight, added in order
+        float p[8][4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] = (((acc[c] + p0[c]) + p1[c]) + p2[c]) + p3[c];
+        for (int u = 0; u < 8; ++u) vload<4>(pb + (sl + u) * NC, p[u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] += p[u][c];
     }
     for (; sl < s1; ++sl) {
         float phi[4];
@@ -684,14 +684,17 @@ __global__ void __launch_bounds__(256) k_flux_gather_g(PairArgs<float> a, FluxEx
     const int nl = a.n_low[i];
     const int32_t* ls = a.low_slot + (r0 - s0);
     int e = 0;
-    for (; e + 4 <= nl; e += 4) {
-        float p0[4], p1[4], p2[4], p3[4];
-        vload<4>(pb + (int64_t)ls[e] * NC, p0);
-        vload<4>(pb + (int64_t)ls[e + 1] * NC, p1);
-        vload<4>(pb + (int64_t)ls[e + 2] * NC, p2);
-        vload<4>(pb + (int64_t)ls[e + 3] * NC, p3);
+    for (; e + 8 <= nl; e += 8) {   // eight slot indices, then eight loads in flight
+        int32_t q[8];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] = (((acc[c] - p0[c]) - p1[c]) - p2[c]) - p3[c];
+        for (int u = 0; u < 8; ++u) q[u] = ls[e + u];
+        float p[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) vload<4>(pb + (int64_t)q[u] * NC, p[u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] -= p[u][c];
     }
     for (; e < nl; ++e) {
         float phi[4];
