@@ -336,7 +336,8 @@ def run_ours(args):
         achieved = flux_flops / pair_avg_s / 1e12 if kflux_n else None
         tune = T.tuning()
         default_shape = (args.config == 2 and prec == "fp32" and args.riemann == "glf"
-                         and tune == {"flux_variant": 2, "gather_variant": 1, "gradient_variant": 1})
+                         and tune["flux_variant"] == 2)   # the pair pass is the same kernel
+                                                           # whatever the other two variants
         traffic = flux_traffic_from_profile(G) if default_shape else None
         pair_kernel = {0: "k_flux", 1: "k_flux_staged", 2: "k_flux_tma"}[tune["flux_variant"]]
         sub_s = (kflux_ms + kgrad_ms) / 1e3 / args.steps

@@ -109,7 +109,7 @@ typedef struct {
     int64_t clamp_events;     /* cumulative count of E < 0 fix-ups */
     int32_t grid[3];          /* cell-list dimensions used by rt_neighbours */
     int32_t threads_per_particle;  /* threads per particle of the float gradient kernel (G,
-                                      at most 4, in gradient_variant 1; else 1) */
+                                      at most 4, in gradient_variants 1 and 2; else 1) */
     int64_t kernel_launches;  /* cumulative launches of the library's own kernels (graph
                                  replays count every kernel node; library sorts and scans
                                  that the build calls are not counted) */
@@ -133,7 +133,11 @@ typedef struct {
  *   gather_variant    0: one thread per particle;
  *                     1: one thread per (particle, group) (default).
  *   gradient_variant  0: one thread per particle;
- *                     1: one thread per (particle, group) (default).
+ *                     1: one thread per (particle, group);
+ *                     2: one thread per (particle, group), the lanes of a particle
+ *                        computing the neighbour separations and kernel weights once between
+ *                        them and exchanging them by warp shuffles (default; as 1 for one
+ *                        group).
  * Changing the variants drops the context's captured sub-cycle graphs. */
 typedef struct {
     int32_t flux_variant;
@@ -330,8 +334,8 @@ rt_status rt_set_tuning(rt_ctx* ctx, const rt_tuning* tuning);
 rt_status rt_get_tuning(const rt_ctx* ctx, rt_tuning* tuning);
 
 /* Number of launch-variant combinations rt_autotune tries: candidate k is
- * {flux_variant k / 4, gather_variant (k / 2) % 2, gradient_variant k % 2}. */
-#define RT_TUNE_CANDIDATES 12
+ * {flux_variant k / 6, gather_variant (k / 3) % 2, gradient_variant k % 3}. */
+#define RT_TUNE_CANDIDATES 18
 
 /* Autotuner (no paper counterpart): times n_sub plain transport steps of every candidate
  * launch-variant combination on the caller's state U_dev (4G x N, caller order, element

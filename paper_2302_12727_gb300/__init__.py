@@ -31,7 +31,7 @@ RT_ENERGY_STATIC_MAX_GROUPS = 16
 RT_KERNEL_INJECT, RT_KERNEL_GRADIENT, RT_KERNEL_FLUX, RT_KERNEL_FLUX_GATHER, RT_KERNEL_KINDS = 0, 1, 2, 3, 4
 RT_RIEMANN_GLF, RT_RIEMANN_HLL = 0, 1
 RT_WAVE_NF, RT_WAVE_NTH = 101, 101
-RT_TUNE_CANDIDATES = 12
+RT_TUNE_CANDIDATES = 18
 
 
 class rt_config(C.Structure):
@@ -285,7 +285,7 @@ def rt_kernel_times(ctx):
     return {names[k]: (ms[k], nl[k]) for k in range(RT_KERNEL_KINDS)}
 
 
-def rt_set_tuning(ctx, flux_variant: int = 2, gather_variant: int = 1, gradient_variant: int = 1):
+def rt_set_tuning(ctx, flux_variant: int = 2, gather_variant: int = 1, gradient_variant: int = 2):
     """Launch variants of the float pair kernels (see rt.h); same results for every choice."""
     t = rt_tuning(int(flux_variant), int(gather_variant), int(gradient_variant))
     _check(ctx, load_library().rt_set_tuning(ctx, C.byref(t)))

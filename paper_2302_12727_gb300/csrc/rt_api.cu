@@ -446,9 +446,9 @@ rt_status rt_diagnostics(rt_ctx* c, rt_diag* out) {
     }
     c->diag.clamp_events = (int64_t)cl;
     c->diag.wait_timeouts = timed_out;
-    // the float gradient and gather run one thread per (particle, group) in variant 1
+    // the float gradient runs one thread per (particle, group) in variants 1 and 2
     const int gc = c->cfg.n_groups < kMaxGC ? c->cfg.n_groups : kMaxGC;
-    c->diag.threads_per_particle = (!c->fp64 && c->tune.gradient_variant == 1) ? gc : 1;
+    c->diag.threads_per_particle = (!c->fp64 && c->tune.gradient_variant >= 1) ? gc : 1;
     c->diag.kernel_launches = c->launches;
     *out = c->diag;
     return RT_OK;
@@ -492,8 +492,9 @@ rt_status rt_set_tuning(rt_ctx* c, const rt_tuning* t) {
     c->err.clear();
     if (!t) return fail(c, RT_ERR_INVALID, "rt_set_tuning: NULL tuning");
     if (t->flux_variant < 0 || t->flux_variant > 2 || t->gather_variant < 0 || t->gather_variant > 1 ||
-        t->gradient_variant < 0 || t->gradient_variant > 1)
-        return fail(c, RT_ERR_INVALID, "rt_set_tuning: flux_variant must be 0, 1 or 2, the others 0 or 1");
+        t->gradient_variant < 0 || t->gradient_variant > 2)
+        return fail(c, RT_ERR_INVALID,
+                    "rt_set_tuning: flux_variant and gradient_variant must be 0, 1 or 2, gather_variant 0 or 1");
     if (t->flux_variant != c->tune.flux_variant || t->gather_variant != c->tune.gather_variant ||
         t->gradient_variant != c->tune.gradient_variant) {
         RT_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -502,6 +503,9 @@ rt_status rt_set_tuning(rt_ctx* c, const rt_tuning* t) {
     }
     return RT_OK;
 }
+
+// candidate k of rt_autotune: flux variant k / 6, gather variant (k / 3) % 2, gradient variant k % 3
+static rt_tuning tune_candidate(int k) { return rt_tuning{k / 6, (k / 3) % 2, k % 3}; }
 
 rt_status rt_autotune(rt_ctx* c, const void* U, double dt, int32_t n_sub, const double* Lsrc, const double* alpha,
                       int32_t repeats, rt_tuning* best, double* ms_out) {
@@ -523,8 +527,7 @@ rt_status rt_autotune(rt_ctx* c, const void* U, double dt, int32_t n_sub, const 
         st = fail(c, RT_ERR_CUDA, "rt_autotune: cudaEventCreate failed");
     }
     for (int k = 0; k < RT_TUNE_CANDIDATES && st == RT_OK; ++k) {
-        // candidate k: flux variant k / 4, gather variant (k / 2) % 2, gradient variant k % 2
-        c->tune = rt_tuning{k / 4, (k / 2) % 2, k % 2};
+        c->tune = tune_candidate(k);
         if (c->fp64 && k > 0) {       // the double path has one variant
             if (ms_out) ms_out[k] = ms_out[0];
             continue;
@@ -560,7 +563,7 @@ rt_status rt_autotune(rt_ctx* c, const void* U, double dt, int32_t n_sub, const 
     if (e1) cudaEventDestroy(e1);
     c->tune = saved;
     if (st != RT_OK) return st;
-    const rt_tuning win = c->fp64 ? saved : rt_tuning{best_k / 4, (best_k / 2) % 2, best_k % 2};
+    const rt_tuning win = c->fp64 ? saved : tune_candidate(best_k);
     *best = win;
     return rt_set_tuning(c, &win);
 }

@@ -122,7 +122,7 @@ struct rt_ctx {
     // diagnostics
     rt_diag diag{};
     // launch variants of the float pair kernels (rt_set_tuning); the double path has one
-    rt_tuning tune{2, 1, 1};
+    rt_tuning tune{2, 1, 2};
 
     std::map<rt::GraphKey, rt::GraphEntry> graphs;
 

@@ -244,6 +244,94 @@ __global__ void __launch_bounds__(256) k_gradient_g(PairArgs<float> a, const flo
     }
 }
 
+// Float gradient with the GC lanes of a particle sharing the neighbour geometry: a warp
+// holds 32 / GC particles; per block of 2 GC neighbours each lane computes the separation,
+// spline weight and w d of two consecutive neighbours and passes them to the particle's
+// other lanes with warp shuffles, so the geometry is computed once instead of GC times.
+// Neighbours stay paired (e, e + 1) from the row start and the accumulation is the same
+// expression in the same order as k_gradient_g, so the result bits are the same.
+template <int GC>
+__global__ void __launch_bounds__(256) k_gradient_s(PairArgs<float> a, const float* __restrict__ rec,
+                                                    float* __restrict__ grad, int g0) {
+    constexpr int P = 32 / GC;                     // particles per warp
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int q = lane / GC, g = lane - (lane / GC) * GC;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t i = warp * P + q;
+    const bool act = q < P && i < a.n;             // lanes past P GC and past the last particle idle
+    const int64_t ii = act ? i : 0;
+    const float* tag = nullptr;
+    const Pos<float> pi = load_pos(tag, a.pos, ii);
+    const float iH = a.geo[8 * ii];
+    const int RS = 4 * a.G;
+    const int off = 4 * (g0 + g);
+    float ui[4];
+    vload<4>(rec + ii * RS + off, ui);
+    float acc[4][3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c][0] = acc[c][1] = acc[c][2] = 0.f;
+    const int64_t e0 = a.row_off[ii], e1 = act ? a.row_off[ii + 1] : e0;
+    int nit = (int)((e1 - e0 + 2 * GC - 1) / (2 * GC));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nit = max(nit, __shfl_xor_sync(FULL, nit, o));
+    const int base = q * GC;                       // first lane of this particle
+    for (int it = 0; it < nit; ++it) {
+        // this lane's pair of neighbours
+        const int64_t ea = e0 + (int64_t)it * 2 * GC + 2 * g;
+        const bool has = ea < e1, two = ea + 1 < e1;
+        const int j0 = has ? a.cols[ea] : 0;
+        const int j1 = two ? a.cols[ea + 1] : j0;
+        const Pos<float> p0 = load_pos(tag, a.pos, j0);
+        const Pos<float> p1 = load_pos(tag, a.pos, j1);
+        float dx0, dy0, dz0, dx1, dy1, dz1;
+        sep(a.sp, pi, p0, dx0, dy0, dz0);
+        sep(a.sp, pi, p1, dx1, dy1, dz1);
+        float w0 = spline_w_(sqrt_(dx0 * dx0 + dy0 * dy0 + dz0 * dz0) * iH);
+        float w1 = two ? spline_w_(sqrt_(dx1 * dx1 + dy1 * dy1 + dz1 * dz1) * iH) : 0.f;
+        float wx0 = w0 * dx0, wy0 = w0 * dy0, wz0 = w0 * dz0;
+        float wx1 = w1 * dx1, wy1 = w1 * dy1, wz1 = w1 * dz1;
+        const int hj0 = has ? j0 : -1;
+#pragma unroll
+        for (int u = 0; u < GC; ++u) {
+            const int src = base + u;
+            const int J0 = __shfl_sync(FULL, hj0, src), J1 = __shfl_sync(FULL, j1, src);
+            const float X0 = __shfl_sync(FULL, wx0, src), Y0 = __shfl_sync(FULL, wy0, src),
+                        Z0 = __shfl_sync(FULL, wz0, src);
+            const float X1 = __shfl_sync(FULL, wx1, src), Y1 = __shfl_sync(FULL, wy1, src),
+                        Z1 = __shfl_sync(FULL, wz1, src);
+            if (J0 < 0) continue;
+            float u0[4], u1[4];
+            vload<4>(rec + (int64_t)J0 * RS + off, u0);
+            vload<4>(rec + (int64_t)J1 * RS + off, u1);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float dq0 = u0[c] - ui[c];
+                float dq1 = u1[c] - ui[c];
+                acc[c][0] += dq0 * X0 + dq1 * X1;
+                acc[c][1] += dq0 * Y0 + dq1 * Y1;
+                acc[c][2] += dq0 * Z0 + dq1 * Z1;
+            }
+        }
+    }
+    if (!act) return;
+    float M[6];
+    const float om = a.omega[i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) M[k] = om * a.geo[8 * i + 2 + k];
+    float out[12];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sym_mv(M, acc[c][0], acc[c][1], acc[c][2], out[3 * c], out[3 * c + 1], out[3 * c + 2]);
+    if (a.frec) {
+        float* row = a.frec + i * a.RW;
+        vstore<12>(row + 12 + 4 * a.G + 12 * (g0 + g), out);
+        vstore<4>(row + 12 + off, ui);
+        if (g0 + g == 0) packed_static(a, i, row);
+    } else {
+        vstore<12>(grad + i * 12 * a.G + 12 * (g0 + g), out);
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // a7 + a8: pair fluxes, explicit update, grey sink, optional fix-up, groups [g0, g0 + GC).
 
@@ -813,7 +901,21 @@ static void launch_gradient_t(rt_ctx* c, cudaStream_t s, T* rec, bool packed = f
         int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
         int pr = prof_begin(c, s, RT_KERNEL_GRADIENT);
         if constexpr (std::is_same<T, float>::value) {
-            if (c->tune.gradient_variant == 1) {
+            if (c->tune.gradient_variant == 2 && gc > 1) {
+                // warps of 32 / gc particles: ceil(n / (32 / gc)) warps of 32 lanes
+                const int64_t warps = (c->n + 32 / gc - 1) / (32 / gc);
+                unsigned nbs = nblk(warps * 32, 256);
+                float* gr = c->grad_t.as<float>();
+                switch (gc) {
+                    case 2: k_gradient_s<2><<<nbs, 256, 0, s>>>(a, rec, gr, g0); break;
+                    case 3: k_gradient_s<3><<<nbs, 256, 0, s>>>(a, rec, gr, g0); break;
+                    default: k_gradient_s<4><<<nbs, 256, 0, s>>>(a, rec, gr, g0); break;
+                }
+                prof_end(c, s, pr);
+                ++c->launches;
+                continue;
+            }
+            if (c->tune.gradient_variant >= 1) {
                 unsigned nbg = nblk(c->n * gc, 256);
                 float* gr = c->grad_t.as<float>();
                 switch (gc) {

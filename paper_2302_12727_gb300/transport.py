@@ -159,7 +159,7 @@ class Transport:
         self._sync_stream()
         return rt_diagnostics(self.ctx)
 
-    def set_tuning(self, flux_variant=2, gather_variant=1, gradient_variant=1):
+    def set_tuning(self, flux_variant=2, gather_variant=1, gradient_variant=2):
         rt_set_tuning(self.ctx, flux_variant, gather_variant, gradient_variant)
 
     def tuning(self):

@@ -10,7 +10,7 @@ def test_cache_round_trip(tmp_path):
 
     def tune():
         calls.append(1)
-        return {"flux_variant": 2, "gather_variant": 1, "gradient_variant": 0}, [1.0] * 12
+        return {"flux_variant": 2, "gather_variant": 1, "gradient_variant": 0}, [1.0] * 18
 
     key = A.shape_key(1000, 3, 24000, "glf", "fp32")
     e1 = A.lookup_or_tune(key, tune, applied.append, path)

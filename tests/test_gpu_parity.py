@@ -366,9 +366,9 @@ def test_sorted_pair_build_on_clustered_particles():
     t.close()
 
 
-@pytest.mark.parametrize("G", [3, 5])
+@pytest.mark.parametrize("G", [2, 3, 5])
 def test_launch_variants_give_identical_results(G):
-    """Every (flux, gather) launch variant of the float pair kernels computes the same fluxes
+    """Every (flux, gather, gradient) launch variant of the float pair kernels computes the same fluxes
     and accumulates them in the same order: results bitwise equal, plain steps and graphs.
     G = 5 runs two group chunks (4 + 1) per pass."""
     _need_gpu()
@@ -387,7 +387,7 @@ def test_launch_variants_give_identical_results(G):
     default = t.tuning()
     for fv in (0, 1, 2):
         for gv in (0, 1):
-            for rv in (0, 1):
+            for rv in (0, 1, 2):
                 t.set_tuning(fv, gv, rv)
                 assert t.tuning() == {"flux_variant": fv, "gather_variant": gv, "gradient_variant": rv}
                 U = t.state(U0)
@@ -403,6 +403,8 @@ def test_launch_variants_give_identical_results(G):
     t.set_tuning(**default)
     with pytest.raises(Err):
         t.set_tuning(3, 0, 0)
+    with pytest.raises(Err):
+        t.set_tuning(0, 0, 3)
     assert t.tuning() == default
     assert t.diagnostics()["wait_timeouts"] == 0
     t.close()
@@ -426,7 +428,7 @@ def test_autotune_adopts_a_candidate_with_identical_results(tmp_path):
         assert len(ms) == RT_TUNE_CANDIDATES and all(m > 0 for m in ms)
         assert t.tuning() == best
         if prec == "fp32":
-            k = 4 * best["flux_variant"] + 2 * best["gather_variant"] + best["gradient_variant"]
+            k = 6 * best["flux_variant"] + 3 * best["gather_variant"] + best["gradient_variant"]
             assert ms[k] == min(ms)
         U = U0.clone()
         t.subcycle(U, 4, dt, L)
