@@ -197,8 +197,11 @@ rt_status rt_neighbours(rt_ctx* c, const double* x, const double* m, const doubl
         return s;
     }
     RT_TRY(ensure_state(c));
-    // captured graphs hold buffer addresses and the injection grid size
-    if (g_generation != gen0 || c->n_inj_targets != targets0) drop_graphs(c);
+    // captured graphs hold buffer addresses, the injection grid size and the pair count (the
+    // pair pass's grid and slot bound), which a rebuild can change without moving a buffer
+    std::vector<int64_t> shape{c->n_directed, c->n_inj_targets, c->n_inj_entries};
+    if (g_generation != gen0 || c->n_inj_targets != targets0 || shape != c->graph_shape) drop_graphs(c);
+    c->graph_shape = shape;
     if (h_out) {
         // h in caller order
         RT_TRY(field_out(c, c->h_d.as<double>(), h_out, 1));

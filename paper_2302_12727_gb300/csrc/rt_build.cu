@@ -1304,17 +1304,16 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         }
     }
 
-    // finish: flags, counters
+    // finish: flags, counters (one synchronisation)
+    double cv[2];
     RT_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+    RT_CUDA(c, cudaMemcpyAsync(cv, red + 2, sizeof(cv), cudaMemcpyDeviceToHost, st));
     RT_CUDA(c, cudaStreamSynchronize(st));
     if (hflags[F_GEOM]) return fail(c, RT_ERR_GEOMETRY, "singular E_i: a particle has fewer than 3 non-coplanar neighbours");
     c->diag.n_ill_conditioned = hflags[F_ILL];
     c->diag.n_directed = P2;
     c->diag.n_pairs = P2 / 2;
     c->diag.n_injection = c->n_inj_entries;
-    double cv[2];
-    RT_CUDA(c, cudaMemcpyAsync(cv, red + 2, sizeof(cv), cudaMemcpyDeviceToHost, st));
-    RT_CUDA(c, cudaStreamSynchronize(st));
     c->diag.cond_max = cv[0];
     c->diag.dx_min = std::cbrt(cv[1] / (4.0 * M_PI / 3.0));
     // keep h in caller order as the first guess of the next call

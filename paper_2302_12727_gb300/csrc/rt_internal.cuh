@@ -83,6 +83,9 @@ struct rt_ctx {
     rt::DevBuf pkeys, pkeys_alt;                        // (row, col) keys of the sort-based build
     rt::DevBuf n_low, n_up, up_off, low_slot, pair_ends; // lower / upper split, pair slots
     rt::DevBuf pairbuf;                                 // per-pair fluxes of one group chunk
+    // sizes that captured graphs bake in besides buffer addresses (pair count, injection
+    // targets and entries): a rebuild that changes them drops the graphs
+    std::vector<int64_t> graph_shape;
     rt::DevBuf flags;                                   // int32 error flags + counters
     rt::DevBuf red_tmp;                                 // small reduction scratch (double)
     int64_t n_directed = 0;

@@ -144,6 +144,42 @@ def test_plain_steps_equal_graph_bitwise(cfg1):
         t.close()
 
 
+@pytest.mark.parametrize("sources", [False, True])
+def test_graphs_follow_a_rebuild_that_changes_the_pair_count(sources):
+    """A captured sub-cycle graph holds the pair count (grid and slot bound of the pair pass)
+    and the injection sizes.  Rebuilds that keep the buffers (the largest pair count comes
+    first) but change the pair count must not replay a stale graph: after each rebuild the
+    graph run equals the plain steps bitwise, in both precisions.  Without sources the
+    injection sizes stay 0, so only the pair count can tell that the graph is stale."""
+    _need_gpu()
+    w = W.config2(24)
+    rng = np.random.default_rng(77)
+    xs = [np.mod(w.x + 0.004 * k * rng.standard_normal(w.x.shape), 1.0) for k in range(5)]
+    xsrc = w.xsrc if sources else None
+    for prec in ("fp32", "fp64"):
+        t = Transport(w.x, w.m, xsrc, n_groups=w.n_groups, precision=prec, c_red=w.c_red)
+        counts = []
+        for x in xs:
+            t.rebuild(x)
+            counts.append(t.diagnostics()["n_pairs"])
+        order = np.argsort(counts)
+        assert counts[order[-1]] > counts[order[1]] > counts[order[0]]
+        L = t.luminosities(w.Lsrc) if sources else None
+        # buffers sized for the largest count; a graph captured at the smallest, then run at
+        # a middle one (a stale replay would skip the extra pair slots)
+        t.rebuild(xs[order[-1]])
+        for k in (order[0], order[1]):
+            t.rebuild(xs[k])
+            dt = 0.9 * t.diagnostics()["dx_min"]
+            U1 = t.state(w.U0)
+            for _ in range(3):
+                t.step(U1, dt, L)
+            U2 = t.state(w.U0)
+            t.subcycle(U2, 3, dt, L)
+            assert torch.equal(U1, U2), (prec, counts[k])
+        t.close()
+
+
 def test_fp32_config1_against_oracle(cfg1):
     """FP32 mixed path: relative L1 <= 1e-5 per step, energy drift <= 1e-6."""
     w, o = cfg1
