@@ -38,11 +38,11 @@ __device__ __forceinline__ T spline_w_(T q) {
     return a * a * a - T(4) * (b * b * b);
 }
 
-// minmod of Eq. rt-minmod as selects: both positive -> min, both negative -> max, else 0
+// minmod of Eq. rt-minmod (both positive -> min, both negative -> max, else 0) as the median
+// of a, b and 0: max(min(a, b), min(max(a, b), 0)), four min/max and no compare or select
 template <class T>
 __device__ __forceinline__ T minmod_(T a, T b) {
-    T lo = fmin_(a, b), hi = fmax_(a, b);
-    return lo > T(0) ? lo : (hi < T(0) ? hi : T(0));
+    return fmax_(fmin_(a, b), fmin_(fmax_(a, b), T(0)));
 }
 
 // smallest normal number: a product or reciprocal below it is flushed by the approximate

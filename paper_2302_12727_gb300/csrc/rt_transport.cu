@@ -249,9 +249,11 @@ __global__ void __launch_bounds__(256) k_gradient_g(PairArgs<float> a, const flo
 // spline weight and w d of two consecutive neighbours and passes them to the particle's
 // other lanes with warp shuffles, so the geometry is computed once instead of GC times.
 // Neighbours stay paired (e, e + 1) from the row start and the accumulation is the same
-// expression in the same order as k_gradient_g, so the result bits are the same.
+// expression in the same order as k_gradient_g, so the result bits are the same.  With four
+// groups (eight particles per warp, every lane busy) five blocks per SM (48 registers, a few
+// spilled) beat four at 64 registers by 7%; with three groups they lose 2%.
 template <int GC>
-__global__ void __launch_bounds__(256) k_gradient_s(PairArgs<float> a, const float* __restrict__ rec,
+__global__ void __launch_bounds__(256, GC == 4 ? 5 : 0) k_gradient_s(PairArgs<float> a, const float* __restrict__ rec,
                                                     float* __restrict__ grad, int g0) {
     constexpr int P = 32 / GC;                     // particles per warp
     const unsigned FULL = 0xffffffffu;
