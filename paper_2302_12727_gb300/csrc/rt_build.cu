@@ -371,42 +371,60 @@ struct PairParams {
     double Hmax;
 };
 
+// FILL = false counts each row into counts[p]; with cap > 0 it also writes the first cap
+// entries of row p to cols[p cap ...] and raises *row_max to the longest row.  FILL = true
+// writes row p to cols[row_off[p] ...].  Both walk the candidates in the same order.
 template <bool FILL>
 __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
                         const double* __restrict__ h, const float* __restrict__ H2f, int64_t n, PairParams pp,
-                        int32_t* counts, const int64_t* __restrict__ row_off, int32_t* cols) {
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
-    double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
-    const float H2i = H2f[p];
-    float R = sqrtf(fmaxf(H2i, (float)(pp.Hmax * pp.Hmax))) * 1.0001f;
+                        int32_t* counts, const int64_t* __restrict__ row_off, int32_t* cols, int cap = 0,
+                        int* row_max = nullptr) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int cnt = 0;
-    int64_t base = FILL ? row_off[p] : 0;
-    for_each_candidate(g, (float)px, (float)py, (float)pz, R, [&](int j) {
-        if (j == p) return;
-        float dx = fsep(xq[j], qx, pp.scale[0]);
-        float dy = fsep(xq[n + j], qy, pp.scale[1]);
-        float dz = fsep(xq[2 * n + j], qz, pp.scale[2]);
-        float r2f = dx * dx + dy * dy + dz * dz;
-        float H2m = fmaxf(H2i, H2f[j]);
-        bool in;
-        if (r2f < H2m * (1.f - 1e-5f)) in = true;
-        else if (r2f > H2m * (1.f + 1e-5f)) in = false;
-        else {
-            // exact double test (no contraction), as a plain double evaluation would do it
-            double Hm = fmax(__dmul_rn(kKappa, h[p]), __dmul_rn(kKappa, h[j]));
-            double ex = sep_exact(xs[j], px, g.box[0], g.periodic);
-            double ey = sep_exact(xs[n + j], py, g.box[1], g.periodic);
-            double ez = sep_exact(xs[2 * n + j], pz, g.box[2], g.periodic);
-            in = norm2_exact(ex, ey, ez) < __dmul_rn(Hm, Hm);
-        }
-        if (in) {
-            if (FILL) cols[base + cnt] = j;
-            ++cnt;
-        }
-    });
-    if (!FILL) counts[p] = cnt;
+    if (p < n) {
+        uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+        double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+        const float H2i = H2f[p];
+        float R = sqrtf(fmaxf(H2i, (float)(pp.Hmax * pp.Hmax))) * 1.0001f;
+        int64_t base = FILL ? row_off[p] : p * (int64_t)cap;
+        for_each_candidate(g, (float)px, (float)py, (float)pz, R, [&](int j) {
+            if (j == p) return;
+            float dx = fsep(xq[j], qx, pp.scale[0]);
+            float dy = fsep(xq[n + j], qy, pp.scale[1]);
+            float dz = fsep(xq[2 * n + j], qz, pp.scale[2]);
+            float r2f = dx * dx + dy * dy + dz * dz;
+            float H2m = fmaxf(H2i, H2f[j]);
+            bool in;
+            if (r2f < H2m * (1.f - 1e-5f)) in = true;
+            else if (r2f > H2m * (1.f + 1e-5f)) in = false;
+            else {
+                // exact double test (no contraction), as a plain double evaluation would do it
+                double Hm = fmax(__dmul_rn(kKappa, h[p]), __dmul_rn(kKappa, h[j]));
+                double ex = sep_exact(xs[j], px, g.box[0], g.periodic);
+                double ey = sep_exact(xs[n + j], py, g.box[1], g.periodic);
+                double ez = sep_exact(xs[2 * n + j], pz, g.box[2], g.periodic);
+                in = norm2_exact(ex, ey, ez) < __dmul_rn(Hm, Hm);
+            }
+            if (in) {
+                if (FILL || cnt < cap) cols[base + cnt] = j;
+                ++cnt;
+            }
+        });
+        if (!FILL) counts[p] = cnt;
+    }
+    if (!FILL && row_max) {   // every lane of the (full) warp takes part
+        const int m = __reduce_max_sync(0xffffffffu, cnt);
+        if ((threadIdx.x & 31) == 0) atomicMax(row_max, m);
+    }
+}
+
+// rows of cap entries (k_pairs' counting walk) -> CSR rows at row_off
+__global__ void k_rows_compact(const int32_t* __restrict__ cols_cap, int64_t cap, const int64_t* __restrict__ row_off,
+                               int64_t n, int32_t* __restrict__ cols) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t b = row_off[p], m = row_off[p + 1] - b;
+    for (int64_t k = 0; k < m; ++k) cols[b + k] = cols_cap[p * cap + k];
 }
 
 // Rows sorted ascending are [lower neighbours j < i | upper neighbours j > i].  Each
@@ -718,6 +736,7 @@ __device__ __forceinline__ void warp_candidates(const Grid& g, int cx, int cy, i
 struct SrcParams {
     double eta, h0, h_cap;
     int max_iter;
+    int warm;       // start from the h of the last call (in hs_out), else from h0
 };
 
 // Rows of the culled walk of for_each_candidate handed out round-robin to the threads of a
@@ -789,7 +808,9 @@ __global__ void __launch_bounds__(kSrcThreads) k_src_h(Grid g, const double* __r
     __shared__ double red_w[kSrcThreads], red_dw[kSrcThreads];
     double p[3] = {xsrc[s_id], xsrc[S + s_id], xsrc[2 * S + s_id]};
     const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
-    double h = sp.h0, lo = 0.0, hi = INFINITY, om = 0.0;
+    double h = sp.warm ? hs_out[s_id] : sp.h0, lo = 0.0, hi = INFINITY, om = 0.0;
+    if (!(h > 0.0) || !(h < sp.h_cap)) h = sp.h0;
+    __syncthreads();    // every thread has read the first guess before thread 0 overwrites it
     bool ok = false;
     for (int it = 0; it < sp.max_iter; ++it) {
         double H = kKappa * h, iH = 1.0 / H, H2 = H * H;
@@ -1113,21 +1134,40 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     c->diag.pair_build = sorted_build ? 1 : 0;
     int64_t P2 = 0;
     if (!sorted_build) {
+        // one walk counts the rows and, when the rows of the last call fit row_cap entries,
+        // also stores them (then compacted); a longer row needs a second, writing walk
+        const int cap = (int)c->row_cap;
+        if (cap > 0) RT_TRY(ensure(c, c->cols_cap, (size_t)n * cap * 4, "pair rows"));
+        int* row_max = c->flags.as<int>() + F_ROWMAX;
+        RT_CUDA(c, cudaMemsetAsync(row_max, 0, 4, st));
         k_pairs<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
                                                       c->h_d.as<double>(), c->H2f.as<float>(), n, pp,
-                                                      c->counts.as<int32_t>(), nullptr, nullptr);
+                                                      c->counts.as<int32_t>(), nullptr,
+                                                      cap > 0 ? c->cols_cap.as<int32_t>() : nullptr, cap, row_max);
         RT_CUDA(c, cudaMemsetAsync(c->counts.as<int32_t>() + n, 0, 4, st));
         tb = c->cub_tmp.bytes;
         RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->counts.as<int32_t>(), c->row_off.as<int64_t>(),
                                                  (int)(n + 1), st));
+        int longest = 0;
         RT_CUDA(c, cudaMemcpyAsync(&P2, c->row_off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st));
+        RT_CUDA(c, cudaMemcpyAsync(&longest, row_max, 4, cudaMemcpyDeviceToHost, st));
         RT_CUDA(c, cudaStreamSynchronize(st));
         if (P2 >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "more than 2^31 neighbour entries");
         RT_TRY(ensure(c, c->cols, std::max<int64_t>(P2, 1) * 4, "pair lists"));
         RT_TRY(ensure(c, c->cols_tmp, std::max<int64_t>(P2, 1) * 4, "pair lists"));
-        k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
-                                                     c->h_d.as<double>(), c->H2f.as<float>(), n, pp, nullptr,
-                                                     c->row_off.as<int64_t>(), c->cols_tmp.as<int32_t>());
+        if (cap > 0 && longest <= cap) {
+            k_rows_compact<<<nblk(n, 128), 128, 0, st>>>(c->cols_cap.as<int32_t>(), cap, c->row_off.as<int64_t>(), n,
+                                                          c->cols_tmp.as<int32_t>());
+        } else {
+            k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
+                                                         c->h_d.as<double>(), c->H2f.as<float>(), n, pp, nullptr,
+                                                         c->row_off.as<int64_t>(), c->cols_tmp.as<int32_t>());
+        }
+        // the next call's rows: the longest row with a quarter to spare, in multiples of 32,
+        // while the padded rows stay within eight times the lists (only the filled part of a
+        // row is written or read)
+        const int64_t next = ((int64_t)longest + longest / 4 + 8 + 31) / 32 * 32;
+        c->row_cap = next * n <= 8 * std::max<int64_t>(P2, 1) ? next : 0;
         RT_CUDA(c, cudaGetLastError());
         c->launches += 2;
         // rows in ascending order
@@ -1243,6 +1283,8 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         sp.h0 = cfg.eta_res_star * std::cbrt(vol / (double)n);
         sp.h_cap = hp.h_cap;
         sp.max_iter = std::max(hp.max_iter, 200);
+        sp.warm = c->has_hs_prev ? 1 : 0;
+        c->has_hs_prev = false;     // set again only when this call succeeds
         unsigned sb = nblk(S * 32, 128);
         k_src_h<<<(unsigned)S, kSrcThreads, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S, sp,
                                                      c->hs_d.as<double>(), c->omegas_d.as<double>(), flags);
@@ -1320,6 +1362,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     RT_TRY(ensure(c, c->h_prev, n * 8, "h"));
     RT_TRY(field_out(c, c->h_d.as<double>(), c->h_prev.as<double>(), 1));
     c->has_h_prev = true;
+    c->has_hs_prev = S > 0;
     return RT_OK;
 }
 

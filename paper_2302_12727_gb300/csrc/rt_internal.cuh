@@ -22,7 +22,7 @@ constexpr double kSigma = 5.0929581789406507446;   // 16 / pi
 // int slots of the context's 64-byte flag buffer (cleared by every rt_neighbours): error
 // flags of the build, the clamp counter (64-bit, slots 8-9) and the device-wait time-out flag
 enum FlagSlot { F_BADPOS = 0, F_NOCONV = 1, F_GEOM = 2, F_ILL = 3, F_SRC_NOCONV = 4, F_NSLOTS = 8, F_CLAMP = 8,
-                F_TIMEOUT = 12, F_SCRATCH = 13 };
+                F_TIMEOUT = 12, F_SCRATCH = 13, F_ROWMAX = 14 };
 constexpr int kMaxGC = 4;                          // groups handled by one pair-kernel launch
 
 // ------------------------------------------------------------------------------------
@@ -78,8 +78,13 @@ struct rt_ctx {
     rt::DevBuf H2f;                                     // float (kappa h)^2, pair-search prefilter
     rt::DevBuf h_prev;                                  // h of the last call, caller order (first guess)
     bool has_h_prev = false;
+    bool has_hs_prev = false;                           // hs_d holds the sources' h of the last call
     rt::DevBuf pos_t, geo_t, omega_t;                   // working precision per particle (pair kernels)
     rt::DevBuf counts, row_off, cols, cols_tmp;         // symmetric pair lists (CSR), rows ascending
+    // rows of row_cap entries that the counting walk of the pair search also fills (0: off);
+    // set from the longest row of the last call
+    rt::DevBuf cols_cap;
+    int64_t row_cap = 0;
     rt::DevBuf pkeys, pkeys_alt;                        // (row, col) keys of the sort-based build
     rt::DevBuf n_low, n_up, up_off, low_slot, pair_ends; // lower / upper split, pair slots
     rt::DevBuf pairbuf;                                 // per-pair fluxes of one group chunk
