@@ -368,6 +368,65 @@ def test_full_size_per_step_parity(cfg):
     t.close()
 
 
+def _brute_force_pairs_check(x, h, off, cols):
+    """The lists (caller indices, CSR) hold exactly the pairs r_ij < max(H_i, H_j), H = H/h h,
+    in the periodic unit box; pairs within 1e-12 of the radius may go either way."""
+    from scipy.spatial import cKDTree
+    n = x.shape[1]
+    H = H_h * h
+    tree = cKDTree(x.T, boxsize=1.0)
+    cand = tree.query_pairs(r=H.max() * (1 + 1e-9), output_type="ndarray")
+    i, j = cand[:, 0], cand[:, 1]
+    d = x[:, j] - x[:, i]
+    d -= np.rint(d)
+    r2 = (d * d).sum(0)
+    Hm2 = np.maximum(H[i], H[j]) ** 2
+    tie = np.abs(r2 - Hm2) < 1e-12 * Hm2
+    want = set(zip(i[(r2 < Hm2) & ~tie].tolist(), j[(r2 < Hm2) & ~tie].tolist()))
+    maybe = set(zip(i[tie].tolist(), j[tie].tolist()))
+    rows = np.repeat(np.arange(n), np.diff(off))
+    got = set((min(a, b), max(a, b)) for a, b in zip(rows.tolist(), cols.tolist()))
+    # symmetric: every unordered pair appears in both rows
+    assert len(cols) == 2 * len(got)
+    assert want <= got and got <= want | maybe
+
+
+def test_rebuild_stores_or_rewalks_the_pair_rows():
+    """The counting walk of the pair search also stores the rows when they fit the longest
+    row of the last call with a margin; a longer row makes the build walk a second time to
+    write them.  A jittered lattice (rows up to 58), then a set with an 8:1 density step
+    (rows up to 127 where the dense side meets the sparse side's larger supports: the second
+    walk), then the same set again (the stored rows): each time the lists are exactly the
+    brute-force pairs for the context's own h, and the FP64 steps equal those of a context
+    built on that set directly to 1e-12."""
+    _need_gpu()
+    w = W.config2(24)
+    n = w.n
+    lat = W.jittered_lattice(24, 0.1, np.random.default_rng(5))
+    x = np.random.default_rng(9).uniform(0, 1, size=(3, n))
+    nd = n * 8 // 9
+    x[0, :nd] *= 0.5
+    x[0, nd:] = 0.5 + 0.5 * x[0, nd:]
+    t = Transport(lat, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64", c_red=w.c_red)
+    assert t.diagnostics()["pair_build"] == 0
+    fresh = Transport(x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64", c_red=w.c_red)
+    dt = 0.9 * fresh.diagnostics()["dx_min"]
+    ref = fresh.state(w.U0)
+    fresh.subcycle(ref, 3, dt, fresh.luminosities(w.Lsrc))
+    for _ in range(2):
+        t.rebuild(x)
+        assert t.diagnostics()["pair_build"] == 0
+        off, cols = (a.cpu().numpy() for a in t.pairs())
+        assert np.diff(off).max() > 96          # longer than the lattice's stored rows
+        _brute_force_pairs_check(x, t.h.cpu().numpy(), off, cols)
+        U = t.state(w.U0)
+        t.subcycle(U, 3, dt, t.luminosities(w.Lsrc))
+        nbad, rmax = fp64_close(U.cpu().numpy(), ref.cpu().numpy())
+        assert nbad == 0, rmax
+    t.close()
+    fresh.close()
+
+
 def test_sorted_pair_build_on_clustered_particles():
     """A clustered (lognormal) set with a wide h range takes the sort-based pair build; its
     lists equal the oracle's (apart from ties at the support radius), and the FP64 state
