@@ -8,7 +8,7 @@ rt_neighbours (cell list, h, pair lists, geometry, source weights) + rt_subcycle
 Metric: pair-group interactions per second, R = P * G * n_sub / t_step, with P the
 unordered interacting pairs (r < max(H_i, H_j)) and G the photon groups.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload poisson-sine-beam] [--impl reference]
 
 Under torchrun (N > 1) every rank runs an independent replica (weak scaling); the time
 is the max over ranks and the value sums all ranks' units.
@@ -66,9 +66,9 @@ def measured_peaks():
     return 6800.0, 2070.0, "fallback"
 
 
-def workload(cfg_id):
+def workload(name):
     from paper_2302_12727_gb300 import workloads as W
-    return W.CONFIGS[cfg_id]()
+    return W.WORKLOADS[name]()
 
 
 # ---------------------------------------------------------------------------------------
@@ -181,7 +181,7 @@ def run_ours(args):
     if ws > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    w = workload(args.config)
+    w = workload(args.workload)
     G, n_sub, n = w.n_groups, w.n_steps, w.n
     prec = args.precision
     T = Transport(w.x, w.m, w.xsrc, n_groups=G, c_red=w.c_red, precision=prec, device=dev, riemann=args.riemann)
@@ -229,7 +229,7 @@ def run_ours(args):
     # U += grad U . v dt_hydro (dt_hydro = n_sub dt) before the particles move on
     drift_ev = []
     if args.drift > 0:
-        rs = np.random.default_rng(12727 + 100 + args.config)
+        rs = np.random.default_rng(12727 + 100 + w.seed_id)
         dirs = rs.standard_normal((3, n))
         dirs /= np.linalg.norm(dirs, axis=0, keepdims=True)
         vnp = args.drift * w.c_red * dirs
@@ -335,7 +335,7 @@ def run_ours(args):
         flux_flops = P * flux_flops_per_pair(G)
         achieved = flux_flops / pair_avg_s / 1e12 if kflux_n else None
         tune = T.tuning()
-        default_shape = (args.config == 2 and prec == "fp32" and args.riemann == "glf"
+        default_shape = (args.workload == "poisson-sine-beam" and prec == "fp32" and args.riemann == "glf"
                          and tune["flux_variant"] == 2)   # the pair pass is the same kernel
                                                            # whatever the other two variants
         traffic = flux_traffic_from_profile(G) if default_shape else None
@@ -497,7 +497,7 @@ def run_reference(args):
     ws, rank, local = dist_setup()
     if rank != 0:
         return
-    w = workload(args.config)
+    w = workload(args.workload)
     import oracle
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
     off, _ = o.pairs()
@@ -527,7 +527,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--workload", default="poisson-sine-beam",
+                    help="lattice-point-source, poisson-sine-beam (the default), lattice-sources, "
+                         "lognormal-sources or lognormal-sources-large")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--cfl", type=float, default=0.9)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

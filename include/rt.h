@@ -129,7 +129,7 @@ typedef struct {
  *                        shared memory by cooperative asynchronous copies;
  *                     2: the same, with the neighbour rows of each warp fetched into shared
  *                        memory by tensor-memory-accelerator row gathers (default; falls back
- *                        to 0 where the driver offers no tensor-map encoder).
+ *                        to 0 where the CUDA driver offers no tensor-map encoder).
  *   gather_variant    0: one thread per particle;
  *                     1: one thread per (particle, group) (default).
  *   gradient_variant  0: one thread per particle;

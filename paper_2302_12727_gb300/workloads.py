@@ -9,7 +9,7 @@ The shapes stand in for the test set-ups of the thesis (uniform and glass-like
 particle sets of 128^3 particles, about 48 neighbours, a few photon groups,
 point sources, reduced speed of light; Part III, Iliev tests).  None of the
 thesis's initial-condition files are used: everything is drawn from
-``numpy.random.default_rng(12727 + config_id)``.
+``numpy.random.default_rng(12727 + seed_id)``, one seed offset per workload.
 
 Arrays are in the layouts of the C interface:
   x      float64 [3, N]      positions, component-major (SoA)
@@ -29,7 +29,7 @@ SEED_BASE = 12727
 @dataclass
 class Workload:
     name: str
-    config_id: int
+    seed_id: int
     x: np.ndarray
     m: np.ndarray
     xsrc: np.ndarray
@@ -54,8 +54,8 @@ class Workload:
         return self.xsrc.shape[1]
 
 
-def _rng(config_id: int) -> np.random.Generator:
-    return np.random.default_rng(SEED_BASE + config_id)
+def _rng(seed_id: int) -> np.random.Generator:
+    return np.random.default_rng(SEED_BASE + seed_id)
 
 
 def jittered_lattice(n_side: int, jitter: float, rng: np.random.Generator) -> np.ndarray:
@@ -116,7 +116,7 @@ def random_unit_vectors(n: int, rng: np.random.Generator) -> np.ndarray:
     return v / np.linalg.norm(v, axis=0, keepdims=True)
 
 
-def config1() -> Workload:
+def lattice_point_source() -> Workload:
     """16^3 jittered lattice, 1 group, one source of luminosity 1 at the centre, 10 steps."""
     rng = _rng(1)
     x = jittered_lattice(16, 0.2, rng)
@@ -128,7 +128,7 @@ def config1() -> Workload:
                     np.array([[0.5], [0.5], [0.5]]), np.ones((1, G)), U0, G, 10)
 
 
-def config2(n_side: int = 64) -> Workload:
+def poisson_sine_beam(n_side: int = 64) -> Workload:
     """64^3 Poisson-sampled sine density, 3 groups, central source plus a collimated beam,
     grey opacity kappa = 0.1, 50 steps."""
     rng = _rng(2)
@@ -147,7 +147,7 @@ def config2(n_side: int = 64) -> Workload:
                     c_red=c, kappa=0.1, extra={"beam_particles": int(beam.sum())})
 
 
-def config3(n_side: int = 32) -> Workload:
+def lattice_sources(n_side: int = 32) -> Workload:
     """32^3 jittered lattice, 2 groups, 8 sources with lognormal(0,1) luminosities,
     16 sub-cycles with a checkpoint every 4."""
     rng = _rng(3)
@@ -167,23 +167,25 @@ def config3(n_side: int = 32) -> Workload:
                     G, 16, c_red=c, ckpt_every=4)
 
 
-def config4(n_side: int = 128, grid: int = 256, sigma_ln: float = 1.0, G: int = 4, S: int = 64,
-            n_sub: int = 32, config_id: int = 4, sigma_L: float = 1.0, kappa: float = 0.0) -> Workload:
+def lognormal_sources(n_side: int = 128, grid: int = 256, sigma_ln: float = 1.0, G: int = 4, S: int = 64,
+                      n_sub: int = 32, seed_id: int = 4, sigma_L: float = 1.0, kappa: float = 0.0) -> Workload:
     """Lognormal clustered particle set (P(k) ~ k^-2), G groups, S sources with lognormal
     luminosities, n_sub sub-cycles."""
-    rng = _rng(config_id)
+    rng = _rng(seed_id)
     n = n_side ** 3
     x = lognormal_field_particles(n, grid, sigma_ln, rng)
     xsrc = rng.uniform(0.0, 1.0, size=(3, S))
     Lsrc = rng.lognormal(0.0, sigma_L, size=(S, G))
     U0 = np.zeros((G, 4, n))
     U0[:, 0, :] = 1e-10
-    return Workload(f"lognormal-{n_side}^3-sigma{sigma_ln:g}-G{G}-S{S}", config_id, x, np.full(n, 1.0 / n),
+    return Workload(f"lognormal-{n_side}^3-sigma{sigma_ln:g}-G{G}-S{S}", seed_id, x, np.full(n, 1.0 / n),
                     xsrc, Lsrc, U0, G, n_sub, kappa=kappa)
 
 
-def config5() -> Workload:
-    return config4(256, 512, 2.0, 4, 1000, 64, config_id=5, sigma_L=2.0, kappa=0.1)
+def lognormal_sources_large() -> Workload:
+    """256^3 lognormal set (sigma_ln = 2, P(k) ~ k^-2), 4 groups, 1000 sources with
+    lognormal(0, 2) luminosities, grey kappa = 0.1, 64 sub-cycles."""
+    return lognormal_sources(256, 512, 2.0, 4, 1000, 64, seed_id=5, sigma_L=2.0, kappa=0.1)
 
 
 def plane_wave(n_side: int, width: float, shape: str = "gaussian", c: float = 1.0) -> Workload:
@@ -201,4 +203,7 @@ def plane_wave(n_side: int, width: float, shape: str = "gaussian", c: float = 1.
                     np.zeros((3, 0)), np.zeros((0, 1)), U0, 1, 0, c_red=c)
 
 
-CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
+# bench.py's --workload names
+WORKLOADS = {"lattice-point-source": lattice_point_source, "poisson-sine-beam": poisson_sine_beam,
+             "lattice-sources": lattice_sources, "lognormal-sources": lognormal_sources,
+             "lognormal-sources-large": lognormal_sources_large}

@@ -1,7 +1,7 @@
 """Hand-written adjoint (rt_adjoint) against the oracle's exact directional derivatives
 (forward-mode dual numbers), finite differences, and the degree-1 homogeneity of the step.
 
-Loss (config 3 reading): L = sum over groups and over particles within 0.15 of the box
+Loss (the reading for the multi-source lattice): L = sum over groups and over particles within 0.15 of the box
 centre of E, so dL/dU(final) is that indicator on the E rows.
 """
 import numpy as np
@@ -30,7 +30,7 @@ def loss_weights(w):
 
 
 def setup(n_side=16, alpha=True):
-    w = W.config3(n_side)
+    w = W.lattice_sources(n_side)
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
     dt = 0.6 * ((o.V / (4 * np.pi / 3)) ** (1 / 3)).min() / w.c_red
     a = 0.3 * w.m * o.omega if alpha else None    # grey alpha = kappa rho, rho = m omega ~ 1
@@ -91,10 +91,10 @@ def test_checkpoint_interval_does_not_change_the_result():
         np.testing.assert_array_equal(x[1], y[1])
 
 
-def test_config3_finite_differences_and_fp32():
-    """Config 3 (32^3, 2 groups, 8 sources, 16 sub-cycles, checkpoint every 4): central
-    differences with a 1e-6 relative step on the FP64 path, and the FP32 adjoint.  The
-    initial state is config 3's scaled by 1e10 (E0 of order one, same pattern), so that a
+def test_lattice_sources_finite_differences_and_fp32():
+    """The multi-source lattice (32^3, 2 groups, 8 sources, 16 sub-cycles, checkpoint every
+    4): central differences with a 1e-6 relative step on the FP64 path, and the FP32
+    adjoint.  The initial state is the workload's scaled by 1e10 (E0 of order one, same pattern), so that a
     1e-6 relative step of U0 moves the loss well above double-precision resolution."""
     _need_gpu()
     w, o, dt, _ = setup(32, alpha=False)

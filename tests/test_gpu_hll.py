@@ -21,9 +21,9 @@ def _need_gpu():
         pytest.skip("no GPU")
 
 
-def test_hll_config1_fp64_and_fp32():
+def test_hll_lattice_point_source_fp64_and_fp32():
     _need_gpu()
-    w = W.config1()
+    w = W.lattice_point_source()
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red, riemann="hll")
     dt = cfl_dt(o)
     ref, _ = o.run(w.U0, w.n_steps, dt, w.Lsrc)
@@ -47,14 +47,14 @@ def test_hll_config1_fp64_and_fp32():
     t.close()
 
 
-def test_hll_config2_reduced_and_launch_variants():
-    """Config 2 shape at 24^3 (3 groups, source, collimated beam with f = 1, grey sink).
+def test_hll_poisson_sine_beam_reduced_and_launch_variants():
+    """The benchmark's shape at 24^3 (3 groups, source, collimated beam with f = 1, grey sink).
     FP64: every step from the oracle's state, per element (over several steps the HLL
     dynamics amplify last-bit differences ~50x in a few elements, so the multi-step
     comparison measures that growth rather than the implementation); FP32: five steps in
     relative L1; every float launch variant gives the same bits."""
     _need_gpu()
-    w = W.config2(24)
+    w = W.poisson_sine_beam(24)
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red, riemann="hll")
     dt = cfl_dt(o)
     alpha = w.kappa * w.m * o.omega

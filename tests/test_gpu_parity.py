@@ -55,15 +55,15 @@ def cfl_dt(o, C=0.9):
 
 
 @pytest.fixture(scope="module")
-def cfg1():
+def lattice1():
     _need_gpu()
-    w = W.config1()
+    w = W.lattice_point_source()
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
     return w, o
 
 
-def test_neighbours_and_geometry_fp64(cfg1):
-    w, o = cfg1
+def test_neighbours_and_geometry_fp64(lattice1):
+    w, o = lattice1
     t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64")
     f = t.fields()
     h = f["h"].cpu().numpy()
@@ -96,8 +96,8 @@ def test_neighbours_and_geometry_fp64(cfg1):
     t.close()
 
 
-def test_gradients_fp64(cfg1):
-    w, o = cfg1
+def test_gradients_fp64(lattice1):
+    w, o = lattice1
     t = Transport(w.x, w.m, w.xsrc, n_groups=2, precision="fp64")
     rng = np.random.default_rng(21)
     U = rng.normal(size=(2, 4, w.n))
@@ -110,9 +110,9 @@ def test_gradients_fp64(cfg1):
 
 
 @pytest.mark.parametrize("dt_reading", ["cfl", "smoothing_length"])
-def test_transport_fp64_config1(cfg1, dt_reading):
-    """Config 1 (16^3 jittered lattice, one source, 10 steps) in FP64: every particle to 1e-12."""
-    w, o = cfg1
+def test_transport_fp64_lattice_point_source(lattice1, dt_reading):
+    """The 16^3 jittered lattice with one source, 10 steps, in FP64: every particle to 1e-12."""
+    w, o = lattice1
     dt = cfl_dt(o) if dt_reading == "cfl" else 0.9 * o.h.min() / w.c_red
     ref, _ = o.run(w.U0, w.n_steps, dt, w.Lsrc)
     t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64")
@@ -126,9 +126,9 @@ def test_transport_fp64_config1(cfg1, dt_reading):
     t.close()
 
 
-def test_plain_steps_equal_graph_bitwise(cfg1):
+def test_plain_steps_equal_graph_bitwise(lattice1):
     """rt_transport_step repeated == one rt_subcycle graph (same kernels, same order)."""
-    w, o = cfg1
+    w, o = lattice1
     dt = cfl_dt(o)
     for prec in ("fp64", "fp32"):
         t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision=prec)
@@ -152,7 +152,7 @@ def test_graphs_follow_a_rebuild_that_changes_the_pair_count(sources):
     graph run equals the plain steps bitwise, in both precisions.  Without sources the
     injection sizes stay 0, so only the pair count can tell that the graph is stale."""
     _need_gpu()
-    w = W.config2(24)
+    w = W.poisson_sine_beam(24)
     rng = np.random.default_rng(77)
     xs = [np.mod(w.x + 0.004 * k * rng.standard_normal(w.x.shape), 1.0) for k in range(5)]
     xsrc = w.xsrc if sources else None
@@ -180,9 +180,9 @@ def test_graphs_follow_a_rebuild_that_changes_the_pair_count(sources):
         t.close()
 
 
-def test_fp32_config1_against_oracle(cfg1):
+def test_fp32_lattice_point_source_against_oracle(lattice1):
     """FP32 mixed path: relative L1 <= 1e-5 per step, energy drift <= 1e-6."""
-    w, o = cfg1
+    w, o = lattice1
     dt = cfl_dt(o)
     t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp32")
     L = t.luminosities(w.Lsrc)
@@ -227,7 +227,7 @@ def test_energy_conserved_without_sources(prec, tol):
 
 def test_injection_energy_and_determinism():
     _need_gpu()
-    w = W.config3(16)
+    w = W.lattice_sources(16)
     t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64")
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups)
     dt = cfl_dt(o, 0.6)
@@ -246,11 +246,11 @@ def test_injection_energy_and_determinism():
     t.close()
 
 
-def test_config2_reduced_against_oracle():
-    """Config 2 shape (Poisson sine density, 3 groups, source + beam, grey sink) at 24^3,
+def test_poisson_sine_beam_reduced_against_oracle():
+    """The benchmark's shape (Poisson sine density, 3 groups, source + beam, grey sink) at 24^3,
     both precisions, all particles."""
     _need_gpu()
-    w = W.config2(24)
+    w = W.poisson_sine_beam(24)
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
     dt = cfl_dt(o)
     alpha = w.kappa * w.m * o.omega
@@ -287,7 +287,7 @@ def test_kernel_times_and_launch_counts():
     graph replays, and the launch counter counts graph kernel nodes."""
     _need_gpu()
     from paper_2302_12727_gb300 import rt_kernel_times, rt_set_profiling
-    w = W.config1()
+    w = W.lattice_point_source()
     t = Transport(w.x, w.m, w.xsrc, n_groups=1, precision="fp32")
     rt_set_profiling(t.ctx, True)
     L = t.luminosities(w.Lsrc)
@@ -338,15 +338,15 @@ def test_failures_are_reported_not_raised_on_the_gpu():
     t.close()
 
 
-@pytest.mark.parametrize("cfg", [2, 4])
-def test_full_size_per_step_parity(cfg):
-    """The benchmark workload (config 2, 262,144 particles, 3 groups, source, beam, grey sink)
-    and config 4 (2,097,152 particles, lognormal density, 4 groups, 64 sources), every
+@pytest.mark.parametrize("name", ["poisson-sine-beam", "lognormal-sources"])
+def test_full_size_per_step_parity(name):
+    """The benchmark workload (262,144 particles, Poisson sine density, 3 groups, source, beam,
+    grey sink) and the lognormal set (2,097,152 particles, 4 groups, 64 sources), every
     particle: the FP32 path's error of one step from the oracle's state, over the first
     steps, relative L1 <= 1e-5 per component and group."""
     _need_gpu()
-    w = W.CONFIGS[cfg]()
-    nsteps = 2 if cfg == 2 else 1
+    w = W.WORKLOADS[name]()
+    nsteps = 2 if name == "poisson-sine-beam" else 1
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
     dt = cfl_dt(o)
     alpha = w.kappa * w.m * o.omega if w.kappa else None
@@ -400,7 +400,7 @@ def test_rebuild_stores_or_rewalks_the_pair_rows():
     brute-force pairs for the context's own h, and the FP64 steps equal those of a context
     built on that set directly to 1e-12."""
     _need_gpu()
-    w = W.config2(24)
+    w = W.poisson_sine_beam(24)
     n = w.n
     lat = W.jittered_lattice(24, 0.1, np.random.default_rng(5))
     x = np.random.default_rng(9).uniform(0, 1, size=(3, n))
@@ -432,7 +432,7 @@ def test_sorted_pair_build_on_clustered_particles():
     lists equal the oracle's (apart from ties at the support radius), and the FP64 state
     after a few steps agrees to 1e-12."""
     _need_gpu()
-    w = W.config4(n_side=64, grid=128, sigma_ln=2.0, G=2, S=4, n_sub=3)
+    w = W.lognormal_sources(n_side=64, grid=128, sigma_ln=2.0, G=2, S=4, n_sub=3)
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
     t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64", c_red=w.c_red)
     d = t.diagnostics()
@@ -468,7 +468,7 @@ def test_launch_variants_give_identical_results(G):
     G = 5 runs two group chunks (4 + 1) per pass."""
     _need_gpu()
     from paper_2302_12727_gb300 import RTError as Err
-    w = W.config2(24)
+    w = W.poisson_sine_beam(24)
     rng = np.random.default_rng(31)
     U0 = np.zeros((G, 4, w.n))
     U0[:, 0] = rng.uniform(0.1, 1.0, size=(G, w.n))
@@ -511,7 +511,7 @@ def test_autotune_adopts_a_candidate_with_identical_results(tmp_path):
     _need_gpu()
     from paper_2302_12727_gb300 import RT_TUNE_CANDIDATES, rt_autotune
     from paper_2302_12727_gb300.autotune import autotune
-    w = W.config2(24)
+    w = W.poisson_sine_beam(24)
     for prec in ("fp32", "fp64"):
         t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision=prec, c_red=w.c_red)
         dt = 0.9 * t.diagnostics()["dx_min"]
@@ -528,7 +528,7 @@ def test_autotune_adopts_a_candidate_with_identical_results(tmp_path):
         U = U0.clone()
         t.subcycle(U, 4, dt, L)
         assert torch.equal(U, ref)
-        # the driver: measured once, then served from its cache
+        # autotune.py: measured once, then served from its cache
         path = str(tmp_path / f"cache_{prec}.json")
         e1 = autotune(t, U0, dt, 3, L, cache_path=path)
         e2 = autotune(t, U0, dt, 3, L, cache_path=path)

@@ -1,6 +1,6 @@
 """Photo-ionisation sink per photon group (rt_set_absorbers; Eqs. dEdt-group, dFdt-group)
 against the oracle: absorption alpha_g = sum_j sigma^N_gj n_j from blackbody-averaged cross
-sections of the thesis's fits, on the config-2 shape (3 groups split at the H0, He0 and He+
+sections of the thesis's fits, on the benchmark's shape (Poisson sine density, 3 groups split at the H0, He0 and He+
 thresholds, source and collimated beam)."""
 import math
 
@@ -26,7 +26,7 @@ def _need_gpu():
 def absorbers(w, o):
     """Species densities (code units) tracing the density with an ionised fraction that
     varies along x, and the three groups' sigma^N scaled so that H0 in group 1 gives
-    alpha = 0.1 rho (the grey kappa of config 2)."""
+    alpha = 0.1 rho (the grey kappa of the benchmark workload)."""
     rho = w.m * o.omega
     xi = 0.5 * (1 + np.sin(2 * np.pi * w.x[0]))
     n = np.stack([rho * (1 - xi), 0.08 * rho * (1 - xi), 0.08 * rho * xi])
@@ -38,7 +38,7 @@ def absorbers(w, o):
 
 def test_group_sink_against_oracle():
     _need_gpu()
-    w = W.config2(24)
+    w = W.poisson_sine_beam(24)
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
     dt = cfl_dt(o)
     n, sig = absorbers(w, o)
@@ -70,7 +70,7 @@ def test_equal_group_absorption_is_the_grey_sink_and_clearing_restores_none():
     """alpha_g equal in every group gives bitwise the grey run; a grey alpha given to the
     call overrides the absorbers; clearing them removes the sink."""
     _need_gpu()
-    w = W.config2(16)
+    w = W.poisson_sine_beam(16)
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
     dt = cfl_dt(o)
     a = w.kappa * w.m * o.omega

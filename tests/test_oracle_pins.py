@@ -444,7 +444,7 @@ def test_wave_table_symmetry_and_free_streaming_limit():
 
 
 def _hll_oracle(table=None):
-    w = W.config1()
+    w = W.lattice_point_source()
     return oracle.Oracle(w.x, w.m, None, n_groups=1, c_red=1.7, riemann="hll", wave_table=table)
 
 
