@@ -1,4 +1,4 @@
-"""Driver of the library's autotuner with a JSON cache.
+"""JSON cache layer around the library's autotuner.
 
 ``rt_autotune`` times every launch-variant combination of the float pair kernels (the
 ``rt_tuning`` space: pair-flux variant, gather variant, gradient variant; all give the same

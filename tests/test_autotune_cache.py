@@ -1,4 +1,4 @@
-"""Host logic of the autotuner driver: cache keys, lookup, store, re-tune (no GPU)."""
+"""Host logic of the autotuner's JSON cache layer: cache keys, lookup, store, re-tune (no GPU)."""
 import json
 
 from paper_2302_12727_gb300 import autotune as A
