@@ -371,21 +371,84 @@ struct PairParams {
     double Hmax;
 };
 
+// Local search radii of the direct pair search.  A pair with r_ij < H_j > H_i must be found
+// from i, so i searches out to max(H_i, H_j) for every j that can reach it.  Over a coarse
+// grid of at most 16^3 blocks, Hb[B] is the largest H in block B and Hreach[A] the largest
+// Hb[B] over the blocks B whose box lies within Hb[B] of A's box (A included): every j that
+// reaches a particle of A has H_j <= Hreach[A], so max(H_i, Hreach[A]) bounds i's search.
+struct Blocks {
+    int nb[3];
+    double len[3];      // block edge per axis
+    int periodic;
+};
+
+__device__ __forceinline__ int block_of(const Blocks& bk, double x, double y, double z) {
+    const double p[3] = {x, y, z};
+    int b[3];
+    for (int a = 0; a < 3; ++a) {
+        int v = (int)floor(p[a] / bk.len[a]);
+        b[a] = v < 0 ? 0 : (v >= bk.nb[a] ? bk.nb[a] - 1 : v);
+    }
+    return (b[2] * bk.nb[1] + b[1]) * bk.nb[0] + b[0];
+}
+
+// Hb (float bits, ordered like integers for H > 0) of every block; the lanes of a warp that
+// fall in the same block (particles are sorted by cell) combine before one atomic
+__global__ void k_block_hmax(const double* __restrict__ xs, const float* __restrict__ H2f, int64_t n, Blocks bk,
+                             unsigned* __restrict__ hb) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool in = p < n;
+    const int b = in ? block_of(bk, xs[p], xs[n + p], xs[2 * n + p]) : -1;
+    const unsigned v = in ? __float_as_uint(sqrtf(H2f[p])) : 0u;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const unsigned m = __reduce_max_sync(peers, v);
+    if (in && (threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&hb[b], m);
+}
+
+// Hreach of every block: one warp per block A, its lanes scanning the blocks B
+__global__ void k_block_reach(const unsigned* __restrict__ hb, Blocks bk, float* __restrict__ reach) {
+    const int nbt = bk.nb[0] * bk.nb[1] * bk.nb[2];
+    const int A = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (A >= nbt) return;      // whole warps
+    const int a[3] = {A % bk.nb[0], (A / bk.nb[0]) % bk.nb[1], A / (bk.nb[0] * bk.nb[1])};
+    const float len[3] = {(float)bk.len[0], (float)bk.len[1], (float)bk.len[2]};
+    unsigned r = hb[A];
+    for (int Bi = lane; Bi < nbt; Bi += 32) {
+        const unsigned hbB = hb[Bi];
+        if (hbB <= r) continue;
+        const float Hb = __uint_as_float(hbB);
+        const int b[3] = {Bi % bk.nb[0], (Bi / bk.nb[0]) % bk.nb[1], Bi / (bk.nb[0] * bk.nb[1])};
+        float d2 = 0.f;
+        for (int x = 0; x < 3; ++x) {
+            int d = abs(a[x] - b[x]);
+            if (bk.periodic) d = min(d, bk.nb[x] - d);
+            const float gap = d > 1 ? (d - 1) * len[x] : 0.f;
+            d2 += gap * gap;
+        }
+        // the gap between the boxes, with a relative margin against rounding
+        if (d2 < Hb * Hb * 1.0002f) r = hbB;
+    }
+    r = __reduce_max_sync(0xffffffffu, r);
+    if (lane == 0) reach[A] = __uint_as_float(r);
+}
+
 // FILL = false counts each row into counts[p]; with cap > 0 it also writes the first cap
 // entries of row p to cols[p cap ...] and raises *row_max to the longest row.  FILL = true
 // writes row p to cols[row_off[p] ...].  Both walk the candidates in the same order.
 template <bool FILL>
 __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
                         const double* __restrict__ h, const float* __restrict__ H2f, int64_t n, PairParams pp,
-                        int32_t* counts, const int64_t* __restrict__ row_off, int32_t* cols, int cap = 0,
-                        int* row_max = nullptr) {
+                        Blocks bk, const float* __restrict__ reach, int32_t* counts,
+                        const int64_t* __restrict__ row_off, int32_t* cols, int cap = 0, int* row_max = nullptr) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int cnt = 0;
     if (p < n) {
         uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
         double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
         const float H2i = H2f[p];
-        float R = sqrtf(fmaxf(H2i, (float)(pp.Hmax * pp.Hmax))) * 1.0001f;
+        const float Hr = reach[block_of(bk, px, py, pz)];
+        float R = sqrtf(fmaxf(H2i, Hr * Hr)) * 1.0001f;
         int64_t base = FILL ? row_off[p] : p * (int64_t)cap;
         for_each_candidate(g, (float)px, (float)py, (float)pz, R, [&](int j) {
             if (j == p) return;
@@ -1109,8 +1172,10 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     c->launches += 1;
     int hflags[8];
     double hmm[2];
+    double sumH3 = 0.0;
     RT_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
     RT_CUDA(c, cudaMemcpyAsync(hmm, red, sizeof(hmm), cudaMemcpyDeviceToHost, st));
+    RT_CUDA(c, cudaMemcpyAsync(&sumH3, red + 4, 8, cudaMemcpyDeviceToHost, st));
     RT_CUDA(c, cudaStreamSynchronize(st));
     if (hflags[F_BADPOS]) return fail(c, RT_ERR_INVALID, "positions must be finite and inside [0, box)");
     if (hflags[F_NOCONV]) return fail(c, RT_ERR_NOCONV, "smoothing-length iteration did not converge");
@@ -1126,14 +1191,27 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     pp.Hmax = Hmax;
     // Searching every particle out to max(H_i, H_max) visits H_max^3 / <H^3> times the volume
     // of its own support; above a ratio of 12 the sort-based build is cheaper.
-    double sumH3 = 0.0;
-    RT_CUDA(c, cudaMemcpyAsync(&sumH3, red + 4, 8, cudaMemcpyDeviceToHost, st));
-    RT_CUDA(c, cudaStreamSynchronize(st));
     const double vol_ratio = Hmax * Hmax * Hmax / std::max(sumH3 / (double)n, 1e-300);
     const bool sorted_build = vol_ratio > 12.0;
     c->diag.pair_build = sorted_build ? 1 : 0;
     int64_t P2 = 0;
     if (!sorted_build) {
+        // search radii from the coarse blocks' largest H
+        Blocks bk;
+        int nbt = 1;
+        for (int a = 0; a < 3; ++a) {
+            bk.nb[a] = std::min(16, c->nc[a]);
+            bk.len[a] = cfg.box[a] / bk.nb[a];
+            nbt *= bk.nb[a];
+        }
+        bk.periodic = cfg.periodic;
+        RT_TRY(ensure(c, c->blk, (size_t)nbt * 8, "blocks"));
+        unsigned* hb = c->blk.as<unsigned>();
+        float* reach = reinterpret_cast<float*>(hb + nbt);
+        RT_CUDA(c, cudaMemsetAsync(hb, 0, (size_t)nbt * 4, st));
+        k_block_hmax<<<nblk(n, 256), 256, 0, st>>>(c->xs_d.as<double>(), c->H2f.as<float>(), n, bk, hb);
+        k_block_reach<<<nblk((int64_t)nbt * 32, 128), 128, 0, st>>>(hb, bk, reach);
+        c->launches += 2;
         // one walk counts the rows and, when the rows of the last call fit row_cap entries,
         // also stores them (then compacted); a longer row needs a second, writing walk
         const int cap = (int)c->row_cap;
@@ -1141,7 +1219,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         int* row_max = c->flags.as<int>() + F_ROWMAX;
         RT_CUDA(c, cudaMemsetAsync(row_max, 0, 4, st));
         k_pairs<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
-                                                      c->h_d.as<double>(), c->H2f.as<float>(), n, pp,
+                                                      c->h_d.as<double>(), c->H2f.as<float>(), n, pp, bk, reach,
                                                       c->counts.as<int32_t>(), nullptr,
                                                       cap > 0 ? c->cols_cap.as<int32_t>() : nullptr, cap, row_max);
         RT_CUDA(c, cudaMemsetAsync(c->counts.as<int32_t>() + n, 0, 4, st));
@@ -1160,8 +1238,8 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
                                                           c->cols_tmp.as<int32_t>());
         } else {
             k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
-                                                         c->h_d.as<double>(), c->H2f.as<float>(), n, pp, nullptr,
-                                                         c->row_off.as<int64_t>(), c->cols_tmp.as<int32_t>());
+                                                         c->h_d.as<double>(), c->H2f.as<float>(), n, pp, bk, reach,
+                                                         nullptr, c->row_off.as<int64_t>(), c->cols_tmp.as<int32_t>());
         }
         // the next call's rows: the longest row with a quarter to spare, in multiples of 32,
         // while the padded rows stay within eight times the lists (only the filled part of a

@@ -85,6 +85,7 @@ struct rt_ctx {
     // set from the longest row of the last call
     rt::DevBuf cols_cap;
     int64_t row_cap = 0;
+    rt::DevBuf blk;                                     // coarse blocks: largest H and reach radius
     rt::DevBuf pkeys, pkeys_alt;                        // (row, col) keys of the sort-based build
     rt::DevBuf n_low, n_up, up_off, low_slot, pair_ends; // lower / upper split, pair slots
     rt::DevBuf pairbuf;                                 // per-pair fluxes of one group chunk
