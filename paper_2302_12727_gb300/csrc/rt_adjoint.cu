@@ -244,6 +244,7 @@ static void launch_adj_step(rt_ctx* c, cudaStream_t s, const T* lamN, const T* W
     x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
     x.alpha_g = nullptr;   // grey sink only
     x.acc = nullptr;
+    x.inj = nullptr;
     x.dt_dev = c->dt_dev.as<double>();
     x.c = (T)c->cfg.c_red;
     x.clamp = 0;

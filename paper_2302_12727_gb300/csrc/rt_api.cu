@@ -112,6 +112,7 @@ static rt_status ensure_state(rt_ctx* c) {
     RT_TRY(ensure(c, c->L_dev, (size_t)std::max<int64_t>(c->n_src, 1) * G * 8, "luminosities"));
     RT_TRY(ensure(c, c->dt_dev, 64, "dt"));
     RT_TRY(ensure(c, c->energy_part, (size_t)G * 512 * 8 + (size_t)G * 8, "energy"));
+    if (c->n_src > 0) RT_TRY(ensure(c, c->inj_dense, (size_t)G * n * 8, "injection"));
     // per-pair flux slots of one group chunk (at most 4 groups)
     const int gc = G < kMaxGC ? G : kMaxGC;
     RT_TRY(ensure(c, c->pairbuf, (size_t)std::max<int64_t>(c->n_directed / 2, 1) * 4 * gc * tsize(c), "pair fluxes"));
@@ -278,6 +279,8 @@ rt_status rt_subcycle(rt_ctx* c, int32_t n_sub, double dt, void* U, const double
     bool has_alpha = alpha != nullptr;
     RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
     RT_TRY(set_step_inputs(c, dt, Lsrc, alpha));
+    // sub-cycles after the first take their injection from the previous gather
+    RT_TRY(set_dense_injection(c, has_src && n_sub > 1));
     GraphKey key{n_sub, has_src ? 1 : 0, has_alpha ? 1 : (c->has_alpha_g ? 2 : 0)};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
@@ -290,7 +293,7 @@ rt_status rt_subcycle(rt_ctx* c, int32_t n_sub, double dt, void* U, const double
         int64_t l0 = c->launches;
         c->prof_sink = c->profiling ? &entry.prof : nullptr;
         for (int k = 0; k < n_sub && s == RT_OK; ++k) {
-            s = launch_step(c, c->cap_stream, a, b, has_src, has_alpha);
+            s = launch_step(c, c->cap_stream, a, b, has_src, has_alpha, k == 0, k + 1 < n_sub);
             std::swap(a, b);
         }
         c->prof_sink = nullptr;

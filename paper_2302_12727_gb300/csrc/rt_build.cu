@@ -379,6 +379,7 @@ struct PairParams {
 struct Blocks {
     int nb[3];
     double len[3];      // block edge per axis
+    int reach[3];       // blocks per axis within H_max of a block (no block farther can qualify)
     int periodic;
 };
 
@@ -405,7 +406,8 @@ __global__ void k_block_hmax(const double* __restrict__ xs, const float* __restr
     if (in && (threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&hb[b], m);
 }
 
-// Hreach of every block: one warp per block A, its lanes scanning the blocks B
+// Hreach of every block: one warp per block A, its lanes scanning the blocks B within
+// bk.reach blocks of A along each axis (each block once, also where that span wraps)
 __global__ void k_block_reach(const unsigned* __restrict__ hb, Blocks bk, float* __restrict__ reach) {
     const int nbt = bk.nb[0] * bk.nb[1] * bk.nb[2];
     const int A = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
@@ -413,12 +415,30 @@ __global__ void k_block_reach(const unsigned* __restrict__ hb, Blocks bk, float*
     if (A >= nbt) return;      // whole warps
     const int a[3] = {A % bk.nb[0], (A / bk.nb[0]) % bk.nb[1], A / (bk.nb[0] * bk.nb[1])};
     const float len[3] = {(float)bk.len[0], (float)bk.len[1], (float)bk.len[2]};
+    // the scanned span per axis: [a - k, a + k] wrapped (or clipped), or the whole axis
+    int lo[3], w[3];
+    for (int x = 0; x < 3; ++x) {
+        const int k = bk.reach[x];
+        if (2 * k + 1 >= bk.nb[x]) {
+            lo[x] = 0;
+            w[x] = bk.nb[x];
+        } else if (bk.periodic) {
+            lo[x] = a[x] - k;
+            w[x] = 2 * k + 1;
+        } else {
+            lo[x] = max(a[x] - k, 0);
+            w[x] = min(a[x] + k, bk.nb[x] - 1) - lo[x] + 1;
+        }
+    }
+    const int span = w[0] * w[1] * w[2];
     unsigned r = hb[A];
-    for (int Bi = lane; Bi < nbt; Bi += 32) {
+    for (int t = lane; t < span; t += 32) {
+        int b[3] = {lo[0] + t % w[0], lo[1] + (t / w[0]) % w[1], lo[2] + t / (w[0] * w[1])};
+        for (int x = 0; x < 3; ++x) b[x] = (b[x] % bk.nb[x] + bk.nb[x]) % bk.nb[x];
+        const int Bi = (b[2] * bk.nb[1] + b[1]) * bk.nb[0] + b[0];
         const unsigned hbB = hb[Bi];
         if (hbB <= r) continue;
         const float Hb = __uint_as_float(hbB);
-        const int b[3] = {Bi % bk.nb[0], (Bi / bk.nb[0]) % bk.nb[1], Bi / (bk.nb[0] * bk.nb[1])};
         float d2 = 0.f;
         for (int x = 0; x < 3; ++x) {
             int d = abs(a[x] - b[x]);
@@ -1205,6 +1225,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
             nbt *= bk.nb[a];
         }
         bk.periodic = cfg.periodic;
+        for (int a = 0; a < 3; ++a) bk.reach[a] = (int)std::ceil(Hmax / bk.len[a]) + 1;
         RT_TRY(ensure(c, c->blk, (size_t)nbt * 8, "blocks"));
         unsigned* hb = c->blk.as<unsigned>();
         float* reach = reinterpret_cast<float*>(hb + nbt);

@@ -103,6 +103,8 @@ struct rt_ctx {
 
     // state records (sorted order, working precision): U [N][4G] (double-buffered), grad U [N][12G]
     rt::DevBuf U_a, U_b, grad_t, alpha_s, L_dev, dt_dev, energy_part;
+    rt::DevBuf inj_dense;                               // dt sum coef L per (particle, group), [N][G] double
+    bool inj_dense_ready = false;                       // filled by set_step_inputs for this call
     rt::DevBuf frec;                                    // packed float flux-input rows (G <= 4)
     rt::DevBuf wave_t;                                  // HLL wave-speed table, working precision
     // photo-ionisation sink per group (rt_set_absorbers): alpha in caller order [G][N]
@@ -177,7 +179,13 @@ rt_status state_out(rt_ctx* c, const void* rec, void* U_user, int comps, int RS,
 // sorted double per-particle fields [comps][N] -> caller order
 rt_status field_out(rt_ctx* c, const double* src_sorted, double* dst_user, int comps);
 rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double* alpha);
-rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha);
+// fills inj_dense from the inputs of set_step_inputs (when on and there are targets)
+rt_status set_dense_injection(rt_ctx* c, bool on);
+// one sub-cycle: injection (if inject_first), gradients, pair fluxes, update and sink; with
+// inject_after the gather also adds the next sub-cycle's injection (inj_dense), which then
+// starts with inject_first = false
+rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha,
+                      bool inject_first = true, bool inject_after = false);
 rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec);
 // one min-step `step` of a hydro step with individual time bins (c->bins_s, c->acc_t)
 rt_status launch_step_bins(rt_ctx* c, cudaStream_t s, int step, void* U, bool has_src, bool has_alpha);

@@ -342,6 +342,9 @@ struct FluxExtra {
     const T* alpha;                 // sorted, or null
     const T* alpha_g;               // sorted per-group absorption [N][G], or null
     T* acc;                         // bins mode: per-particle flux accumulators [N][4G]
+    // the next sub-cycle's injection dt sum coef L per (particle, group) [N][G] (zero off the
+    // targets), added to E after the update; null when the next sub-cycle injects itself
+    const double* inj;
     const double* dt_dev;
     T c;
     int clamp;

@@ -98,7 +98,24 @@ __global__ void k_inject(const int32_t* __restrict__ targets, const int32_t* __r
         double acc = 0.0;
         for (int e = off[t]; e < off[t + 1]; ++e) acc += coef[e] * L[(int64_t)src[e] * G + g];
         T* E = rec + p * RS + 4 * g;
-        *E = (T)((double)*E + dt * acc);
+        *E = (T)__dadd_rn((double)*E, __dmul_rn(dt, acc));
+    }
+}
+
+// The same increments dt sum coef L per (particle, group) into inj [N][G] (zeroed before),
+// for a gather epilogue to add: E = (T)((double)E + inj) rounds as k_inject does.
+__global__ void k_inject_dense(const int32_t* __restrict__ targets, const int32_t* __restrict__ off,
+                               const int32_t* __restrict__ src, const double* __restrict__ coef,
+                               const double* __restrict__ L, int G, const double* __restrict__ dt_dev,
+                               int64_t n_targets, double* __restrict__ inj) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_targets) return;
+    const double dt = *dt_dev;
+    const int64_t p = targets[t];
+    for (int g = 0; g < G; ++g) {
+        double acc = 0.0;
+        for (int e = off[t]; e < off[t + 1]; ++e) acc += coef[e] * L[(int64_t)src[e] * G + g];
+        inj[p * G + g] = __dmul_rn(dt, acc);
     }
 }
 
@@ -556,6 +573,7 @@ __global__ void __launch_bounds__(128) k_flux_gather(PairArgs<T> a, FluxExtra<T>
             v = T(0);
             ++nclamp;
         }
+        if (x.inj && (c & 3) == 0) v = (T)__dadd_rn((double)v, x.inj[i * a.G + g0 + c / 4]);
         ui[c] = v;
     }
     vstore<NC>(out + i * RS + 4 * g0, ui);
@@ -808,6 +826,7 @@ __global__ void __launch_bounds__(256) k_flux_gather_g(PairArgs<float> a, FluxEx
             v = 0.f;
             ++nclamp;
         }
+        if (x.inj && c == 0) v = (float)__dadd_rn((double)v, x.inj[i * a.G + g0 + g]);
         ui[c] = v;
     }
     vstore<4>(out + o, ui);
@@ -1017,7 +1036,8 @@ static void flux_float(rt_ctx* c, cudaStream_t s, const PairArgs<float>& a, cons
 }
 
 template <class T>
-static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool has_alpha, bool packed = false) {
+static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool has_alpha, bool packed = false,
+                          bool inject_after = false) {
     PairArgs<T> a = pair_args<T>(c);
     if (packed) a.frec = c->frec.as<T>();
     FluxExtra<T> x;
@@ -1026,6 +1046,7 @@ static void launch_flux_t(rt_ctx* c, cudaStream_t s, const T* rec, T* out, bool 
     x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
     x.alpha_g = c->step_alpha_g ? c->alpha_g_s.as<T>() : nullptr;
     x.acc = nullptr;
+    x.inj = inject_after ? c->inj_dense.as<double>() : nullptr;
     x.dt_dev = c->dt_dev.as<double>();
     x.c = (T)c->cfg.c_red;
     x.clamp = c->cfg.clamp_negative;
@@ -1132,6 +1153,7 @@ static void launch_step_bins_t(rt_ctx* c, cudaStream_t s, int step, T* rec, bool
     x.alpha = has_alpha ? c->alpha_s.as<T>() : nullptr;
     x.alpha_g = c->step_alpha_g ? c->alpha_g_s.as<T>() : nullptr;
     x.acc = c->acc_t.as<T>();
+    x.inj = nullptr;
     x.dt_dev = c->dt_dev.as<double>();
     x.c = (T)c->cfg.c_red;
     x.clamp = c->cfg.clamp_negative;
@@ -1199,17 +1221,20 @@ rt_status launch_step_bins(rt_ctx* c, cudaStream_t s, int step, void* U, bool ha
     return RT_OK;
 }
 
-rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha) {
+rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha,
+                      bool inject_first, bool inject_after) {
+    inject_first = inject_first && has_src;
+    inject_after = inject_after && has_src && c->inj_dense_ready;
     if (c->fp64) {
-        if (has_src) launch_inject_t<double>(c, s, (double*)Uin);
+        if (inject_first) launch_inject_t<double>(c, s, (double*)Uin);
         launch_gradient_t<double>(c, s, (double*)Uin);
-        launch_flux_t<double>(c, s, (const double*)Uin, (double*)Uout, has_alpha);
+        launch_flux_t<double>(c, s, (const double*)Uin, (double*)Uout, has_alpha, false, inject_after);
     } else {
-        if (has_src) launch_inject_t<float>(c, s, (float*)Uin);
+        if (inject_first) launch_inject_t<float>(c, s, (float*)Uin);
         // packed rows for the tensor-memory-accelerator pair pass (one group chunk only)
         const bool packed = c->tune.flux_variant == 2 && c->cfg.n_groups <= kMaxGC && packed_rows_map(c);
         launch_gradient_t<float>(c, s, (float*)Uin, packed);
-        launch_flux_t<float>(c, s, (const float*)Uin, (float*)Uout, has_alpha, packed);
+        launch_flux_t<float>(c, s, (const float*)Uin, (float*)Uout, has_alpha, packed, inject_after);
     }
     RT_CUDA(c, cudaGetLastError());
     return RT_OK;
@@ -1276,6 +1301,21 @@ rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double
         ++c->launches;
     }
     RT_CUDA(c, cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status set_dense_injection(rt_ctx* c, bool on) {
+    c->inj_dense_ready = false;
+    if (!on || c->n_inj_targets <= 0 || !c->inj_dense.p) return RT_OK;
+    cudaStream_t s = c->stream;
+    const int G = c->cfg.n_groups;
+    RT_CUDA(c, cudaMemsetAsync(c->inj_dense.p, 0, (size_t)G * c->n * 8, s));
+    k_inject_dense<<<nblk(c->n_inj_targets, 128), 128, 0, s>>>(
+        c->inj_targets.as<int32_t>(), c->inj_off.as<int32_t>(), c->inj_src.as<int32_t>(), c->inj_coef.as<double>(),
+        c->L_dev.as<double>(), G, c->dt_dev.as<double>(), c->n_inj_targets, c->inj_dense.as<double>());
+    ++c->launches;
+    RT_CUDA(c, cudaGetLastError());
+    c->inj_dense_ready = true;
     return RT_OK;
 }
 
