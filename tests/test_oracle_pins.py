@@ -739,3 +739,41 @@ def test_cfl_bins():
     lim = 0.9 * dx
     assert np.all(dt_min * 2.0 ** b <= lim)
     assert np.all((b == 3) | (dt_min * 2.0 ** (b + 1) > lim))
+
+
+@pytest.mark.parametrize("box, periodic", [((1.0, 1.0, 1.0), False), ((2.0, 1.0, 0.5), True),
+                                            ((2.0, 1.0, 0.5), False)])
+def test_pair_lists_in_other_boxes_are_the_brute_force_lists(box, periodic):
+    """Eq. HopkinsAij's support condition r_ij < max(H_i, H_j) in a non-periodic box (no
+    wrap: particles near a wall have truncated supports and larger h) and in a non-cubic
+    periodic box (minimal image per axis): the oracle's lists equal the brute-force lists
+    over all pairs for its own h, and each h satisfies Eq. number-of-neighbors."""
+    rng = np.random.default_rng(41)
+    x = W.jittered_lattice(14, 0.2, rng) * np.asarray(box)[:, None]
+    n = x.shape[1]
+    m = np.full(n, box[0] * box[1] * box[2] / n)
+    o = oracle.Oracle(x, m, np.zeros((3, 0)), n_groups=1, box=box, periodic=periodic)
+    off, cols = o.pairs()
+    H = H_h * o.h
+    b = np.asarray(box)[:, None, None]
+    d = x[:, None, :] - x[:, :, None]
+    if periodic:
+        d -= b * np.rint(d / b)
+    r2 = (d * d).sum(0)
+    Hm2 = np.maximum(H[:, None], H[None, :]) ** 2
+    want = r2 < Hm2
+    np.fill_diagonal(want, False)
+    got = np.zeros_like(want)
+    got[np.repeat(np.arange(n), np.diff(off)), cols] = True
+    tie = np.abs(r2 - Hm2) < 1e-12 * Hm2
+    assert not ((got != want) & ~tie).any()
+    # h_i = eta (sum_j W(r_ij, h_i))^(-1/3), the sum over the particle's own support
+    # (self term included), with the cubic spline of Eq. cubic-spline-kernel
+    q = np.sqrt(r2) / H[:, None]
+    w = np.where(q < 0.5, 1 - 6 * q ** 2 + 6 * q ** 3, np.where(q < 1, 2 * (1 - q) ** 3, 0.0))
+    omega = (8 / np.pi) / H ** 3 * w.sum(1)
+    assert np.allclose(o.h, 1.2348 * omega ** (-1 / 3), rtol=1e-10)
+    if not periodic:
+        # truncated supports at the walls: the particles nearest a wall have the largest h
+        wall = np.min(np.minimum(x, np.asarray(box)[:, None] - x) / np.asarray(box)[:, None], axis=0)
+        assert o.h[wall < 0.03].mean() > 1.1 * o.h[wall > 0.25].mean()
