@@ -261,6 +261,14 @@ rt_status rt_energy(rt_ctx* ctx, const void* U_dev, double* E_tot_host);
 rt_status rt_energy_static(const void* U_dev, const double* V_dev, int64_t n, int32_t n_groups, int32_t precision,
                            void* cuda_stream, double* E_tot_dev);
 
+/* Self-test of the bounded device waits (no paper counterpart): one warp waits, with the
+ * wait of the pair kernels, on a shared-memory barrier that nothing completes, for
+ * budget_cycles SM clock cycles (1 to 4e9), then records that the wait ran out.  Returns
+ * RT_ERR_TIMEOUT when it did (the expected outcome) and RT_OK otherwise; the context stays
+ * usable either way and its own time-out flag (rt_diag.wait_timeouts) is not touched.
+ * Synchronises the context's stream; RT_ERR_INVALID for a budget outside the range. */
+rt_status rt_wait_selftest(rt_ctx* ctx, uint64_t budget_cycles);
+
 /* Per-particle geometry in caller order (device pointers, each may be NULL):
  * h [N], omega [N], V [N], B [N][3][3] (double). */
 rt_status rt_particle_fields(rt_ctx* ctx, double* h_dev, double* omega_dev, double* V_dev, double* B_dev);

@@ -24,7 +24,7 @@ EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_t
             "rt_photon_number_to_luminosity",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
             "rt_kernel_times", "rt_set_tuning", "rt_get_tuning", "rt_autotune", "rt_wave_table",
-            "rt_energy_static", "rt_last_error", "rt_destroy"]
+            "rt_energy_static", "rt_wait_selftest", "rt_last_error", "rt_destroy"]
 
 RT_ENERGY_STATIC_MAX_GROUPS = 16
 
@@ -104,6 +104,7 @@ def load_library():
     lib.rt_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     lib.rt_wave_table.argtypes = [dp, dp]
     lib.rt_set_tuning.argtypes = [vp, C.POINTER(rt_tuning)]
+    lib.rt_wait_selftest.argtypes = [vp, C.c_uint64]
     lib.rt_get_tuning.argtypes = [vp, C.POINTER(rt_tuning)]
     lib.rt_autotune.argtypes = [vp, dp, C.c_double, C.c_int32, dp, dp, C.c_int32, C.POINTER(rt_tuning),
                                 C.POINTER(C.c_double)]
@@ -289,6 +290,16 @@ def rt_set_tuning(ctx, flux_variant: int = 2, gather_variant: int = 1, gradient_
     """Launch variants of the float pair kernels (see rt.h); same results for every choice."""
     t = rt_tuning(int(flux_variant), int(gather_variant), int(gradient_variant))
     _check(ctx, load_library().rt_set_tuning(ctx, C.byref(t)))
+
+
+def rt_wait_selftest(ctx, budget_cycles: int) -> bool:
+    """True when the bounded device wait on a barrier that nothing completes ran out after
+    budget_cycles SM cycles (the expected outcome, status RT_ERR_TIMEOUT); other errors raise."""
+    s = load_library().rt_wait_selftest(ctx, int(budget_cycles))
+    if s == 6:
+        return True
+    _check(ctx, s)
+    return False
 
 
 def rt_get_tuning(ctx) -> dict:

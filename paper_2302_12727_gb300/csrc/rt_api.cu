@@ -574,6 +574,18 @@ rt_status rt_autotune(rt_ctx* c, const void* U, double dt, int32_t n_sub, const 
     return rt_set_tuning(c, &win);
 }
 
+rt_status rt_wait_selftest(rt_ctx* c, uint64_t budget_cycles) {
+    if (!c) return RT_ERR_INVALID;
+    c->err.clear();
+    if (budget_cycles < 1 || budget_cycles > 4000000000ull)
+        return fail(c, RT_ERR_INVALID, "rt_wait_selftest: budget_cycles must be in [1, 4e9]");
+    RT_CUDA(c, cudaSetDevice(c->device));
+    bool ran_out = false;
+    RT_TRY(wait_selftest(c, budget_cycles, &ran_out));
+    if (ran_out) return fail(c, RT_ERR_TIMEOUT, "rt_wait_selftest: the bounded wait ran out, as expected");
+    return RT_OK;
+}
+
 rt_status rt_get_tuning(const rt_ctx* c, rt_tuning* t) {
     if (!c || !t) return RT_ERR_INVALID;
     *t = c->tune;

@@ -22,7 +22,7 @@ constexpr double kSigma = 5.0929581789406507446;   // 16 / pi
 // int slots of the context's 64-byte flag buffer (cleared by every rt_neighbours): error
 // flags of the build, the clamp counter (64-bit, slots 8-9) and the device-wait time-out flag
 enum FlagSlot { F_BADPOS = 0, F_NOCONV = 1, F_GEOM = 2, F_ILL = 3, F_SRC_NOCONV = 4, F_NSLOTS = 8, F_CLAMP = 8,
-                F_TIMEOUT = 12, F_SCRATCH = 13, F_ROWMAX = 14 };
+                F_TIMEOUT = 12, F_SCRATCH = 13, F_ROWMAX = 14, F_SELFTEST = 15 };
 constexpr int kMaxGC = 4;                          // groups handled by one pair-kernel launch
 
 // ------------------------------------------------------------------------------------
@@ -181,6 +181,8 @@ rt_status field_out(rt_ctx* c, const double* src_sorted, double* dst_user, int c
 rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double* alpha);
 // fills inj_dense from the inputs of set_step_inputs (when on and there are targets)
 rt_status set_dense_injection(rt_ctx* c, bool on);
+// rt_wait_selftest's kernel: *ran_out = the bounded wait on a never-completed barrier ran out
+rt_status wait_selftest(rt_ctx* c, unsigned long long budget, bool* ran_out);
 // one sub-cycle: injection (if inject_first), gradients, pair fluxes, update and sink; with
 // inject_after the gather also adds the next sub-cycle's injection (inj_dense), which then
 // starts with inject_first = false

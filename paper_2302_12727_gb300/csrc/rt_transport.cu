@@ -726,7 +726,9 @@ __global__ void __launch_bounds__(128) k_flux_tma(PairArgs<float> a, FluxExtra<f
     vload<8>(rk + 4, gi8);
     if (!mbar_wait(mb, 0, budget)) {
         atomicExch(err_flag, 1);
-        mbar_wait(mb, 0, budget);     // let copies still in flight land before the block exits
+        // let the copies still in flight land before the block exits, however short the
+        // caller's budget (a copy lands in microseconds; this wait too is bounded)
+        mbar_wait(mb, 0, budget > 2000000000ull ? budget : 2000000000ull);
         return;
     }
     // this lane's row: slot lane / 4, row lane % 4 within it
@@ -1308,6 +1310,29 @@ rt_status set_step_inputs(rt_ctx* c, double dt, const double* Lsrc, const double
         ++c->launches;
     }
     RT_CUDA(c, cudaGetLastError());
+    return RT_OK;
+}
+
+// one warp waits on a barrier that nothing completes (rt_wait_selftest)
+__global__ void k_wait_selftest(unsigned long long budget, int* ran_out) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    if (threadIdx.x == 0) mbar_init(b, 1);
+    __syncwarp();
+    const bool done = mbar_wait(b, 0, budget);
+    if (!__any_sync(0xffffffffu, done) && threadIdx.x == 0) *ran_out = 1;
+}
+
+rt_status wait_selftest(rt_ctx* c, unsigned long long budget, bool* ran_out) {
+    int* f = c->flags.as<int>() + F_SELFTEST;
+    RT_CUDA(c, cudaMemsetAsync(f, 0, sizeof(int), c->stream));
+    k_wait_selftest<<<1, 32, 0, c->stream>>>(budget, f);
+    ++c->launches;
+    RT_CUDA(c, cudaGetLastError());
+    int h = 0;
+    RT_CUDA(c, cudaMemcpyAsync(&h, f, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    RT_CUDA(c, cudaStreamSynchronize(c->stream));
+    *ran_out = h != 0;
     return RT_OK;
 }
 

@@ -359,6 +359,32 @@ def test_kernel_times_and_launch_counts():
     t.close()
 
 
+def test_bounded_device_wait_runs_out_and_the_context_stays_usable():
+    """The device waits are bounded: a warp waiting on a barrier that nothing completes gives
+    up after its budget of SM cycles and the host reads RT_ERR_TIMEOUT (no trap, no hang).
+    The context's own time-out flag stays clear and its next steps are right."""
+    _need_gpu()
+    import time
+    from paper_2302_12727_gb300 import rt_wait_selftest
+    w = W.lattice_point_source()
+    t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64")
+    t0 = time.perf_counter()
+    assert rt_wait_selftest(t.ctx, 2_000_000)        # ~1 ms at 2 GHz
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(RTError):
+        rt_wait_selftest(t.ctx, 0)
+    assert t.diagnostics()["wait_timeouts"] == 0
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
+    dt = cfl_dt(o)
+    ref, _ = o.run(w.U0, 2, dt, w.Lsrc)
+    U = t.state(w.U0)
+    t.subcycle(U, 2, dt, t.luminosities(w.Lsrc))
+    nbad, rmax = fp64_close(U.cpu().numpy(), ref)
+    assert nbad == 0, rmax
+    t.energy(U)
+    t.close()
+
+
 def test_failures_are_reported_not_raised_on_the_gpu():
     """Host-made faults come back as status codes: NaN position, a flat (coplanar) particle
     set whose E_i is singular, an iteration cap too small for the h solve, bad arguments."""
