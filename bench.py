@@ -32,6 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RT pair interactions/s/group, FP32 vs FP64 at rel err<=1e-5; % of HBM peak"
+BREAKDOWN_STEPS = 2     # untimed steps with every kernel bracketed, after the timed ones
+PAIR_EVENT_EVERY = 10   # timed steps: events around one pair-pass launch in this many
 UNIT = "pair-group interactions/s"
 H_OVER_h = 1.825742
 
@@ -221,7 +223,11 @@ def run_ours(args):
         from paper_2302_12727_gb300.autotune import autotune
         tune_info = autotune(T, U0, dt, min(n_sub, 10), L, alpha, repeats=2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
-    rt_set_profiling(T.ctx, True)
+    # the timed steps bracket one pair-pass launch in PAIR_EVENT_EVERY with events (each
+    # event pair serialises the graph around its kernel: bracketing all kernels costs ~5% of
+    # a step, all pair passes ~2%); the other kernels' times come from an untimed pass after
+    # the timed region
+    rt_set_profiling(T.ctx, PAIR_EVENT_EVERY + 1)
     stream = torch.cuda.current_stream(dev)
 
     # moving particles (--drift V): seeded directions at speed V c; every step searches
@@ -236,7 +242,7 @@ def run_ours(args):
         vel = torch.as_tensor(vnp, device=dev)
         dt_h = n_sub * dt
         xs = [torch.as_tensor(np.mod(w.x + k * dt_h * vnp, 1.0), device=dev)
-              for k in range(args.warmup + args.steps)]
+              for k in range(args.warmup + args.steps + BREAKDOWN_STEPS)]
     counter = [0]
     bins_info = None
     if args.bins >= 0:
@@ -282,7 +288,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     drift_ev.clear()
 
-    kflux_ms, kflux_n, kgrad_ms, kgrad_n, kpair_ms, kgath_ms = 0.0, 0, 0.0, 0, 0.0, 0.0
+    kflux_n, kgrad_ms, kgrad_n, kpair_ms, kgath_ms = 0, 0.0, 0, 0.0, 0.0
     times = []
     launches0 = T.diagnostics()["kernel_launches"]
     sampler = ClockSampler(local)
@@ -303,18 +309,27 @@ def run_ours(args):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
         kt = rt_kernel_times(T.ctx)
-        kflux_ms += kt["flux"][0] + kt["flux_gather"][0]     # both passes of the pair flux
         kflux_n += kt["flux"][1]
         kpair_ms += kt["flux"][0]
-        kgath_ms += kt["flux_gather"][0]
-        kgrad_ms += kt["gradient"][0]
-        kgrad_n += kt["gradient"][1]
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
     launches = T.diagnostics()["kernel_launches"] - launches0
+    # untimed pass with every kernel bracketed: the gradient / gather / injection breakdown
+    rt_set_profiling(T.ctx, 1)
+    bd_sc = 0
+    for _ in range(BREAKDOWN_STEPS):
+        U.copy_(U0)
+        step()
+        torch.cuda.synchronize()
+        kt = rt_kernel_times(T.ctx)
+        kgath_ms += kt["flux_gather"][0]
+        kgrad_ms += kt["gradient"][0]
+        kgrad_n += kt["gradient"][1]
+        bd_sc += n_sub
+    rt_set_profiling(T.ctx, 0)
     # U.copy_ and flush.fill_ are torch's kernels, outside the per-step events
     t_total = max_over_ranks(sum(times) / 1e3, ws, dev)
     units_rank = P * G * n_sub * args.steps
@@ -326,10 +341,13 @@ def run_ours(args):
     out = None
     if rank == 0:
         hbm_gbs, sm_max_mhz, peak_kind = measured_peaks()
-        # per sub-cycle: one pair-pass launch and one gather launch per group chunk (G <= 4: one)
+        # per sub-cycle: one pair-pass launch and one gather launch per group chunk (G <= 4: one);
+        # the pair pass from the timed steps, gather and gradient from the untimed pass
         n_sc = args.steps * n_sub
-        flux_avg_s = kflux_ms / n_sc / 1e3
-        grad_avg_s = kgrad_ms / n_sc / 1e3
+        chunks = (G + 3) // 4                                          # group chunks per pass
+        pair_sc_ms = kpair_ms / kflux_n * chunks if kflux_n else 0.0
+        gath_sc_ms = kgath_ms / bd_sc if bd_sc else 0.0
+        grad_sc_ms = kgrad_ms / bd_sc if bd_sc else 0.0
         pair_avg_s = kpair_ms / kflux_n / 1e3 if kflux_n else None    # one launch of the pair pass
         alu_peak = 152 * 128 * 2 * 2070e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x max clock
         flux_flops = P * flux_flops_per_pair(G)
@@ -340,7 +358,7 @@ def run_ours(args):
                                                            # whatever the other two variants
         traffic = flux_traffic_from_profile(G) if default_shape else None
         pair_kernel = {0: "k_flux", 1: "k_flux_staged", 2: "k_flux_tma"}[tune["flux_variant"]]
-        sub_s = (kflux_ms + kgrad_ms) / 1e3 / args.steps
+        sub_s = (pair_sc_ms + gath_sc_ms + grad_sc_ms) * n_sub / 1e3     # per step
         out = {
             "metric": METRIC,
             "value": value,
@@ -371,11 +389,14 @@ def run_ours(args):
                          "traffic_note": "ncu DRAM read + write of one pair-pass launch (cold cache), from "
                                          "profiles/k_flux_poisson-sine-64^3-G3.md; null unless the kernel "
                                          "sources and the launch variants match that capture"},
-            "kernels": {"flux_stage_ms_per_subcycle": flux_avg_s * 1e3, "gradient_ms_per_subcycle": grad_avg_s * 1e3,
-                        "pair_flux_ms_per_subcycle": kpair_ms / n_sc, "gather_ms_per_subcycle": kgath_ms / n_sc,
-                        "flux_launches": kflux_n, "gradient_launches": kgrad_n},
+            "kernels": {"flux_stage_ms_per_subcycle": pair_sc_ms + gath_sc_ms, "gradient_ms_per_subcycle": grad_sc_ms,
+                        "pair_flux_ms_per_subcycle": pair_sc_ms, "gather_ms_per_subcycle": gath_sc_ms,
+                        "pair_launches_with_events": kflux_n, "gradient_launches_untimed": kgrad_n,
+                        "note": f"pair pass: events around one launch in {PAIR_EVENT_EVERY} (sub-cycles 0, "
+                                f"{PAIR_EVENT_EVERY}, ...) of the timed steps; gather and gradient: "
+                                f"{BREAKDOWN_STEPS} untimed steps after them with every kernel bracketed"},
             "subcycle_only": {"value": P * G * n_sub / sub_s if sub_s > 0 else None, "unit": UNIT,
-                              "note": "gradient + flux kernel time only (events around each launch)",
+                              "note": "gradient + pair pass + gather kernel time only (events around each launch)",
                               "hbm_frac_of_" + peak_kind: sub_bytes_per_particle(G) * n * n_sub / sub_s / 1e9 / hbm_gbs
                               if sub_s > 0 else None},
             "time_bins": (dict(bins_info, uniform_equivalent_value=P * G * bins_info["min_steps"] * args.steps / t_total,

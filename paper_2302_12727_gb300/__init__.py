@@ -273,8 +273,10 @@ def rt_step_bins(ctx, U, Lsrc=None, alpha=None):
     _check(ctx, load_library().rt_step_bins(ctx, _ptr(U), _ptr(Lsrc), _ptr(alpha)))
 
 
-def rt_set_profiling(ctx, on: bool):
-    _check(ctx, load_library().rt_set_profiling(ctx, 1 if on else 0))
+def rt_set_profiling(ctx, on):
+    """on: False / 0 off, True / 1 every kernel of the step, k >= 2 the pair-flux launches
+    only, one in every k - 1 of a call."""
+    _check(ctx, load_library().rt_set_profiling(ctx, int(on)))
 
 
 def rt_kernel_times(ctx):

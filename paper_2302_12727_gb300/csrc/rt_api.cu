@@ -74,6 +74,10 @@ static void record_event(cudaEvent_t e, cudaStream_t s) {
 
 int prof_begin(rt_ctx* c, cudaStream_t s, int kind) {
     if (!c->profiling || !c->prof_sink) return -1;
+    if (c->profiling >= 2) {   // pair passes only, one in every profiling - 1
+        if (kind != RT_KERNEL_FLUX) return -1;
+        if (c->prof_pairs++ % (c->profiling - 1) != 0) return -1;
+    }
     ProfRec r;
     r.kind = kind;
     if (cudaEventCreate(&r.start) != cudaSuccess) return -1;
@@ -259,6 +263,7 @@ rt_status rt_transport_step(rt_ctx* c, double dt, void* U, const double* Lsrc, c
     if (c->profiling) {
         destroy_prof(c->plain_prof);
         c->prof_sink = &c->plain_prof;
+        c->prof_pairs = 0;
     }
     rt_status s = launch_step(c, c->stream, c->U_a.p, c->U_b.p, has_src, alpha != nullptr);
     c->prof_sink = nullptr;
@@ -292,6 +297,7 @@ rt_status rt_subcycle(rt_ctx* c, int32_t n_sub, double dt, void* U, const double
         rt_status s = RT_OK;
         int64_t l0 = c->launches;
         c->prof_sink = c->profiling ? &entry.prof : nullptr;
+        c->prof_pairs = 0;
         for (int k = 0; k < n_sub && s == RT_OK; ++k) {
             s = launch_step(c, c->cap_stream, a, b, has_src, has_alpha, k == 0, k + 1 < n_sub);
             std::swap(a, b);
@@ -463,7 +469,8 @@ rt_status rt_diagnostics(rt_ctx* c, rt_diag* out) {
 rt_status rt_set_profiling(rt_ctx* c, int32_t on) {
     if (!c) return RT_ERR_INVALID;
     c->err.clear();
-    int v = on ? 1 : 0;
+    if (on < 0 || on > 1000) return fail(c, RT_ERR_INVALID, "rt_set_profiling: on must be in [0, 1000]");
+    const int v = on;
     if (v != c->profiling) {
         RT_CUDA(c, cudaStreamSynchronize(c->stream));
         drop_graphs(c);

@@ -138,7 +138,8 @@ struct rt_ctx {
     std::map<rt::GraphKey, rt::GraphEntry> graphs;
 
     // tracing
-    int profiling = 0;
+    int profiling = 0;                       // rt_set_profiling's mode
+    int64_t prof_pairs = 0;                  // pair-pass launches seen in the current call
     int64_t launches = 0;                    // own kernel launches (see rt_diag)
     std::vector<rt::ProfRec>* prof_sink = nullptr;   // where launch helpers append records
     std::vector<rt::ProfRec> plain_prof;     // records of the last plain step
