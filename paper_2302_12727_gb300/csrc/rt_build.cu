@@ -779,43 +779,6 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// warp-cooperative candidate visit: every lane walks the same ranges, lane l takes every
-// 32nd candidate; f(j, active) is called by all lanes for every chunk of 32.
-template <class F>
-__device__ __forceinline__ void warp_candidates(const Grid& g, int cx, int cy, int cz, const int k[3], int lane, F&& f) {
-    int lo[3], hi[3];
-    int c0[3] = {cx, cy, cz};
-    for (int a = 0; a < 3; ++a) {
-        bool all = (2 * k[a] + 1 >= g.nc[a]);
-        lo[a] = all ? 0 : c0[a] - k[a];
-        hi[a] = all ? g.nc[a] - 1 : c0[a] + k[a];
-        if (!g.periodic && !all) {
-            lo[a] = max(lo[a], 0);
-            hi[a] = min(hi[a], g.nc[a] - 1);
-        }
-    }
-    for (int z = lo[2]; z <= hi[2]; ++z) {
-        int zz = wrap_cell(z, g.nc[2]);
-        for (int y = lo[1]; y <= hi[1]; ++y) {
-            int yy = wrap_cell(y, g.nc[1]);
-            int64_t base = ((int64_t)zz * g.nc[1] + yy) * g.nc[0];
-            int xa = lo[0], xb = hi[0];
-            int sl[2], sh[2], ns = 0;
-            if (xa < 0) { sl[ns] = xa + g.nc[0]; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb; }
-            else if (xb >= g.nc[0]) { sl[ns] = xa; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb - g.nc[0]; }
-            else { sl[ns] = xa; sh[ns++] = xb; }
-            for (int s = 0; s < ns; ++s) {
-                int b = g.cell_start[base + sl[s]];
-                int e = g.cell_start[base + sh[s] + 1];
-                for (int j0 = b; j0 < e; j0 += 32) {
-                    int j = j0 + lane;
-                    f(j, j < e);
-                }
-            }
-        }
-    }
-}
-
 struct SrcParams {
     double eta, h0, h_cap;
     int max_iter;
@@ -950,76 +913,168 @@ __global__ void __launch_bounds__(kSrcThreads) k_src_h(Grid g, const double* __r
     }
 }
 
-// count (FILL = false) or write (FILL = true) the gas entries of every source, in the
-// candidate order of the cell walk; the fill pass also forms xi.
+// The (z, y) rows of the cell cube [c - k, c + k] around a source, numbered
+// z-major; row r's particles are one or two contiguous ranges of the sorted order.
+struct CubeRows {
+    int lo[3], hi[3];
+    int ny, rows;
+};
+
+__device__ __forceinline__ CubeRows cube_rows(const Grid& g, const int c0[3], const int k[3]) {
+    CubeRows cr;
+    for (int a = 0; a < 3; ++a) {
+        bool all = (2 * k[a] + 1 >= g.nc[a]);
+        cr.lo[a] = all ? 0 : c0[a] - k[a];
+        cr.hi[a] = all ? g.nc[a] - 1 : c0[a] + k[a];
+        if (!g.periodic && !all) {
+            cr.lo[a] = max(cr.lo[a], 0);
+            cr.hi[a] = min(cr.hi[a], g.nc[a] - 1);
+        }
+    }
+    cr.ny = cr.hi[1] - cr.lo[1] + 1;
+    cr.rows = cr.ny * (cr.hi[2] - cr.lo[2] + 1);
+    return cr;
+}
+
+// every lane walks row r of the cube, lane l taking every 32nd candidate
+template <class F>
+__device__ __forceinline__ void warp_row(const Grid& g, const CubeRows& cr, int r, int lane, F&& f) {
+    const int zz = wrap_cell(cr.lo[2] + r / cr.ny, g.nc[2]);
+    const int yy = wrap_cell(cr.lo[1] + r % cr.ny, g.nc[1]);
+    const int64_t base = ((int64_t)zz * g.nc[1] + yy) * g.nc[0];
+    const int xa = cr.lo[0], xb = cr.hi[0];
+    int sl[2], sh[2], ns = 0;
+    if (xa < 0) { sl[ns] = xa + g.nc[0]; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb; }
+    else if (xb >= g.nc[0]) { sl[ns] = xa; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb - g.nc[0]; }
+    else { sl[ns] = xa; sh[ns++] = xb; }
+    for (int q = 0; q < ns; ++q) {
+        const int b = g.cell_start[base + sl[q]];
+        const int e = g.cell_start[base + sh[q] + 1];
+        for (int j0 = b; j0 < e; j0 += 32) f(j0 + lane, j0 + lane < e);
+    }
+}
+
+constexpr int kSrcWarps = 8, kSrcRowsMax = 1024;
+
+// Count (FILL = false) or write (FILL = true) the gas entries of every source, one block of
+// kSrcWarps warps per source.  The cube's rows are dealt to the warps (row r to warp
+// r mod kSrcWarps); the fill pass first counts every row, scans the counts in row order and
+// then writes each row's entries from its offset, so the entries come in the row-major
+// candidate order of a single warp's walk.  Cubes of more than kSrcRowsMax rows are walked
+// by warp 0 alone.  The fill pass also forms xi.
 template <bool FILL>
-__global__ void k_src_entries(Grid g, const double* __restrict__ xs, int64_t n, const double* __restrict__ xsrc,
-                              int64_t S, const double* __restrict__ hs, const double* __restrict__ oms,
-                              int32_t* counts, const int64_t* __restrict__ off, int32_t* e_gas, double* e_xi,
-                              double* octw_out) {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= S) return;
-    double p[3] = {xsrc[warp], xsrc[S + warp], xsrc[2 * S + warp]};
+__global__ void __launch_bounds__(kSrcWarps * 32)
+k_src_entries(Grid g, const double* __restrict__ xs, int64_t n, const double* __restrict__ xsrc, int64_t S,
+              const double* __restrict__ hs, const double* __restrict__ oms, int32_t* counts,
+              const int64_t* __restrict__ off, int32_t* e_gas, double* e_xi, double* octw_out) {
+    __shared__ int row_n[kSrcRowsMax];
+    __shared__ double w8s[kSrcWarps][8];
+    __shared__ int total;
+    const int src = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double p[3] = {xsrc[src], xsrc[S + src], xsrc[2 * S + src]};
     int c[3];
     for (int a = 0; a < 3; ++a) c[a] = cell_coord(p[a], g.inv_cell[a], g.nc[a]);
     const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
-    double h = hs[warp], H = kKappa * h, iH = 1.0 / H, H2 = H * H;
-    double fac = kSigma * iH * iH * iH / oms[warp];
+    const double h = hs[src], H = kKappa * h, iH = 1.0 / H, H2 = H * H;
+    const double fac = kSigma * iH * iH * iH / oms[src];
     int k[3];
     for (int a = 0; a < 3; ++a) k[a] = (int)ceil(H * g.inv_cell[a]);
-    int cnt = 0;
-    int64_t base = FILL ? off[warp] : 0;
-    double w8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    warp_candidates(g, c[0], c[1], c[2], k, lane, [&](int j, bool act) {
-        bool in = false;
-        double ps = 0.0;
-        int oct = 0;
-        if (act) {
-            double dx = sep_fast(xs[j], p[0], g.box[0], half[0], g.periodic);
-            double dy = sep_fast(xs[n + j], p[1], g.box[1], half[1], g.periodic);
-            double dz = sep_fast(xs[2 * n + j], p[2], g.box[2], half[2], g.periodic);
-            double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < H2) {
-                in = true;
-                ps = fac * spline_w(sqrt(r2) * iH);
-                oct = (dx < 0 ? 1 : 0) | (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
-            }
+    const CubeRows cr = cube_rows(g, c, k);
+    const bool split = cr.rows <= kSrcRowsMax;
+    const int nw = split ? kSrcWarps : 1;
+    // candidate j of the source's support?  psi and octant when it is
+    auto test = [&](int j, bool act, double& ps, int& oct) {
+        if (!act) return false;
+        const double dx = sep_fast(xs[j], p[0], g.box[0], half[0], g.periodic);
+        const double dy = sep_fast(xs[n + j], p[1], g.box[1], half[1], g.periodic);
+        const double dz = sep_fast(xs[2 * n + j], p[2], g.box[2], half[2], g.periodic);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < H2)) return false;
+        ps = fac * spline_w(sqrt(r2) * iH);
+        oct = (dx < 0 ? 1 : 0) | (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
+        return true;
+    };
+    // pass 1: entries per row (per warp when the rows are not split)
+    if (threadIdx.x == 0) total = 0;
+    __syncthreads();
+    int mine = 0;
+    if (wid < nw) {
+        for (int r = wid; r < cr.rows; r += nw) {
+            int cnt = 0;
+            warp_row(g, cr, r, lane, [&](int j, bool act) {
+                double ps;
+                int oct;
+                cnt += __popc(__ballot_sync(0xffffffffu, test(j, act, ps, oct)));
+            });
+            if (split && lane == 0) row_n[r] = cnt;
+            mine += cnt;
         }
-        unsigned bal = __ballot_sync(0xffffffffu, in);
-        if (in) {
-            int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-            if (FILL) {
-                e_gas[base + pos] = j;
-                e_xi[base + pos] = ps;   // psi for now; mu_a applied below
-            }
-            w8[oct] += ps;
-        }
-        cnt += __popc(bal);
-    });
+        if (lane == 0) atomicAdd(&total, mine);
+    }
+    __syncthreads();
     if (!FILL) {
-        if (lane == 0) counts[warp] = cnt;
+        if (threadIdx.x == 0) counts[src] = total;
         return;
     }
-    double wsum = 0.0;
+    // row offsets in row order (exclusive prefix sums of row_n)
+    if (split && threadIdx.x == 0) {
+        int acc = 0;
+        for (int r = 0; r < cr.rows; ++r) {
+            const int v = row_n[r];
+            row_n[r] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    // pass 2: write the entries (psi for now; mu_a applied below) and the octant sums
+    const int64_t base = off[src];
+    double w8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (wid < nw) {
+        int run = 0;
+        for (int r = wid; r < cr.rows; r += nw) {
+            int pos0 = split ? row_n[r] : run;
+            warp_row(g, cr, r, lane, [&](int j, bool act) {
+                double ps = 0.0;
+                int oct = 0;
+                const bool in = test(j, act, ps, oct);
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (in) {
+                    const int pos = pos0 + __popc(bal & ((1u << lane) - 1u));
+                    e_gas[base + pos] = j;
+                    e_xi[base + pos] = ps;
+                    w8[oct] += ps;
+                }
+                pos0 += __popc(bal);
+            });
+            run = pos0;
+        }
+    }
+    for (int a = 0; a < 8; ++a) {
+        const double v = warp_sum(w8[a]);
+        if (lane == 0) w8s[wid][a] = v;
+    }
+    __syncthreads();
+    // octant sums over the warps in warp order; xi = mu_a psi, mu_a = sum_b w_b / (q_nz w_a)
+    double ws8[8], wsum = 0.0;
     int qnz = 0;
     for (int a = 0; a < 8; ++a) {
-        w8[a] = warp_sum(w8[a]);
-        wsum += w8[a];
-        qnz += (w8[a] > 0.0);
+        double v = 0.0;
+        for (int w = 0; w < kSrcWarps; ++w) v += w8s[w][a];
+        ws8[a] = v;
+        wsum += v;
+        qnz += (v > 0.0);
     }
-    if (lane == 0)
-        for (int a = 0; a < 8; ++a) octw_out[8 * warp + a] = w8[a];
-    __syncwarp();
-    // xi = mu_a psi with mu_a = sum_b w_b / (q_nz w_a)
-    for (int e = lane; e < cnt; e += 32) {
-        int j = e_gas[base + e];
-        double dx = sep_fast(xs[j], p[0], g.box[0], half[0], g.periodic);
-        double dy = sep_fast(xs[n + j], p[1], g.box[1], half[1], g.periodic);
-        double dz = sep_fast(xs[2 * n + j], p[2], g.box[2], half[2], g.periodic);
-        int oct = (dx < 0 ? 1 : 0) | (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
-        double mu = wsum / ((double)qnz * w8[oct]);
-        e_xi[base + e] = mu * e_xi[base + e];
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 8; ++a) octw_out[8 * src + a] = ws8[a];
+    __syncthreads();   // the entries of pass 2 are visible to every thread
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int j = e_gas[base + e];
+        const double dx = sep_fast(xs[j], p[0], g.box[0], half[0], g.periodic);
+        const double dy = sep_fast(xs[n + j], p[1], g.box[1], half[1], g.periodic);
+        const double dz = sep_fast(xs[2 * n + j], p[2], g.box[2], half[2], g.periodic);
+        const int oct = (dx < 0 ? 1 : 0) | (dy < 0 ? 2 : 0) | (dz < 0 ? 4 : 0);
+        e_xi[base + e] = wsum / ((double)qnz * ws8[oct]) * e_xi[base + e];
     }
 }
 
@@ -1384,10 +1439,10 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         sp.max_iter = std::max(hp.max_iter, 200);
         sp.warm = c->has_hs_prev ? 1 : 0;
         c->has_hs_prev = false;     // set again only when this call succeeds
-        unsigned sb = nblk(S * 32, 128);
+        const unsigned sb = (unsigned)S;   // one block of kSrcWarps warps per source
         k_src_h<<<(unsigned)S, kSrcThreads, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S, sp,
                                                      c->hs_d.as<double>(), c->omegas_d.as<double>(), flags);
-        k_src_entries<false><<<sb, 128, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S,
+        k_src_entries<false><<<sb, kSrcWarps * 32, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S,
                                                  c->hs_d.as<double>(), c->omegas_d.as<double>(),
                                                  c->src_counts.as<int32_t>(), nullptr, nullptr, nullptr, nullptr);
         RT_CUDA(c, cudaMemsetAsync(c->src_counts.as<int32_t>() + S, 0, 4, st));
@@ -1414,7 +1469,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         RT_TRY(ensure(c, c->inj_targets, NEa * 4, "injection"));
         RT_TRY(ensure(c, c->inj_off, (NEa + 1) * 4, "injection"));
         double* octw = c->omegas_d.as<double>() + S;   // 8 per source after omega_s
-        k_src_entries<true><<<sb, 128, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S,
+        k_src_entries<true><<<sb, kSrcWarps * 32, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S,
                                                 c->hs_d.as<double>(), c->omegas_d.as<double>(), nullptr,
                                                 c->src_off.as<int64_t>(), c->src_entry_gas.as<int32_t>(),
                                                 c->src_entry_xi.as<double>(), octw);
