@@ -355,7 +355,19 @@ def test_kernel_times_and_launch_counts():
     t.step(U, 0.01, L)
     kt = rt_kernel_times(t.ctx)
     assert kt["flux"][1] == 1 and kt["flux"][0] > 0 and kt["inject"][1] == 1
-    rt_set_profiling(t.ctx, False)
+    # on = k >= 2: the pair passes only, one in every k - 1 of a call (the first included)
+    rt_set_profiling(t.ctx, 11)
+    Ug = t.state(w.U0)
+    t.subcycle(Ug, 20, 0.01, L)
+    kt = rt_kernel_times(t.ctx)
+    assert kt["flux"][1] == 2 and kt["flux"][0] > 0
+    assert kt["gradient"][1] == kt["flux_gather"][1] == kt["inject"][1] == 0
+    rt_set_profiling(t.ctx, 0)
+    Uo = t.state(w.U0)
+    t.subcycle(Uo, 20, 0.01, L)
+    assert torch.equal(Ug, Uo)           # the events do not change the result
+    with pytest.raises(RTError):
+        rt_set_profiling(t.ctx, 1001)
     t.close()
 
 
