@@ -692,7 +692,9 @@ struct PackedRows {
     static constexpr uint32_t bytes = 32u * RW * 4u;    // bytes gathered per warp
 };
 
-template <int G, bool HLL>
+// BINS: the pairs of the ordered prefix a.order[0, a.count) (time bins: those with a
+// starting member), their fluxes scaled by 2^min(b_k, b_l) as in k_flux.
+template <int G, bool HLL, bool BINS = false>
 __global__ void __launch_bounds__(128) k_flux_tma(PairArgs<float> a, FluxExtra<float> x,
                                                   float* __restrict__ pairbuf,
                                                   const __grid_constant__ CUtensorMap rows, int* err_flag,
@@ -703,8 +705,9 @@ __global__ void __launch_bounds__(128) k_flux_tma(PairArgs<float> a, FluxExtra<f
     __shared__ __align__(8) uint64_t bar[4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float* ws = sm + wid * R::WF;
-    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const bool act = slot < a.n_pairs;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool act = t < (BINS ? a.count : a.n_pairs);
+    const int64_t slot = BINS ? (act ? (int64_t)a.order[t] : 0) : t;
     // lanes past the last slot gather particle 0 (always present) and store nothing
     const int2 kl = act ? a.ends[slot] : make_int2(0, 0);
     const uint32_t mb = smem_u32(&bar[wid]);
@@ -759,6 +762,11 @@ __global__ void __launch_bounds__(128) k_flux_tma(PairArgs<float> a, FluxExtra<f
         vload<12>(rk + 12 + 4 * G + 12 * g, gri);
         vload<12>(rl + 12 + 4 * G + 12 * g, grj);
         pair_flux<HLL>(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
+    }
+    if constexpr (BINS) {
+        const float wgt = (float)(1 << min(a.bins[kl.x], a.bins[kl.y]));   // min(dt_k, dt_l) / dt_min
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c] *= wgt;
     }
     if (act) vstore<NC>(pairbuf + slot * NC, out);
 }
@@ -1143,6 +1151,28 @@ rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec) {
 // injection and gradients of the starting particles, the pair fluxes of the pairs with a
 // starting member, the gather of the particles they touch (finalising those whose step ends
 // now), and the finalisation of the other particles whose step ends now.  In place.
+// the time-bin pair pass by row gathers (float, one group chunk); other T: never called
+template <int GC, class T>
+static void bins_flux_tma(rt_ctx* c, cudaStream_t s, const PairArgs<T>& af, const FluxExtra<T>& x, T* pb, bool hll) {
+    if constexpr (std::is_same<T, float>::value) {
+        static bool attr = false;
+        if (!attr) {
+            attr = true;
+            cudaFuncSetAttribute((const void*)k_flux_tma<GC, false, true>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+            cudaFuncSetAttribute((const void*)k_flux_tma<GC, true, true>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+            (void)cudaGetLastError();
+        }
+        const unsigned nbf = nblk(std::max<int64_t>(af.count, 1), 128);
+        const unsigned long long budget = c->cfg.device_wait_budget_cycles ? c->cfg.device_wait_budget_cycles
+                                                                           : 4000000000ull;
+        int* ef = c->flags.as<int>() + F_TIMEOUT;
+        if (hll) k_flux_tma<GC, true, true><<<nbf, 128, 0, s>>>(af, x, pb, c->rows_map, ef, budget);
+        else k_flux_tma<GC, false, true><<<nbf, 128, 0, s>>>(af, x, pb, c->rows_map, ef, budget);
+    }
+}
+
 template <class T>
 static void launch_step_bins_t(rt_ctx* c, cudaStream_t s, int step, T* rec, bool has_src, bool has_alpha) {
     set_carveouts<T>();
@@ -1182,6 +1212,17 @@ static void launch_step_bins_t(rt_ctx* c, cudaStream_t s, int step, T* rec, bool
     ae.count = n_end;
     const unsigned nbg = nblk(std::max<int64_t>(n_start, 1), 128), nbf = nblk(std::max<int64_t>(n_pairs, 1), 128);
     const unsigned nbh = nblk(std::max<int64_t>(n_touch, 1), 128), nbe = nblk(std::max<int64_t>(n_end, 1), 128);
+    // the float pair pass by row gathers of the packed rows: the gradient kernel writes the
+    // rows of the particles starting a step (their state after injection and their new
+    // gradient); every other particle's row still holds the state and gradient of its own
+    // step start, which is what its pairs use until its step ends
+    bool packed = false;
+    if constexpr (std::is_same<T, float>::value)
+        packed = c->tune.flux_variant == 2 && G <= kMaxGC && packed_rows_map(c);
+    if (packed) {
+        ag.frec = c->frec.as<T>();
+        af.frec = c->frec.as<T>();
+    }
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         const int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
         if (n_start == 0) break;
@@ -1197,7 +1238,9 @@ static void launch_step_bins_t(rt_ctx* c, cudaStream_t s, int step, T* rec, bool
         const int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
 #define RT_BINS_FLUX(GC_)                                                                    \
     if (n_pairs > 0) {                                                                       \
-        if (hll)                                                                             \
+        if (packed)                                                                          \
+            bins_flux_tma<GC_>(c, s, af, x, pb, hll);                                        \
+        else if (hll)                                                                        \
             k_flux<T, GC_, true, true><<<nbf, 128, 0, s>>>(af, x, rec, pb, g0);              \
         else                                                                                 \
             k_flux<T, GC_, false, true><<<nbf, 128, 0, s>>>(af, x, rec, pb, g0);             \
