@@ -536,15 +536,17 @@ __global__ void k_pair_ends(const int64_t* __restrict__ row_off, const int32_t* 
     for (int64_t e = e0; e < e1; ++e, ++slot) ends[slot] = make_int2((int)i, cols[e]);
 }
 
-// for every lower entry (i, k), k < i: the slot of the pair in k's upper list
+// for every lower entry (i, k), k < i: the slot of the pair in k's upper list.  One warp per
+// particle, its lanes taking the lower entries (each a binary search in row k's upper part).
 __global__ void k_low_slots(const int64_t* __restrict__ row_off, const int32_t* __restrict__ cols,
                             const int32_t* __restrict__ n_low, const int64_t* __restrict__ up_off, int64_t n,
                             int32_t* low_slot) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
     int64_t r0 = row_off[i];
     int64_t lbase = r0 - up_off[i];       // lower entries before row i
-    for (int e = 0; e < n_low[i]; ++e) {
+    for (int e = lane; e < n_low[i]; e += 32) {
         int k = cols[r0 + e];
         int64_t b = row_off[k] + n_low[k], hi = row_off[k + 1], t = hi;
         while (b < t) {
@@ -1399,8 +1401,9 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     tb = c->cub_tmp.bytes;
     RT_CUDA(c, cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tb, c->n_up.as<int32_t>(), c->up_off.as<int64_t>(),
                                              (int)(n + 1), st));
-    k_low_slots<<<nblk(n, 128), 128, 0, st>>>(c->row_off.as<int64_t>(), c->cols.as<int32_t>(), c->n_low.as<int32_t>(),
-                                               c->up_off.as<int64_t>(), n, c->low_slot.as<int32_t>());
+    k_low_slots<<<nblk(n * 32, 256), 256, 0, st>>>(c->row_off.as<int64_t>(), c->cols.as<int32_t>(),
+                                                    c->n_low.as<int32_t>(), c->up_off.as<int64_t>(), n,
+                                                    c->low_slot.as<int32_t>());
     RT_TRY(ensure(c, c->pair_ends, std::max<int64_t>(P2 / 2, 1) * 8, "pair split"));
     k_pair_ends<<<nblk(n, 128), 128, 0, st>>>(c->row_off.as<int64_t>(), c->cols.as<int32_t>(), c->n_low.as<int32_t>(),
                                                c->up_off.as<int64_t>(), n, c->pair_ends.as<int2>());
