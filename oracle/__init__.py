@@ -55,6 +55,9 @@ def _load():
         lib.orc_create.restype = vp
         lib.orc_create.argtypes = [C.POINTER(_Cfg), C.c_long, dp, dp, C.c_long, dp, C.POINTER(C.c_int)]
         lib.orc_destroy.argtypes = [vp]
+        lib.orc_create_given_h.restype = vp
+        lib.orc_create_given_h.argtypes = [C.POINTER(_Cfg), C.c_long, dp, dp, C.c_long, dp, dp, dp,
+                                           C.POINTER(C.c_int)]
         lib.orc_num_directed_pairs.restype = C.c_long
         lib.orc_num_directed_pairs.argtypes = [vp]
         lib.orc_get_pairs.argtypes = [vp, lp, ip]
@@ -69,6 +72,8 @@ def _load():
         lib.orc_run.restype = C.c_long
         lib.orc_run.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp]
         lib.orc_jvp.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp]
+        lib.orc_jvp_kinks.restype = C.c_long
+        lib.orc_jvp_kinks.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, C.c_double]
         lib.orc_energy.argtypes = [vp, dp, dp]
         lib.orc_dt_positivity.restype = C.c_double
         lib.orc_dt_positivity.argtypes = [vp]
@@ -90,6 +95,7 @@ def _load():
         lib.orc_run_groups.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp]
         lib.orc_hll_flux.argtypes = [vp, dp, dp, dp, dp]
         lib.orc_wave_speeds.argtypes = [vp, dp, dp, dp, dp]
+        lib.orc_pair_flops.argtypes = [vp, dp]
         _lib = lib
     return _lib
 
@@ -123,9 +129,10 @@ class Oracle:
 
     def __init__(self, x, m, xsrc=None, *, n_groups=1, c_red=1.0, eta_res=1.2348, eta_res_star=1.2348,
                  box=(1.0, 1.0, 1.0), periodic=True, clamp_negative=False, h_tol=1e-15, h_max_iter=200,
-                 brute_force=False, riemann="glf", wave_table=None):
+                 brute_force=False, riemann="glf", wave_table=None, h=None, hs=None):
         """riemann: "glf" (Eq. riemann-GLF) or "hll" (Eq. riemann-HLL); for HLL the wave-speed
-        table (lmax, lmin) over (f, theta) defaults to m1_eigen.default_table()."""
+        table (lmax, lmin) over (f, theta) defaults to m1_eigen.default_table().  h [N] and hs
+        [S]: smoothing lengths given instead of solved (omega is then evaluated at them)."""
         lib = _load()
         self.lib = lib
         self.x = _c(x)
@@ -140,8 +147,15 @@ class Oracle:
         cfg = _Cfg(n_groups, c_red, eta_res, eta_res_star, (C.c_double * 3)(*box), int(periodic),
                    int(clamp_negative), h_tol, h_max_iter, int(brute_force), int(riemann == "hll"))
         st = C.c_int(0)
-        self._p = lib.orc_create(C.byref(cfg), self.n, _dp(self.x), _dp(self.m), self.n_src,
-                                 _dp(self.xsrc) if self.n_src else _dp(np.zeros(3)), C.byref(st))
+        if h is None:
+            self._p = lib.orc_create(C.byref(cfg), self.n, _dp(self.x), _dp(self.m), self.n_src,
+                                     _dp(self.xsrc) if self.n_src else _dp(np.zeros(3)), C.byref(st))
+        else:
+            hh = _c(h)
+            hsa = _c(hs if hs is not None and self.n_src else np.zeros(1))
+            self._p = lib.orc_create_given_h(C.byref(cfg), self.n, _dp(self.x), _dp(self.m), self.n_src,
+                                             _dp(self.xsrc) if self.n_src else _dp(np.zeros(3)), _dp(hh),
+                                             _dp(hsa), C.byref(st))
         if st.value != 0:
             lib.orc_destroy(self._p)
             self._p = None
@@ -274,6 +288,18 @@ class Oracle:
                          _dp(dL) if dL.size else z, _dp(a), _dp(U), _dp(dU))
         return U, dU
 
+    def jvp_kinks(self, U0, dU0, n_sub, dt, L, dL, alpha=None, eps=1e-6):
+        """Branch points of the limiter and the closure within eps along (dU0, dL) over n_sub
+        steps (first order): 0 means central differences of step eps see a smooth map."""
+        U0 = _c(U0).reshape(self.G, 4, self.n)
+        dU0 = _c(dU0).reshape(self.G, 4, self.n)
+        L = _c(L).reshape(self.n_src, self.G)
+        dL = _c(dL).reshape(self.n_src, self.G)
+        a = None if alpha is None else _c(alpha)
+        z = _dp(np.zeros(1))
+        return int(self.lib.orc_jvp_kinks(self._p, int(n_sub), float(dt), _dp(U0), _dp(dU0),
+                                          _dp(L) if L.size else z, _dp(dL) if dL.size else z, _dp(a), float(eps)))
+
     def step_bins(self, U0, dt_min, bins, L=None, alpha=None, limit=True):
         """One hydro step with individual time bins (see rt_oracle.cpp): returns
         (U, bins after the limiter, clamp count)."""
@@ -298,6 +324,19 @@ class Oracle:
         out = np.empty_like(U)
         self.lib.orc_drift(self._p, _dp(U), _dp(_c(v)), float(dt_drift), _dp(out))
         return out
+
+    def pair_flops(self):
+        """Floating-point operations of one pair evaluation, counted on the oracle's own pair
+        arithmetic (add, sub, mul, div, sqrt one each): dict with flux_geometry (per
+        unordered pair, averaged over this particle set's pairs), flux_per_group (per pair
+        and group, general branch), accumulate_per_group (both particles' sums),
+        gradient_geometry (per directed entry, averaged) and gradient_per_group (per
+        directed entry and group)."""
+        out = np.zeros(5)
+        self.lib.orc_pair_flops(self._p, _dp(out))
+        keys = ("flux_geometry", "flux_per_group", "accumulate_per_group", "gradient_geometry",
+                "gradient_per_group")
+        return dict(zip(keys, out.tolist()))
 
     def energy(self, U):
         U = _c(U)

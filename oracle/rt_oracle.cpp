@@ -63,6 +63,8 @@
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
+
+#include <atomic>
 #endif
 
 namespace orc {
@@ -110,26 +112,59 @@ inline Dual sqrt(Dual a) {
     double s = std::sqrt(a.v);
     return Dual(s, s > 0 ? a.d / (2.0 * s) : 0.0);
 }
+// Kinks of the piecewise-smooth step near a forward-mode evaluation: with g_kink_eps > 0, the
+// JVP counts every branch point of the limiter and the closure that a change of the inputs by
+// g_kink_eps times the direction could cross (to first order), i.e. where a central
+// difference of that step size straddles a kink and so cannot equal the derivative.
+static double g_kink_eps = 0.0;
+static std::atomic<long> g_kinks{0};
+inline void kink_if(double dist, double rate) {
+    if (g_kink_eps > 0.0 && std::fabs(dist) <= g_kink_eps * std::fabs(rate)) g_kinks.fetch_add(1);
+}
+
 inline double val(double a) { return a; }
 inline double val(Dual a) { return a.v; }
 inline double sqrt_(double a) { return std::sqrt(a); }
 inline Dual sqrt_(Dual a) { return sqrt(a); }
 
+// A double that counts the floating-point operations done on it (add, subtract, multiply,
+// divide, square root: one each; comparisons and conversions are not counted).  The pair
+// arithmetic instantiated on it measures the work of one pair evaluation (orc_pair_flops).
+static long g_flops = 0;
+struct Counted {
+    double v;
+    Counted() : v(0) {}
+    Counted(double a) : v(a) {}
+};
+inline Counted operator+(Counted a, Counted b) { ++g_flops; return Counted(a.v + b.v); }
+inline Counted operator-(Counted a, Counted b) { ++g_flops; return Counted(a.v - b.v); }
+inline Counted operator-(Counted a) { return Counted(-a.v); }
+inline Counted operator*(Counted a, Counted b) { ++g_flops; return Counted(a.v * b.v); }
+inline Counted operator/(Counted a, Counted b) { ++g_flops; return Counted(a.v / b.v); }
+inline Counted& operator+=(Counted& a, Counted b) { a = a + b; return a; }
+inline Counted& operator-=(Counted& a, Counted b) { a = a - b; return a; }
+inline Counted& operator*=(Counted& a, Counted b) { a = a * b; return a; }
+inline double val(Counted a) { return a.v; }
+inline Counted sqrt_(Counted a) { ++g_flops; return Counted(std::sqrt(a.v)); }
+
 // ---------------------------------------------------------------------------------------
 // Cubic spline kernel, Eq. cubic-spline-kernel, nu = 3.  H = kHoverh * h.
-double kernel_W(double r, double h) {
+// (S: the scalar of the distance and the result; H and sigma / H^3 are per-particle constants)
+template <class S>
+S kernel_W_t(S r, double h) {
     const double H = kHoverh * h;
-    const double q = r / H;
-    double w;
-    if (q <= 0.5) {
-        w = (1.0 - q) * (1.0 - q) * (1.0 - q) - 4.0 * (0.5 - q) * (0.5 - q) * (0.5 - q);
-    } else if (q < 1.0) {
-        w = (1.0 - q) * (1.0 - q) * (1.0 - q);
+    const S q = r / S(H);
+    S w;
+    if (val(q) <= 0.5) {
+        w = (S(1.0) - q) * (S(1.0) - q) * (S(1.0) - q) - S(4.0) * (S(0.5) - q) * (S(0.5) - q) * (S(0.5) - q);
+    } else if (val(q) < 1.0) {
+        w = (S(1.0) - q) * (S(1.0) - q) * (S(1.0) - q);
     } else {
-        w = 0.0;
+        w = S(0.0);
     }
-    return kSigma3 / (H * H * H) * w;
+    return S(kSigma3 / (H * H * H)) * w;
 }
+double kernel_W(double r, double h) { return kernel_W_t<double>(r, h); }
 
 // ---------------------------------------------------------------------------------------
 struct Particles {
@@ -158,7 +193,8 @@ static void sep_point(const Particles& P, const double p[3], long j, double d[3]
     }
 }
 
-static double norm2(const double d[3]) { return d[0] * d[0] + d[1] * d[1] + d[2] * d[2]; }
+template <class S>
+static S norm2(const S d[3]) { return d[0] * d[0] + d[1] * d[1] + d[2] * d[2]; }
 
 // Simple uniform cell list used only to find candidates; every candidate is then tested
 // with the exact distance.  brute_force bypasses it.
@@ -286,6 +322,22 @@ static HSolve solve_h(const Particles& P, const CellList& cl, const double p[3],
     return res;
 }
 
+// omega(h) = sum_j W(|x_j - p|, h) over the particles around p (Eq. omega; p a particle's own
+// position includes its self term), for a given h
+static double omega_given(const Particles& P, const CellList& cl, const double p[3], double h) {
+    std::vector<long> cand;
+    const double R = kHoverh * h;
+    cl.candidates(p, R * 1.25, cand);
+    double w = 0.0;
+    for (long j : cand) {
+        double d[3];
+        sep_point(P, p, j, d);
+        double q = norm2(d);
+        if (q < R * R * 1.5625) w += kernel_W(std::sqrt(q), h);
+    }
+    return w;
+}
+
 // ---------------------------------------------------------------------------------------
 // Symmetric 3x3 helpers
 static double det3(const double E[9]) {
@@ -358,26 +410,33 @@ struct Model {
     std::vector<double> wmax, wmin;
 
     double H(long i) const { return kHoverh * h[i]; }
+    // smoothing lengths given by the caller instead of solved (a rank of a domain
+    // decomposition takes them from the particles' owners); empty: solve
+    std::vector<double> h_given, hs_given;
 };
 
 // psi_j(x_i) = W(|x_i - x_j|, h_i) / omega_i     (Eq. psi with h evaluated at x_i)
-static double psi_at(const Model& M, long i, double r) { return kernel_W(r, M.h[i]) / M.omega[i]; }
+template <class S>
+static S psi_at(const Model& M, long i, S r) { return kernel_W_t<S>(r, M.h[i]) / S(M.omega[i]); }
 
 // psitilde_j(x_i) = B_i (x_j - x_i) psi_j(x_i)     (Eq. psitilde)
-static void psitilde(const Model& M, long i, const double d[3], double r, double out[3]) {
-    double ps = psi_at(M, i, r);
+template <class S>
+static void psitilde(const Model& M, long i, const S d[3], S r, S out[3]) {
+    S ps = psi_at<S>(M, i, r);
     const double* Bi = &M.B[9 * i];
-    for (int a = 0; a < 3; ++a) out[a] = (Bi[3 * a] * d[0] + Bi[3 * a + 1] * d[1] + Bi[3 * a + 2] * d[2]) * ps;
+    for (int a = 0; a < 3; ++a)
+        out[a] = (S(Bi[3 * a]) * d[0] + S(Bi[3 * a + 1]) * d[1] + S(Bi[3 * a + 2]) * d[2]) * ps;
 }
 
 // A_ij = V_i psitilde_j(x_i) - V_j psitilde_i(x_j)     (Eq. HopkinsAij), d = x_j - x_i
-static void surface(const Model& M, long i, long j, const double d[3], double A[3]) {
-    double r = std::sqrt(norm2(d));
-    double mdv[3] = {-d[0], -d[1], -d[2]};
-    double pi_[3], pj_[3];
-    psitilde(M, i, d, r, pi_);    // psitilde_j(x_i)
-    psitilde(M, j, mdv, r, pj_);  // psitilde_i(x_j)
-    for (int a = 0; a < 3; ++a) A[a] = M.V[i] * pi_[a] - M.V[j] * pj_[a];
+template <class S>
+static void surface(const Model& M, long i, long j, const S d[3], S A[3]) {
+    S r = sqrt_(norm2(d));
+    S mdv[3] = {-d[0], -d[1], -d[2]};
+    S pi_[3], pj_[3];
+    psitilde<S>(M, i, d, r, pi_);    // psitilde_j(x_i)
+    psitilde<S>(M, j, mdv, r, pj_);  // psitilde_i(x_j)
+    for (int a = 0; a < 3; ++a) A[a] = S(M.V[i]) * pi_[a] - S(M.V[j]) * pj_[a];
 }
 
 static int build(Model& M) {
@@ -397,6 +456,15 @@ static int build(Model& M) {
 #pragma omp parallel for schedule(dynamic, 64)
     for (long i = 0; i < n; ++i) {
         double p[3] = {M.P.coord(i, 0), M.P.coord(i, 1), M.P.coord(i, 2)};
+        if (!M.h_given.empty()) {
+            M.h[i] = M.h_given[i];
+            M.omega[i] = omega_given(M.P, cl, p, M.h[i]);
+            if (!(M.h[i] > 0.0)) {
+#pragma omp critical
+                bad = ERR_INVALID;
+            }
+            continue;
+        }
         HSolve s = solve_h(M.P, cl, p, c.eta_res, h0, c.h_tol, c.h_max_iter, h_cap);
         if (s.status != OK) {
 #pragma omp critical
@@ -467,7 +535,14 @@ static int build(Model& M) {
     M.octw.assign(8 * M.n_src, 0.0);
     for (long s = 0; s < M.n_src; ++s) {
         double p[3] = {M.xsrc[s], M.xsrc[M.n_src + s], M.xsrc[2 * M.n_src + s]};
-        HSolve hsol = solve_h(M.P, cl, p, c.eta_res_star, h0, c.h_tol, c.h_max_iter, h_cap);
+        HSolve hsol;
+        if (!M.hs_given.empty()) {
+            hsol.h = M.hs_given[s];
+            hsol.omega = omega_given(M.P, cl, p, hsol.h);
+            if (!(hsol.h > 0.0) || !(hsol.omega > 0.0)) return ERR_INVALID;
+        } else {
+            hsol = solve_h(M.P, cl, p, c.eta_res_star, h0, c.h_tol, c.h_max_iter, h_cap);
+        }
         if (hsol.status != OK) return hsol.status;
         M.hs[s] = hsol.h;
         M.omegas[s] = hsol.omega;
@@ -535,6 +610,15 @@ static void gradients(const Model& M, const std::vector<T>& U, std::vector<T>& g
 // minmod, Eq. rt-minmod
 template <class T>
 static T minmod(T a, T b) {
+    if constexpr (std::is_same<T, Dual>::value) {
+        // branch points: either slope changing sign, or their magnitudes changing order
+        kink_if(a.v, a.d);
+        kink_if(b.v, b.d);
+        if (a.v * b.v > 0.0) {
+            const double sa = a.v > 0.0 ? 1.0 : -1.0, sb = b.v > 0.0 ? 1.0 : -1.0;
+            kink_if(std::fabs(a.v) - std::fabs(b.v), sa * a.d - sb * b.d);
+        }
+    }
     if (val(a) * val(b) <= 0.0) return T(0.0);
     if (std::fabs(val(a)) < std::fabs(val(b))) return a;
     return b;
@@ -557,6 +641,10 @@ static void m1_flux_dot(const T u[4], const double A[3], double c, T out[4]) {
     }
     T Fn = sqrt_(F2);
     T f = Fn / (T(c) * E);
+    if constexpr (std::is_same<T, Dual>::value) {
+        kink_if(E.v, E.d);            // zero pressure below E = 0
+        kink_if(f.v - 1.0, f.d);      // reduced flux clipped to 1
+    }
     if (val(f) > 1.0) f = T(1.0);
     T f2 = f * f;
     T chi = (T(3.0) + T(4.0) * f2) / (T(5.0) + T(2.0) * sqrt_(T(4.0) - T(3.0) * f2));
@@ -572,8 +660,9 @@ static void m1_flux_dot(const T u[4], const double A[3], double c, T out[4]) {
 template <class T>
 static void face_states(const T uk[4], const T ul[4], const T gk[4][3], const T gl[4][3], const double d[3],
                         double hk, double hl, T uL[4], T uR[4]) {
-    double wk = hk / (hk + hl);
-    double wl = hl / (hk + hl);
+    const T hs = T(hk) + T(hl);
+    const T wk = T(hk) / hs;
+    const T wl = T(hl) / hs;
     for (int q = 0; q < 4; ++q) {
         T dQk = T(0.0), dQl = T(0.0);
         for (int a = 0; a < 3; ++a) {
@@ -581,8 +670,8 @@ static void face_states(const T uk[4], const T ul[4], const T gk[4][3], const T 
             dQl += gl[q][a] * T(d[a]);
         }
         T s = minmod(dQk, dQl);
-        uL[q] = uk[q] + T(wk) * s;
-        uR[q] = ul[q] - T(wl) * s;
+        uL[q] = uk[q] + wk * s;
+        uR[q] = ul[q] - wl * s;
     }
 }
 
@@ -885,6 +974,39 @@ void* orc_create(const orc_config* cfg, long n, const double* x, const double* m
     return M;
 }
 
+// as orc_create, with the smoothing lengths given: h [n] for the particles, hs [n_src] for the
+// sources (omega then evaluated at them)
+void* orc_create_given_h(const orc_config* cfg, long n, const double* x, const double* m, long n_src,
+                         const double* xsrc, const double* h, const double* hs, int* status) {
+    Model* M = new Model();
+    M->h_given.assign(h, h + n);
+    if (n_src > 0) M->hs_given.assign(hs, hs + n_src);
+    M->cfg.n_groups = cfg->n_groups;
+    M->cfg.c_red = cfg->c_red;
+    M->cfg.eta_res = cfg->eta_res;
+    M->cfg.eta_res_star = cfg->eta_res_star;
+    for (int a = 0; a < 3; ++a) M->cfg.box[a] = cfg->box[a];
+    M->cfg.periodic = cfg->periodic;
+    M->cfg.clamp_negative = cfg->clamp_negative;
+    M->cfg.h_tol = cfg->h_tol;
+    M->cfg.h_max_iter = cfg->h_max_iter;
+    M->cfg.brute_force = cfg->brute_force;
+    M->cfg.riemann = cfg->riemann;
+    M->P.n = n;
+    for (int a = 0; a < 3; ++a) M->P.box[a] = cfg->box[a];
+    M->P.periodic = cfg->periodic != 0;
+    M->P.x.assign(x, x + 3 * n);
+    M->m.assign(m, m + n);
+    M->n_src = n_src;
+    M->xsrc.assign(xsrc, xsrc + 3 * n_src);
+    if (n < 2 || cfg->n_groups < 1) {
+        *status = ERR_INVALID;
+        return M;
+    }
+    *status = build(*M);
+    return M;
+}
+
 void orc_destroy(void* p) { delete (Model*)p; }
 
 long orc_num_directed_pairs(void* p) {
@@ -1054,6 +1176,21 @@ void orc_jvp(void* p, int n_sub, double dt, const double* U0, const double* dU0,
     }
 }
 
+// The number of kinks (see kink_if) that n_sub steps along the direction (dU0, dL) pass within
+// eps of: central differences of step eps along that direction match the derivative only
+// where this is zero.
+long orc_jvp_kinks(void* p, int n_sub, double dt, const double* U0, const double* dU0, const double* L,
+                   const double* dL, const double* alpha, double eps) {
+    Model* M = (Model*)p;
+    size_t n = M->P.n, C = 4 * M->cfg.n_groups;
+    std::vector<double> U(C * n), dU(C * n);
+    g_kinks = 0;
+    g_kink_eps = eps;
+    orc_jvp(p, n_sub, dt, U0, dU0, L, dL, alpha, U.data(), dU.data());
+    g_kink_eps = 0.0;
+    return g_kinks.load();
+}
+
 // Drift correction (Sec. "Dealing With Particle Drifts"): a particle moved by dx = v dt_drift
 // takes the state extrapolated with its gradient (Eq. gradient) at the old position,
 // U_i + grad U_i . dx_i, for every component.  U, Uout: [G][4][N]; v: [3][N].
@@ -1102,6 +1239,92 @@ double orc_dt_positivity(void* p) {
 void orc_m1_flux(const double* u4, const double* A, double c, double* out) { m1_flux_dot<double>(u4, A, c, out); }
 
 double orc_kernel_W(double r, double h) { return kernel_W(r, h); }
+
+// Floating-point operations of the pair loops, counted by running the oracle's own pair
+// arithmetic on the counting scalar (add, subtract, multiply, divide, square root: one each;
+// comparisons, conversions and the periodic wrap of separations are not counted):
+//   out[0] flux geometry per unordered pair: separation, A_kl (Eq. HopkinsAij), |A_kl| and the
+//          GLF dissipation factor c/2 |A_kl|; averaged over the model's pairs (the spline's
+//          two branches differ in cost);
+//   out[1] flux per unordered pair and group: the face states of Eq. rt-riemann-problem with
+//          the minmod slopes and the GLF flux of Eq. riemann-GLF with two M1 closures
+//          (Eq. eddington-group), for a state in the general branch (E > 0, 0 < f < 1, slopes
+//          of equal sign, so no branch of the closure or the limiter returns early);
+//   out[2] accumulation of that flux into both particles' sums, per pair and group;
+//   out[3] gradient geometry per directed neighbour entry: separation, |d| and
+//          psitilde_j(x_i) (Eq. psitilde); averaged over the model's entries;
+//   out[4] gradient per directed entry and group: (Q_j - Q_i) psitilde for the four components
+//          (Eq. gradient).
+void orc_pair_flops(void* p, double* out) {
+    const Model& M = *(const Model*)p;
+    const long n = M.P.n;
+    const double c = M.cfg.c_red;
+    long geo = 0, npair = 0, ggeo = 0, nent = 0;
+    for (long i = 0; i < n; ++i)
+        for (long j : M.nbr[i]) {
+            double dd[3];
+            M.P.sep(i, j, dd);
+            // x_j - x_i: three subtractions (the periodic wrap is not arithmetic of the method)
+            g_flops = 3;
+            Counted d[3];
+            for (int a = 0; a < 3; ++a) d[a] = Counted(dd[a]);
+            Counted r = sqrt_(norm2(d));
+            Counted pt[3];
+            psitilde<Counted>(M, i, d, r, pt);
+            ggeo += g_flops;
+            ++nent;
+            if (j < i) continue;
+            g_flops = 3;
+            Counted A[3];
+            surface<Counted>(M, i, j, d, A);
+            Counted An = sqrt_(norm2(A));
+            Counted diss = Counted(0.5 * c) * An;
+            (void)diss;
+            geo += g_flops;
+            ++npair;
+        }
+    // one pair in the general branch
+    long k = -1, l = -1;
+    for (long i = 0; i < n && k < 0; ++i)
+        if (!M.nbr[i].empty()) { k = i; l = M.nbr[i][0]; }
+    double dd[3];
+    M.P.sep(k, l, dd);
+    const double uk0[4] = {1.0, 0.3 * c, 0.2 * c, -0.1 * c}, ul0[4] = {0.8, 0.1 * c, 0.25 * c, 0.05 * c};
+    Counted uk[4], ul[4], gk[4][3], gl[4][3], uL[4], uR[4], phi[4];
+    for (int q = 0; q < 4; ++q) {
+        uk[q] = uk0[q];
+        ul[q] = ul0[q];
+        for (int a = 0; a < 3; ++a) {       // grad Q . d = s |d|^2 with s > 0 on both sides
+            gk[q][a] = (1.0 + 0.5 * q) * dd[a];
+            gl[q][a] = (2.0 + 0.25 * q) * dd[a];
+        }
+    }
+    double A[3];
+    surface<double>(M, k, l, dd, A);
+    g_flops = 0;
+    face_states<Counted>(uk, ul, gk, gl, dd, M.h[k], M.h[l], uL, uR);
+    glf_flux<Counted>(uL, uR, A, c, phi);
+    const long per_group = g_flops;
+    g_flops = 0;
+    Counted acc_k[4], acc_l[4];
+    for (int q = 0; q < 4; ++q) {
+        acc_k[q] += phi[q];
+        acc_l[q] -= phi[q];
+    }
+    const long gather = g_flops;
+    g_flops = 0;
+    Counted grad[4][3], ps[3] = {Counted(0.1), Counted(0.2), Counted(0.3)};
+    for (int q = 0; q < 4; ++q) {
+        Counted dq = ul[q] - uk[q];
+        for (int a = 0; a < 3; ++a) grad[q][a] += dq * ps[a];
+    }
+    const long grad_group = g_flops;
+    out[0] = npair ? (double)geo / (double)npair : 0.0;
+    out[1] = (double)per_group;
+    out[2] = (double)gather;
+    out[3] = nent ? (double)ggeo / (double)nent : 0.0;
+    out[4] = (double)grad_group;
+}
 
 // face states of one pair and group: u*/g* per component (E, Fx, Fy, Fz), g* row-major [4][3]
 void orc_face_states(const double* uk, const double* ul, const double* gk, const double* gl, const double* d,

@@ -127,6 +127,58 @@ def test_m1_chi_monotone():
     assert np.all(np.diff(chis) > 0)
 
 
+def _boosted_isotropic_moments(beta, nq=400):
+    """Angular moments of radiation that is isotropic in a frame moving at speed beta c along
+    +z, computed by Gauss-Legendre quadrature over mu = cos(angle to z).  The frequency-
+    integrated intensity transforms with the fourth power of the Doppler factor,
+    I(mu) = I0 / (gamma (1 - beta mu))^4, so E = 2 pi/c int I dmu, F_z = 2 pi int I mu dmu,
+    P_zz = 2 pi/c int I mu^2 dmu (c = 1 here).  Returns f = F/(cE) and chi = P_zz / E."""
+    mu, wq = np.polynomial.legendre.leggauss(nq)
+    gam = 1.0 / np.sqrt(1.0 - beta * beta)
+    intensity = 1.0 / (gam * (1.0 - beta * mu)) ** 4
+    E = 2 * np.pi * (wq * intensity).sum()
+    F = 2 * np.pi * (wq * intensity * mu).sum()
+    P = 2 * np.pi * (wq * intensity * mu * mu).sum()
+    return F / E, P / E, E
+
+
+def test_m1_closure_exact_for_boosted_isotropic_radiation():
+    """Eq. eddington-group between its limits.  The M1 closure the thesis adopts (Levermore
+    1984, cited in Sec. "The Equations of Radiative Transfer and the M1 Closure") is exact for
+    radiation that is isotropic in some moving frame; the thesis verifies its two limits by
+    the same kind of angular moments (isotropic intensity: chi = 1/3; a delta beam: chi = 1).
+    For boosts beta in (0, 1) the quadrature gives states of every reduced flux f in (0, 1)
+    and their exact n.D.n = P_zz/E; the oracle's flux rows, contracted with n and with a
+    direction normal to it, must give chi and (1 - chi)/2.  A wrong chi between the limits
+    (e.g. sqrt(4 - 3f) for sqrt(4 - 3f^2)) fails this; the limit tests above cannot see it."""
+    c = 1.3
+    n = np.array([2.0, -1.0, 2.0]) / 3.0
+    t = np.array([1.0, 2.0, 0.0]) / np.sqrt(5.0)        # normal to n
+    fs = []
+    for beta in (0.05, 0.2, 0.35, 0.5, 0.65, 0.8, 0.95, 0.99):
+        f, chi_exact, E = _boosted_isotropic_moments(beta)
+        fs.append(f)
+        u = np.r_[E, f * c * E * n]
+        chi = oracle.m1_flux(u, n, c)[1:] @ n / (c * c * E)
+        a_iso = oracle.m1_flux(u, t, c)[1:] @ t / (c * c * E)
+        assert chi == pytest.approx(chi_exact, rel=2e-13), (beta, f)
+        assert a_iso == pytest.approx((1 - chi_exact) / 2, rel=2e-13, abs=1e-15), (beta, f)
+    assert min(fs) < 0.1 and max(fs) > 0.99         # the boosts span the reduced fluxes
+
+
+def test_m1_chi_printed_closed_form_at_intermediate_f():
+    """Eq. eddington-group's chi(f) = (3 + 4 f^2) / (5 + 2 sqrt(4 - 3 f^2)) at f = 1/4, 1/2, 3/4,
+    numerators 3 + 4 f^2 written out as 3.25, 4 and 5.25, against n.D.n of the oracle's flux
+    rows."""
+    c, E = 1.0, 2.0
+    n = np.array([0.0, 0.6, 0.8])
+    want = {0.25: 3.25 / (5 + 2 * np.sqrt(4 - 3 / 16)), 0.5: 4.0 / (5 + 2 * np.sqrt(3.25)),
+            0.75: 5.25 / (5 + 2 * np.sqrt(4 - 27 / 16))}
+    for f, chi in want.items():
+        out = oracle.m1_flux(np.r_[E, f * c * E * n], n, c)
+        assert out[1:] @ n / (c * c * E) == pytest.approx(chi, rel=1e-14), f
+
+
 # --------------------------------------------------------------------------------- O8
 def test_appendix5_worked_example(golden):
     """App. 5: zero-flux particle next to an empty one, GLF flux and one explicit update."""
