@@ -11,7 +11,9 @@ unordered interacting pairs (r < max(H_i, H_j)) and G the photon groups.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload poisson-sine-beam] [--impl reference]
 
 Under torchrun (N > 1) every rank runs an independent replica (weak scaling); the time
-is the max over ranks and the value sums all ranks' units.
+is the max over ranks and the value sums all ranks' units.  --gpus must equal the number of
+ranks.  --decompose splits one particle set over the ranks instead (spatial domain
+decomposition with halo exchanges; strong scaling).
 """
 from __future__ import annotations
 
@@ -37,21 +39,53 @@ PAIR_EVENT_EVERY = 10   # timed steps: events around one pair-pass launch in thi
 UNIT = "pair-group interactions/s"
 H_OVER_h = 1.825742
 
-# Algorithmic FP32 operations of one pair in one sub-cycle (one evaluation per unordered
-# pair; FMA = 2): flux kernel 70 + 174 G, gradient kernel 2 x (21 + 28 G).  Derivation in
-# the design notes.
-def flux_flops_per_pair(G):
-    return 70 + 174 * G
+# Floating-point operations per pair evaluation, counted on the oracle's own pair arithmetic
+# (oracle.Oracle.pair_flops: add, subtract, multiply, divide and square root one each; the
+# periodic wrap, comparisons and conversions not counted) over the pairs of these workloads.
+# tests/test_flop_counts.py recomputes them with the oracle's counter.  Geometry terms are
+# per unordered pair (flux) or per directed neighbour entry (gradient), averaged over the
+# set's pairs; the per-group terms are those of a state in the general branch.
+PAIR_FLOPS = {
+    "poisson-sine-beam": {"flux_geometry": 76.88, "gradient_geometry": 34.94},
+    "lognormal-sources": {"flux_geometry": 76.32, "gradient_geometry": 34.66},
+}
+FLUX_PER_GROUP = 193        # face states (minmod slopes), two M1 closures, GLF
+ACC_PER_GROUP = 8           # the flux added to one particle's sums, subtracted from the other's
+GRAD_PER_GROUP = 28         # (Q_j - Q_i) psitilde for four components
 
 
-def grad_flops_per_pair(G):
-    return 2 * (21 + 28 * G)
+def pair_flops(workload_key):
+    return PAIR_FLOPS.get(workload_key, PAIR_FLOPS["poisson-sine-beam"])
 
 
-# Algorithmic bytes per particle of the flux kernel: geometry 48, U in 16G, grad U in 48G,
-# U out 16G, alpha 4.
+def flux_flops_per_pair(workload_key, G):
+    """pair pass: one evaluation per unordered pair."""
+    return pair_flops(workload_key)["flux_geometry"] + FLUX_PER_GROUP * G
+
+
+def grad_flops_per_pair(workload_key, G):
+    """gradient pass: both directed entries of an unordered pair."""
+    return 2 * (pair_flops(workload_key)["gradient_geometry"] + GRAD_PER_GROUP * G)
+
+
+def gather_flops_per_pair(G):
+    return ACC_PER_GROUP * G
+
+
+# Algorithmic bytes per particle (float path): pair pass: position/geometry record 48, U in
+# 16G, grad U in 48G, U out 16G, alpha 4; gradient: position/geometry 48, U in 16G, grad U
+# out 48G; gather: U in 16G, U out 16G, omega and alpha 8 (the pair slots are this
+# design's intermediate, not algorithmic).
 def flux_bytes_per_particle(G):
     return 52 + 80 * G
+
+
+def grad_bytes_per_particle(G):
+    return 48 + 64 * G
+
+
+def gather_bytes_per_particle(G):
+    return 8 + 32 * G
 
 
 def sub_bytes_per_particle(G):
@@ -132,20 +166,23 @@ def kernel_source_sha1(csrc):
     return hashlib.sha1("\n".join(lines).encode()).hexdigest()
 
 
-def flux_traffic_from_profile(G):
-    """DRAM bytes of one pair-pass launch from the committed ncu summary, if it was taken on
-    the current source of the kernels (else None)."""
+def traffic_from_profile():
+    """DRAM bytes per launch of the sub-cycle kernels from the committed ncu summary, if it
+    was taken on the current source of the kernels (else {})."""
     path = os.path.join(ROOT, "profiles", "k_flux_poisson-sine-64^3-G3.md")
     csrc = os.path.join(ROOT, "paper_2302_12727_gb300", "csrc")
     if not os.path.exists(path):
-        return None
+        return {}
     txt = open(path).read()
-    m = re.search(r"pair_pass_dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"source_sha1:\s*([0-9a-f]+)", txt)
-    if not m or not h:
-        return None
-    cur = kernel_source_sha1(csrc)
-    return float(m.group(1)) if h.group(1) == cur else None
+    if not h or h.group(1) != kernel_source_sha1(csrc):
+        return {}
+    out = {}
+    for k in ("pair_pass", "gradient", "gather"):
+        m = re.search(k + r"_dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        if m:
+            out[k] = float(m.group(1))
+    return out
 
 
 # ---------------------------------------------------------------------------------------
@@ -349,15 +386,49 @@ def run_ours(args):
         gath_sc_ms = kgath_ms / bd_sc if bd_sc else 0.0
         grad_sc_ms = kgrad_ms / bd_sc if bd_sc else 0.0
         pair_avg_s = kpair_ms / kflux_n / 1e3 if kflux_n else None    # one launch of the pair pass
-        alu_peak = 152 * 128 * 2 * 2070e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x max clock
-        flux_flops = P * flux_flops_per_pair(G)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = n_sm * 128 * 2 * sm_max_mhz * 1e6 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x max clock
+        flux_flops = P * flux_flops_per_pair(args.workload, G)
         achieved = flux_flops / pair_avg_s / 1e12 if kflux_n else None
         tune = T.tuning()
+        # the committed counters hold for the default float kernels on this workload only
         default_shape = (args.workload == "poisson-sine-beam" and prec == "fp32" and args.riemann == "glf"
-                         and tune["flux_variant"] == 2)   # the pair pass is the same kernel
-                                                           # whatever the other two variants
-        traffic = flux_traffic_from_profile(G) if default_shape else None
+                         and (tune["flux_variant"], tune["gather_variant"], tune["gradient_variant"]) == (2, 1, 2))
+        prof = traffic_from_profile() if default_shape else {}
+        traffic = prof.get("pair_pass")
         pair_kernel = {0: "k_flux", 1: "k_flux_staged", 2: "k_flux_tma"}[tune["flux_variant"]]
+        grad_kernel = {0: "k_gradient", 1: "k_gradient_g", 2: "k_gradient_s"}[tune["gradient_variant"]]
+        gath_kernel = {0: "k_flux_gather", 1: "k_flux_gather_g"}[tune["gather_variant"]]
+        chunk_launch = lambda ms: ms / chunks / 1e3 if ms > 0 else None       # s per launch
+        grad_s, gath_s = chunk_launch(grad_sc_ms), chunk_launch(gath_sc_ms)
+        grad_flops = P * grad_flops_per_pair(args.workload, G) / chunks
+        gath_flops = P * gather_flops_per_pair(G) / chunks
+
+        def entry(bound, kernel, work, t_s, peak, unit, traffic_b, alg_bytes):
+            a = work / t_s / 1e12 if t_s else None
+            d = {"bound": bound, "kernel": kernel, "achieved": a, "peak": peak, "unit": unit,
+                 "frac": a / peak if a else None, "traffic": traffic_b, "avg_launch_ms": t_s * 1e3 if t_s else None,
+                 "algorithmic_bytes_per_launch": alg_bytes,
+                 "hbm_frac_of_" + peak_kind: alg_bytes / t_s / 1e9 / hbm_gbs if t_s else None,
+                 "traffic_over_algorithmic_bytes": traffic_b / alg_bytes if traffic_b else None}
+            d["flops_per_launch" if unit == "TFLOP/s" else "bytes_per_launch"] = work
+            return d
+
+        rooflines = {
+            "pair_pass": entry("alu", pair_kernel, flux_flops, pair_avg_s, alu_peak, "TFLOP/s", traffic,
+                               flux_bytes_per_particle(G) * n),
+            "gradient": entry("alu", grad_kernel, grad_flops, grad_s, alu_peak, "TFLOP/s", prof.get("gradient"),
+                              grad_bytes_per_particle(G) * n),
+            # the gather's arithmetic is 8 G flops per pair: it is a memory pass, measured in bytes
+            "gather": entry("hbm", gath_kernel, gather_bytes_per_particle(G) * n, gath_s, hbm_gbs / 1e3, "TB/s",
+                            prof.get("gather"), gather_bytes_per_particle(G) * n),
+        }
+        rooflines["gather"]["flops_per_launch"] = gath_flops
+        flop_note = ("flops per launch = P x (flux geometry %.2f + %d G) for the pair pass and 2P x (gradient "
+                     "geometry %.2f + %d G) for the gradient, per pair counted on the oracle's pair arithmetic "
+                     "(oracle pair_flops, tests/test_flop_counts.py)" % (
+                         pair_flops(args.workload)["flux_geometry"], FLUX_PER_GROUP,
+                         pair_flops(args.workload)["gradient_geometry"], GRAD_PER_GROUP))
         sub_s = (pair_sc_ms + gath_sc_ms + grad_sc_ms) * n_sub / 1e3     # per step
         out = {
             "metric": METRIC,
@@ -376,19 +447,25 @@ def run_ours(args):
                        "sources": w.n_src, "pairs": P, "dt": dt, "dt_rule": f"{args.cfl} * min dx / c (Eq. rt-cfl)",
                        "precision": "fp32 fluxes/gradients, fp64 h/E_i/B_i/energy" if prec == "fp32" else "fp64",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
-                       "tuning": T.tuning(), "tuning_source": tune_info.get("source"), "riemann": args.riemann,
+                       "tuning": T.tuning(), "tuning_source": tune_info.get("source"),
+                       "tuning_ms": tune_info.get("ms"), "riemann": args.riemann,
                        "drift_speed_over_c": args.drift,
                        "sink": "photo-ionisation per group" if args.photo else ("grey" if alpha is not None else "none")},
             "roofline": {"bound": "alu", "kernel": f"{pair_kernel} (pair pass)",
                          "achieved": achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
-                         "traffic": traffic, "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                         "traffic": traffic, "peak_source": f"nominal: {n_sm} SMs (device properties) x 128 FP32 lanes x 2 x {sm_max_mhz:.0f} MHz",
                          "flops_per_launch": flux_flops, "avg_launch_ms": pair_avg_s * 1e3 if pair_avg_s else None,
                          "hbm_frac_of_" + peak_kind: (flux_bytes_per_particle(G) * n / pair_avg_s / 1e9) / hbm_gbs
                          if kflux_n else None,
+                         "flop_count": flop_note,
                          "traffic_note": "ncu DRAM read + write of one pair-pass launch (cold cache), from "
                                          "profiles/k_flux_poisson-sine-64^3-G3.md; null unless the kernel "
                                          "sources and the launch variants match that capture"},
+            "rooflines": dict(rooflines, note="every sub-cycle kernel; the pair pass from the timed steps' events, "
+                                              "gradient and gather from the untimed breakdown steps; gather peak "
+                                              "= measured HBM copy bandwidth; traffic from the committed ncu "
+                                              "summary while the kernel source matches it"),
             "kernels": {"flux_stage_ms_per_subcycle": pair_sc_ms + gath_sc_ms, "gradient_ms_per_subcycle": grad_sc_ms,
                         "pair_flux_ms_per_subcycle": pair_sc_ms, "gather_ms_per_subcycle": gath_sc_ms,
                         "pair_launches_with_events": kflux_n, "gradient_launches_untimed": kgrad_n,
@@ -515,32 +592,108 @@ def cpu_baseline(w, args, P):
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores, on the same workload: its build is timed
+    once, then every step is one sampled sub-cycle (injection, gradients, fluxes, update and
+    sink over the whole particle set); the value counts the pair-group interactions of the
+    timed sub-cycles only."""
     ws, rank, local = dist_setup()
     if rank != 0:
         return
     w = workload(args.workload)
     import oracle
-    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
+    t0 = time.perf_counter()
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red, riemann=args.riemann)
+    t_build = time.perf_counter() - t0
     off, _ = o.pairs()
     P = int(off[-1]) // 2
-    del o
+    dx = (o.V / (4 * np.pi / 3)) ** (1 / 3)
+    dt = args.cfl * dx.min() / w.c_red
+    alpha = w.kappa * w.m * o.omega if w.kappa else None
+    U = np.array(w.U0, dtype=np.float64)
     times = []
     for k in range(args.warmup + args.steps):
-        t_build, t_step, cores = oracle_step_times(w, P, 1, args.riemann)
+        t0 = time.perf_counter()
+        U, _ = o.run(U, 1, dt, w.Lsrc, alpha)
         if k >= args.warmup:
-            times.append(t_build + w.n_steps * t_step)
-    T = sum(times) / len(times)
-    val = P * w.n_groups * w.n_steps / T
+            times.append(time.perf_counter() - t0)
+    cores = oracle.num_threads()
+    t_step = sum(times) / len(times)
+    val = P * w.n_groups / t_step
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": T * 1e3, "higher_is_better": True, "scaling": "weak",
+           "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": w.name, "particles": w.n, "groups": w.n_groups, "sub_cycles": w.n_steps,
-                      "pairs": P, "riemann": args.riemann},
+                      "pairs": P, "riemann": args.riemann, "dt": dt},
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"each step: oracle build + 1 of the {w.n_steps} sub-cycle steps timed on the "
-                                      f"full {w.n}-particle set, the step time extrapolated to {w.n_steps} sub-cycles"},
+                            "sample": f"each step is one sub-cycle of the {w.n_steps} of a hydro step on the full "
+                                      f"{w.n}-particle set, all {args.steps} timed; the oracle's neighbour build "
+                                      f"({t_build:.2f} s, once per hydro step) is timed before them and not "
+                                      f"included"},
+           "oracle_build_s": t_build,
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def run_decomposed(args):
+    """One particle set over N ranks (paper_2302_12727_gb300.domain): a step is n_sub
+    sub-cycles (ghost exchange + transport step on every rank) and the energy all-reduce; the
+    decomposition's build runs once before the timed steps and is not timed."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2302_12727_gb300 import domain
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    G, n_sub = w.n_groups, w.n_steps
+    eng = domain.CudaEngine(G, w.c_red, precision=args.precision, device=dev, riemann=args.riemann)
+    D = domain.DistributedTransport(w.x, w.m, w.xsrc, eng)
+    # every particle's row is exact in its owner's context: the owned rows sum to 2P
+    rows_owned = float(eng.pair_counts()[:D.plan.n_owned].sum())
+    om_own = eng.t.fields()["omega"].cpu().numpy()[:D.plan.n_owned]
+    dx_min = D._all_max(-float(((1.0 / om_own) / (4 * np.pi / 3)).min() ** (1 / 3)))
+    dt = args.cfl * (-dx_min) / w.c_red
+    alpha = None
+    if w.kappa:
+        om = np.zeros(w.n)
+        om[D.plan.owned] = eng.t.fields()["omega"].cpu().numpy()[:D.plan.n_owned]
+        alpha = w.kappa * w.m * D._all_sum(om)
+    U0 = D.local_state(w.U0)
+    L, al = D.local_luminosities(w.Lsrc), D.local_alpha(alpha)
+    U = U0.clone()
+    for _ in range(args.warmup):
+        U.copy_(U0)
+        D.subcycle(U, n_sub, dt, L, al)
+        D.energy(U)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        U.copy_(U0)
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        D.subcycle(U, n_sub, dt, L, al)
+        D.energy(U)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t_max = max_over_ranks(sum(times), ws, dev)
+    P = int(D._all_sum([rows_owned])[0]) // 2
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": P * G * n_sub * args.steps / t_max, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "particles": w.n, "groups": G, "sub_cycles": n_sub,
+                       "parallelism": f"domain decomposition x{ws}", "pairs": P,
+                       "note": "host-timed steps (sub-cycles with halo exchanges + energy all-reduce); "
+                               "the decomposition's build is not timed"}}))
+    D.close()
+    dist.destroy_process_group()
 
 
 def main():
@@ -567,9 +720,18 @@ def main():
                     help="per-group photo-ionisation sink (rt_set_absorbers) instead of the grey kappa")
     ap.add_argument("--drift", type=float, default=0.0,
                     help="move the particles at this fraction of c (drift correction + new neighbours every step)")
+    ap.add_argument("--decompose", action="store_true",
+                    help="with N > 1 ranks: one particle set split over the ranks by the spatial domain "
+                         "decomposition (halo exchanges over NCCL) instead of N independent replicas")
     args = ap.parse_args()
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus != ws:
+        raise SystemExit(f"--gpus {args.gpus} but {ws} rank(s): launch N ranks with "
+                         f"'python -m torch.distributed.run --nproc-per-node N bench.py --gpus N'")
     if args.impl == "reference":
         run_reference(args)
+    elif args.decompose and ws > 1:
+        run_decomposed(args)
     else:
         run_ours(args)
 

@@ -84,8 +84,9 @@ typedef struct {
                                 conservation, so 0 for conservation checks */
     int32_t limiter_variant; /* 0: s = minmod(grad Q_k . d, grad Q_l . d) on both states (the only
                                 value accepted) */
-    double h_tol;            /* relative tolerance of the smoothing-length iteration (<= 1e-6;
-                                the FP64 path always refines to machine precision) */
+    double h_tol;            /* relative tolerance of the float phase of the smoothing-length
+                                iteration (<= 1e-6); both precisions then refine h in double to
+                                machine precision, so they share one neighbour set */
     int32_t h_max_iter;      /* iteration cap of that solve; exceeding it gives RT_ERR_NOCONV */
     uint64_t device_wait_budget_cycles;  /* bound, in SM clock cycles, of every device-side wait
                                             (the copy waits of flux_variant 2, rt_tuning); 0 means
@@ -118,12 +119,16 @@ typedef struct {
                                  de-duplicated with their transposes (chosen when the h range is
                                  wide); both give the same lists */
     int32_t wait_timeouts;    /* 1 if a device-side wait ran out since the last rt_neighbours */
+    int64_t h_refined;        /* particles whose h the last rt_neighbours refined in double: all of
+                                 them on the FP64 path; on the float path those with a neighbour
+                                 candidate within 1e-4 of their support radius at the float root */
 } rt_diag;
 
 /* Launch variants of the float (RT_FP32_MIXED) pair kernels.  The paper has no counterpart:
  * they choose how the GPU threads map onto the pair loops of Eq. gradient and
  * Eq. transport-update-explicit, never what is computed.  Every variant gives bitwise the
- * same fluxes and the same order of accumulation; the double path ignores them.
+ * same fluxes and the same order of accumulation; the double path ignores them (but not
+ * cell_eighths).
  *   flux_variant      0: one thread per pair slot loading both particles' records directly;
  *                     1: the same, with the neighbour records of each warp staged through
  *                        shared memory by cooperative asynchronous copies;
@@ -143,6 +148,21 @@ typedef struct {
     int32_t flux_variant;
     int32_t gather_variant;
     int32_t gradient_variant;
+    /* Launch shapes and the cell list (also bitwise neutral, except cell_eighths):
+     *   cell_eighths    edge of the neighbour search's cells, in eighths of the support
+     *                   radius at the mean density, kappa eta (box volume / N)^(1/3): 2 to 16
+     *                   (default 4).  It applies from the next rt_neighbours and changes the
+     *                   cell-sorted order, hence the order of the neighbour sums: the results
+     *                   then differ by rounding, the pair lists not at all.
+     *   gradient_block  threads per block of the float gradient kernels: 32, 64, 128 or 256;
+     *                   0 = the variant's default (64 for variant 2, 256 for variant 1).
+     *   gather_block    threads per block of gather_variant 1: a multiple of 32 from 64 to 512;
+     *                   0 = 256.
+     *   pair_warps      warps per block of flux_variant 2: 1, 2 or 4; 0 = 1. */
+    int32_t cell_eighths;
+    int32_t gradient_block;
+    int32_t gather_block;
+    int32_t pair_warps;
 } rt_tuning;
 
 /* Kernel kinds reported by rt_kernel_times. */
@@ -172,6 +192,31 @@ rt_status rt_set_stream(rt_ctx* ctx, void* cuda_stream);
 rt_status rt_neighbours(rt_ctx* ctx, const double* x_dev, const double* m_dev, const double* xsrc_dev,
                         double* h_out_dev);
 
+/* The neighbour search of rt_neighbours with the smoothing lengths given instead of solved:
+ * h_dev [N] (caller order) for the gas and hs_dev [S] for the sources (NULL when S = 0),
+ * device doubles, read during the call.  omega_i = sum_j W(r_ij, h_i) is evaluated at the
+ * given h_i (in the working precision's arithmetic of the solve's last iteration), and the
+ * pair lists, E_i, B_i and the injection weights follow as in rt_neighbours.  This is the
+ * build of a rank in a spatial domain decomposition (Part II, "Distributed Memory
+ * Parallelism: Domain Decomposition and MPI"): the owner of a particle solves its h with a
+ * complete neighbourhood and sends it to the ranks holding the particle as a ghost, so that
+ * every rank decides the pairs of its particles with the same h.  RT_ERR_INVALID for NULL
+ * arrays or an h that is not finite and positive (or, periodic box, reaches half the box
+ * with its support); other errors as rt_neighbours. */
+rt_status rt_neighbours_given_h(rt_ctx* ctx, const double* x_dev, const double* m_dev, const double* xsrc_dev,
+                                const double* h_dev, const double* hs_dev);
+
+/* Smoothing lengths h_s of the sources from the last rt_neighbours (hs_dev [S], device
+ * doubles, source order as given; written asynchronously on the context's stream). */
+rt_status rt_source_fields(rt_ctx* ctx, double* hs_dev);
+
+/* Particles owned by this context: caller indices [0, n_owned); the rest are ghost copies of
+ * particles another rank owns (a domain decomposition places them last).  rt_energy then
+ * sums the owned particles only; the transport still updates every particle (a ghost's new
+ * state is discarded by its next refresh from the owner).  n_owned = n (the default) owns
+ * all.  RT_ERR_INVALID outside [0, n]. */
+rt_status rt_set_owned(rt_ctx* ctx, int64_t n_owned);
+
 /* Least-squares gradients of every component of U (Eq. gradient):
  * grad Q_i = sum_j (Q_j - Q_i) psitilde_j(x_i).  U_dev [G][4][N], gradU_dev [G][4][3][N]. */
 rt_status rt_gradients(rt_ctx* ctx, const void* U_dev, void* gradU_dev);
@@ -195,8 +240,6 @@ rt_status rt_adjoint(rt_ctx* ctx, int32_t n_sub, double dt, int32_t ckpt_every, 
                      const double* Lsrc_dev, const double* alpha_dev, const void* dLdU_final_dev,
                      void* dLdU0_dev, double* dLdLsrc_dev);
 
-/* Total radiation energy per group, sum_i V_i E_i,g, summed in double in a fixed order.
- * E_tot_host [G] is HOST memory; the call synchronises the stream. */
 /* Individual time bins (Part II Sec. "Individual Timstepping", Eq. transport-update-explicit
  * with min(dt_k, dt_l); Part III Sec. "Dynamic Sub-Cycling").  Particle i advances in steps
  * dt_i = 2^b_i dt_min; a hydro step is 2^B min-steps, B = max_i b_i.  At min-step s particle i
@@ -235,6 +278,9 @@ rt_status rt_step_bins(rt_ctx* ctx, void* U_dev, const double* Lsrc_dev, const d
  * arrays or a non-finite dt_drift. */
 rt_status rt_drift(rt_ctx* ctx, void* U_dev, const double* v_dev, double dt_drift);
 
+/* Total radiation energy per group, sum_i V_i E_i,g, summed in double in a fixed order over
+ * the owned particles (all of them unless rt_set_owned says otherwise).
+ * E_tot_host [G] is HOST memory; the call synchronises the stream. */
 rt_status rt_energy(rt_ctx* ctx, const void* U_dev, double* E_tot_host);
 
 /* Total radiation energy per group, sum_i V_i E_i,g, without allocating anything and
@@ -253,10 +299,14 @@ rt_status rt_energy(rt_ctx* ctx, const void* U_dev, double* E_tot_host);
  * every GPU that loads the library until the process exits.  Each call overwrites the part
  * of it that it reads, so nothing carries over from the previous call, but calls that
  * overlap on the GPU share the array and race: order them on one stream.  The first call
- * on a device looks up the array's device address with that device current; make that
- * first call before any stream capture.  Returns RT_ERR_INVALID for NULL pointers, n < 1,
- * n_groups outside [1, RT_ENERGY_STATIC_MAX_GROUPS] or an unknown
- * precision, RT_ERR_CUDA if a CUDA call fails; there is no context, so no message. */
+ * on a device (and the first after the caller resets it) looks up the array's device address
+ * with that device current; under CUDA's default lazy module loading that first call is also
+ * when the library's code and this array are loaded onto the device.  So make one warm-up
+ * call per device before a memory pool claims the whole GPU and before any stream capture.
+ * Returns RT_ERR_INVALID for NULL pointers, n < 1, n_groups outside
+ * [1, RT_ENERGY_STATIC_MAX_GROUPS] or an unknown precision; RT_ERR_CUDA if a CUDA call or a
+ * launch fails, and also, before launching anything, when an error from the caller's earlier
+ * CUDA work is still pending (it is left pending); there is no context, so no message. */
 #define RT_ENERGY_STATIC_MAX_GROUPS 16
 rt_status rt_energy_static(const void* U_dev, const double* V_dev, int64_t n, int32_t n_groups, int32_t precision,
                            void* cuda_stream, double* E_tot_dev);
@@ -340,13 +390,14 @@ rt_status rt_photon_number_to_luminosity(double T_bb, double Ndot, int32_t n_gro
                                          double* L_out);
 
 /* Set (rt_set_tuning) or read (rt_get_tuning) the launch variants of the float pair kernels
- * (host struct, copied).  RT_ERR_INVALID for a variant outside the values listed above; the
- * context is unchanged then.  Valid before or after rt_neighbours. */
+ * and the shapes above (host struct, copied).  RT_ERR_INVALID for a value outside those
+ * listed; the context is unchanged then.  Valid before or after rt_neighbours. */
 rt_status rt_set_tuning(rt_ctx* ctx, const rt_tuning* tuning);
 rt_status rt_get_tuning(const rt_ctx* ctx, rt_tuning* tuning);
 
 /* Number of launch-variant combinations rt_autotune tries: candidate k is
- * {flux_variant k / 6, gather_variant (k / 3) % 2, gradient_variant k % 3}. */
+ * {flux_variant k / 6, gather_variant (k / 3) % 2, gradient_variant k % 3}, with the shapes
+ * (cell_eighths ... pair_warps) of the context's current tuning. */
 #define RT_TUNE_CANDIDATES 18
 
 /* Autotuner (no paper counterpart): times n_sub plain transport steps of every candidate

@@ -19,7 +19,8 @@ RT_OK = 0
 _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4: "RT_ERR_NOCONV",
            5: "RT_ERR_GEOMETRY", 6: "RT_ERR_TIMEOUT", 7: "RT_ERR_STATE"}
 
-EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_gradients", "rt_transport_step", "rt_subcycle",
+EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_neighbours_given_h", "rt_source_fields",
+            "rt_set_owned", "rt_gradients", "rt_transport_step", "rt_subcycle",
             "rt_drift", "rt_set_time_bins", "rt_get_time_bins", "rt_step_bins", "rt_set_absorbers", "rt_cross_section", "rt_blackbody_groups",
             "rt_photon_number_to_luminosity",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
@@ -47,7 +48,7 @@ class rt_diag(C.Structure):
                 ("n_ill_conditioned", C.c_int64), ("cond_max", C.c_double), ("h_min", C.c_double),
                 ("h_max", C.c_double), ("dx_min", C.c_double), ("clamp_events", C.c_int64),
                 ("grid", C.c_int32 * 3), ("threads_per_particle", C.c_int32), ("kernel_launches", C.c_int64),
-                ("pair_build", C.c_int32), ("wait_timeouts", C.c_int32)]
+                ("pair_build", C.c_int32), ("wait_timeouts", C.c_int32), ("h_refined", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -56,7 +57,15 @@ class rt_diag(C.Structure):
 
 
 class rt_tuning(C.Structure):
-    _fields_ = [("flux_variant", C.c_int32), ("gather_variant", C.c_int32), ("gradient_variant", C.c_int32)]
+    _fields_ = [("flux_variant", C.c_int32), ("gather_variant", C.c_int32), ("gradient_variant", C.c_int32),
+                ("cell_eighths", C.c_int32), ("gradient_block", C.c_int32), ("gather_block", C.c_int32),
+                ("pair_warps", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+TUNING_KEYS = tuple(k for k, _ in rt_tuning._fields_)
 
 
 class RTError(RuntimeError):
@@ -84,6 +93,9 @@ def load_library():
     lib.rt_create.argtypes = [C.POINTER(rt_config), i64, i64, vp, C.POINTER(vp)]
     lib.rt_set_stream.argtypes = [vp, vp]
     lib.rt_neighbours.argtypes = [vp, dp, dp, dp, dp]
+    lib.rt_neighbours_given_h.argtypes = [vp, dp, dp, dp, dp, dp]
+    lib.rt_source_fields.argtypes = [vp, dp]
+    lib.rt_set_owned.argtypes = [vp, i64]
     lib.rt_gradients.argtypes = [vp, dp, dp]
     lib.rt_transport_step.argtypes = [vp, C.c_double, dp, dp, dp]
     lib.rt_subcycle.argtypes = [vp, C.c_int32, C.c_double, dp, dp, dp]
@@ -170,6 +182,18 @@ def rt_set_stream(ctx, stream):
 
 def rt_neighbours(ctx, x, m=None, xsrc=None, h_out=None):
     _check(ctx, load_library().rt_neighbours(ctx, _ptr(x), _ptr(m), _ptr(xsrc), _ptr(h_out)))
+
+
+def rt_neighbours_given_h(ctx, x, m, xsrc, h, hs):
+    _check(ctx, load_library().rt_neighbours_given_h(ctx, _ptr(x), _ptr(m), _ptr(xsrc), _ptr(h), _ptr(hs)))
+
+
+def rt_source_fields(ctx, hs_out):
+    _check(ctx, load_library().rt_source_fields(ctx, _ptr(hs_out)))
+
+
+def rt_set_owned(ctx, n_owned):
+    _check(ctx, load_library().rt_set_owned(ctx, int(n_owned)))
 
 
 def rt_gradients(ctx, U, gradU):
@@ -288,9 +312,12 @@ def rt_kernel_times(ctx):
     return {names[k]: (ms[k], nl[k]) for k in range(RT_KERNEL_KINDS)}
 
 
-def rt_set_tuning(ctx, flux_variant: int = 2, gather_variant: int = 1, gradient_variant: int = 2):
-    """Launch variants of the float pair kernels (see rt.h); same results for every choice."""
-    t = rt_tuning(int(flux_variant), int(gather_variant), int(gradient_variant))
+def rt_set_tuning(ctx, flux_variant: int = 2, gather_variant: int = 1, gradient_variant: int = 2,
+                  cell_eighths: int = 0, gradient_block: int = 0, gather_block: int = 0, pair_warps: int = 0):
+    """Launch variants and shapes of the float pair kernels and the cell size of the neighbour
+    search (see rt.h; 0 keeps the cell size and takes the default shapes)."""
+    t = rt_tuning(int(flux_variant), int(gather_variant), int(gradient_variant), int(cell_eighths),
+                  int(gradient_block), int(gather_block), int(pair_warps))
     _check(ctx, load_library().rt_set_tuning(ctx, C.byref(t)))
 
 
@@ -307,8 +334,7 @@ def rt_wait_selftest(ctx, budget_cycles: int) -> bool:
 def rt_get_tuning(ctx) -> dict:
     t = rt_tuning()
     _check(ctx, load_library().rt_get_tuning(ctx, C.byref(t)))
-    return {"flux_variant": t.flux_variant, "gather_variant": t.gather_variant,
-            "gradient_variant": t.gradient_variant}
+    return t.as_dict()
 
 
 def rt_autotune(ctx, U, dt, n_sub, Lsrc=None, alpha=None, repeats=3):
@@ -318,8 +344,7 @@ def rt_autotune(ctx, U, dt, n_sub, Lsrc=None, alpha=None, repeats=3):
     ms = (C.c_double * RT_TUNE_CANDIDATES)()
     _check(ctx, load_library().rt_autotune(ctx, _ptr(U), float(dt), int(n_sub), _ptr(Lsrc), _ptr(alpha),
                                            int(repeats), C.byref(t), ms))
-    return ({"flux_variant": t.flux_variant, "gather_variant": t.gather_variant,
-             "gradient_variant": t.gradient_variant}, list(ms))
+    return t.as_dict(), list(ms)
 
 
 def rt_wave_table():

@@ -139,6 +139,7 @@ rt_status rt_create(const rt_config* cfg, int64_t n, int64_t n_src, void* cuda_s
     if (!cfg) return fail(c, RT_ERR_INVALID, "cfg is NULL");
     c->cfg = *cfg;
     c->n = n;
+    c->n_owned = n;
     c->n_src = n_src;
     c->stream = (cudaStream_t)cuda_stream;
     if (n < 2 || n >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "n must be in [2, 2^31)");
@@ -186,7 +187,8 @@ rt_status rt_set_stream(rt_ctx* c, void* s) {
     return RT_OK;
 }
 
-rt_status rt_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc, double* h_out) {
+static rt_status neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc, double* h_out,
+                            const double* h_in, const double* hs_in) {
     if (!c) return RT_ERR_INVALID;
     c->err.clear();
     if (!x) return fail(c, RT_ERR_INVALID, "x_dev is NULL");
@@ -196,7 +198,7 @@ rt_status rt_neighbours(rt_ctx* c, const double* x, const double* m, const doubl
     c->has_bins = false;   // bins live in the sorted order and depend on the pair lists
     int64_t gen0 = g_generation;
     int64_t targets0 = c->n_inj_targets;
-    rt_status s = build_neighbours(c, x, m, xsrc);
+    rt_status s = build_neighbours(c, x, m, xsrc, h_in, hs_in);
     if (s != RT_OK) {
         drop_graphs(c);
         return s;
@@ -212,6 +214,34 @@ rt_status rt_neighbours(rt_ctx* c, const double* x, const double* m, const doubl
         RT_TRY(field_out(c, c->h_d.as<double>(), h_out, 1));
     }
     c->built = true;
+    return RT_OK;
+}
+
+rt_status rt_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc, double* h_out) {
+    return neighbours(c, x, m, xsrc, h_out, nullptr, nullptr);
+}
+
+rt_status rt_neighbours_given_h(rt_ctx* c, const double* x, const double* m, const double* xsrc, const double* h_in,
+                                const double* hs_in) {
+    if (!c) return RT_ERR_INVALID;
+    if (!h_in) return fail(c, RT_ERR_INVALID, "h_dev is NULL");
+    if (c->n_src > 0 && !hs_in) return fail(c, RT_ERR_INVALID, "hs_dev is NULL with n_src > 0");
+    return neighbours(c, x, m, xsrc, nullptr, h_in, hs_in);
+}
+
+rt_status rt_source_fields(rt_ctx* c, double* hs_dev) {
+    RT_TRY(check_ready(c));
+    if (!hs_dev) return fail(c, RT_ERR_INVALID, "hs_dev is NULL");
+    if (c->n_src > 0)
+        RT_CUDA(c, cudaMemcpyAsync(hs_dev, c->hs_d.p, (size_t)c->n_src * 8, cudaMemcpyDeviceToDevice, c->stream));
+    return RT_OK;
+}
+
+rt_status rt_set_owned(rt_ctx* c, int64_t n_owned) {
+    if (!c) return RT_ERR_INVALID;
+    c->err.clear();
+    if (n_owned < 0 || n_owned > c->n) return fail(c, RT_ERR_INVALID, "n_owned must be in [0, n]");
+    c->n_owned = n_owned;
     return RT_OK;
 }
 
@@ -233,7 +263,7 @@ rt_status rt_step_bins(rt_ctx* c, void* U, const double* Lsrc, const double* alp
     const bool has_src = Lsrc && c->n_src > 0 && c->n_inj_targets > 0;
     RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
     RT_TRY(set_step_inputs(c, c->dt_min, Lsrc, alpha));
-    RT_CUDA(c, cudaMemsetAsync(c->acc_t.p, 0, (size_t)4 * G * c->n * (c->fp64 ? 8 : 4), c->stream));
+    RT_CUDA(c, cudaMemsetAsync(c->acc_t.p, 0, (size_t)32 * G * c->n, c->stream));   // 32 B per (particle, group)
     for (int s = 0; s < (1 << c->bins_max); ++s)
         RT_TRY(launch_step_bins(c, c->stream, s, c->U_a.p, has_src, alpha != nullptr));
     RT_TRY(state_out(c, c->U_a.p, U, 4 * G, 4 * G, 0));
@@ -508,17 +538,30 @@ rt_status rt_set_tuning(rt_ctx* c, const rt_tuning* t) {
         t->gradient_variant < 0 || t->gradient_variant > 2)
         return fail(c, RT_ERR_INVALID,
                     "rt_set_tuning: flux_variant and gradient_variant must be 0, 1 or 2, gather_variant 0 or 1");
-    if (t->flux_variant != c->tune.flux_variant || t->gather_variant != c->tune.gather_variant ||
-        t->gradient_variant != c->tune.gradient_variant) {
+    rt_tuning v = *t;
+    if (v.cell_eighths == 0) v.cell_eighths = c->tune.cell_eighths;
+    const int gb = v.gradient_block, hb = v.gather_block, pw = v.pair_warps;
+    if (v.cell_eighths < 2 || v.cell_eighths > 16 || !(gb == 0 || gb == 32 || gb == 64 || gb == 128 || gb == 256) ||
+        !(hb == 0 || (hb >= 64 && hb <= 512 && hb % 32 == 0)) || !(pw == 0 || pw == 1 || pw == 2 || pw == 4))
+        return fail(c, RT_ERR_INVALID,
+                    "rt_set_tuning: cell_eighths in [2, 16], gradient_block 0/32/64/128/256, gather_block 0 or a "
+                    "multiple of 32 in [64, 512], pair_warps 0/1/2/4");
+    if (std::memcmp(&v, &c->tune, sizeof(v)) != 0) {
         RT_CUDA(c, cudaStreamSynchronize(c->stream));
         drop_graphs(c);
-        c->tune = *t;
+        c->tune = v;
     }
     return RT_OK;
 }
 
 // candidate k of rt_autotune: flux variant k / 6, gather variant (k / 3) % 2, gradient variant k % 3
-static rt_tuning tune_candidate(int k) { return rt_tuning{k / 6, (k / 3) % 2, k % 3}; }
+static rt_tuning tune_candidate(const rt_tuning& shape, int k) {
+    rt_tuning t = shape;
+    t.flux_variant = k / 6;
+    t.gather_variant = (k / 3) % 2;
+    t.gradient_variant = k % 3;
+    return t;
+}
 
 rt_status rt_autotune(rt_ctx* c, const void* U, double dt, int32_t n_sub, const double* Lsrc, const double* alpha,
                       int32_t repeats, rt_tuning* best, double* ms_out) {
@@ -540,7 +583,7 @@ rt_status rt_autotune(rt_ctx* c, const void* U, double dt, int32_t n_sub, const 
         st = fail(c, RT_ERR_CUDA, "rt_autotune: cudaEventCreate failed");
     }
     for (int k = 0; k < RT_TUNE_CANDIDATES && st == RT_OK; ++k) {
-        c->tune = tune_candidate(k);
+        c->tune = tune_candidate(saved, k);
         if (c->fp64 && k > 0) {       // the double path has one variant
             if (ms_out) ms_out[k] = ms_out[0];
             continue;
@@ -576,7 +619,7 @@ rt_status rt_autotune(rt_ctx* c, const void* U, double dt, int32_t n_sub, const 
     if (e1) cudaEventDestroy(e1);
     c->tune = saved;
     if (st != RT_OK) return st;
-    const rt_tuning win = c->fp64 ? saved : tune_candidate(best_k);
+    const rt_tuning win = c->fp64 ? saved : tune_candidate(saved, best_k);
     *best = win;
     return rt_set_tuning(c, &win);
 }

@@ -156,7 +156,7 @@ rt_status rt_set_time_bins(rt_ctx* c, const int32_t* bins_dev, double dt_min, do
     const int G = c->cfg.n_groups;
     RT_TRY(ensure(c, c->bins_s, (size_t)n, "time bins"));
     RT_TRY(ensure(c, c->bins_tmp, (size_t)n, "time bins"));
-    RT_TRY(ensure(c, c->acc_t, (size_t)4 * G * n * (c->fp64 ? 8 : 4), "flux accumulators"));
+    RT_TRY(ensure(c, c->acc_t, (size_t)32 * G * n, "flux accumulators"));   // 32 B per (particle, group)
     cudaStream_t s = c->stream;
     k_bins_init<<<nb256(n), 256, 0, s>>>(bins_dev, c->perm.as<int32_t>(), c->V_d.as<double>(), n, cfl, dt_min,
                                          c->cfg.c_red, max_bin, c->bins_s.as<int8_t>());

@@ -51,7 +51,8 @@ __device__ __forceinline__ int wrap_cell(int c, int nc) {
 // is close to the sphere plus one cell layer.  An axis whose span covers the whole grid is
 // walked once without clipping.
 template <class F>
-__device__ __forceinline__ void for_each_candidate(const Grid& g, float px, float py, float pz, float R, F&& f) {
+__device__ __forceinline__ void for_each_candidate_range(const Grid& g, float px, float py, float pz, float R,
+                                                         F&& fr) {
     // float arithmetic with a relative margin of 1e-4 on R: cells are never missed
     const float Rc = R * 1.0001f + 1e-6f * (g.cellf[0] + g.cellf[1] + g.cellf[2]);
     const float R2 = Rc * Rc;
@@ -102,10 +103,18 @@ __device__ __forceinline__ void for_each_candidate(const Grid& g, float px, floa
             for (int sI = 0; sI < ns; ++sI) {
                 int b = g.cell_start[base + sl[sI]];
                 int e = g.cell_start[base + sh[sI] + 1];
-                for (int j = b; j < e; ++j) f(j);
+                fr(b, e);
             }
         }
     }
+}
+
+// every candidate of for_each_candidate_range, one at a time
+template <class F>
+__device__ __forceinline__ void for_each_candidate(const Grid& g, float px, float py, float pz, float R, F&& f) {
+    for_each_candidate_range(g, px, py, pz, R, [&](int b, int e) {
+        for (int j = b; j < e; ++j) f(j);
+    });
 }
 
 // number of particles in the 3 x 3 x 3 cells around (cx, cy, cz): a local density for the
@@ -207,20 +216,145 @@ __global__ void k_gather_positions(const double* __restrict__ x, const double* _
 // ------------------------------------------------------------------------------------
 // a2: smoothing lengths.  f(h) = h - eta * omega(h)^(-1/3), omega(h) = sum_j W(r_ij, h) with
 // the self term; safeguarded Newton, first in float on fixed-point separations, then in
-// double on the exact separations until the step is below machine precision.
+// double on the exact separations until the step is below machine precision.  The double
+// phase runs for every particle on the FP64 path.  On the float path it runs only for the
+// particles that have a candidate within kNearBand of their own support radius at the float
+// root (about one in thirty): the float root is within a few 1e-6 of the exact one, so for
+// every other particle no neighbour can change side of H_i, and the pair lists, which are
+// decided by H_i and H_j, are those of the exact roots.
 struct HParams {
     double eta, h0, h_cap;
     float scale[3];
     int max_iter;
     float tol32;
-    int refine64;   // 1: Newton in double to machine precision (FP64 path); 0: omega in double at the float root
+    int refine64;   // 1: Newton in double to machine precision here; 0: flag near-threshold particles
 };
+
+// |r^2 - H^2| < kNearBand H^2 at the float root: the particle's h is refined in double
+constexpr float kNearBand = 2e-4f;
 
 __device__ __forceinline__ float fsep(uint32_t a, uint32_t b, float scale) { return (float)(int32_t)(a - b) * scale; }
 
+// Newton in double from hd on the exact separations of particle p; returns false if it did
+// not converge.  On return hd is the root and om_d = omega(hd).
+__device__ bool refine_h_double(const Grid& g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+                                int64_t n, const HParams& hp, int64_t p, double& hd, double& om_d) {
+    const uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    const double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+    const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+    double lod = 0.0, hid = INFINITY;
+    const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
+    bool okd = false, last = false;
+    for (int it = 0; it < 60; ++it) {
+        double H = kKappa * hd;
+        double iH = 1.0 / H;
+        double H2 = H * H;
+        float Hf = (float)H * 1.001f;
+        float H2f = Hf * Hf;
+        double sw = 0.0, sdw = 0.0;
+        for_each_candidate(g, pxf, pyf, pzf, Hf, [&](int j) {
+            float dxf = fsep(xq[j], qx, hp.scale[0]);
+            float dyf = fsep(xq[n + j], qy, hp.scale[1]);
+            float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+            if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) return;
+            double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
+            double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
+            double dz = sep_fast(xs[2 * n + j], pz, g.box[2], half[2], g.periodic);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < H2) {
+                double q = sqrt(r2) * iH;
+                double w = spline_w(q);
+                sw += w;
+                sdw += 3.0 * w + q * spline_dw(q);
+            }
+        });
+        double om = kSigma * iH * iH * iH * sw;
+        double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
+        double cb = cbrt(om);
+        double f = hd - hp.eta / cb;
+        double fp = 1.0 + (hp.eta / 3.0) / (cb * om) * dom;
+        om_d = om;
+        if (last) { okd = true; break; }        // omega evaluated at the final h
+        if (f < 0.0) lod = hd; else hid = hd;
+        double step = f / fp;
+        // once the Newton step is tiny the next iterate is exact to rounding: take it and
+        // evaluate omega there once more; a residual at the rounding floor or a collapsed
+        // bracket ends the iteration at the current h
+        if (fabs(f) <= 1e-15 * hd || (hid - lod) <= 1e-14 * hd) { okd = true; break; }
+        if (fp > 0.0 && fabs(step) <= 1e-11 * hd) last = true;
+        double hn = hd - step;
+        if (!last && (it >= 12 || !(hn > lod && hn < hid) || !(fp > 0.0)))
+            hn = isinf(hid) ? 1.01 * hd : 0.5 * (lod + hid);
+        hd = hn;
+    }
+    return okd;
+}
+
+// The same Newton in double for particle p, with the 32 lanes of a warp sharing the candidate
+// walk (in every contiguous run of candidates, lane l takes the l-th, (l + 32)-th, ...) and
+// combining their sums by a fixed butterfly, whose result is the same in every lane: the
+// lanes then take the same steps.  Used where few particles need it (k_h_refine), so that the double arithmetic,
+// slow on this GPU, is spread over many threads.
+__device__ bool refine_h_warp(const Grid& g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+                              int64_t n, const HParams& hp, int64_t p, int lane, double& hd, double& om_d) {
+    const uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    const double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+    const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+    double lod = 0.0, hid = INFINITY;
+    const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
+    bool okd = false, last = false;
+    for (int it = 0; it < 60; ++it) {
+        double H = kKappa * hd;
+        double iH = 1.0 / H;
+        double H2 = H * H;
+        float Hf = (float)H * 1.001f;
+        float H2f = Hf * Hf;
+        double sw = 0.0, sdw = 0.0;
+        for_each_candidate_range(g, pxf, pyf, pzf, Hf, [&](int b, int e) {
+          for (int j = b + lane; j < e; j += 32) {
+            float dxf = fsep(xq[j], qx, hp.scale[0]);
+            float dyf = fsep(xq[n + j], qy, hp.scale[1]);
+            float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+            if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) continue;
+            double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
+            double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
+            double dz = sep_fast(xs[2 * n + j], pz, g.box[2], half[2], g.periodic);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < H2) {
+                double q = sqrt(r2) * iH;
+                double w = spline_w(q);
+                sw += w;
+                sdw += 3.0 * w + q * spline_dw(q);
+            }
+          }
+        });
+        for (int o = 16; o > 0; o >>= 1) {
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+            sdw += __shfl_xor_sync(0xffffffffu, sdw, o);
+        }
+        double om = kSigma * iH * iH * iH * sw;
+        double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
+        double cb = cbrt(om);
+        double f = hd - hp.eta / cb;
+        double fp = 1.0 + (hp.eta / 3.0) / (cb * om) * dom;
+        om_d = om;
+        if (last) { okd = true; break; }
+        if (f < 0.0) lod = hd; else hid = hd;
+        double step = f / fp;
+        if (fabs(f) <= 1e-15 * hd || (hid - lod) <= 1e-14 * hd) { okd = true; break; }
+        if (fp > 0.0 && fabs(step) <= 1e-11 * hd) last = true;
+        double hn = hd - step;
+        if (!last && (it >= 12 || !(hn > lod && hn < hid) || !(fp > 0.0)))
+            hn = isinf(hid) ? 1.01 * hd : 0.5 * (lod + hid);
+        hd = hn;
+    }
+    return okd;
+}
+
 __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
                           HParams hp, const double* __restrict__ h_prev, const int32_t* __restrict__ perm,
-                          double* h_out, double* omega_out, float* H2f_out, unsigned long long* hminmax, int* flags) {
+                          double* h_out, double* omega_out, float* H2f_out, unsigned long long* hminmax, int* flags,
+                          int32_t* refine_list, int* refine_count) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double hd = 0.0, om_d = 0.0;
     bool active = p < n;
@@ -247,7 +381,7 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
         // ---- float phase: Newton on float separations, omega summed in double
         float lo = 0.f, hi = INFINITY;
         const float eta = (float)hp.eta;
-        bool ok = false;
+        bool ok = false, near = false;
         double sw_last = 0.0;
         for (int it = 0; it < hp.max_iter; ++it) {
             float H = kapf * h;
@@ -255,11 +389,13 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
             float H2 = H * H;
             double sw = 0.0;
             float sdw = 0.f;
+            bool nb = false;
             for_each_candidate(g, pxf, pyf, pzf, H, [&](int j) {
                 float dx = fsep(xq[j], qx, hp.scale[0]);
                 float dy = fsep(xq[n + j], qy, hp.scale[1]);
                 float dz = fsep(xq[2 * n + j], qz, hp.scale[2]);
                 float r2 = dx * dx + dy * dy + dz * dz;
+                nb |= fabsf(r2 - H2) < kNearBand * H2;
                 if (r2 < H2) {
                     float q = sqrtf(r2) * iH;
                     float w = spline_w(q);
@@ -268,6 +404,7 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
                 }
             });
             sw_last = sw;
+            near = nb;
             float om = sigf * iH * iH * iH * (float)sw;
             float dom = -kapf * sigf * iH * iH * iH * iH * sdw;      // d omega / d h
             float cb = cbrtf(om);
@@ -296,54 +433,12 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
             om_d = kSigma / (H * H * H) * sw_last;
         }
 
-        // ---- double phase (FP64 path): Newton on the exact separations to machine precision
-        if (hp.refine64 && ok) {
-            double lod = 0.0, hid = INFINITY;
-            const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
-            bool okd = false, last = false;
-            for (int it = 0; it < 60; ++it) {
-                double H = kKappa * hd;
-                double iH = 1.0 / H;
-                double H2 = H * H;
-                float Hf = (float)H * 1.001f;
-                float H2f = Hf * Hf;
-                double sw = 0.0, sdw = 0.0;
-                for_each_candidate(g, pxf, pyf, pzf, Hf, [&](int j) {
-                    float dxf = fsep(xq[j], qx, hp.scale[0]);
-                    float dyf = fsep(xq[n + j], qy, hp.scale[1]);
-                    float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
-                    if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) return;
-                    double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
-                    double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
-                    double dz = sep_fast(xs[2 * n + j], pz, g.box[2], half[2], g.periodic);
-                    double r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 < H2) {
-                        double q = sqrt(r2) * iH;
-                        double w = spline_w(q);
-                        sw += w;
-                        sdw += 3.0 * w + q * spline_dw(q);
-                    }
-                });
-                double om = kSigma * iH * iH * iH * sw;
-                double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
-                double cb = cbrt(om);
-                double f = hd - hp.eta / cb;
-                double fp = 1.0 + (hp.eta / 3.0) / (cb * om) * dom;
-                om_d = om;
-                if (last) { okd = true; break; }        // omega evaluated at the final h
-                if (f < 0.0) lod = hd; else hid = hd;
-                double step = f / fp;
-                // once the Newton step is tiny the next iterate is exact to rounding: take it and
-                // evaluate omega there once more; a residual at the rounding floor or a
-                // collapsed bracket ends the iteration at the current h
-                if (fabs(f) <= 1e-15 * hd || (hid - lod) <= 1e-14 * hd) { okd = true; break; }
-                if (fp > 0.0 && fabs(step) <= 1e-11 * hd) last = true;
-                double hn = hd - step;
-                if (!last && (it >= 12 || !(hn > lod && hn < hid) || !(fp > 0.0)))
-                    hn = isinf(hid) ? 1.01 * hd : 0.5 * (lod + hid);
-                hd = hn;
-            }
-            if (!okd) atomicExch(&flags[F_NOCONV], 1);
+        // ---- double phase: Newton on the exact separations to machine precision, here for
+        // every particle (FP64 path), else later (k_h_refine) for the near-threshold ones
+        if (ok && hp.refine64) {
+            if (!refine_h_double(g, xs, xq, n, hp, p, hd, om_d)) atomicExch(&flags[F_NOCONV], 1);
+        } else if (ok && near) {
+            refine_list[atomicAdd(refine_count, 1)] = (int32_t)p;
         }
         h_out[p] = hd;
         omega_out[p] = om_d;
@@ -359,6 +454,93 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
         atomic_min_pos(&hminmax[0], mn);
         atomic_max_pos(&hminmax[1], mx);
         atomicAdd(reinterpret_cast<double*>(&hminmax[4]), h3);
+    }
+}
+
+// Smoothing lengths given by the caller (rt_neighbours_given_h): h_i from h_in (caller order)
+// and omega_i = sum_j W(r_ij, h_i) at it, evaluated like the last iteration of the solve (the
+// float path: float weights summed in double; the FP64 path: double).  Non-positive or
+// non-finite h sets the F_BADH flag.
+__global__ void k_h_given(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
+                          HParams hp, const double* __restrict__ h_in, const int32_t* __restrict__ perm,
+                          double* h_out, double* omega_out, float* H2f_out, unsigned long long* hminmax, int* flags) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool active = p < n;
+    double hd = 0.0;
+    if (active) {
+        hd = h_in[perm[p]];
+        if (!(hd > 0.0) || !(hd < (double)hp.h_cap) || !isfinite(hd)) {
+            atomicExch(&flags[F_BADH], 1);
+            hd = hp.h0;
+        }
+        const uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+        const double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+        const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+        const double H = kKappa * hd, iH = 1.0 / H, H2 = H * H;
+        double sw = 0.0;
+        if (hp.refine64) {
+            const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
+            const float Hf = (float)H * 1.001f, H2f = Hf * Hf;
+            for_each_candidate(g, pxf, pyf, pzf, Hf, [&](int j) {
+                float dxf = fsep(xq[j], qx, hp.scale[0]);
+                float dyf = fsep(xq[n + j], qy, hp.scale[1]);
+                float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+                if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) return;
+                double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
+                double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
+                double dz = sep_fast(xs[2 * n + j], pz, g.box[2], half[2], g.periodic);
+                double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < H2) sw += spline_w(sqrt(r2) * iH);
+            });
+        } else {
+            const float Hf = (float)H, iHf = 1.f / Hf, H2f = Hf * Hf;
+            for_each_candidate(g, pxf, pyf, pzf, Hf, [&](int j) {
+                float dx = fsep(xq[j], qx, hp.scale[0]);
+                float dy = fsep(xq[n + j], qy, hp.scale[1]);
+                float dz = fsep(xq[2 * n + j], qz, hp.scale[2]);
+                float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < H2f) sw += (double)spline_w(sqrtf(r2) * iHf);
+            });
+        }
+        h_out[p] = hd;
+        omega_out[p] = kSigma * iH * iH * iH * sw;
+        H2f_out[p] = (float)(H * H);
+    }
+    double mn = active ? hd : INFINITY, mx = active ? hd : 0.0;
+    warp_minmax(mn, mx);
+    double h3 = active ? (kKappa * hd) * (kKappa * hd) * (kKappa * hd) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) h3 += __shfl_xor_sync(0xffffffffu, h3, o);
+    if ((threadIdx.x & 31) == 0 && mx > 0.0) {
+        atomic_min_pos(&hminmax[0], mn);
+        atomic_max_pos(&hminmax[1], mx);
+        atomicAdd(reinterpret_cast<double*>(&hminmax[4]), h3);
+    }
+}
+
+// Float path: the double phase for the particles k_h_solve flagged, one warp per particle
+// (grid-stride over the list; its order is arbitrary, and each particle's result depends on
+// its own position and neighbours only).  The smallest and largest h are widened to the
+// refined values (the pair search's bound must cover them).
+__global__ void k_h_refine(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
+                           HParams hp, const int32_t* __restrict__ list, const int* __restrict__ count, double* h_out,
+                           double* omega_out, float* H2f_out, unsigned long long* hminmax, int* flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int cnt = *count;
+    for (int64_t t = w0; t < cnt; t += nw) {
+        const int64_t p = list[t];
+        double hd = h_out[p], om_d = omega_out[p];
+        const bool ok = refine_h_warp(g, xs, xq, n, hp, p, lane, hd, om_d);
+        if (lane == 0) {
+            if (!ok) atomicExch(&flags[F_NOCONV], 1);
+            h_out[p] = hd;
+            omega_out[p] = om_d;
+            const double Hd = kKappa * hd;
+            H2f_out[p] = (float)(Hd * Hd);
+            atomic_min_pos(&hminmax[0], hd);
+            atomic_max_pos(&hminmax[1], hd);
+        }
     }
 }
 
@@ -785,6 +967,7 @@ struct SrcParams {
     double eta, h0, h_cap;
     int max_iter;
     int warm;       // start from the h of the last call (in hs_out), else from h0
+    int fixed;      // hs_out holds given smoothing lengths: only omega_s at them
 };
 
 // Rows of the culled walk of for_each_candidate handed out round-robin to the threads of a
@@ -856,10 +1039,13 @@ __global__ void __launch_bounds__(kSrcThreads) k_src_h(Grid g, const double* __r
     __shared__ double red_w[kSrcThreads], red_dw[kSrcThreads];
     double p[3] = {xsrc[s_id], xsrc[S + s_id], xsrc[2 * S + s_id]};
     const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
-    double h = sp.warm ? hs_out[s_id] : sp.h0, lo = 0.0, hi = INFINITY, om = 0.0;
-    if (!(h > 0.0) || !(h < sp.h_cap)) h = sp.h0;
-    __syncthreads();    // every thread has read the first guess before thread 0 overwrites it
+    double h = (sp.warm || sp.fixed) ? hs_out[s_id] : sp.h0, lo = 0.0, hi = INFINITY, om = 0.0;
     bool ok = false;
+    if (!(h > 0.0) || !(h < sp.h_cap)) {
+        if (sp.fixed && t == 0) atomicExch(&flags[F_BADH], 1);
+        h = sp.h0;
+    }
+    __syncthreads();    // every thread has read the first guess before thread 0 overwrites it
     for (int it = 0; it < sp.max_iter; ++it) {
         double H = kKappa * h, iH = 1.0 / H, H2 = H * H;
         double sw = 0.0, sdw = 0.0;
@@ -889,6 +1075,10 @@ __global__ void __launch_bounds__(kSrcThreads) k_src_h(Grid g, const double* __r
         sdw = red_dw[0];
         __syncthreads();
         om = kSigma * iH * iH * iH * sw;
+        if (sp.fixed) {   // given h: omega there, no iteration
+            ok = om > 0.0;
+            break;
+        }
         double f, fp;
         if (om > 0.0) {
             double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
@@ -1123,19 +1313,21 @@ __global__ void k_inj_targets(const uint64_t* __restrict__ keys, const int32_t* 
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // ------------------------------------------------------------------------------------
-rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc) {
+rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc, const double* h_in,
+                           const double* hs_in) {
     const int64_t n = c->n, S = c->n_src;
     const rt_config& cfg = c->cfg;
     cudaStream_t st = c->stream;
     const int B = 256;
 
-    // grid: cells of about half the mean-density support radius
+    // grid: cells of cell_eighths / 8 of the mean-density support radius (default one half)
     double vol = cfg.box[0] * cfg.box[1] * cfg.box[2];
     double h0 = cfg.eta_res * std::cbrt(vol / (double)n);
     double H0 = kKappa * h0;
+    const double cell_frac = (c->tune.cell_eighths > 0 ? c->tune.cell_eighths : 4) / 8.0;
     int64_t ncells = 1;
     for (int a = 0; a < 3; ++a) {
-        int nca = (int)std::floor(cfg.box[a] / (0.5 * H0));
+        int nca = (int)std::floor(cfg.box[a] / (cell_frac * H0));
         nca = std::max(1, std::min(nca, 1024));
         c->nc[a] = nca;
         c->cell[a] = cfg.box[a] / nca;
@@ -1240,13 +1432,30 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     for (int a = 0; a < 3; ++a) hp.scale[a] = qscale[a];
     hp.max_iter = cfg.h_max_iter > 0 ? cfg.h_max_iter : 100;
     hp.tol32 = (float)std::max(cfg.h_tol, 2e-6);
+    // the FP64 path refines every h in double; the float path only those of particles with a
+    // candidate near their support radius, which is enough for the exact root's pair lists
     hp.refine64 = c->fp64 ? 1 : 0;
-    k_h_solve<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp,
-                                             warm ? c->h_prev.as<double>() : nullptr, c->perm.as<int32_t>(),
-                                             c->h_d.as<double>(), c->omega_d.as<double>(), c->H2f.as<float>(), red,
-                                             flags);
+    int* refine_count = flags + F_REFINE;
+    if (h_in) {
+        hp.refine64 = c->fp64 ? 1 : 0;   // omega in the working path's arithmetic
+        k_h_given<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp, h_in,
+                                                 c->perm.as<int32_t>(), c->h_d.as<double>(), c->omega_d.as<double>(),
+                                                 c->H2f.as<float>(), red, flags);
+    } else {
+        k_h_solve<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp,
+                                                 warm ? c->h_prev.as<double>() : nullptr, c->perm.as<int32_t>(),
+                                                 c->h_d.as<double>(), c->omega_d.as<double>(), c->H2f.as<float>(), red,
+                                                 flags, c->idx_in.as<int32_t>(), refine_count);
+    }
     RT_CUDA(c, cudaGetLastError());
     c->launches += 1;
+    if (!c->fp64 && !h_in) {
+        k_h_refine<<<(unsigned)c->sm_count * 8, 256, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp,
+                                                  c->idx_in.as<int32_t>(), refine_count, c->h_d.as<double>(),
+                                                  c->omega_d.as<double>(), c->H2f.as<float>(), red, flags);
+        RT_CUDA(c, cudaGetLastError());
+        c->launches += 1;
+    }
     int hflags[8];
     double hmm[2];
     double sumH3 = 0.0;
@@ -1256,6 +1465,9 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     RT_CUDA(c, cudaStreamSynchronize(st));
     if (hflags[F_BADPOS]) return fail(c, RT_ERR_INVALID, "positions must be finite and inside [0, box)");
     if (hflags[F_NOCONV]) return fail(c, RT_ERR_NOCONV, "smoothing-length iteration did not converge");
+    if (hflags[F_BADH]) return fail(c, RT_ERR_INVALID, "given smoothing lengths must be finite, > 0 and below the "
+                                                       "quarter of the periodic box over the support ratio");
+    c->diag.h_refined = h_in ? 0 : (c->fp64 ? n : (int64_t)hflags[F_REFINE]);
     c->diag.h_min = hmm[0];
     c->diag.h_max = hmm[1];
     double Hmax = kKappa * hmm[1];
@@ -1441,7 +1653,9 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         sp.h_cap = hp.h_cap;
         sp.max_iter = std::max(hp.max_iter, 200);
         sp.warm = c->has_hs_prev ? 1 : 0;
+        sp.fixed = hs_in ? 1 : 0;
         c->has_hs_prev = false;     // set again only when this call succeeds
+        if (hs_in) RT_CUDA(c, cudaMemcpyAsync(c->hs_d.p, hs_in, S * 8, cudaMemcpyDeviceToDevice, st));
         const unsigned sb = (unsigned)S;   // one block of kSrcWarps warps per source
         k_src_h<<<(unsigned)S, kSrcThreads, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S, sp,
                                                      c->hs_d.as<double>(), c->omegas_d.as<double>(), flags);
@@ -1457,6 +1671,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         RT_CUDA(c, cudaMemcpyAsync(&NE, c->src_off.as<int64_t>() + S, 8, cudaMemcpyDeviceToHost, st));
         RT_CUDA(c, cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
         RT_CUDA(c, cudaStreamSynchronize(st));
+        if (hflags[F_BADH]) return fail(c, RT_ERR_INVALID, "given source smoothing lengths must be finite and > 0");
         if (hflags[F_SRC_NOCONV]) return fail(c, RT_ERR_NOCONV, "source smoothing-length iteration did not converge");
         if (NE > Smax) return fail(c, RT_ERR_INVALID, "too many injection entries");
         c->n_inj_entries = NE;

@@ -52,19 +52,48 @@ __global__ void k_energy_static_final(const double* __restrict__ part, int G, do
 
 // Device address of g_energy_scratch, looked up once per device with that device current.
 // In host code the symbol only names a host-side stand-in, so kernels are given this address.
+// The address belongs to the device's current context: a caller that resets the device
+// (cudaDeviceReset) gets a new context, in which the array has a new address, so the cache
+// remembers the context it was taken in and looks the address up again when that changes.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    }
+    return fn;
+}
+
+struct ScratchEntry {
+    CUcontext ctx = nullptr;
+    double* addr = nullptr;
+};
 std::mutex g_scratch_mu;
-std::vector<double*> g_scratch_addr;
+std::vector<ScratchEntry> g_scratch;
 
 cudaError_t scratch_address(int device, double** out) {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if ((int)g_scratch_addr.size() <= device) g_scratch_addr.resize(device + 1, nullptr);
-    if (!g_scratch_addr[device]) {
+    if ((int)g_scratch.size() <= device) g_scratch.resize(device + 1);
+    CUcontext cur = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (get && get(&cur) != CUDA_SUCCESS) cur = nullptr;
+    ScratchEntry& e = g_scratch[device];
+    if (!e.addr || (cur && cur != e.ctx)) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_energy_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[device] = static_cast<double*>(p);
+        cudaError_t r = cudaGetSymbolAddress(&p, g_energy_scratch);
+        if (r != cudaSuccess) return r;
+        if (!cur && get && get(&cur) != CUDA_SUCCESS) cur = nullptr;   // made current by the lookup
+        e.addr = static_cast<double*>(p);
+        e.ctx = cur;
     }
-    *out = g_scratch_addr[device];
+    *out = e.addr;
     return cudaSuccess;
 }
 
@@ -78,6 +107,9 @@ extern "C" rt_status rt_energy_static(const void* U_dev, const double* V_dev, in
     if (n < 1) return RT_ERR_INVALID;
     if (n_groups < 1 || n_groups > kStaticMaxGroups) return RT_ERR_INVALID;
     if (precision != RT_FP64 && precision != RT_FP32_MIXED) return RT_ERR_INVALID;
+    // an error left pending by the caller's earlier CUDA work is reported before any launch
+    // (and left pending: this call does not clear what it did not cause)
+    if (cudaPeekAtLastError() != cudaSuccess) return RT_ERR_CUDA;
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return RT_ERR_CUDA;
     double* part = nullptr;
@@ -89,6 +121,7 @@ extern "C" rt_status rt_energy_static(const void* U_dev, const double* V_dev, in
     else
         k_energy_static_part<float><<<kStaticBlocks, kStaticThreads, 0, s>>>((const float*)U_dev, V_dev, n, n_groups,
                                                                               part);
+    if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
     k_energy_static_final<<<1, 32, 0, s>>>(part, n_groups, E_tot_dev);
     if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
     return RT_OK;

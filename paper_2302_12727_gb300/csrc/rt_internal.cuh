@@ -21,7 +21,8 @@ constexpr double kKappa = 1.825742;
 constexpr double kSigma = 5.0929581789406507446;   // 16 / pi
 // int slots of the context's 64-byte flag buffer (cleared by every rt_neighbours): error
 // flags of the build, the clamp counter (64-bit, slots 8-9) and the device-wait time-out flag
-enum FlagSlot { F_BADPOS = 0, F_NOCONV = 1, F_GEOM = 2, F_ILL = 3, F_SRC_NOCONV = 4, F_NSLOTS = 8, F_CLAMP = 8,
+enum FlagSlot { F_BADPOS = 0, F_NOCONV = 1, F_GEOM = 2, F_ILL = 3, F_SRC_NOCONV = 4, F_REFINE = 5, F_BADH = 6,
+                F_NSLOTS = 8, F_CLAMP = 8,
                 F_TIMEOUT = 12, F_SCRATCH = 13, F_ROWMAX = 14, F_SELFTEST = 15 };
 constexpr int kMaxGC = 4;                          // groups handled by one pair-kernel launch
 
@@ -95,6 +96,7 @@ struct rt_ctx {
     rt::DevBuf flags;                                   // int32 error flags + counters
     rt::DevBuf red_tmp;                                 // small reduction scratch (double)
     int64_t n_directed = 0;
+    int64_t n_owned = 0;                                // rt_energy sums caller indices [0, n_owned)
 
     // sources / injection
     rt::DevBuf xsrc_d, hs_d, omegas_d, src_counts, src_off, inj_key, inj_key_out, inj_val, inj_val_out;
@@ -133,7 +135,7 @@ struct rt_ctx {
     // diagnostics
     rt_diag diag{};
     // launch variants of the float pair kernels (rt_set_tuning); the double path has one
-    rt_tuning tune{2, 1, 2};
+    rt_tuning tune{2, 1, 2, 4, 0, 0, 0};
 
     std::map<rt::GraphKey, rt::GraphEntry> graphs;
 
@@ -173,7 +175,9 @@ void prof_end(rt_ctx* c, cudaStream_t s, int idx);
 
 // entry points of the kernel files
 namespace rt {
-rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc);
+// h_in [N] / hs_in [S] (caller order, device): given smoothing lengths (no solve), or NULL
+rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc,
+                           const double* h_in = nullptr, const double* hs_in = nullptr);
 // caller-order component-major arrays <-> sorted records (comps values at record offset off)
 rt_status state_in(rt_ctx* c, const void* U_user, void* rec, int comps, int RS, int off);
 rt_status state_out(rt_ctx* c, const void* rec, void* U_user, int comps, int RS, int off);

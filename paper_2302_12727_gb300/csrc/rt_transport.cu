@@ -28,12 +28,21 @@ namespace rt {
 
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// Block sizes of the shuffle gradient and the per-group gather.  Rows of different lengths
+// Default block sizes of the shuffle gradient and the per-group gather (rt_tuning's
+// gradient_block and gather_block choose others at run time).  Rows of different lengths
 // make the warps of a block finish at different times, and a block's registers are freed
 // only with its last warp: 64-thread gradient blocks run 3% faster than 256-thread ones
 // (0.139 against 0.144 ms per launch on the 262,144-particle set); the gather, whose warps
-// finish more evenly, keeps 256 (128 is 2% slower there).
-constexpr int kGradBlock = 64, kGatherBlock = 256;
+// finish more evenly, keeps 256 (128 is 2% slower there).  The kernels are compiled for the
+// largest block of their range, with the register cap the default block had.
+constexpr int kGradBlock = 64, kGatherBlock = 256, kGradBlockMax = 256, kGatherBlockMax = 512;
+
+static int grad_block(const rt_ctx* c) {
+    if (c->tune.gradient_block > 0) return c->tune.gradient_block;
+    return c->tune.gradient_variant == 2 ? kGradBlock : 256;
+}
+static int gather_block(const rt_ctx* c) { return c->tune.gather_block > 0 ? c->tune.gather_block : kGatherBlock; }
+static int pair_warps(const rt_ctx* c) { return c->tune.pair_warps > 0 ? c->tune.pair_warps : 1; }
 
 // ------------------------------------------------------------------------------------
 // caller order <-> cell-sorted records
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(256) k_gradient_g(PairArgs<float> a, const flo
 // groups (eight particles per warp, every lane busy) five blocks per SM (48 registers, a few
 // spilled) beat four at 64 registers by 7%; with three groups they lose 2%.
 template <int GC>
-__global__ void __launch_bounds__(kGradBlock, GC == 4 ? 1280 / kGradBlock : 0) k_gradient_s(PairArgs<float> a, const float* __restrict__ rec,
+__global__ void __launch_bounds__(kGradBlockMax, GC == 4 ? 1280 / kGradBlockMax : 0) k_gradient_s(PairArgs<float> a, const float* __restrict__ rec,
                                                     float* __restrict__ grad, int g0) {
     constexpr int P = 32 / GC;                     // particles per warp
     const unsigned FULL = 0xffffffffu;
@@ -422,23 +431,124 @@ __global__ void __launch_bounds__(128) k_flux(PairArgs<T> a, FluxExtra<T> x, con
     vstore<NC>(pairbuf + slot * NC, out);
 }
 
-// Pass 2 with individual time bins: particle i adds to its accumulator the slots of the pairs
-// that interacted at min-step s (all of them if i starts a step, else those whose partner
-// starts one), in the same order as the uniform gather; at the end of its own step
+// ------------------------------------------------------------------------------------
+// Per-particle sum of one group's pair fluxes (E, Fx, Fy, Fz), in a fixed order.  The double
+// path adds in double.  The float path keeps the energy row as a compensated float sum:
+// Knuth's TwoSum gives the exact rounding error of every addition and a second float
+// collects those errors (the cascaded summation of Ogita, Rump and Oishi, "Accurate sum and
+// dot product", 2005), so for the ~50 terms of a particle the sum's error stays near
+// (50 u)^2 of the sum of magnitudes (u = 2^-24) instead of 50 u; the update then forms the
+// energy from the pair in double.  The flux rows add in float.  (A double energy sum costs
+// the same gather 2.4 times its time on GB300, whose FP64 rate is 1/64 of FP32; compensated
+// flux rows 1.3 times.)  With individual time bins the accumulators stay in memory between
+// min-steps: 32 bytes per (particle, group) in both precisions.
+template <class T>
+struct FluxAcc;
+
+template <>
+struct FluxAcc<double> {
+    double v[4];
+    __device__ __forceinline__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.0; }
+    __device__ __forceinline__ void add(const double p[4]) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] += p[c];
+    }
+    __device__ __forceinline__ void sub(const double p[4]) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] -= p[c];
+    }
+    __device__ __forceinline__ double energy() const { return v[0]; }
+    __device__ __forceinline__ double flux(int c) const { return v[1 + c]; }
+    __device__ __forceinline__ void load(const double* m) { vload<4>(m, v); }
+    __device__ __forceinline__ void store(double* m) const { vstore<4>(m, v); }
+};
+
+// s + x = t + e exactly (TwoSum, branch-free); e is added to the error sum k
+__device__ __forceinline__ void two_sum_into(float& s, float& k, float x) {
+    const float t = __fadd_rn(s, x);
+    const float z = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
+    k = __fadd_rn(k, e);
+    s = t;
+}
+
+template <>
+struct FluxAcc<float> {
+    float es, ek;    // energy row: sum and error sum
+    float f[3];      // flux rows
+    __device__ __forceinline__ void zero() { es = ek = f[0] = f[1] = f[2] = 0.f; }
+    __device__ __forceinline__ void add(const float p[4]) {
+        two_sum_into(es, ek, p[0]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] += p[1 + c];
+    }
+    __device__ __forceinline__ void sub(const float p[4]) {
+        two_sum_into(es, ek, -p[0]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] -= p[1 + c];
+    }
+    __device__ __forceinline__ double energy() const { return (double)es + (double)ek; }
+    __device__ __forceinline__ float flux(int c) const { return f[c]; }
+    // record: {es, ek, f0, f1 | f2, unused x 3}
+    __device__ __forceinline__ void load(const float* m) {
+        const float4 a = *reinterpret_cast<const float4*>(m);
+        es = a.x; ek = a.y; f[0] = a.z; f[1] = a.w;
+        f[2] = m[4];
+    }
+    __device__ __forceinline__ void store(float* m) const {
+        *reinterpret_cast<float4*>(m) = make_float4(es, ek, f[0], f[1]);
+        m[4] = f[2];
+    }
+};
+
+// words of T per (particle, group) accumulator record in memory (32 bytes)
+template <class T>
+struct AccRec {
+    static constexpr int words = 32 / (int)sizeof(T);
+};
+
+// U_g(t + dt) = (U_g - f acc_g) sink for one group (Eq. transport-update-explicit with
+// f = dt / V_i, then the forward-Euler sink), the fix-up E >= 0 when on (returns 1 if it
+// fired), then the next sub-cycle's injection inj (double, 0 when none).  The float path
+// forms the energy from its compensated sum in double and rounds once, before the fix-up
+// and the injection, exactly where a plain step stores it.
+template <class T>
+__device__ __forceinline__ int update_group(T u[4], const FluxAcc<T>& acc, T f, T sink, int clamp, const double* inj) {
+    T v0;
+    if constexpr (std::is_same<T, float>::value)
+        v0 = (float)(((double)u[0] - (double)f * acc.energy()) * (double)sink);
+    else
+        v0 = (u[0] - f * acc.energy()) * sink;
+    int fired = 0;
+    if (clamp && v0 < T(0)) {
+        v0 = T(0);
+        fired = 1;
+    }
+    if (inj) v0 = (T)__dadd_rn((double)v0, *inj);
+    u[0] = v0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[1 + c] = (u[1 + c] - f * acc.flux(c)) * sink;
+    return fired;
+}
+
+// Pass 2 with individual time bins: particle i adds to its accumulators the slots of the
+// pairs that interacted at min-step s (all of them if i starts a step, else those whose
+// partner starts one), in the same order as the uniform gather; at the end of its own step
 // ((s + 1) mod 2^b_i = 0) it applies U_i - dt_min / V_i acc_i, the sink over its step
-// dt_min 2^b_i and the fix-up, and clears the accumulator.  The states are updated in place
+// dt_min 2^b_i and the fix-up, and clears the accumulators.  The states are updated in place
 // (this pass runs after the pair pass, and each particle writes only its own record).
 template <class T, int GC>
 __device__ __forceinline__ void gather_bins(const PairArgs<T>& a, const FluxExtra<T>& x, const T* __restrict__ rec,
                                             const T* __restrict__ pairbuf, T* __restrict__ out, int g0, int64_t i) {
-    constexpr int NC = 4 * GC;
+    constexpr int NC = 4 * GC, AW = AccRec<T>::words;
     const int RS = 4 * a.G;
     const int bi = a.bins[i];
     const int mask = (1 << bi) - 1;
     const bool start_i = !(a.s & mask);
-    T* accp = x.acc + i * RS + 4 * g0;
-    T acc[NC];
-    vload<NC>(accp, acc);
+    T* accp = x.acc + (i * a.G + g0) * AW;
+    FluxAcc<T> acc[GC];
+#pragma unroll
+    for (int g = 0; g < GC; ++g) acc[g].load(accp + g * AW);
     const int64_t r0 = a.row_off[i], s0 = a.up_off[i], s1 = a.up_off[i + 1];
     const int nl = a.n_low[i];
     for (int64_t sl = s0; sl < s1; ++sl) {
@@ -447,7 +557,7 @@ __device__ __forceinline__ void gather_bins(const PairArgs<T>& a, const FluxExtr
         T phi[NC];
         vload<NC>(pairbuf + sl * NC, phi);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] += phi[c];
+        for (int g = 0; g < GC; ++g) acc[g].add(phi + 4 * g);
     }
     const int32_t* ls = a.low_slot + (r0 - s0);
     for (int e = 0; e < nl; ++e) {
@@ -456,10 +566,11 @@ __device__ __forceinline__ void gather_bins(const PairArgs<T>& a, const FluxExtr
         T phi[NC];
         vload<NC>(pairbuf + (int64_t)ls[e] * NC, phi);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] -= phi[c];
+        for (int g = 0; g < GC; ++g) acc[g].sub(phi + 4 * g);
     }
     if ((a.s + 1) & mask) {   // the step of i goes on (the state is updated in place)
-        vstore<NC>(accp, acc);
+#pragma unroll
+        for (int g = 0; g < GC; ++g) acc[g].store(accp + g * AW);
         return;
     }
     T ui[NC];
@@ -471,34 +582,28 @@ __device__ __forceinline__ void gather_bins(const PairArgs<T>& a, const FluxExtr
     if (x.alpha) sink = fmax_(T(1) - x.c * x.alpha[i] * dti, T(0));
     int nclamp = 0;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const T sk = x.alpha_g ? fmax_(T(1) - x.c * x.alpha_g[i * a.G + g0 + c / 4] * dti, T(0)) : sink;
-        T v = (ui[c] - f * acc[c]) * sk;
-        if (x.clamp && (c & 3) == 0 && v < T(0)) {
-            v = T(0);
-            ++nclamp;
-        }
-        ui[c] = v;
-        acc[c] = T(0);
+    for (int g = 0; g < GC; ++g) {
+        const T sk = x.alpha_g ? fmax_(T(1) - x.c * x.alpha_g[i * a.G + g0 + g] * dti, T(0)) : sink;
+        nclamp += update_group<T>(ui + 4 * g, acc[g], f, sk, x.clamp, nullptr);
+        acc[g].zero();
+        acc[g].store(accp + g * AW);
     }
-    vstore<NC>(accp, acc);
     vstore<NC>(out + i * RS + 4 * g0, ui);
     if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
 }
 
 // particles whose step ends at min-step s without any interaction at s (no starting partner,
-// nmin > tz): apply the accumulator, the sink over the step and the fix-up, in place
+// nmin > tz): apply the accumulators, the sink over the step and the fix-up, in place
 template <class T, int GC>
 __global__ void k_finalize_bins(PairArgs<T> a, FluxExtra<T> x, T* __restrict__ rec, int g0) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= a.count) return;
     const int64_t i = a.order[t];
     if (a.nmin[i] <= a.tz) return;       // finalised by the gather of this min-step
-    constexpr int NC = 4 * GC;
+    constexpr int NC = 4 * GC, AW = AccRec<T>::words;
     const int RS = 4 * a.G;
-    T* accp = x.acc + i * RS + 4 * g0;
-    T acc[NC], ui[NC];
-    vload<NC>(accp, acc);
+    T* accp = x.acc + (i * a.G + g0) * AW;
+    T ui[NC];
     vload<NC>(rec + i * RS + 4 * g0, ui);
     const int bi = a.bins[i];
     const T dt = (T)(*x.dt_dev);
@@ -508,17 +613,14 @@ __global__ void k_finalize_bins(PairArgs<T> a, FluxExtra<T> x, T* __restrict__ r
     if (x.alpha) sink = fmax_(T(1) - x.c * x.alpha[i] * dti, T(0));
     int nclamp = 0;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const T sk = x.alpha_g ? fmax_(T(1) - x.c * x.alpha_g[i * a.G + g0 + c / 4] * dti, T(0)) : sink;
-        T v = (ui[c] - f * acc[c]) * sk;
-        if (x.clamp && (c & 3) == 0 && v < T(0)) {
-            v = T(0);
-            ++nclamp;
-        }
-        ui[c] = v;
-        acc[c] = T(0);
+    for (int g = 0; g < GC; ++g) {
+        FluxAcc<T> acc;
+        acc.load(accp + g * AW);
+        const T sk = x.alpha_g ? fmax_(T(1) - x.c * x.alpha_g[i * a.G + g0 + g] * dti, T(0)) : sink;
+        nclamp += update_group<T>(ui + 4 * g, acc, f, sk, x.clamp, nullptr);
+        acc.zero();
+        acc.store(accp + g * AW);
     }
-    vstore<NC>(accp, acc);
     vstore<NC>(rec + i * RS + 4 * g0, ui);
     if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
 }
@@ -537,33 +639,33 @@ __global__ void __launch_bounds__(128) k_flux_gather(PairArgs<T> a, FluxExtra<T>
     if (i >= a.n) return;
     constexpr int NC = 4 * GC;
     const int RS = 4 * a.G;
-    T acc[NC];
+    FluxAcc<T> acc[GC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = T(0);
+    for (int g = 0; g < GC; ++g) acc[g].zero();
     const int64_t r0 = a.row_off[i], s0 = a.up_off[i], s1 = a.up_off[i + 1];
     for (int64_t sl = s0; sl < s1; ++sl) {
         T phi[NC];
         vload<NC>(pairbuf + sl * NC, phi);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] += phi[c];
+        for (int g = 0; g < GC; ++g) acc[g].add(phi + 4 * g);
     }
     const int nl = a.n_low[i];
     const int32_t* ls = a.low_slot + (r0 - s0);
     int e = 0;
     for (; e + 4 <= nl; e += 4) {     // four loads in flight, subtracted in order
-        T p0[NC], p1[NC], p2[NC], p3[NC];
-        vload<NC>(pairbuf + (int64_t)ls[e] * NC, p0);
-        vload<NC>(pairbuf + (int64_t)ls[e + 1] * NC, p1);
-        vload<NC>(pairbuf + (int64_t)ls[e + 2] * NC, p2);
-        vload<NC>(pairbuf + (int64_t)ls[e + 3] * NC, p3);
+        T p[4][NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = (((acc[c] - p0[c]) - p1[c]) - p2[c]) - p3[c];
+        for (int u = 0; u < 4; ++u) vload<NC>(pairbuf + (int64_t)ls[e + u] * NC, p[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int g = 0; g < GC; ++g) acc[g].sub(p[u] + 4 * g);
     }
     for (; e < nl; ++e) {
         T phi[NC];
         vload<NC>(pairbuf + (int64_t)ls[e] * NC, phi);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] -= phi[c];
+        for (int g = 0; g < GC; ++g) acc[g].sub(phi + 4 * g);
     }
     const T dt = (T)(*x.dt_dev);
     const T f = dt * a.omega[i];
@@ -573,15 +675,9 @@ __global__ void __launch_bounds__(128) k_flux_gather(PairArgs<T> a, FluxExtra<T>
     vload<NC>(rec + i * RS + 4 * g0, ui);
     int nclamp = 0;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const T sk = x.alpha_g ? fmax_(T(1) - x.c * x.alpha_g[i * a.G + g0 + c / 4] * dt, T(0)) : sink;
-        T v = (ui[c] - f * acc[c]) * sk;
-        if (x.clamp && (c & 3) == 0 && v < T(0)) {
-            v = T(0);
-            ++nclamp;
-        }
-        if (x.inj && (c & 3) == 0) v = (T)__dadd_rn((double)v, x.inj[i * a.G + g0 + c / 4]);
-        ui[c] = v;
+    for (int g = 0; g < GC; ++g) {
+        const T sk = x.alpha_g ? fmax_(T(1) - x.c * x.alpha_g[i * a.G + g0 + g] * dt, T(0)) : sink;
+        nclamp += update_group<T>(ui + 4 * g, acc[g], f, sk, x.clamp, x.inj ? x.inj + i * a.G + g0 + g : nullptr);
     }
     vstore<NC>(out + i * RS + 4 * g0, ui);
     if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
@@ -699,21 +795,27 @@ struct PackedRows {
 // resident blocks per SM lets shared memory, not registers, bound the occupancy.  Measured
 // against four-warp blocks at 80 registers: 0.169 against 0.180 ms per launch on the
 // 262,144-particle set (G = 3), 1.78 against 1.93 ms on the 2,097,152-particle set (G = 4).
-constexpr int kTmaWarps = 1;
+// Up to kTmaWarpsMax warps per block (rt_tuning's pair_warps, default 1); the register cap is
+// that of 27 (24 at G = 4) one-warp blocks per SM whatever the block size
+constexpr int kTmaWarpsMax = 4;
 template <int G>
 struct TmaMinBlocks {
-    static constexpr int value = G >= 4 ? 24 : 27;
+    static constexpr int value = G >= 4 ? 6 : 7;   // blocks of kTmaWarpsMax warps
 };
 template <int G, bool HLL, bool BINS = false>
-__global__ void __launch_bounds__(kTmaWarps * 32, TmaMinBlocks<G>::value) k_flux_tma(PairArgs<float> a, FluxExtra<float> x,
+__global__ void __launch_bounds__(kTmaWarpsMax * 32, TmaMinBlocks<G>::value) k_flux_tma(PairArgs<float> a, FluxExtra<float> x,
                                                   float* __restrict__ pairbuf,
                                                   const __grid_constant__ CUtensorMap rows, int* err_flag,
                                                   unsigned long long budget) {
     using R = PackedRows<G>;
     constexpr int NC = 4 * G, RW = R::RW;
-    __shared__ __align__(128) float sm[kTmaWarps * R::WF];
-    __shared__ __align__(8) uint64_t bar[kTmaWarps];
+    // dynamic: R::WF floats per warp of the block plus 128 bytes, from which the rows start at
+    // the first 128-byte boundary (the slots of the row gathers are 128-byte aligned)
+    extern __shared__ __align__(128) float sm_dyn[];
+    __shared__ __align__(8) uint64_t bar[kTmaWarpsMax];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t sm0 = smem_u32(sm_dyn);
+    float* sm = sm_dyn + (((sm0 + 127u) & ~127u) - sm0) / 4u;
     float* ws = sm + wid * R::WF;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool act = t < (BINS ? a.count : a.n_pairs);
@@ -785,7 +887,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32, TmaMinBlocks<G>::value) k_flux
 // 16-byte pieces of a slot that lie side by side, so a warp request touches about 32 / GC
 // slots instead of 32.  Same order of additions and subtractions as k_flux_gather.
 template <int GC>
-__global__ void __launch_bounds__(kGatherBlock) k_flux_gather_g(PairArgs<float> a, FluxExtra<float> x,
+__global__ void __launch_bounds__(kGatherBlockMax) k_flux_gather_g(PairArgs<float> a, FluxExtra<float> x,
                                                        const float* __restrict__ rec,
                                                        const float* __restrict__ pairbuf, float* __restrict__ out,
                                                        int g0) {
@@ -798,7 +900,8 @@ __global__ void __launch_bounds__(kGatherBlock) k_flux_gather_g(PairArgs<float> 
     constexpr int NC = 4 * GC;
     const int RS = 4 * a.G;
     const float* pb = pairbuf + 4 * g;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    FluxAcc<float> acc;
+    acc.zero();
     const int64_t r0 = a.row_off[i], s0 = a.up_off[i], s1 = a.up_off[i + 1];
     int64_t sl = s0;
     for (; sl + 8 <= s1; sl += 8) {   // eight loads in flight, added in order
@@ -806,15 +909,12 @@ __global__ void __launch_bounds__(kGatherBlock) k_flux_gather_g(PairArgs<float> 
 #pragma unroll
         for (int u = 0; u < 8; ++u) vload<4>(pb + (sl + u) * NC, p[u]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] += p[u][c];
+        for (int u = 0; u < 8; ++u) acc.add(p[u]);
     }
     for (; sl < s1; ++sl) {
         float phi[4];
         vload<4>(pb + sl * NC, phi);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] += phi[c];
+        acc.add(phi);
     }
     const int nl = a.n_low[i];
     const int32_t* ls = a.low_slot + (r0 - s0);
@@ -827,15 +927,12 @@ __global__ void __launch_bounds__(kGatherBlock) k_flux_gather_g(PairArgs<float> 
 #pragma unroll
         for (int u = 0; u < 8; ++u) vload<4>(pb + (int64_t)q[u] * NC, p[u]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] -= p[u][c];
+        for (int u = 0; u < 8; ++u) acc.sub(p[u]);
     }
     for (; e < nl; ++e) {
         float phi[4];
         vload<4>(pb + (int64_t)ls[e] * NC, phi);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] -= phi[c];
+        acc.sub(phi);
     }
     const float dt = (float)(*x.dt_dev);
     const float f = dt * a.omega[i];
@@ -845,17 +942,7 @@ __global__ void __launch_bounds__(kGatherBlock) k_flux_gather_g(PairArgs<float> 
     float ui[4];
     const int64_t o = i * RS + 4 * (g0 + g);
     vload<4>(rec + o, ui);
-    int nclamp = 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        float v = (ui[c] - f * acc[c]) * sink;
-        if (x.clamp && c == 0 && v < 0.f) {
-            v = 0.f;
-            ++nclamp;
-        }
-        if (x.inj && c == 0) v = (float)__dadd_rn((double)v, x.inj[i * a.G + g0 + g]);
-        ui[c] = v;
-    }
+    const int nclamp = update_group<float>(ui, acc, f, sink, x.clamp, x.inj ? x.inj + i * a.G + g0 + g : nullptr);
     vstore<4>(out + o, ui);
     if (nclamp) atomicAdd(x.clamp_count, (unsigned long long)nclamp);
 }
@@ -892,14 +979,15 @@ rt_status launch_drift(rt_ctx* c, cudaStream_t s, void* rec, const double* v, do
 // a10: energy per group, sum_i V_i E_i,g in double; fixed grid and tree order.
 constexpr int kEnergyBlocks = 512;
 
+// Particles of caller index >= owned (the ghost copies of a domain decomposition) are left out.
 template <class T>
 __global__ void k_energy_part(const T* __restrict__ rec, int RS, const double* __restrict__ V, int64_t n, int G,
-                              double* part) {
+                              const int32_t* __restrict__ perm, int64_t owned, double* part) {
     __shared__ double sm[256];
     for (int g = 0; g < G; ++g) {
         double s = 0.0;
         for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
-            s += V[p] * (double)rec[p * RS + 4 * g];
+            if (owned >= n || perm[p] < owned) s += V[p] * (double)rec[p * RS + 4 * g];
         sm[threadIdx.x] = s;
         __syncthreads();
         for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -952,25 +1040,27 @@ static void launch_gradient_t(rt_ctx* c, cudaStream_t s, T* rec, bool packed = f
             if (c->tune.gradient_variant == 2 && gc > 1) {
                 // warps of 32 / gc particles: ceil(n / (32 / gc)) warps of 32 lanes
                 const int64_t warps = (c->n + 32 / gc - 1) / (32 / gc);
-                unsigned nbs = nblk(warps * 32, kGradBlock);
+                const int gb = grad_block(c);
+                unsigned nbs = nblk(warps * 32, gb);
                 float* gr = c->grad_t.as<float>();
                 switch (gc) {
-                    case 2: k_gradient_s<2><<<nbs, kGradBlock, 0, s>>>(a, rec, gr, g0); break;
-                    case 3: k_gradient_s<3><<<nbs, kGradBlock, 0, s>>>(a, rec, gr, g0); break;
-                    default: k_gradient_s<4><<<nbs, kGradBlock, 0, s>>>(a, rec, gr, g0); break;
+                    case 2: k_gradient_s<2><<<nbs, gb, 0, s>>>(a, rec, gr, g0); break;
+                    case 3: k_gradient_s<3><<<nbs, gb, 0, s>>>(a, rec, gr, g0); break;
+                    default: k_gradient_s<4><<<nbs, gb, 0, s>>>(a, rec, gr, g0); break;
                 }
                 prof_end(c, s, pr);
                 ++c->launches;
                 continue;
             }
             if (c->tune.gradient_variant >= 1) {
-                unsigned nbg = nblk(c->n * gc, 256);
+                const int gb = c->tune.gradient_block > 0 ? c->tune.gradient_block : 256;
+                unsigned nbg = nblk(c->n * gc, gb);
                 float* gr = c->grad_t.as<float>();
                 switch (gc) {
-                    case 1: k_gradient_g<1><<<nbg, 256, 0, s>>>(a, rec, gr, g0); break;
-                    case 2: k_gradient_g<2><<<nbg, 256, 0, s>>>(a, rec, gr, g0); break;
-                    case 3: k_gradient_g<3><<<nbg, 256, 0, s>>>(a, rec, gr, g0); break;
-                    default: k_gradient_g<4><<<nbg, 256, 0, s>>>(a, rec, gr, g0); break;
+                    case 1: k_gradient_g<1><<<nbg, gb, 0, s>>>(a, rec, gr, g0); break;
+                    case 2: k_gradient_g<2><<<nbg, gb, 0, s>>>(a, rec, gr, g0); break;
+                    case 3: k_gradient_g<3><<<nbg, gb, 0, s>>>(a, rec, gr, g0); break;
+                    default: k_gradient_g<4><<<nbg, gb, 0, s>>>(a, rec, gr, g0); break;
                 }
                 prof_end(c, s, pr);
                 ++c->launches;
@@ -1046,7 +1136,10 @@ static void flux_float(rt_ctx* c, cudaStream_t s, const PairArgs<float>& a, cons
     if (variant == 2) {
         unsigned long long budget = c->cfg.device_wait_budget_cycles ? c->cfg.device_wait_budget_cycles
                                                                      : 4000000000ull;
-        k_flux_tma<GC, HLL><<<nblk(std::max<int64_t>(a.n_pairs, 1), kTmaWarps * 32), kTmaWarps * 32, 0, s>>>(a, x, pb, c->rows_map, c->flags.as<int>() + F_TIMEOUT, budget);
+        const int pw = pair_warps(c);
+        k_flux_tma<GC, HLL><<<nblk(std::max<int64_t>(a.n_pairs, 1), pw * 32), pw * 32,
+                              (size_t)pw * PackedRows<GC>::WF * sizeof(float) + 128, s>>>(
+            a, x, pb, c->rows_map, c->flags.as<int>() + F_TIMEOUT, budget);
     } else if (variant == 1) {
         k_flux_staged<GC, HLL><<<npb, 128, 0, s>>>(a, x, rec, pb, g0);
     } else {
@@ -1055,7 +1148,7 @@ static void flux_float(rt_ctx* c, cudaStream_t s, const PairArgs<float>& a, cons
     prof_end(c, s, pr);
     pr = prof_begin(c, s, RT_KERNEL_FLUX_GATHER);
     if (c->tune.gather_variant == 1)
-        k_flux_gather_g<GC><<<nblk(c->n * GC, kGatherBlock), kGatherBlock, 0, s>>>(a, x, rec, pb, out, g0);
+        k_flux_gather_g<GC><<<nblk(c->n * GC, gather_block(c)), gather_block(c), 0, s>>>(a, x, rec, pb, out, g0);
     else
         k_flux_gather<float, GC><<<nblk(c->n, 128), 128, 0, s>>>(a, x, rec, pb, out, g0);
     prof_end(c, s, pr);
@@ -1178,9 +1271,11 @@ static void bins_flux_tma(rt_ctx* c, cudaStream_t s, const PairArgs<T>& af, cons
         const unsigned long long budget = c->cfg.device_wait_budget_cycles ? c->cfg.device_wait_budget_cycles
                                                                            : 4000000000ull;
         int* ef = c->flags.as<int>() + F_TIMEOUT;
-        const unsigned nbt = nblk(std::max<int64_t>(af.count, 1), kTmaWarps * 32);
-        if (hll) k_flux_tma<GC, true, true><<<nbt, kTmaWarps * 32, 0, s>>>(af, x, pb, c->rows_map, ef, budget);
-        else k_flux_tma<GC, false, true><<<nbt, kTmaWarps * 32, 0, s>>>(af, x, pb, c->rows_map, ef, budget);
+        const int pw = pair_warps(c);
+        const size_t smem = (size_t)pw * PackedRows<GC>::WF * sizeof(float) + 128;
+        const unsigned nbt = nblk(std::max<int64_t>(af.count, 1), pw * 32);
+        if (hll) k_flux_tma<GC, true, true><<<nbt, pw * 32, smem, s>>>(af, x, pb, c->rows_map, ef, budget);
+        else k_flux_tma<GC, false, true><<<nbt, pw * 32, smem, s>>>(af, x, pb, c->rows_map, ef, budget);
     }
 }
 
@@ -1408,12 +1503,13 @@ rt_status set_dense_injection(rt_ctx* c, bool on) {
 rt_status launch_energy(rt_ctx* c, cudaStream_t s, const void* rec, double* out_dev) {
     double* part = c->energy_part.as<double>();
     int RS = 4 * c->cfg.n_groups;
+    const int32_t* perm = c->perm.as<int32_t>();
     if (c->fp64)
         k_energy_part<double><<<kEnergyBlocks, 256, 0, s>>>((const double*)rec, RS, c->V_d.as<double>(), c->n,
-                                                            c->cfg.n_groups, part);
+                                                            c->cfg.n_groups, perm, c->n_owned, part);
     else
         k_energy_part<float><<<kEnergyBlocks, 256, 0, s>>>((const float*)rec, RS, c->V_d.as<double>(), c->n,
-                                                           c->cfg.n_groups, part);
+                                                           c->cfg.n_groups, perm, c->n_owned, part);
     k_energy_final<<<1, 32 * ((c->cfg.n_groups + 31) / 32), 0, s>>>(part, kEnergyBlocks, c->cfg.n_groups, out_dev);
     c->launches += 2;
     RT_CUDA(c, cudaGetLastError());

@@ -12,8 +12,9 @@ import numpy as np
 import torch
 
 from . import (RT_FP32_MIXED, RT_FP64, make_config, rt_adjoint, rt_create, rt_destroy, rt_diagnostics, rt_drift,
-               rt_energy, rt_get_tuning, rt_gradients, rt_neighbours, rt_pairs, rt_particle_fields, rt_set_stream,
-               rt_set_tuning, rt_subcycle, rt_transport_step)
+               rt_energy, rt_get_tuning, rt_gradients, rt_neighbours, rt_neighbours_given_h, rt_pairs,
+               rt_particle_fields, rt_set_owned, rt_set_stream, rt_set_tuning, rt_source_fields, rt_subcycle,
+               rt_transport_step)
 
 
 def _dev(a, dtype, device):
@@ -33,7 +34,7 @@ class Transport:
 
     def __init__(self, x, m=None, xsrc=None, *, n_groups=1, c_red=1.0, eta_res=1.2348, eta_res_star=None,
                  box=(1.0, 1.0, 1.0), periodic=True, precision="fp32", clamp_negative=False, h_tol=1e-6,
-                 h_max_iter=100, device="cuda:0", riemann="glf"):
+                 h_max_iter=100, device="cuda:0", riemann="glf", h=None, hs=None):
         self.device = torch.device(device)
         self.x = _dev(x, torch.float64, self.device)
         self.n = int(self.x.shape[1])
@@ -53,7 +54,33 @@ class Transport:
         with torch.cuda.device(self.device):
             self.ctx = rt_create(self.cfg, self.n, self.n_src, self._stream())
             self.h = torch.empty(self.n, dtype=torch.float64, device=self.device)
-            rt_neighbours(self.ctx, self.x, self.m, self.xsrc if self.n_src else None, self.h)
+            if h is None:
+                rt_neighbours(self.ctx, self.x, self.m, self.xsrc if self.n_src else None, self.h)
+            else:
+                self.rebuild_given_h(h, hs)
+
+    def rebuild_given_h(self, h, hs=None, x=None):
+        """Neighbour search with given smoothing lengths h [N] and source lengths hs [S]
+        (rt_neighbours_given_h)."""
+        if x is not None:
+            self.x = _dev(x, torch.float64, self.device)
+        self._sync_stream()
+        hd = _dev(h, torch.float64, self.device)
+        hsd = _dev(hs, torch.float64, self.device) if self.n_src else None
+        rt_neighbours_given_h(self.ctx, self.x, self.m, self.xsrc if self.n_src else None, hd, hsd)
+        self.h = hd.clone()
+
+    def source_h(self):
+        """Smoothing lengths of the sources [S] (device tensor)."""
+        self._sync_stream()
+        out = torch.zeros(self.n_src, dtype=torch.float64, device=self.device)
+        if self.n_src:
+            rt_source_fields(self.ctx, out)
+        return out
+
+    def set_owned(self, n_owned):
+        """Particles [0, n_owned) are owned; rt_energy sums those only (rt_set_owned)."""
+        rt_set_owned(self.ctx, n_owned)
 
     def _stream(self):
         return torch.cuda.current_stream(self.device).cuda_stream
@@ -159,8 +186,10 @@ class Transport:
         self._sync_stream()
         return rt_diagnostics(self.ctx)
 
-    def set_tuning(self, flux_variant=2, gather_variant=1, gradient_variant=2):
-        rt_set_tuning(self.ctx, flux_variant, gather_variant, gradient_variant)
+    def set_tuning(self, flux_variant=2, gather_variant=1, gradient_variant=2, cell_eighths=0, gradient_block=0,
+                   gather_block=0, pair_warps=0):
+        rt_set_tuning(self.ctx, flux_variant, gather_variant, gradient_variant, cell_eighths, gradient_block,
+                      gather_block, pair_warps)
 
     def tuning(self):
         return rt_get_tuning(self.ctx)

@@ -54,3 +54,15 @@ def test_two_gloo_ranks_take_the_slowest_time_and_sum_units():
             tmax, value = out[r]
             assert tmax == 2.0
             assert value == pytest.approx(1000.0 * 2 / 2.0)
+
+
+def test_gpus_must_match_the_ranks():
+    """A plain `python bench.py --gpus 2` (one rank) refuses to run instead of measuring one
+    replica under an N-GPU label."""
+    import subprocess
+    import sys
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2"], capture_output=True,
+                       text=True, env=env, timeout=120)
+    assert r.returncode != 0
+    assert "--gpus 2 but 1 rank" in r.stderr

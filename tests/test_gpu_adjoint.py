@@ -91,41 +91,65 @@ def test_checkpoint_interval_does_not_change_the_result():
         np.testing.assert_array_equal(x[1], y[1])
 
 
+def kink_free_direction(o, kind, U0, L0, dt, n_sub, eps, w, first_seed):
+    """A seeded direction (dU0, dL) along which n_sub steps cross no branch point of the
+    limiter or the closure within eps (the oracle's kink count, first order), so that central
+    differences of step eps see a smooth map.  U: normal perturbations of U0 on the particles
+    within 0.08 of a point near the loss sphere; L: normal perturbations of two sources'
+    luminosities.  Returns the direction, its seed and how many seeds were rejected."""
+    for seed in range(first_seed, first_seed + 40):
+        rng = np.random.default_rng(seed)
+        if kind == "U":
+            c = 0.5 + rng.uniform(-0.12, 0.12, size=(3, 1))
+            d = w.x - c
+            d -= np.rint(d)
+            near = np.sqrt((d * d).sum(0)) < 0.08
+            vU, vL = rng.normal(size=U0.shape) * U0 * near, np.zeros_like(L0)
+        else:
+            vU = np.zeros_like(U0)
+            vL = np.zeros_like(L0)
+            pick = rng.choice(L0.shape[0], size=2, replace=False)
+            vL[pick] = rng.normal(size=(2, L0.shape[1])) * L0[pick]
+        if o.jvp_kinks(U0, vU, n_sub, dt, L0, vL, None, eps) == 0:
+            return vU, vL, seed, seed - first_seed
+    raise AssertionError("no kink-free direction among 40 seeds")
+
+
 def test_lattice_sources_finite_differences_and_fp32():
     """The multi-source lattice (32^3, 2 groups, 8 sources, 16 sub-cycles, checkpoint every
-    4): central differences with a 1e-6 relative step on the FP64 path, and the FP32
-    adjoint.  The initial state is the workload's scaled by 1e10 (E0 of order one, same pattern), so that a
-    1e-6 relative step of U0 moves the loss well above double-precision resolution."""
+    4): central differences with a 1e-6 relative step on the FP64 path agree with the adjoint
+    to 1e-6 along the luminosities and along U0, and the FP32 adjoint is within 1e-4 of the
+    FP64 one.  The limiter (minmod) and the closure's clip are piecewise smooth: a random
+    direction over the whole state crosses hundreds of their branch points within a 1e-6 step
+    (the oracle counts 550), and a difference quotient across a kink is no derivative.  So the
+    directions are chosen among seeded candidates by the oracle's kink count (zero within the
+    step).  Along L the workload's own state is used (E0 = 1e-10: the loss is then mostly
+    injected energy, and its change stands far above rounding); along U0 that state scaled
+    by 1e10 (E0 of order one, same pattern), for the same reason."""
     _need_gpu()
     w, o, dt, _ = setup(32, alpha=False)
     n_sub, ck = w.n_steps, w.ckpt_every
-    U0 = w.U0 * 1e10
-    dU0, dL, _ = gpu_adjoint(w, dt, None, n_sub, ck, U0=U0)
     wt = loss_weights(w)
-    rng = np.random.default_rng(9)
     t = Transport(w.x, w.m, w.xsrc, n_groups=w.n_groups, precision="fp64", c_red=w.c_red)
     L0 = w.Lsrc
-    for kind in ("L", "U"):
-        if kind == "L":
-            vU, vL = np.zeros_like(U0), rng.normal(size=L0.shape) * L0
-        else:
-            vU, vL = rng.normal(size=U0.shape) * U0, np.zeros_like(L0)
+    eps = 1e-6
+    for kind, U0 in (("L", w.U0), ("U", w.U0 * 1e10)):
+        dU0, dL, _ = gpu_adjoint(w, dt, None, n_sub, ck, U0=U0)
+        vU, vL, seed, rejected = kink_free_direction(o, kind, U0, L0, dt, n_sub, eps, w, 100)
         adj = (dU0 * vU).sum() + (dL * vL).sum()
-        errs = {}
-        for eps in (1e-6, 1e-7, 1e-8):
-            vals = []
-            for sgn in (1, -1):
-                U = t.state(U0 + sgn * eps * vU)
-                t.subcycle(U, n_sub, dt, t.luminosities(L0 + sgn * eps * vL))
-                vals.append((wt * U.cpu().numpy()).sum())
-            fd = (vals[0] - vals[1]) / (2 * eps)
-            errs[eps] = abs(adj - fd) / abs(fd)
-        print(kind, errs)
-        # ~1e8 minmod evaluations: a 1e-6 stencil crosses some of their kinks, so the
-        # agreement improves as the stencil shrinks until rounding takes over
-        assert errs[1e-6] <= 2e-3, (kind, errs)
-        assert min(errs.values()) <= 2e-6, (kind, errs)
+        vals = []
+        for sgn in (1, -1):
+            U = t.state(U0 + sgn * eps * vU)
+            t.subcycle(U, n_sub, dt, t.luminosities(L0 + sgn * eps * vL))
+            vals.append((wt * U.cpu().numpy()).sum())
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        err = abs(adj - fd) / abs(fd)
+        print(kind, "seed", seed, "rejected", rejected, "fd", fd, "rel err", err)
+        assert abs(vals[0] - vals[1]) > 1e-9 * abs(vals[0])    # far above the loss's rounding
+        assert err <= 1e-6, (kind, seed, err)
     t.close()
+    U0 = w.U0 * 1e10
+    dU0, dL, _ = gpu_adjoint(w, dt, None, n_sub, ck, U0=U0)
     dU32, dL32, _ = gpu_adjoint(w, dt, None, n_sub, ck, precision="fp32", U0=U0)
     assert np.linalg.norm(dL32 - dL) <= 1e-4 * np.linalg.norm(dL)
     assert np.linalg.norm(dU32 - dU0) <= 1e-4 * np.linalg.norm(dU0)

@@ -1,0 +1,74 @@
+"""The spatial domain decomposition with the library as every rank's engine.
+
+Two processes share the one GPU, each with its own context, and exchange their ghosts'
+states through gloo on the host between steps (no kernel waits on another process).  The
+decomposed run equals a single context's run of the whole set: FP64 to 1e-12 per element
+and the energy to 1e-13; FP32 within the FP32 bar against the oracle (relative L1 1e-5 per
+component and group after the steps)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import oracle  # noqa: E402
+from paper_2302_12727_gb300 import Transport, domain  # noqa: E402
+
+from test_domain import _case, _free_port  # noqa: E402
+from test_gpu_parity import rel_l1  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _rank_main(rank, ws, port, name, precision, dt, out_path):
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
+    try:
+        torch.cuda.set_device(0)
+        x, m, xsrc, U0, Ls, alpha, G, c, nsteps = _case(name)
+        eng = domain.CudaEngine(G, c, precision=precision, device=torch.device("cuda", 0))
+        D = domain.DistributedTransport(x, m, xsrc, eng, nb=32)
+        U = D.local_state(U0)
+        D.subcycle(U, nsteps, dt, D.local_luminosities(Ls), D.local_alpha(alpha))
+        full = D.gather(U)
+        E = D.energy(U)
+        n_local = D._all_sum(np.eye(ws)[rank] * len(D.plan.local))
+        if rank == 0:
+            np.savez(out_path, U=full, E=E, n_local=n_local)
+        D.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_decomposed_library_run_equals_single_context(tmp_path, precision):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    name, ws = "lattice-48", 2
+    x, m, xsrc, U0, Ls, alpha, G, c, nsteps = _case(name)
+    o = oracle.Oracle(x, m, xsrc, n_groups=G, c_red=c)
+    dt = 0.6 * ((o.V / (4 * np.pi / 3)) ** (1 / 3)).min() / c
+    out = str(tmp_path / "dd")
+    mp.start_processes(_rank_main, args=(ws, _free_port(), name, precision, dt, out), nprocs=ws,
+                       start_method="spawn")
+    r = np.load(out + ".npz")
+    assert r["n_local"].max() < x.shape[1]
+    if precision == "fp64":
+        t = Transport(x, m, xsrc, n_groups=G, c_red=c, precision="fp64")
+        U = t.state(U0)
+        for _ in range(nsteps):
+            t.step(U, dt, t.luminosities(Ls), t.alpha(alpha))
+        ref = U.cpu().numpy()
+        E_ref = t.energy(U)
+        t.close()
+        scale = np.abs(ref).reshape(G, -1).max(axis=1)[:, None, None]
+        err = np.abs(r["U"] - ref) / (1e-12 * np.abs(ref) + 1e-14 * scale)
+        assert err.max() <= 1.0, err.max()
+        np.testing.assert_allclose(r["E"], E_ref, rtol=1e-13)
+    else:
+        ref, _ = o.run(U0, nsteps, dt, Ls, alpha)
+        assert rel_l1(r["U"], ref).max() <= 1e-5
+        np.testing.assert_allclose(r["E"], o.energy(ref), rtol=1e-6)

@@ -37,6 +37,15 @@ def test_energy_static_matches_rt_energy_on_consecutive_calls(precision):
         got = out.cpu().numpy()
         # both sum in double; only the order of the summation differs
         np.testing.assert_allclose(got, want, rtol=1e-13)
+    # after those calls (the first loaded the array), a further call leaves the device's free
+    # memory exactly where it was: it allocated nothing, directly or through the driver
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    rt_energy_static(U, V, n, G, prec, out, stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    np.testing.assert_allclose(out.cpu().numpy(), want, rtol=1e-13)
     t.close()
 
 
