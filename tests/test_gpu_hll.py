@@ -74,6 +74,7 @@ def test_hll_poisson_sine_beam_reduced_and_launch_variants():
             U = t.state(w.U0)
             t.subcycle(U, 5, dt, L, al)
             Ug = U.cpu().numpy().astype(np.float64)
+            # five steps of the per-step FP32 bar (1e-5 each)
             assert rel_l1(Ug, ref).max() <= 5e-5
             for fv in (0, 1, 2):
                 t.set_tuning(fv, 1, 1)

@@ -59,6 +59,7 @@ def test_group_sink_against_oracle():
         else:
             U = t.state(w.U0)
             t.subcycle(U, 5, dt, L)
+            # five steps of the per-step FP32 bar (1e-5 each)
             assert rel_l1(U.cpu().numpy().astype(np.float64), ref).max() <= 5e-5
         # the adjoint covers the grey sink only
         with pytest.raises(RTError):
