@@ -351,6 +351,95 @@ __device__ bool refine_h_warp(const Grid& g, const double* __restrict__ xs, cons
     return okd;
 }
 
+// The same for one warp, walking the candidates once: the double Newton moves h by far less
+// than 1e-4 from the float root, so the particles within 1.0009 of its support radius contain
+// every neighbour of every iteration.  Their exact distances are dealt to the lanes in walk
+// order (candidate c to lane c mod 32) and kept in registers (kRefineSlots a lane); the
+// iterations then sum the spline over them.  A lane that would need more slots, or an
+// iterate beyond that radius, sends the warp to refine_h_warp.
+constexpr int kRefineSlots = 8;
+
+__device__ bool refine_h_warp_cached(const Grid& g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+                                     int64_t n, const HParams& hp, int64_t p, int lane, double& hd, double& om_d) {
+    const uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    const double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
+    const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+    const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
+    const double h_start = hd;
+    const double Rc = kKappa * hd * 1.0009, Rc2 = Rc * Rc;
+    const float Hf = (float)(kKappa * hd) * 1.001f, H2f = Hf * Hf;
+    double r[kRefineSlots];
+    int cnt = 0;
+    bool over = false;
+    int seen = 0;     // candidates of the earlier ranges (walk order)
+    for_each_candidate_range(g, pxf, pyf, pzf, Hf, [&](int b, int e) {
+        const int first = (lane - seen) & 31;    // this lane's first candidate of the range
+        for (int j = b + first; j < e; j += 32) {
+            float dxf = fsep(xq[j], qx, hp.scale[0]);
+            float dyf = fsep(xq[n + j], qy, hp.scale[1]);
+            float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+            if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) continue;
+            double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
+            double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
+            double dz = sep_fast(xs[2 * n + j], pz, g.box[2], half[2], g.periodic);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < Rc2) {
+                if (cnt < kRefineSlots) {
+                    const double rr = sqrt(r2);
+#pragma unroll
+                    for (int k = 0; k < kRefineSlots; ++k)   // static indices keep r in registers
+                        if (k == cnt) r[k] = rr;
+                    ++cnt;
+                } else {
+                    over = true;
+                }
+            }
+        }
+        seen += e - b;
+    });
+    if (__any_sync(0xffffffffu, over)) return refine_h_warp(g, xs, xq, n, hp, p, lane, hd, om_d);
+    double lod = 0.0, hid = INFINITY;
+    bool okd = false, last = false;
+    for (int it = 0; it < 60; ++it) {
+        double H = kKappa * hd;
+        if (H > Rc) {   // beyond the cached radius (never expected): walk again
+            hd = h_start;
+            return refine_h_warp(g, xs, xq, n, hp, p, lane, hd, om_d);
+        }
+        double iH = 1.0 / H;
+        double sw = 0.0, sdw = 0.0;
+#pragma unroll
+        for (int k = 0; k < kRefineSlots; ++k) {
+            if (k < cnt && r[k] < H) {
+                double q = r[k] * iH;
+                double w = spline_w(q);
+                sw += w;
+                sdw += 3.0 * w + q * spline_dw(q);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+            sdw += __shfl_xor_sync(0xffffffffu, sdw, o);
+        }
+        double om = kSigma * iH * iH * iH * sw;
+        double dom = -kKappa * kSigma * iH * iH * iH * iH * sdw;
+        double cb = cbrt(om);
+        double f = hd - hp.eta / cb;
+        double fp = 1.0 + (hp.eta / 3.0) / (cb * om) * dom;
+        om_d = om;
+        if (last) { okd = true; break; }
+        if (f < 0.0) lod = hd; else hid = hd;
+        double step = f / fp;
+        if (fabs(f) <= 1e-15 * hd || (hid - lod) <= 1e-14 * hd) { okd = true; break; }
+        if (fp > 0.0 && fabs(step) <= 1e-11 * hd) last = true;
+        double hn = hd - step;
+        if (!last && (it >= 12 || !(hn > lod && hn < hid) || !(fp > 0.0)))
+            hn = isinf(hid) ? 1.0001 * hd : 0.5 * (lod + hid);
+        hd = hn;
+    }
+    return okd;
+}
+
 __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
                           HParams hp, const double* __restrict__ h_prev, const int32_t* __restrict__ perm,
                           double* h_out, double* omega_out, float* H2f_out, unsigned long long* hminmax, int* flags,
@@ -531,7 +620,7 @@ __global__ void k_h_refine(Grid g, const double* __restrict__ xs, const uint32_t
     for (int64_t t = w0; t < cnt; t += nw) {
         const int64_t p = list[t];
         double hd = h_out[p], om_d = omega_out[p];
-        const bool ok = refine_h_warp(g, xs, xq, n, hp, p, lane, hd, om_d);
+        const bool ok = refine_h_warp_cached(g, xs, xq, n, hp, p, lane, hd, om_d);
         if (lane == 0) {
             if (!ok) atomicExch(&flags[F_NOCONV], 1);
             h_out[p] = hd;
