@@ -497,10 +497,69 @@ def run_ours(args):
         out["fp64_plain"] = run_fp64_plain(w, args, dev, out["ms_per_step"], P)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, args, P)
+    if rank == 0 and ws == 1 and not args.no_secondary and args.workload == "poisson-sine-beam":
+        out["secondary"] = {name: run_secondary(name, args, dev, flush, fp64=(name == "lognormal-sources"))
+                            for name in ("lognormal-sources", "lognormal-sources-large")}
     if ws > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_secondary(name, args, dev, flush, fp64=False, steps=2, warmup=1):
+    """The larger workloads of the same path, measured after the main line (not part of its
+    value): per step rt_neighbours + rt_subcycle(n_sub) + rt_energy with the FP32 graph path
+    and the library's default launch shapes, CUDA events, the L2 flushed between steps; with
+    fp64, one step of the plain FP64 path launched step by step for the speed-up."""
+    import torch
+    from paper_2302_12727_gb300 import Transport
+    t0 = time.perf_counter()
+    w = workload(name)
+    t_gen = time.perf_counter() - t0
+    G, n_sub = w.n_groups, w.n_steps
+    stream = torch.cuda.current_stream(dev)
+    res = {"particles": w.n, "groups": G, "sub_cycles": n_sub, "sources": w.n_src, "input_generation_s": t_gen}
+    for prec in (("fp32", "fp64") if fp64 else ("fp32",)):
+        T = Transport(w.x, w.m, w.xsrc, n_groups=G, c_red=w.c_red, precision=prec, device=dev)
+        d = T.diagnostics()
+        P = d["n_pairs"]
+        dt = args.cfl * d["dx_min"] / w.c_red
+        alpha = None
+        if w.kappa:
+            alpha = (w.kappa * torch.as_tensor(w.m, device=dev) * T.fields()["omega"]).contiguous()
+        L = T.luminosities(w.Lsrc)
+        U0 = T.state(w.U0)
+        U = U0.clone()
+        times = []
+        n_st = 1 if prec == "fp64" else steps
+        for k in range((0 if prec == "fp64" else warmup) + n_st):
+            U.copy_(U0)
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            T.rebuild()
+            if prec == "fp64":
+                for _ in range(n_sub):
+                    T.step(U, dt, L, alpha)
+            else:
+                T.subcycle(U, n_sub, dt, L, alpha)
+            T.energy(U)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= (0 if prec == "fp64" else warmup):
+                times.append(e0.elapsed_time(e1))
+        ms = sum(times) / len(times)
+        res[prec] = {"ms_per_step": ms, "value": P * G * n_sub / (ms / 1e3), "unit": UNIT, "pairs": P,
+                     "steps": len(times), "path": "plain per-step FP64 launches" if prec == "fp64" else
+                     "FP32 graph-captured sub-cycles"}
+        T.close()
+        del U, U0
+        torch.cuda.empty_cache()
+    if fp64:
+        res["speedup_of_fp32_graph"] = res["fp64"]["ms_per_step"] / res["fp32"]["ms_per_step"]
+    return res
 
 
 def run_e2e(args, T, w, dt, alpha, L, dev, flush, P):
@@ -710,6 +769,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary measurements of the 2,097,152- and 16,777,216-particle workloads")
     ap.add_argument("--riemann", default="glf", choices=["glf", "hll"],
                     help="pair-flux Riemann solver (Eq. riemann-GLF or Eq. riemann-HLL)")
     ap.add_argument("--tuning", default="", help="flux,gather,gradient variants of the float pair kernels")

@@ -491,6 +491,43 @@ def test_full_size_per_step_parity(name):
     t.close()
 
 
+def test_largest_set_float_against_double_at_full_size():
+    """The 16,777,216-particle clustered set (lognormal density with sigma_ln = 2, about a
+    hundredfold range of h, 1000 sources, grey sink proportional to the density) at full size,
+    where the oracle is out of reach.  Both precisions decide every pair with double smoothing
+    lengths, and the double path's lists and steps equal the oracle's on the smaller clustered
+    set (test_sorted_pair_build_on_clustered_particles): here the float context's pair lists
+    equal the double context's exactly, and one float step from the same state agrees with the
+    double step within the float bar (relative L1 1e-5 per component and group)."""
+    _need_gpu()
+    if torch.cuda.mem_get_info()[0] < 120e9:
+        pytest.skip("needs about 120 GB of free device memory")
+    w = W.lognormal_sources_large()
+    n, G = w.n, w.n_groups
+    keys, U = {}, {}
+    for prec in ("fp64", "fp32"):
+        t = Transport(w.x, w.m, w.xsrc, n_groups=G, precision=prec, c_red=w.c_red)
+        d = t.diagnostics()
+        off, cols = t.pairs()
+        rows = torch.repeat_interleave(torch.arange(n, device=off.device), off[1:] - off[:-1])
+        keys[prec] = torch.sort(rows * n + cols.long()).values
+        del rows, off, cols
+        if prec == "fp64":
+            dt = 0.9 * d["dx_min"] / w.c_red
+            alpha = (w.kappa * torch.as_tensor(w.m, device="cuda") * t.fields()["omega"]).contiguous()
+        Ug = t.state(w.U0)
+        t.step(Ug, dt, t.luminosities(w.Lsrc), alpha)
+        U[prec] = Ug.double().cpu().numpy()
+        t.close()
+        del Ug
+        torch.cuda.empty_cache()
+    assert torch.equal(keys["fp64"], keys["fp32"])
+    del keys
+    err = rel_l1(U["fp32"], U["fp64"])
+    nz = np.abs(U["fp64"].reshape(-1, n)).sum(1) > 0
+    assert err[nz].max() <= 1e-5, err
+
+
 def _brute_force_pairs_check(x, h, off, cols):
     """The lists (caller indices, CSR) hold exactly the pairs r_ij < max(H_i, H_j), H = H/h h,
     in the periodic unit box; pairs within 1e-12 of the radius may go either way."""
