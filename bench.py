@@ -410,7 +410,10 @@ def run_ours(args):
                  "frac": a / peak if a else None, "traffic": traffic_b, "avg_launch_ms": t_s * 1e3 if t_s else None,
                  "algorithmic_bytes_per_launch": alg_bytes,
                  "hbm_frac_of_" + peak_kind: alg_bytes / t_s / 1e9 / hbm_gbs if t_s else None,
-                 "traffic_over_algorithmic_bytes": traffic_b / alg_bytes if traffic_b else None}
+                 "traffic_over_algorithmic_bytes": traffic_b / alg_bytes if traffic_b else None,
+                 # the DRAM bytes the kernel actually moves (ncu, cold cache) over its live time
+                 "dram_gbs": traffic_b / t_s / 1e9 if (traffic_b and t_s) else None,
+                 "dram_frac_of_" + peak_kind: traffic_b / t_s / 1e9 / hbm_gbs if (traffic_b and t_s) else None}
             d["flops_per_launch" if unit == "TFLOP/s" else "bytes_per_launch"] = work
             return d
 
