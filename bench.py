@@ -444,6 +444,7 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
+            "value_per_group": value / G,
             "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": w.name, "particles": n, "groups": G, "sub_cycles": n_sub,

@@ -69,6 +69,16 @@ def _free_port():
 
 
 def _case(name):
+    if name == "lattice-40-walls":
+        # non-periodic unit box (walls: truncated supports), two groups, one source
+        rng = np.random.default_rng(77)
+        x = W.jittered_lattice(40, 0.2, rng)
+        n = x.shape[1]
+        G = 2
+        U0 = np.zeros((G, 4, n))
+        U0[:, 0] = 1e-3 * (1 + 0.2 * rng.uniform(-1, 1, size=(G, n)))
+        U0[:, 1:] = 0.3 * U0[:, :1] * rng.normal(size=(G, 3, n)) / np.sqrt(3)
+        return x, np.full(n, 1.0 / n), np.array([[0.3], [0.6], [0.5]]), U0, np.array([[1.0, 2.0]]), None, G, 1.0, 3
     if name == "lattice-point-source":
         w = W.lattice_point_source()
         return w.x, w.m, w.xsrc, w.U0, w.Lsrc, None, w.n_groups, w.c_red, 4
@@ -90,9 +100,11 @@ def _rank_main(rank, ws, port, name, out_path):
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
     try:
         x, m, xsrc, U0, Ls, alpha, G, c, nsteps = _case(name)
-        eng = OracleEngine(G, c)
+        periodic = name != "lattice-40-walls"
+        eng = OracleEngine(G, c, periodic=periodic)
         dt_ = 0.6 * float(np.load(out_path + ".dt.npy"))
-        D = domain.DistributedTransport(x, m, xsrc, eng, nb=16 if name == "lattice-point-source" else 32)
+        D = domain.DistributedTransport(x, m, xsrc, eng, nb=16 if name == "lattice-point-source" else 32,
+                                        periodic=periodic)
         U = D.local_state(U0)
         D.subcycle(U, nsteps, dt_, D.local_luminosities(Ls), D.local_alpha(alpha))
         full = D.gather(U)
@@ -107,10 +119,11 @@ def _rank_main(rank, ws, port, name, out_path):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name, ws", [("lattice-point-source", 2), ("lattice-48", 2), ("lattice-48", 4)])
+@pytest.mark.parametrize("name, ws", [("lattice-point-source", 2), ("lattice-48", 2), ("lattice-48", 4),
+                                      ("lattice-40-walls", 3)])
 def test_decomposed_oracle_run_equals_single_rank(tmp_path, name, ws):
     x, m, xsrc, U0, Ls, alpha, G, c, nsteps = _case(name)
-    o = oracle.Oracle(x, m, xsrc, n_groups=G, c_red=c)
+    o = oracle.Oracle(x, m, xsrc, n_groups=G, c_red=c, periodic=name != "lattice-40-walls")
     dxm = ((o.V / (4 * np.pi / 3)) ** (1 / 3)).min()
     out = str(tmp_path / "dd")
     np.save(out + ".dt.npy", np.array(dxm / c))
