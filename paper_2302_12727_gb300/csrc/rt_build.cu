@@ -197,18 +197,20 @@ __global__ void k_cell_start(const uint32_t* __restrict__ keys, int64_t n, int64
 
 __global__ void k_gather_positions(const double* __restrict__ x, const double* __restrict__ m,
                                    const int32_t* __restrict__ perm, int64_t n, double q0, double q1, double q2,
-                                   double* xs, uint32_t* xq, double* ms, int32_t* inv_perm) {
+                                   double* xs, uint4* xq, double* ms, int32_t* inv_perm) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
     int64_t i = perm[p];
     double qs[3] = {q0, q1, q2};
+    uint32_t qv[3];
     for (int a = 0; a < 3; ++a) {
         double v = x[a * n + i];
         xs[a * n + p] = v;
         double f = floor(v * qs[a]);
         f = fmin(fmax(f, 0.0), 4294967295.0);
-        xq[a * n + p] = (uint32_t)f;
+        qv[a] = (uint32_t)f;
     }
+    xq[p] = make_uint4(qv[0], qv[1], qv[2], 0u);   // one 16-byte record a particle for the walks
     ms[p] = m ? m[i] : 0.0;
     inv_perm[i] = (int32_t)p;
 }
@@ -237,9 +239,10 @@ __device__ __forceinline__ float fsep(uint32_t a, uint32_t b, float scale) { ret
 
 // Newton in double from hd on the exact separations of particle p; returns false if it did
 // not converge.  On return hd is the root and om_d = omega(hd).
-__device__ bool refine_h_double(const Grid& g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+__device__ bool refine_h_double(const Grid& g, const double* __restrict__ xs, const uint4* __restrict__ xq,
                                 int64_t n, const HParams& hp, int64_t p, double& hd, double& om_d) {
-    const uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    const uint4 q4p = xq[p];
+    const uint32_t qx = q4p.x, qy = q4p.y, qz = q4p.z;
     const double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
     const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
     double lod = 0.0, hid = INFINITY;
@@ -253,9 +256,9 @@ __device__ bool refine_h_double(const Grid& g, const double* __restrict__ xs, co
         float H2f = Hf * Hf;
         double sw = 0.0, sdw = 0.0;
         for_each_candidate(g, pxf, pyf, pzf, Hf, [&](int j) {
-            float dxf = fsep(xq[j], qx, hp.scale[0]);
-            float dyf = fsep(xq[n + j], qy, hp.scale[1]);
-            float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+            float dxf = fsep(xq[j].x, qx, hp.scale[0]);
+            float dyf = fsep(xq[j].y, qy, hp.scale[1]);
+            float dzf = fsep(xq[j].z, qz, hp.scale[2]);
             if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) return;
             double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
             double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
@@ -295,9 +298,10 @@ __device__ bool refine_h_double(const Grid& g, const double* __restrict__ xs, co
 // combining their sums by a fixed butterfly, whose result is the same in every lane: the
 // lanes then take the same steps.  Used where few particles need it (k_h_refine), so that the double arithmetic,
 // slow on this GPU, is spread over many threads.
-__device__ bool refine_h_warp(const Grid& g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+__device__ bool refine_h_warp(const Grid& g, const double* __restrict__ xs, const uint4* __restrict__ xq,
                               int64_t n, const HParams& hp, int64_t p, int lane, double& hd, double& om_d) {
-    const uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    const uint4 q4p = xq[p];
+    const uint32_t qx = q4p.x, qy = q4p.y, qz = q4p.z;
     const double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
     const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
     double lod = 0.0, hid = INFINITY;
@@ -312,9 +316,9 @@ __device__ bool refine_h_warp(const Grid& g, const double* __restrict__ xs, cons
         double sw = 0.0, sdw = 0.0;
         for_each_candidate_range(g, pxf, pyf, pzf, Hf, [&](int b, int e) {
           for (int j = b + lane; j < e; j += 32) {
-            float dxf = fsep(xq[j], qx, hp.scale[0]);
-            float dyf = fsep(xq[n + j], qy, hp.scale[1]);
-            float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+            float dxf = fsep(xq[j].x, qx, hp.scale[0]);
+            float dyf = fsep(xq[j].y, qy, hp.scale[1]);
+            float dzf = fsep(xq[j].z, qz, hp.scale[2]);
             if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) continue;
             double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
             double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
@@ -359,9 +363,10 @@ __device__ bool refine_h_warp(const Grid& g, const double* __restrict__ xs, cons
 // iterate beyond that radius, sends the warp to refine_h_warp.
 constexpr int kRefineSlots = 8;
 
-__device__ bool refine_h_warp_cached(const Grid& g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+__device__ bool refine_h_warp_cached(const Grid& g, const double* __restrict__ xs, const uint4* __restrict__ xq,
                                      int64_t n, const HParams& hp, int64_t p, int lane, double& hd, double& om_d) {
-    const uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    const uint4 q4p = xq[p];
+    const uint32_t qx = q4p.x, qy = q4p.y, qz = q4p.z;
     const double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
     const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
     const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
@@ -375,9 +380,9 @@ __device__ bool refine_h_warp_cached(const Grid& g, const double* __restrict__ x
     for_each_candidate_range(g, pxf, pyf, pzf, Hf, [&](int b, int e) {
         const int first = (lane - seen) & 31;    // this lane's first candidate of the range
         for (int j = b + first; j < e; j += 32) {
-            float dxf = fsep(xq[j], qx, hp.scale[0]);
-            float dyf = fsep(xq[n + j], qy, hp.scale[1]);
-            float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+            float dxf = fsep(xq[j].x, qx, hp.scale[0]);
+            float dyf = fsep(xq[j].y, qy, hp.scale[1]);
+            float dzf = fsep(xq[j].z, qz, hp.scale[2]);
             if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) continue;
             double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
             double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
@@ -440,7 +445,7 @@ __device__ bool refine_h_warp_cached(const Grid& g, const double* __restrict__ x
     return okd;
 }
 
-__global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
+__global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint4* __restrict__ xq, int64_t n,
                           HParams hp, const double* __restrict__ h_prev, const int32_t* __restrict__ perm,
                           double* h_out, double* omega_out, float* H2f_out, unsigned long long* hminmax, int* flags,
                           int32_t* refine_list, int* refine_count) {
@@ -450,7 +455,8 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
     if (active) {
         const float kapf = (float)kKappa;
         const float sigf = (float)kSigma;
-        uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+        const uint4 q4p = xq[p];
+        uint32_t qx = q4p.x, qy = q4p.y, qz = q4p.z;
         double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
         float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
 
@@ -480,9 +486,9 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
             float sdw = 0.f;
             bool nb = false;
             for_each_candidate(g, pxf, pyf, pzf, H, [&](int j) {
-                float dx = fsep(xq[j], qx, hp.scale[0]);
-                float dy = fsep(xq[n + j], qy, hp.scale[1]);
-                float dz = fsep(xq[2 * n + j], qz, hp.scale[2]);
+                float dx = fsep(xq[j].x, qx, hp.scale[0]);
+                float dy = fsep(xq[j].y, qy, hp.scale[1]);
+                float dz = fsep(xq[j].z, qz, hp.scale[2]);
                 float r2 = dx * dx + dy * dy + dz * dz;
                 nb |= fabsf(r2 - H2) < kNearBand * H2;
                 if (r2 < H2) {
@@ -550,7 +556,7 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint32_t*
 // and omega_i = sum_j W(r_ij, h_i) at it, evaluated like the last iteration of the solve (the
 // float path: float weights summed in double; the FP64 path: double).  Non-positive or
 // non-finite h sets the F_BADH flag.
-__global__ void k_h_given(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
+__global__ void k_h_given(Grid g, const double* __restrict__ xs, const uint4* __restrict__ xq, int64_t n,
                           HParams hp, const double* __restrict__ h_in, const int32_t* __restrict__ perm,
                           double* h_out, double* omega_out, float* H2f_out, unsigned long long* hminmax, int* flags) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -562,7 +568,8 @@ __global__ void k_h_given(Grid g, const double* __restrict__ xs, const uint32_t*
             atomicExch(&flags[F_BADH], 1);
             hd = hp.h0;
         }
-        const uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+        const uint4 q4p = xq[p];
+        const uint32_t qx = q4p.x, qy = q4p.y, qz = q4p.z;
         const double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
         const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
         const double H = kKappa * hd, iH = 1.0 / H, H2 = H * H;
@@ -571,9 +578,9 @@ __global__ void k_h_given(Grid g, const double* __restrict__ xs, const uint32_t*
             const double half[3] = {0.5 * g.box[0], 0.5 * g.box[1], 0.5 * g.box[2]};
             const float Hf = (float)H * 1.001f, H2f = Hf * Hf;
             for_each_candidate(g, pxf, pyf, pzf, Hf, [&](int j) {
-                float dxf = fsep(xq[j], qx, hp.scale[0]);
-                float dyf = fsep(xq[n + j], qy, hp.scale[1]);
-                float dzf = fsep(xq[2 * n + j], qz, hp.scale[2]);
+                float dxf = fsep(xq[j].x, qx, hp.scale[0]);
+                float dyf = fsep(xq[j].y, qy, hp.scale[1]);
+                float dzf = fsep(xq[j].z, qz, hp.scale[2]);
                 if (dxf * dxf + dyf * dyf + dzf * dzf >= H2f) return;
                 double dx = sep_fast(xs[j], px, g.box[0], half[0], g.periodic);
                 double dy = sep_fast(xs[n + j], py, g.box[1], half[1], g.periodic);
@@ -584,9 +591,9 @@ __global__ void k_h_given(Grid g, const double* __restrict__ xs, const uint32_t*
         } else {
             const float Hf = (float)H, iHf = 1.f / Hf, H2f = Hf * Hf;
             for_each_candidate(g, pxf, pyf, pzf, Hf, [&](int j) {
-                float dx = fsep(xq[j], qx, hp.scale[0]);
-                float dy = fsep(xq[n + j], qy, hp.scale[1]);
-                float dz = fsep(xq[2 * n + j], qz, hp.scale[2]);
+                float dx = fsep(xq[j].x, qx, hp.scale[0]);
+                float dy = fsep(xq[j].y, qy, hp.scale[1]);
+                float dz = fsep(xq[j].z, qz, hp.scale[2]);
                 float r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < H2f) sw += (double)spline_w(sqrtf(r2) * iHf);
             });
@@ -610,7 +617,7 @@ __global__ void k_h_given(Grid g, const double* __restrict__ xs, const uint32_t*
 // (grid-stride over the list; its order is arbitrary, and each particle's result depends on
 // its own position and neighbours only).  The smallest and largest h are widened to the
 // refined values (the pair search's bound must cover them).
-__global__ void k_h_refine(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq, int64_t n,
+__global__ void k_h_refine(Grid g, const double* __restrict__ xs, const uint4* __restrict__ xq, int64_t n,
                            HParams hp, const int32_t* __restrict__ list, const int* __restrict__ count, double* h_out,
                            double* omega_out, float* H2f_out, unsigned long long* hminmax, int* flags) {
     const int lane = threadIdx.x & 31;
@@ -728,14 +735,15 @@ __global__ void k_block_reach(const unsigned* __restrict__ hb, Blocks bk, float*
 // entries of row p to cols[p cap ...] and raises *row_max to the longest row.  FILL = true
 // writes row p to cols[row_off[p] ...].  Both walk the candidates in the same order.
 template <bool FILL>
-__global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+__global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint4* __restrict__ xq,
                         const double* __restrict__ h, const float* __restrict__ H2f, int64_t n, PairParams pp,
                         Blocks bk, const float* __restrict__ reach, int32_t* counts,
                         const int64_t* __restrict__ row_off, int32_t* cols, int cap = 0, int* row_max = nullptr) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int cnt = 0;
     if (p < n) {
-        uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+        const uint4 q4p = xq[p];
+        uint32_t qx = q4p.x, qy = q4p.y, qz = q4p.z;
         double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
         const float H2i = H2f[p];
         const float Hr = reach[block_of(bk, px, py, pz)];
@@ -743,9 +751,9 @@ __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint32_t* _
         int64_t base = FILL ? row_off[p] : p * (int64_t)cap;
         for_each_candidate(g, (float)px, (float)py, (float)pz, R, [&](int j) {
             if (j == p) return;
-            float dx = fsep(xq[j], qx, pp.scale[0]);
-            float dy = fsep(xq[n + j], qy, pp.scale[1]);
-            float dz = fsep(xq[2 * n + j], qz, pp.scale[2]);
+            float dx = fsep(xq[j].x, qx, pp.scale[0]);
+            float dy = fsep(xq[j].y, qy, pp.scale[1]);
+            float dz = fsep(xq[j].z, qz, pp.scale[2]);
             float r2f = dx * dx + dy * dy + dz * dz;
             float H2m = fmaxf(H2i, H2f[j]);
             bool in;
@@ -833,21 +841,22 @@ __global__ void k_low_slots(const int64_t* __restrict__ row_off, const int32_t* 
 // and removing duplicates gives the same symmetric lists, rows ascending, without any
 // particle searching out to the largest H of the set.
 template <bool FILL>
-__global__ void k_pairs_gather(Grid g, const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+__global__ void k_pairs_gather(Grid g, const double* __restrict__ xs, const uint4* __restrict__ xq,
                                const double* __restrict__ h, const float* __restrict__ H2f, int64_t n, PairParams pp,
                                int32_t* counts, const int64_t* __restrict__ off, uint64_t* keys) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
-    uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    const uint4 q4p = xq[p];
+    uint32_t qx = q4p.x, qy = q4p.y, qz = q4p.z;
     double px = xs[p], py = xs[n + p], pz = xs[2 * n + p];
     const float H2i = H2f[p];
     int cnt = 0;
     int64_t base = FILL ? off[p] : 0;
     for_each_candidate(g, (float)px, (float)py, (float)pz, sqrtf(H2i) * 1.0001f, [&](int j) {
         if (j == p) return;
-        float dx = fsep(xq[j], qx, pp.scale[0]);
-        float dy = fsep(xq[n + j], qy, pp.scale[1]);
-        float dz = fsep(xq[2 * n + j], qz, pp.scale[2]);
+        float dx = fsep(xq[j].x, qx, pp.scale[0]);
+        float dy = fsep(xq[j].y, qy, pp.scale[1]);
+        float dz = fsep(xq[j].z, qz, pp.scale[2]);
         float r2f = dx * dx + dy * dy + dz * dz;
         bool in;
         if (r2f < H2i * (1.f - 1e-5f)) in = true;
@@ -901,13 +910,13 @@ __device__ void sym3_eigs(double a, double b, double c, double d, double e, doub
 }
 
 template <class T>
-__device__ __forceinline__ void store_pos(void* pos, int64_t p, const double* xs, const uint32_t* xq, int64_t n);
+__device__ __forceinline__ void store_pos(void* pos, int64_t p, const double* xs, const uint4* xq, int64_t n);
 template <>
-__device__ __forceinline__ void store_pos<float>(void* pos, int64_t p, const double*, const uint32_t* xq, int64_t n) {
-    reinterpret_cast<uint4*>(pos)[p] = make_uint4(xq[p], xq[n + p], xq[2 * n + p], 0u);
+__device__ __forceinline__ void store_pos<float>(void* pos, int64_t p, const double*, const uint4* xq, int64_t n) {
+    reinterpret_cast<uint4*>(pos)[p] = xq[p];
 }
 template <>
-__device__ __forceinline__ void store_pos<double>(void* pos, int64_t p, const double* xs, const uint32_t*, int64_t n) {
+__device__ __forceinline__ void store_pos<double>(void* pos, int64_t p, const double* xs, const uint4*, int64_t n) {
     double2* d = reinterpret_cast<double2*>(pos) + 2 * p;
     d[0] = make_double2(xs[p], xs[n + p]);
     d[1] = make_double2(xs[2 * n + p], 0.0);
@@ -929,12 +938,12 @@ struct Kahan {
 };
 
 template <class T>
-__device__ __forceinline__ void accumulate_E(const double* xs, const uint32_t* xq, const double* box, int periodic,
+__device__ __forceinline__ void accumulate_E(const double* xs, const uint4* xq, const double* box, int periodic,
                                              float s0, float s1, float s2, int64_t n, int64_t p, double H,
                                              const int64_t* row_off, const int32_t* cols, double E[6]);
 
 template <>
-__device__ __forceinline__ void accumulate_E<double>(const double* xs, const uint32_t*, const double* box,
+__device__ __forceinline__ void accumulate_E<double>(const double* xs, const uint4*, const double* box,
                                                      int periodic, float, float, float, int64_t n, int64_t p,
                                                      double H, const int64_t* row_off, const int32_t* cols,
                                                      double E[6]) {
@@ -956,15 +965,16 @@ __device__ __forceinline__ void accumulate_E<double>(const double* xs, const uin
 }
 
 template <>
-__device__ __forceinline__ void accumulate_E<float>(const double*, const uint32_t* xq, const double*, int, float s0,
+__device__ __forceinline__ void accumulate_E<float>(const double*, const uint4* xq, const double*, int, float s0,
                                                     float s1, float s2, int64_t n, int64_t p, double H,
                                                     const int64_t* row_off, const int32_t* cols, double E[6]) {
-    uint32_t qx = xq[p], qy = xq[n + p], qz = xq[2 * n + p];
+    const uint4 q4p = xq[p];
+    uint32_t qx = q4p.x, qy = q4p.y, qz = q4p.z;
     float iH = (float)(1.0 / H), H2 = (float)(H * H);
     Kahan acc[6];
     for (int64_t e = row_off[p]; e < row_off[p + 1]; ++e) {
         int j = cols[e];
-        float dx = fsep(xq[j], qx, s0), dy = fsep(xq[n + j], qy, s1), dz = fsep(xq[2 * n + j], qz, s2);
+        float dx = fsep(xq[j].x, qx, s0), dy = fsep(xq[j].y, qy, s1), dz = fsep(xq[j].z, qz, s2);
         float r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 < H2)) continue;
         float w = spline_w(sqrtf(r2) * iH);
@@ -978,7 +988,7 @@ __device__ __forceinline__ void accumulate_E<float>(const double*, const uint32_
 // Bp = V^2 sigma / H^3 B (so that V_i psitilde_j(x_i) = Bp_i d w(q)), and omega; reduces
 // max cond_2(E_i) and min V_i into red[2], red[3].
 template <class T>
-__global__ void k_geometry(const double* __restrict__ xs, const uint32_t* __restrict__ xq,
+__global__ void k_geometry(const double* __restrict__ xs, const uint4* __restrict__ xq,
                            const double* __restrict__ h, const double* __restrict__ omega,
                            const int64_t* __restrict__ row_off, const int32_t* __restrict__ cols, int64_t n, double b0,
                            double b1, double b2, int periodic, float s0, float s1, float s2, double* V_out,
@@ -1455,7 +1465,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     RT_TRY(ensure(c, c->inv_perm, n * 4, "inv_perm"));
     RT_TRY(ensure(c, c->cell_start, (ncells + 1) * 4, "cells"));
     RT_TRY(ensure(c, c->xs_d, 3 * n * 8, "positions"));
-    RT_TRY(ensure(c, c->xq, 3 * n * 4, "positions"));
+    RT_TRY(ensure(c, c->xq, 16 * n, "positions"));
     RT_TRY(ensure(c, c->m_s, n * 8, "masses"));
     RT_TRY(ensure(c, c->h_d, n * 8, "h"));
     RT_TRY(ensure(c, c->H2f, n * 4, "h"));
@@ -1507,7 +1517,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         qscale[a] = (float)(cfg.box[a] / units);
     }
     k_gather_positions<<<nblk(n, B), B, 0, st>>>(x, m, c->perm.as<int32_t>(), n, qmul[0], qmul[1], qmul[2],
-                                                  c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->m_s.as<double>(),
+                                                  c->xs_d.as<double>(), c->xq.as<uint4>(), c->m_s.as<double>(),
                                                   c->inv_perm.as<int32_t>());
     RT_CUDA(c, cudaGetLastError());
     c->launches += 3;   // keys, cell table, gather
@@ -1527,11 +1537,11 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     int* refine_count = flags + F_REFINE;
     if (h_in) {
         hp.refine64 = c->fp64 ? 1 : 0;   // omega in the working path's arithmetic
-        k_h_given<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp, h_in,
+        k_h_given<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint4>(), n, hp, h_in,
                                                  c->perm.as<int32_t>(), c->h_d.as<double>(), c->omega_d.as<double>(),
                                                  c->H2f.as<float>(), red, flags);
     } else {
-        k_h_solve<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp,
+        k_h_solve<<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint4>(), n, hp,
                                                  warm ? c->h_prev.as<double>() : nullptr, c->perm.as<int32_t>(),
                                                  c->h_d.as<double>(), c->omega_d.as<double>(), c->H2f.as<float>(), red,
                                                  flags, c->idx_in.as<int32_t>(), refine_count);
@@ -1539,7 +1549,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     RT_CUDA(c, cudaGetLastError());
     c->launches += 1;
     if (!c->fp64 && !h_in) {
-        k_h_refine<<<(unsigned)c->sm_count * 8, 256, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(), n, hp,
+        k_h_refine<<<(unsigned)c->sm_count * 8, 256, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint4>(), n, hp,
                                                   c->idx_in.as<int32_t>(), refine_count, c->h_d.as<double>(),
                                                   c->omega_d.as<double>(), c->H2f.as<float>(), red, flags);
         RT_CUDA(c, cudaGetLastError());
@@ -1597,7 +1607,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         if (cap > 0) RT_TRY(ensure(c, c->cols_cap, (size_t)n * cap * 4, "pair rows"));
         int* row_max = c->flags.as<int>() + F_ROWMAX;
         RT_CUDA(c, cudaMemsetAsync(row_max, 0, 4, st));
-        k_pairs<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
+        k_pairs<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint4>(),
                                                       c->h_d.as<double>(), c->H2f.as<float>(), n, pp, bk, reach,
                                                       c->counts.as<int32_t>(), nullptr,
                                                       cap > 0 ? c->cols_cap.as<int32_t>() : nullptr, cap, row_max);
@@ -1616,7 +1626,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
             k_rows_compact<<<nblk(n, 128), 128, 0, st>>>(c->cols_cap.as<int32_t>(), cap, c->row_off.as<int64_t>(), n,
                                                           c->cols_tmp.as<int32_t>());
         } else {
-            k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
+            k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint4>(),
                                                          c->h_d.as<double>(), c->H2f.as<float>(), n, pp, bk, reach,
                                                          nullptr, c->row_off.as<int64_t>(), c->cols_tmp.as<int32_t>());
         }
@@ -1638,7 +1648,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
                                                       c->row_off.as<int64_t>() + 1, st));
     } else {
         int64_t* goff = c->row_off.as<int64_t>();      // gather offsets first, CSR offsets after
-        k_pairs_gather<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
+        k_pairs_gather<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint4>(),
                                                              c->h_d.as<double>(), c->H2f.as<float>(), n, pp,
                                                              c->counts.as<int32_t>(), nullptr, nullptr);
         RT_CUDA(c, cudaMemsetAsync(c->counts.as<int32_t>() + n, 0, 4, st));
@@ -1651,7 +1661,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         const int64_t K = std::max<int64_t>(2 * Mg, 1);
         RT_TRY(ensure(c, c->pkeys, K * 8, "pair keys"));
         RT_TRY(ensure(c, c->pkeys_alt, K * 8, "pair keys"));
-        k_pairs_gather<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint32_t>(),
+        k_pairs_gather<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint4>(),
                                                             c->h_d.as<double>(), c->H2f.as<float>(), n, pp, nullptr,
                                                             goff, c->pkeys.as<uint64_t>());
         c->launches += 2;
@@ -1714,13 +1724,13 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     // a4: geometry
     if (c->fp64)
         k_geometry<double><<<nblk(n, 128), 128, 0, st>>>(
-            c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(), c->omega_d.as<double>(),
+            c->xs_d.as<double>(), c->xq.as<uint4>(), c->h_d.as<double>(), c->omega_d.as<double>(),
             c->row_off.as<int64_t>(), c->cols.as<int32_t>(), n, cfg.box[0], cfg.box[1], cfg.box[2], cfg.periodic,
             qscale[0], qscale[1], qscale[2], c->V_d.as<double>(), c->B_d.as<double>(), c->cond_d.as<double>(),
             c->pos_t.p, c->geo_t.as<double>(), c->omega_t.as<double>(), red, flags);
     else
         k_geometry<float><<<nblk(n, 128), 128, 0, st>>>(
-            c->xs_d.as<double>(), c->xq.as<uint32_t>(), c->h_d.as<double>(), c->omega_d.as<double>(),
+            c->xs_d.as<double>(), c->xq.as<uint4>(), c->h_d.as<double>(), c->omega_d.as<double>(),
             c->row_off.as<int64_t>(), c->cols.as<int32_t>(), n, cfg.box[0], cfg.box[1], cfg.box[2], cfg.periodic,
             qscale[0], qscale[1], qscale[2], c->V_d.as<double>(), c->B_d.as<double>(), c->cond_d.as<double>(),
             c->pos_t.p, c->geo_t.as<float>(), c->omega_t.as<float>(), red, flags);
