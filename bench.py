@@ -707,8 +707,12 @@ def run_decomposed(args):
     from paper_2302_12727_gb300 import domain
 
     ws, rank, local = dist_setup()
+    if args.backend == "gloo":
+        # host-staged exchanges; the ranks may share a GPU (a check of this path on one GPU:
+        # no kernel of one rank waits on another's)
+        local = local % torch.cuda.device_count()
     torch.cuda.set_device(local)
-    dist.init_process_group("nccl")
+    dist.init_process_group(args.backend)
     dev = torch.device("cuda", local)
     w = workload(args.workload)
     G, n_sub = w.n_groups, w.n_steps
@@ -742,7 +746,7 @@ def run_decomposed(args):
         D.energy(U)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
-    t_max = max_over_ranks(sum(times), ws, dev)
+    t_max = max_over_ranks(sum(times), ws, dev if args.backend == "nccl" else torch.device("cpu"))
     P = int(D._all_sum([rows_owned])[0]) // 2
     if rank == 0:
         print(json.dumps({
@@ -785,6 +789,8 @@ def main():
                     help="per-group photo-ionisation sink (rt_set_absorbers) instead of the grey kappa")
     ap.add_argument("--drift", type=float, default=0.0,
                     help="move the particles at this fraction of c (drift correction + new neighbours every step)")
+    ap.add_argument("--backend", default="nccl", choices=["nccl", "gloo"],
+                    help="process-group backend of --decompose (gloo: exchanges through the host)")
     ap.add_argument("--decompose", action="store_true",
                     help="with N > 1 ranks: one particle set split over the ranks by the spatial domain "
                          "decomposition (halo exchanges over NCCL) instead of N independent replicas")

@@ -72,3 +72,28 @@ def test_decomposed_library_run_equals_single_context(tmp_path, precision):
         ref, _ = o.run(U0, nsteps, dt, Ls, alpha)
         assert rel_l1(r["U"], ref).max() <= 1e-5
         np.testing.assert_allclose(r["E"], o.energy(ref), rtol=1e-6)
+
+
+def test_bench_decomposed_mode_runs():
+    """bench.py --decompose under torchrun: two ranks split one particle set (gloo backend,
+    sharing the one GPU) and print one JSON line whose pair count is the whole set's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(_free_port()), os.path.join(root, "bench.py"), "--gpus", "2",
+           "--decompose", "--backend", "gloo", "--workload", "lattice-sources", "--steps", "2", "--warmup", "1"]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-3000:]
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1]
+    d = json.loads(line)
+    from paper_2302_12727_gb300 import workloads as W
+    w = W.lattice_sources()
+    o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
+    assert d["config"]["pairs"] == int(o.pairs()[0][-1]) // 2
+    assert d["n_gpus"] == 2 and d["value"] > 0 and d["scaling"] == "strong"
