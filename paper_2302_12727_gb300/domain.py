@@ -152,7 +152,6 @@ def make_plan(x: np.ndarray, box, periodic: bool, nb: int, block_owner: np.ndarr
     owned = np.flatnonzero(pown == rank)
     gm = ghost_mask(rank)
     ghosts = np.flatnonzero(gm)
-    pos = {}
     local = np.concatenate([owned, ghosts])
     loc = np.full(x.shape[1], -1, dtype=np.int64)
     loc[local] = np.arange(len(local))
@@ -167,7 +166,6 @@ def make_plan(x: np.ndarray, box, periodic: bool, nb: int, block_owner: np.ndarr
             plan.send[q] = loc[s]
         if len(r):
             plan.recv[q] = loc[r]
-    del pos
     return plan
 
 
@@ -384,7 +382,6 @@ class DistributedTransport:
 
     def gather(self, U):
         """The global [G, 4, N] state assembled from every rank's owned particles (float64)."""
-        import torch
         own = U[..., :self.plan.n_owned]
         own = own.detach().cpu().numpy() if hasattr(own, "detach") else np.asarray(own)
         full = np.zeros(U.shape[:-1] + (self.x.shape[1],))

@@ -6,7 +6,6 @@ decomposed run equals a single context's run of the whole set: FP64 to 1e-12 per
 and the energy to 1e-13; FP32 within the FP32 bar against the oracle (relative L1 1e-5 per
 component and group after the steps)."""
 import os
-import socket
 
 import numpy as np
 import pytest
