@@ -32,7 +32,7 @@
 //   individual time bins, min(dt_k, dt_l)  Sec. "Individual Timstepping", Eq. transport-update-explicit
 //   factor-4 time-step limiter             Sec. "Dynamic Sub-Cycling"
 //
-// Readings where the thesis is silent or inconsistent (each is listed in the design notes):
+// Readings where the thesis is silent or inconsistent:
 //   * update sign: U_k(t+dt) = U_k - dt/V_k sum_l F_kl . A_kl (the RT chapter's form; the
 //     "+" of the hydro chapter's explicit update contradicts d(UV)/dt + sum F.A = 0).
 //   * minmod: s = minmod(grad Q_k . d, grad Q_l . d) with d = x_l - x_k, and both states use s:

@@ -1,7 +1,7 @@
 """The non-default branches of the pair flux and the update against the FP64 oracle.
 
 Eq. eddington-group defines the closure for E > 0 and |F| <= cE only.  The readings the
-library and the oracle share (M1 in the design notes): the reduced flux is clipped to 1
+library and the oracle share: the reduced flux is clipped to 1
 when |F| > cE, a state with E <= 0 carries no pressure (its energy flux F . A stays), and
 the fix-up of the thesis's Riemann-solver and limiter tests (Part III, "Testing Riemann
 Solvers and Limiters") sets E < 0 to 0 after the sink and counts the events.  These tests

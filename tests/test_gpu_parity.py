@@ -1,6 +1,6 @@
 """CUDA library vs the FP64 oracle, element by element, through the C interface.
 
-Tolerances (derived from the arithmetic, see the design notes):
+Tolerances (FP64: the rounding bound of ~50-term neighbour sums; FP32: the float path's stated bar):
   FP64 path:  |gpu - oracle| <= 1e-12 |oracle| + 1e-14 max|oracle of that component| per element
   FP32 path:  relative L1 per component and group <= 1e-5 per step; energy drift <= 1e-6
   neighbour sets: identical except pairs whose r^2 lies within 1e-12 H^2 of the threshold
