@@ -71,6 +71,7 @@ def _load():
         lib.orc_gradients.argtypes = [vp, dp, dp]
         lib.orc_run.restype = C.c_long
         lib.orc_run.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp]
+        lib.orc_inject.argtypes = [vp, C.c_double, dp, dp]
         lib.orc_jvp.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp]
         lib.orc_jvp_kinks.restype = C.c_long
         lib.orc_jvp_kinks.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, C.c_double]
@@ -274,6 +275,13 @@ class Oracle:
         nclamp = self.lib.orc_run(self._p, int(n_sub), float(dt), _dp(U), _dp(L) if L.size else _dp(np.zeros(1)),
                                   _dp(a))
         return U, nclamp
+
+    def inject(self, U0, dt, L):
+        """The injection stage of one step alone (E_g += xi_sg L_s dt / V_g); returns U."""
+        U = _c(U0).copy().reshape(self.G, 4, self.n)
+        L = _c(np.zeros((self.n_src, self.G)) if L is None else L).reshape(self.n_src, self.G)
+        self.lib.orc_inject(self._p, float(dt), _dp(U), _dp(L) if L.size else _dp(np.zeros(1)))
+        return U
 
     def jvp(self, U0, dU0, n_sub, dt, L, dL, alpha=None):
         U0 = _c(U0).reshape(self.G, 4, self.n)

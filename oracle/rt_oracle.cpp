@@ -849,6 +849,19 @@ static void limit_bins(const Model& M, std::vector<int>& b) {
     }
 }
 
+// The injection of one step (Sec. "Weights For Distribution Of Energy Density"): each
+// source's luminosity times dt, spread over its gas neighbours by the weights xi and turned
+// into energy density by the target's volume, E_g += xi_sg L_s dt / V_g.  U: [G][4][N].
+template <class T>
+static void inject(const Model& M, double dt, std::vector<T>& U, const std::vector<T>& L) {
+    const long n = M.P.n;
+    const int G = M.cfg.n_groups;
+    for (long s = 0; s < M.n_src; ++s)
+        for (const Target& t : M.inj[s])
+            for (int g = 0; g < G; ++g)
+                U[(size_t)(4 * g) * n + t.g] += T(t.xi * dt / M.V[t.g]) * L[(size_t)s * G + g];
+}
+
 // One time step: injection -> transport -> grey sink (-> optional fix-up).
 // U: [G][4][N] in/out, L: [S][G], alpha: [N] or null.
 template <class T>
@@ -859,11 +872,8 @@ static void step(const Model& M, double dt, std::vector<T>& U, const std::vector
     const int C = 4 * G;
     const double c = M.cfg.c_red;
 
-    // 1. injection: E_g += xi_sg L_s dt / V_g
-    for (long s = 0; s < M.n_src; ++s)
-        for (const Target& t : M.inj[s])
-            for (int g = 0; g < G; ++g)
-                U[(size_t)(4 * g) * n + t.g] += T(t.xi * dt / M.V[t.g]) * L[(size_t)s * G + g];
+    // 1. injection
+    inject(M, dt, U, L);
 
     // 2. gradients of the injected state
     std::vector<T> grad;
@@ -1117,6 +1127,16 @@ long orc_run(void* p, int n_sub, double dt, double* U, const double* L, const do
     for (int k = 0; k < n_sub; ++k) step(*M, dt, u, l, alpha, &st);
     std::memcpy(U, u.data(), C * n * sizeof(double));
     return st.clamped;
+}
+
+// the injection of one step alone (the first stage of orc_run's step); U in/out [G][4][N]
+void orc_inject(void* p, double dt, double* U, const double* L) {
+    Model* M = (Model*)p;
+    size_t n = M->P.n, C = 4 * M->cfg.n_groups;
+    std::vector<double> u(U, U + C * n);
+    std::vector<double> l(L, L + (size_t)M->n_src * M->cfg.n_groups);
+    inject(*M, dt, u, l);
+    std::memcpy(U, u.data(), C * n * sizeof(double));
 }
 
 // as orc_run, with the photo-ionisation sink per group: alpha_g [G][N]

@@ -353,6 +353,16 @@ def test_injection_weights_and_energy():
     E0 = o.energy(U)
     U1, _ = o.run(U, 3, dt, L)
     np.testing.assert_allclose(o.energy(U1), E0 + 3 * dt * L.sum(0), rtol=1e-13)
+    # the injection stage alone: L dt more energy per group, in the E rows of the sources'
+    # gas neighbours only; a step is that stage followed by a step without sources
+    Ui = o.inject(U, dt, L)
+    np.testing.assert_allclose(o.energy(Ui), E0 + dt * L.sum(0), rtol=1e-13)
+    changed = np.flatnonzero((Ui != U).any(axis=(0, 1)))
+    assert np.array_equal(changed, np.unique(s.e_gas))
+    assert np.array_equal(Ui[:, 1:], U[:, 1:])
+    a, _ = o.run(U, 1, dt, L)
+    b, _ = o.run(Ui, 1, dt)
+    assert np.array_equal(a, b)
 
 
 # --------------------------------------------------------------------------------- O11, O14
