@@ -225,6 +225,15 @@ rt_status rt_gradients(rt_ctx* ctx, const void* U_dev, void* gradU_dev);
  * Lsrc_dev may be NULL when S = 0; alpha_dev may be NULL (no sink).  Plain kernel launches. */
 rt_status rt_transport_step(rt_ctx* ctx, double dt, void* U_dev, const double* Lsrc_dev, const double* alpha_dev);
 
+/* The injection stage of one step alone (Sec. "Weights For Distribution Of Energy
+ * Density"): E_g += sum_s xi_sg Lsrc_s,g dt / V_g over the injection targets, in place on
+ * U_dev ([G][4][N], caller order, element type per precision; device).  Lsrc_dev [S][G]
+ * (double, device) may be NULL, and with it, with S = 0 or with no targets, the call
+ * changes nothing.  rt_inject followed by rt_transport_step with Lsrc_dev = NULL gives
+ * bitwise the result of rt_transport_step with Lsrc_dev (the same injection kernel on the
+ * same values).  RT_ERR_INVALID for a NULL U_dev or a dt that is negative or not finite. */
+rt_status rt_inject(rt_ctx* ctx, double dt, void* U_dev, const double* Lsrc_dev);
+
 /* n_sub steps of size dt without any neighbour search in between (Sec. "Dynamic
  * Sub-Cycling"), replayed from one CUDA graph that the library captures once per
  * (n_sub, source/sink presence) and reuses; dt, Lsrc and alpha live in device buffers,

@@ -303,6 +303,19 @@ rt_status rt_transport_step(rt_ctx* c, double dt, void* U, const double* Lsrc, c
     return RT_OK;
 }
 
+rt_status rt_inject(rt_ctx* c, double dt, void* U, const double* Lsrc) {
+    RT_TRY(check_ready(c));
+    if (!U) return fail(c, RT_ERR_INVALID, "U_dev is NULL");
+    if (!std::isfinite(dt) || dt < 0) return fail(c, RT_ERR_INVALID, "dt must be finite and >= 0");
+    if (!Lsrc || c->n_src == 0 || c->n_inj_targets == 0) return RT_OK;
+    const int G = c->cfg.n_groups;
+    RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
+    RT_TRY(set_step_inputs(c, dt, Lsrc, nullptr));
+    RT_TRY(launch_inject(c, c->stream, c->U_a.p));
+    RT_TRY(state_out(c, c->U_a.p, U, 4 * G, 4 * G, 0));
+    return RT_OK;
+}
+
 rt_status rt_subcycle(rt_ctx* c, int32_t n_sub, double dt, void* U, const double* Lsrc, const double* alpha) {
     RT_TRY(check_ready(c));
     if (!U) return fail(c, RT_ERR_INVALID, "U_dev is NULL");

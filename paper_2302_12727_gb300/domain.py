@@ -18,21 +18,25 @@ its domain, and only the ghosts' data crosses ranks:
               2. the owners send h to the ranks holding the particles as ghosts, and every
                  rank learns every h_s (a sum over ranks);
               3. each rank builds its lists, geometry and injection weights with all h given
-                 (rt_neighbours_given_h), on ghosts out to D = 2 (H_max + H_s,max);
-  sub-cycle   the owners send the ghosts' states (U), then every rank runs one transport
-              step (rt_transport_step) on its own particles and ghosts; the energy is summed
-              over owned particles in double and over ranks by an all-reduce.
+                 (rt_neighbours_given_h), on ghosts out to D = 2 max(H_max, H_s,max), with
+                 the sources within H_s,max of its blocks;
+  sub-cycle   every rank injects its sources' energy (rt_inject), the owners send the
+              ghosts' injected states (U), then every rank runs the rest of the step
+              (rt_transport_step without sources: gradients, fluxes, update, sink) on its own
+              particles and ghosts; the energy is summed over owned particles in double and
+              over ranks by an all-reduce.
 
-Why D = 2 (H_max + H_s,max) reproduces the single-rank result on every owned particle: an
-owned particle's pairs reach at most H_max, so its partners j lie within H_max of the domain;
-the flux of (i, j) needs grad U_j and B_j, i.e. j's own pair list and the states of j's
-neighbours, all within 2 H_max; those states are refreshed from their owners before the
-step, and the injection they receive in it comes from sources within 2 H_max + H_s,max, whose
-gas neighbourhoods lie within D.  Every h is the owner's, so every rank decides each pair
-with the same two smoothing lengths.  The ghosts' own results are discarded: the next
-refresh overwrites them.  Unlike the thesis's scheme, gradients are not exchanged: the ghosts
-within H_max of the domain compute them (the halo is one H_max deeper), so a sub-cycle has
-one exchange instead of two.
+Why D = 2 max(H_max, H_s,max) reproduces the single-rank result on every owned particle.
+Injection: an owned particle receives energy from sources within H_s,max, whose weights are
+normalised over their gas neighbours, within 2 H_s,max of the domain; the target's volume is
+its own.  Transport: an owned particle's pairs reach at most H_max, so its partners j lie
+within H_max of the domain; the flux of (i, j) needs grad U_j and B_j, i.e. j's own pair list
+and the states of j's neighbours, all within 2 H_max, and those states are the owners'
+injected states, refreshed after the injection.  Every h is the owner's, so every rank
+decides each pair with the same two smoothing lengths.  The ghosts' own results are
+discarded: the next refresh overwrites them.  Unlike the thesis's scheme, gradients are not
+exchanged: the ghosts within H_max of the domain compute them (the halo is one H_max deeper),
+so a sub-cycle has one exchange instead of two.
 
 The exchanges are grouped point-to-point sends and receives (torch.distributed: NCCL between
 GPUs, gloo between CPU ranks); the energy all-reduce is in float64.  A rank's engine is the
@@ -253,6 +257,9 @@ class CudaEngine:
     def luminosities(self, L):
         return self.t.luminosities(L)
 
+    def inject(self, U, dt, L):
+        self.t.inject(U, dt, L)
+
     def step(self, U, dt, L, alpha):
         self.t.step(U, dt, L, alpha)
 
@@ -277,7 +284,7 @@ class DistributedTransport:
     holds).  ``engine`` runs one rank's share; ``nb`` is the number of partition blocks per
     axis (a power of two)."""
 
-    def __init__(self, x, m, xsrc, engine, *, box=(1.0, 1.0, 1.0), periodic=True, nb=16, group=None,
+    def __init__(self, x, m, xsrc, engine, *, box=(1.0, 1.0, 1.0), periodic=True, nb=32, group=None,
                  work=None, eta_res=1.2348):
         import torch.distributed as dist
         self.dist = dist
@@ -315,10 +322,12 @@ class DistributedTransport:
         self.hs = self._all_sum(self.hs)
         self.H_max = H_OVER_h * self._all_max(float(self.h[plan.owned].max(initial=0.0)))
         self.Hs_max = H_OVER_h * float(self.hs.max(initial=0.0))
-        # 2.-3. the halo of the transport and the build with every h given
-        self.depth = 2.0 * (self.H_max + self.Hs_max)
-        reach_src = reach_blocks(2.0 * self.H_max + self.Hs_max, box, nb)
-        reach = reach_src + reach_blocks(self.Hs_max, box, nb)
+        # 2.-3. the halo of the transport and the build with every h given: the transport
+        #    needs 2 H_max, the injection into owned particles the sources within H_s,max
+        #    and their gas neighbours
+        self.depth = 2.0 * max(self.H_max, self.Hs_max)
+        reach_src = reach_blocks(self.Hs_max, box, nb)
+        reach = max(reach_blocks(2.0 * self.H_max, box, nb), reach_src + reach_blocks(self.Hs_max, box, nb))
         self.plan = make_plan(self.x, box, periodic, nb, self.block_owner, self.rank, reach)
         self.reach = reach
         self._exchange_owned_h()
@@ -370,10 +379,13 @@ class DistributedTransport:
         return self.engine.luminosities(np.ascontiguousarray(np.asarray(L_global)[self.src_mask]))
 
     def subcycle(self, U, n_sub, dt, L=None, alpha=None):
-        """n_sub transport steps of the local state U (in place): ghost refresh, then a step."""
+        """n_sub transport steps of the local state U (in place): the injection, the ghost
+        refresh (carrying the owners' injected states), then the rest of the step."""
         for _ in range(n_sub):
+            if L is not None:
+                self.engine.inject(U, dt, L)
             exchange(U, self.plan, self.group)
-            self.engine.step(U, dt, L, alpha)
+            self.engine.step(U, dt, None, alpha)
         return U
 
     def energy(self, U):

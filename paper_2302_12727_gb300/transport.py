@@ -13,8 +13,8 @@ import torch
 
 from . import (RT_FP32_MIXED, RT_FP64, make_config, rt_adjoint, rt_create, rt_destroy, rt_diagnostics, rt_drift,
                rt_energy, rt_get_tuning, rt_gradients, rt_neighbours, rt_neighbours_given_h, rt_pairs,
-               rt_particle_fields, rt_set_owned, rt_set_stream, rt_set_tuning, rt_source_fields, rt_subcycle,
-               rt_transport_step)
+               rt_inject, rt_particle_fields, rt_set_owned, rt_set_stream, rt_set_tuning, rt_source_fields,
+               rt_subcycle, rt_transport_step)
 
 
 def _dev(a, dtype, device):
@@ -116,6 +116,12 @@ class Transport:
     def step(self, U, dt, L=None, alpha=None):
         self._sync_stream()
         rt_transport_step(self.ctx, dt, U, L, alpha)
+        return U
+
+    def inject(self, U, dt, L=None):
+        """The injection stage of one step alone, in place (rt_inject)."""
+        self._sync_stream()
+        rt_inject(self.ctx, dt, U, L)
         return U
 
     def subcycle(self, U, n_sub, dt, L=None, alpha=None):

@@ -48,6 +48,10 @@ class OracleEngine:
     def luminosities(self, L):
         return None if L is None else np.asarray(L, dtype=np.float64)
 
+    def inject(self, U, dt, L):
+        if self.ns:
+            U.copy_(torch.from_numpy(self.o.inject(U.numpy(), dt, L)))
+
     def step(self, U, dt, L, alpha):
         Un, _ = self.o.run(U.numpy(), 1, dt, L if self.ns else None, alpha)
         U.copy_(torch.from_numpy(Un))

@@ -73,6 +73,46 @@ def test_decomposed_library_run_equals_single_context(tmp_path, precision):
         np.testing.assert_allclose(r["E"], o.energy(ref), rtol=1e-6)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_inject_then_sourceless_step_equals_step(precision):
+    """rt_inject, the injection stage alone, against the oracle's (Sec. "Weights For
+    Distribution Of Energy Density"), adding L dt per group; followed by rt_transport_step
+    without sources it is bitwise rt_transport_step with them (the decomposition exchanges
+    ghosts between the two)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2302_12727_gb300 import RTError
+    x, m, xsrc, U0, Ls, alpha, G, c, _ = _case("lattice-48")
+    t = Transport(x, m, xsrc, n_groups=G, c_red=c, precision=precision)
+    dt = 0.5 * t.diagnostics()["dx_min"] / c
+    L, al = t.luminosities(Ls), t.alpha(alpha)
+    U1 = t.state(U0)
+    t.step(U1, dt, L, al)
+    U2 = t.state(U0)
+    t.inject(U2, dt, L)
+    t.step(U2, dt, None, al)
+    assert torch.equal(U1, U2)
+    U3 = t.state(U0)
+    E0 = np.asarray(t.energy(U3))
+    t.inject(U3, dt, L)
+    fp64 = precision == "fp64"
+    np.testing.assert_allclose(np.asarray(t.energy(U3)) - E0, dt * Ls.sum(0), rtol=1e-12 if fp64 else 1e-5)
+    o = oracle.Oracle(x, m, xsrc, n_groups=G, c_red=c)
+    ref = o.inject(U0, dt, Ls)
+    got = U3.cpu().numpy().astype(np.float64)
+    if fp64:
+        scale = np.abs(ref).reshape(G, -1).max(axis=1)[:, None, None]
+        assert (np.abs(got - ref) <= 1e-12 * np.abs(ref) + 1e-14 * scale).all()
+    else:
+        assert rel_l1(got, ref).max() <= 1e-6
+    U4 = t.state(U0)
+    t.inject(U4, dt, None)                 # no luminosities: nothing changes
+    assert torch.equal(U4, t.state(U0))
+    with pytest.raises(RTError):
+        t.inject(U4, -dt, L)
+    t.close()
+
+
 def test_bench_decomposed_mode_runs():
     """bench.py --decompose under torchrun: two ranks split one particle set (gloo backend,
     sharing the one GPU) and print one JSON line whose pair count is the whole set's."""
