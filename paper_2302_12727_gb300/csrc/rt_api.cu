@@ -665,7 +665,7 @@ void rt_destroy(rt_ctx* c) {
     destroy_prof(c->plain_prof);
     DevBuf* bufs[] = {&c->keys_in, &c->keys_out, &c->idx_in, &c->perm, &c->inv_perm, &c->cell_start, &c->cub_tmp,
                       &c->xs_d, &c->xq, &c->m_s, &c->h_d, &c->H2f, &c->h_prev, &c->omega_d, &c->V_d, &c->B_d, &c->cond_d, &c->pos_t,
-                      &c->geo_t, &c->omega_t, &c->counts, &c->row_off, &c->cols, &c->cols_tmp, &c->cols_cap, &c->blk, &c->pkeys, &c->pkeys_alt, &c->n_low,
+                      &c->geo_t, &c->omega_t, &c->counts, &c->row_off, &c->cols, &c->cols_cap, &c->blk, &c->pkeys, &c->pkeys_alt, &c->n_low,
                       &c->n_up, &c->up_off, &c->low_slot, &c->pair_ends, &c->pairbuf, &c->flags, &c->red_tmp,
                       &c->xsrc_d, &c->hs_d, &c->omegas_d, &c->src_counts, &c->src_off, &c->inj_key,
                       &c->inj_key_out, &c->inj_val, &c->inj_val_out, &c->inj_targets, &c->inj_off, &c->inj_src,

@@ -49,8 +49,14 @@ __device__ __forceinline__ int wrap_cell(int c, int nc) {
 // cells along x are contiguous in sorted order; rows whose (y, z) extent is farther than R
 // are skipped and each row is clipped to the chord of the sphere, so the visited volume
 // is close to the sphere plus one cell layer.  An axis whose span covers the whole grid is
-// walked once without clipping.
-template <class F>
+// walked once without clipping.  With ASC the ranges come in ascending cell index (a
+// periodic axis is walked from the cell that wraps to the lowest index), so that the
+// candidates, being sorted by cell, come in ascending particle index.
+__device__ __forceinline__ int first_wrapped(int lo, int hi, int nc) {
+    return lo < 0 ? 0 : (hi >= nc ? nc : lo);
+}
+
+template <bool ASC = false, class F>
 __device__ __forceinline__ void for_each_candidate_range(const Grid& g, float px, float py, float pz, float R,
                                                          F&& fr) {
     // float arithmetic with a relative margin of 1e-4 on R: cells are never missed
@@ -71,12 +77,19 @@ __device__ __forceinline__ void for_each_candidate_range(const Grid& g, float px
             hi[a] = min(hi[a], g.nc[a] - 1);
         }
     }
-    for (int z = lo[2]; z <= hi[2]; ++z) {
+    const int nzs = hi[2] - lo[2] + 1, nys = hi[1] - lo[1] + 1;
+    const int z0 = ASC ? first_wrapped(lo[2], hi[2], g.nc[2]) : lo[2];
+    const int y0 = ASC ? first_wrapped(lo[1], hi[1], g.nc[1]) : lo[1];
+    for (int kz = 0; kz < nzs; ++kz) {
+        int z = z0 + kz;
+        if (z > hi[2]) z -= nzs;
         float dz = 0.f;
         if (!all[2]) dz = fmaxf(0.f, fmaxf(z * g.cellf[2] - pz, pz - (z + 1) * g.cellf[2]));
         if (dz * dz >= R2) continue;
         int zz = wrap_cell(z, g.nc[2]);
-        for (int y = lo[1]; y <= hi[1]; ++y) {
+        for (int ky = 0; ky < nys; ++ky) {
+            int y = y0 + ky;
+            if (y > hi[1]) y -= nys;
             float dy = 0.f;
             if (!all[1]) dy = fmaxf(0.f, fmaxf(y * g.cellf[1] - py, py - (y + 1) * g.cellf[1]));
             float rem = R2 - dy * dy - dz * dz;
@@ -97,9 +110,13 @@ __device__ __forceinline__ void for_each_candidate_range(const Grid& g, float px
                 }
             }
             int sl[2], sh[2], ns = 0;
-            if (xa < 0) { sl[ns] = xa + g.nc[0]; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb; }
-            else if (xb >= g.nc[0]) { sl[ns] = xa; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb - g.nc[0]; }
-            else { sl[ns] = xa; sh[ns++] = xb; }
+            if (xa < 0) {
+                if (ASC) { sl[ns] = 0; sh[ns++] = xb; sl[ns] = xa + g.nc[0]; sh[ns++] = g.nc[0] - 1; }
+                else { sl[ns] = xa + g.nc[0]; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb; }
+            } else if (xb >= g.nc[0]) {
+                if (ASC) { sl[ns] = 0; sh[ns++] = xb - g.nc[0]; sl[ns] = xa; sh[ns++] = g.nc[0] - 1; }
+                else { sl[ns] = xa; sh[ns++] = g.nc[0] - 1; sl[ns] = 0; sh[ns++] = xb - g.nc[0]; }
+            } else { sl[ns] = xa; sh[ns++] = xb; }
             for (int sI = 0; sI < ns; ++sI) {
                 int b = g.cell_start[base + sl[sI]];
                 int e = g.cell_start[base + sh[sI] + 1];
@@ -110,9 +127,9 @@ __device__ __forceinline__ void for_each_candidate_range(const Grid& g, float px
 }
 
 // every candidate of for_each_candidate_range, one at a time
-template <class F>
+template <bool ASC = false, class F>
 __device__ __forceinline__ void for_each_candidate(const Grid& g, float px, float py, float pz, float R, F&& f) {
-    for_each_candidate_range(g, px, py, pz, R, [&](int b, int e) {
+    for_each_candidate_range<ASC>(g, px, py, pz, R, [&](int b, int e) {
         for (int j = b; j < e; ++j) f(j);
     });
 }
@@ -733,7 +750,8 @@ __global__ void k_block_reach(const unsigned* __restrict__ hb, Blocks bk, float*
 
 // FILL = false counts each row into counts[p]; with cap > 0 it also writes the first cap
 // entries of row p to cols[p cap ...] and raises *row_max to the longest row.  FILL = true
-// writes row p to cols[row_off[p] ...].  Both walk the candidates in the same order.
+// writes row p to cols[row_off[p] ...].  Both walk the candidates in ascending index, so
+// every row comes out in ascending column order.
 template <bool FILL>
 __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint4* __restrict__ xq,
                         const double* __restrict__ h, const float* __restrict__ H2f, int64_t n, PairParams pp,
@@ -749,7 +767,7 @@ __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint4* __re
         const float Hr = reach[block_of(bk, px, py, pz)];
         float R = sqrtf(fmaxf(H2i, Hr * Hr)) * 1.0001f;
         int64_t base = FILL ? row_off[p] : p * (int64_t)cap;
-        for_each_candidate(g, (float)px, (float)py, (float)pz, R, [&](int j) {
+        for_each_candidate<true>(g, (float)px, (float)py, (float)pz, R, [&](int j) {
             if (j == p) return;
             float dx = fsep(xq[j].x, qx, pp.scale[0]);
             float dy = fsep(xq[j].y, qy, pp.scale[1]);
@@ -780,14 +798,16 @@ __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint4* __re
     }
 }
 
-// rows of cap entries (k_pairs' counting walk) -> CSR rows at row_off
+// rows of cap entries (k_pairs' counting walk) -> CSR rows at row_off, one warp per row
 __global__ void k_rows_compact(const int32_t* __restrict__ cols_cap, int64_t cap, const int64_t* __restrict__ row_off,
                                int64_t n, int32_t* __restrict__ cols) {
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (p >= n) return;
     const int64_t b = row_off[p], m = row_off[p + 1] - b;
-    for (int64_t k = 0; k < m; ++k) cols[b + k] = cols_cap[p * cap + k];
+    for (int64_t k = lane; k < m; k += 32) cols[b + k] = cols_cap[p * cap + k];
 }
+
 
 // Rows sorted ascending are [lower neighbours j < i | upper neighbours j > i].  Each
 // unordered pair is the upper entry of its lower particle; slot(i, j) numbers those entries.
@@ -1492,11 +1512,12 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
     RT_CUDA(c, cudaMemsetAsync(red, 0xff, 8, st));
     RT_CUDA(c, cudaMemsetAsync(red + 3, 0xff, 8, st));
 
-    // cub scratch: radix sort of N and scan of N+1
+    // cub scratch: radix sort of N, scans of N+1 and S+1, radix sort of the injection entries
     size_t t1 = 0, t2 = 0, t3 = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, t1, (const uint32_t*)nullptr, (uint32_t*)nullptr,
                                     (const int32_t*)nullptr, (int32_t*)nullptr, (int)n, 0, bits, st);
-    cub::DeviceScan::ExclusiveSum(nullptr, t2, (const int32_t*)nullptr, (int64_t*)nullptr, (int)(n + 1), st);
+    cub::DeviceScan::ExclusiveSum(nullptr, t2, (const int32_t*)nullptr, (int64_t*)nullptr,
+                                  (int)(std::max<int64_t>(n, S) + 1), st);
     int64_t Smax = std::max<int64_t>(S, 1) * 4096;
     cub::DeviceRadixSort::SortPairs(nullptr, t3, (const uint64_t*)nullptr, (uint64_t*)nullptr,
                                     (const int32_t*)nullptr, (int32_t*)nullptr, (int)Smax, 0, 64, st);
@@ -1621,14 +1642,14 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         RT_CUDA(c, cudaStreamSynchronize(st));
         if (P2 >= ((int64_t)1 << 31)) return fail(c, RT_ERR_INVALID, "more than 2^31 neighbour entries");
         RT_TRY(ensure(c, c->cols, std::max<int64_t>(P2, 1) * 4, "pair lists"));
-        RT_TRY(ensure(c, c->cols_tmp, std::max<int64_t>(P2, 1) * 4, "pair lists"));
+        // the walks visit the candidates in ascending index: the rows need no sort
         if (cap > 0 && longest <= cap) {
-            k_rows_compact<<<nblk(n, 128), 128, 0, st>>>(c->cols_cap.as<int32_t>(), cap, c->row_off.as<int64_t>(), n,
-                                                          c->cols_tmp.as<int32_t>());
+            k_rows_compact<<<nblk(n * 32, 256), 256, 0, st>>>(c->cols_cap.as<int32_t>(), cap,
+                                                              c->row_off.as<int64_t>(), n, c->cols.as<int32_t>());
         } else {
             k_pairs<true><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint4>(),
                                                          c->h_d.as<double>(), c->H2f.as<float>(), n, pp, bk, reach,
-                                                         nullptr, c->row_off.as<int64_t>(), c->cols_tmp.as<int32_t>());
+                                                         nullptr, c->row_off.as<int64_t>(), c->cols.as<int32_t>());
         }
         // the next call's rows: the longest row with a quarter to spare, in multiples of 32,
         // while the padded rows stay within eight times the lists (only the filled part of a
@@ -1637,15 +1658,6 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         c->row_cap = next * n <= 8 * std::max<int64_t>(P2, 1) ? next : 0;
         RT_CUDA(c, cudaGetLastError());
         c->launches += 2;
-        // rows in ascending order
-        size_t need = 0;
-        cub::DeviceSegmentedSort::SortKeys(nullptr, need, c->cols_tmp.as<int32_t>(), c->cols.as<int32_t>(), (int)P2,
-                                           (int)n, c->row_off.as<int64_t>(), c->row_off.as<int64_t>() + 1, st);
-        RT_TRY(ensure(c, c->cub_tmp, need + 256, "cub scratch"));
-        tb = c->cub_tmp.bytes;
-        RT_CUDA(c, cub::DeviceSegmentedSort::SortKeys(c->cub_tmp.p, tb, c->cols_tmp.as<int32_t>(), c->cols.as<int32_t>(),
-                                                      (int)P2, (int)n, c->row_off.as<int64_t>(),
-                                                      c->row_off.as<int64_t>() + 1, st));
     } else {
         int64_t* goff = c->row_off.as<int64_t>();      // gather offsets first, CSR offsets after
         k_pairs_gather<false><<<nblk(n, 128), 128, 0, st>>>(g, c->xs_d.as<double>(), c->xq.as<uint4>(),

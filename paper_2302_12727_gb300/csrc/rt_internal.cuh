@@ -81,7 +81,7 @@ struct rt_ctx {
     bool has_h_prev = false;
     bool has_hs_prev = false;                           // hs_d holds the sources' h of the last call
     rt::DevBuf pos_t, geo_t, omega_t;                   // working precision per particle (pair kernels)
-    rt::DevBuf counts, row_off, cols, cols_tmp;         // symmetric pair lists (CSR), rows ascending
+    rt::DevBuf counts, row_off, cols;                   // symmetric pair lists (CSR), rows ascending
     // rows of row_cap entries that the counting walk of the pair search also fills (0: off);
     // set from the longest row of the last call
     rt::DevBuf cols_cap;
