@@ -120,7 +120,8 @@ static rt_status ensure_state(rt_ctx* c) {
     // per-pair flux slots of one group chunk (at most 4 groups)
     const int gc = G < kMaxGC ? G : kMaxGC;
     RT_TRY(ensure(c, c->pairbuf, (size_t)std::max<int64_t>(c->n_directed / 2, 1) * 4 * gc * tsize(c), "pair fluxes"));
-    if (!c->fp64 && G <= kMaxGC) RT_TRY(ensure(c, c->frec, (size_t)(12 + 16 * G) * n * 4, "packed flux rows"));
+    if (!c->fp64 && G <= kMaxGC)
+        RT_TRY(ensure(c, c->frec, (size_t)(12 + 16 * G + kRowRot) * n * 4, "packed flux rows"));
     return RT_OK;
 }
 

@@ -25,6 +25,10 @@ enum FlagSlot { F_BADPOS = 0, F_NOCONV = 1, F_GEOM = 2, F_ILL = 3, F_SRC_NOCONV 
                 F_NSLOTS = 8, F_CLAMP = 8,
                 F_TIMEOUT = 12, F_SCRATCH = 13, F_ROWMAX = 14, F_SELFTEST = 15 };
 constexpr int kMaxGC = 4;                          // groups handled by one pair-kernel launch
+// Packed flux rows start with a prefix that repeats their last kRowRot words: a row copy that
+// starts at word kRowRot delivers the row, one that starts at word 0 delivers it rotated by
+// four 16-byte chunks (the pair pass uses both, see k_flux_tma).
+constexpr int kRowRot = 16;
 
 // ------------------------------------------------------------------------------------
 // Device buffer that only grows.

@@ -231,9 +231,10 @@ struct PairArgs {
     const int2* ends;         // (k, l) of each pair slot
     int64_t n_pairs;
     int G;
-    // packed flux-input rows [N][RW], RW = 12 + 16G: {pos (4 words), geo (8), U (4G), grad U
-    // (12G)}; when set, the gradient kernels write U, grad U and the static part there
-    // (instead of grad) for the tensor-memory-accelerator flux pass
+    // packed flux-input rows [N][kRowRot + RW], RW = 12 + 16G logical words {pos (4), geo
+    // (8), U (4G), grad U (12G)} after a prefix that repeats the last kRowRot of them; when
+    // set, the gradient kernels write U, grad U and the static part there (instead of grad)
+    // for the tensor-memory-accelerator flux pass
     T* frec;
     int RW;
     // individual time bins (bins mode only): sorted bin per particle and the min-step index

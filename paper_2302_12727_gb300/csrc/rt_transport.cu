@@ -135,7 +135,23 @@ __global__ void k_inject_dense(const int32_t* __restrict__ targets, const int32_
     }
 }
 
-// position and geometry words of particle i's packed flux row
+// the logical words of particle i's packed flux row (after its prefix)
+template <class T>
+__device__ __forceinline__ T* packed_row(const PairArgs<T>& a, int64_t i) {
+    return a.frec + i * (int64_t)(a.RW + kRowRot) + kRowRot;
+}
+
+// logical words [w, w + K) of a packed row (w a multiple of 4); those among the last kRowRot
+// are written into the prefix too
+template <int K, class T>
+__device__ __forceinline__ void row_store(const PairArgs<T>& a, T* row, int w, const T* v) {
+    vstore<K>(row + w, v);
+#pragma unroll
+    for (int k = 0; k < K; k += 4)
+        if (w + k >= a.RW - kRowRot) vstore<4>(row + (w + k) - a.RW, v + k);
+}
+
+// position and geometry words of particle i's packed flux row (never among the last kRowRot)
 template <class T>
 __device__ __forceinline__ void packed_static(const PairArgs<T>& a, int64_t i, T* row) {
     if constexpr (std::is_same<T, float>::value) {
@@ -204,9 +220,9 @@ __global__ void __launch_bounds__(128) k_gradient(PairArgs<T> a, const T* __rest
 #pragma unroll
     for (int c = 0; c < NC; ++c) sym_mv(M, acc[c][0], acc[c][1], acc[c][2], out[3 * c], out[3 * c + 1], out[3 * c + 2]);
     if (a.frec) {
-        T* row = a.frec + i * a.RW;
-        vstore<3 * NC>(row + 12 + 4 * a.G + 12 * g0, out);
-        vstore<NC>(row + 12 + 4 * g0, ui);
+        T* row = packed_row(a, i);
+        row_store<3 * NC>(a, row, 12 + 4 * a.G + 12 * g0, out);
+        row_store<NC>(a, row, 12 + 4 * g0, ui);
         if (g0 == 0) packed_static(a, i, row);
     } else {
         vstore<3 * NC>(grad + i * 12 * a.G + 12 * g0, out);
@@ -268,9 +284,9 @@ __global__ void __launch_bounds__(256) k_gradient_g(PairArgs<float> a, const flo
 #pragma unroll
     for (int c = 0; c < 4; ++c) sym_mv(M, acc[c][0], acc[c][1], acc[c][2], out[3 * c], out[3 * c + 1], out[3 * c + 2]);
     if (a.frec) {
-        float* row = a.frec + i * a.RW;
-        vstore<12>(row + 12 + 4 * a.G + 12 * (g0 + g), out);
-        vstore<4>(row + 12 + off, ui);
+        float* row = packed_row(a, i);
+        row_store<12>(a, row, 12 + 4 * a.G + 12 * (g0 + g), out);
+        row_store<4>(a, row, 12 + off, ui);
         if (g0 + g == 0) packed_static(a, i, row);
     } else {
         vstore<12>(grad + i * 12 * a.G + 12 * (g0 + g), out);
@@ -358,9 +374,9 @@ __global__ void __launch_bounds__(kGradBlockMax, GC == 4 ? 1280 / kGradBlockMax 
 #pragma unroll
     for (int c = 0; c < 4; ++c) sym_mv(M, acc[c][0], acc[c][1], acc[c][2], out[3 * c], out[3 * c + 1], out[3 * c + 2]);
     if (a.frec) {
-        float* row = a.frec + i * a.RW;
-        vstore<12>(row + 12 + 4 * a.G + 12 * (g0 + g), out);
-        vstore<4>(row + 12 + off, ui);
+        float* row = packed_row(a, i);
+        row_store<12>(a, row, 12 + 4 * a.G + 12 * (g0 + g), out);
+        row_store<4>(a, row, 12 + off, ui);
         if (g0 + g == 0) packed_static(a, i, row);
     } else {
         vstore<12>(grad + i * 12 * a.G + 12 * (g0 + g), out);
@@ -832,9 +848,11 @@ __global__ void __launch_bounds__(kTmaWarpsMax * 32, TmaMinBlocks<G>::value) k_f
     const int q = lane & 7;
     const int r0 = __shfl_sync(FULL, kl.y, 4 * q), r1 = __shfl_sync(FULL, kl.y, 4 * q + 1);
     const int r2 = __shfl_sync(FULL, kl.y, 4 * q + 2), r3 = __shfl_sync(FULL, kl.y, 4 * q + 3);
-    if (lane < 8) tma_gather4(smem_u32(ws + q * R::SLOT), &rows, 0, r0, r1, r2, r3, mb);
+    // even slots get the rows as they are (copy from word kRowRot), odd slots rotated by four
+    // chunks (copy from word 0 of the prefixed row)
+    if (lane < 8) tma_gather4(smem_u32(ws + q * R::SLOT), &rows, (q & 1) ? 0 : kRowRot, r0, r1, r2, r3, mb);
     const int64_t i = kl.x;
-    const float* rk = a.frec + i * RW;
+    const float* rk = packed_row(a, i);
     const uint4 pkv = *reinterpret_cast<const uint4*>(rk);
     const Pos<float> pi = {pkv.x, pkv.y, pkv.z};
     float gi8[8], gj8[8];
@@ -846,11 +864,20 @@ __global__ void __launch_bounds__(kTmaWarpsMax * 32, TmaMinBlocks<G>::value) k_f
         mbar_wait(mb, 0, budget > 2000000000ull ? budget : 2000000000ull);
         return;
     }
-    // this lane's row: slot lane / 4, row lane % 4 within it
+    // this lane's row: slot lane / 4, row lane % 4 within it.  A quarter-warp reads the rows
+    // of one even and one odd slot; the slots start on the same bank, and the rows of a slot
+    // cover four of the eight 16-byte bank groups at any one chunk, so the odd slot's rotation
+    // by four chunks sends its lanes to the other four (all but the last four chunks).
+    // Logical chunk c is at chunk c (even slot), c + 4 or, for the last four, c + 4 - RW / 4.
     const float* rl = ws + (lane >> 2) * R::SLOT + (lane & 3) * RW;
-    const uint4 pv = *reinterpret_cast<const uint4*>(rl);
+    const bool odd = (lane >> 2) & 1;
+    const float* rlA = rl + (odd ? kRowRot : 0);
+    const float* rlB = rl + (odd ? kRowRot - RW : 0);
+    constexpr int NCH = RW / 4;
+    auto lrow = [&](int c) -> const float* { return (c < NCH - kRowRot / 4 ? rlA : rlB) + 4 * c; };
+    const uint4 pv = *reinterpret_cast<const uint4*>(lrow(0));
     const Pos<float> pj = {pv.x, pv.y, pv.z};
-    vload<8>(rl + 4, gj8);
+    vload<8>(lrow(1), gj8);
     float dx, dy, dz;
     sep(a.sp, pi, pj, dx, dy, dz);
     float r = sqrt_(dx * dx + dy * dy + dz * dz);
@@ -870,9 +897,11 @@ __global__ void __launch_bounds__(kTmaWarpsMax * 32, TmaMinBlocks<G>::value) k_f
     for (int g = 0; g < G; ++g) {
         float ui[4], uj[4], gri[12], grj[12];
         vload<4>(rk + 12 + 4 * g, ui);
-        vload<4>(rl + 12 + 4 * g, uj);
+        vload<4>(lrow(3 + g), uj);
         vload<12>(rk + 12 + 4 * G + 12 * g, gri);
-        vload<12>(rl + 12 + 4 * G + 12 * g, grj);
+        vload<4>(lrow(3 + G + 3 * g), grj);
+        vload<4>(lrow(4 + G + 3 * g), grj + 4);
+        vload<4>(lrow(5 + G + 3 * g), grj + 8);
         pair_flux<HLL>(ui, uj, gri, grj, dx, dy, dz, wi, wj, Ax, Ay, Az, diss, x.c, x.wave, An, &out[4 * g]);
     }
     if constexpr (BINS) {
@@ -1095,15 +1124,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// tensor map of the packed rows [n][12 + 16G] floats, box of one whole row (for
-// tile::gather4); encoded again whenever the buffer or its shape changes
+// tensor map of the packed rows [n][kRowRot + 12 + 16G] floats, box of the 12 + 16G logical
+// words of a row (for tile::gather4); encoded again whenever the buffer or its shape changes
 static bool packed_rows_map(rt_ctx* c) {
     const int RW = 12 + 16 * c->cfg.n_groups;
     if (c->rows_map_for == c->frec.p && c->rows_map_n == c->n) return true;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || !c->frec.p) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)RW, (cuuint64_t)c->n};
-    cuuint64_t strides[1] = {(cuuint64_t)RW * 4};
+    // rows of kRowRot + RW words (the prefix first); the box is the RW logical words
+    cuuint64_t dims[2] = {(cuuint64_t)(RW + kRowRot), (cuuint64_t)c->n};
+    cuuint64_t strides[1] = {(cuuint64_t)(RW + kRowRot) * 4};
     cuuint32_t box[2] = {(cuuint32_t)RW, 1};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&c->rows_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->frec.p, dims, strides, box, estr,
