@@ -279,7 +279,7 @@ __device__ __forceinline__ void wave_speeds_(const T* __restrict__ tab, T E, T F
         return;
     }
     const T Fn = sqrt_(Fx * Fx + Fy * Fy + Fz * Fz);
-    const T f = fmin_(Fn / (c * E), T(1));
+    const T f = fmin_(Fn * rcp_(c * E), T(1));
     const T cx = Fy * Az - Fz * Ay, cy = Fz * Ax - Fx * Az, cz = Fx * Ay - Fy * Ax;
     const T th = atan2(sqrt_(cx * cx + cy * cy + cz * cz), Fx * Ax + Fy * Ay + Fz * Az);
     const T x = f * T(RT_WAVE_NF - 1), y = th / T(3.14159265358979323846) * T(RT_WAVE_NTH - 1);
@@ -324,8 +324,9 @@ __device__ __forceinline__ void pair_flux(const T uk[4], const T ul[4], const T 
         const T den = lp - lm;
         if (den > T(0)) {
             const T jm = lp * lm * An;
+            const T iden = T(1) / den;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) phi[q] = (lp * fL[q] - lm * fR[q] + jm * (R[q] - L[q])) / den;
+            for (int q = 0; q < 4; ++q) phi[q] = (lp * fL[q] - lm * fR[q] + jm * (R[q] - L[q])) * iden;
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) phi[q] = T(0.5) * (fL[q] + fR[q]);
