@@ -258,7 +258,7 @@ def run_ours(args):
         tune_info = {"source": "--tuning"}
     elif not args.no_autotune:
         from paper_2302_12727_gb300.autotune import autotune
-        tune_info = autotune(T, U0, dt, min(n_sub, 10), L, alpha, repeats=2)
+        tune_info = autotune(T, U0, dt, min(n_sub, 10), L, alpha, repeats=2, subcycles_per_build=n_sub)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     # the timed steps bracket one pair-pass launch in PAIR_EVENT_EVERY with events (each
     # event pair serialises the graph around its kernel: bracketing all kernels costs ~5% of

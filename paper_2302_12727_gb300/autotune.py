@@ -87,9 +87,12 @@ def _time_ms(fn, repeats):
     return best
 
 
-def tune_shapes(transport, U, dt, n_sub, L=None, alpha=None, repeats=2, tuning=None) -> tuple:
+def tune_shapes(transport, U, dt, n_sub, L=None, alpha=None, repeats=2, tuning=None,
+                subcycles_per_build=None) -> tuple:
     """Stages 2 and 3 from the variants in `tuning` (default: the context's): returns the
-    tuning with the fastest shapes and cell size, and the times of every candidate."""
+    tuning with the fastest shapes and cell size, and the times of every candidate.  The
+    cell size sets the particle order, so it is scored by one rebuild plus the
+    `subcycles_per_build` steps (default n_sub) that one build serves."""
     t = dict(tuning or transport.tuning())
     report = {}
 
@@ -110,23 +113,30 @@ def tune_shapes(transport, U, dt, n_sub, L=None, alpha=None, repeats=2, tuning=N
             times[v] = _time_ms(steps, repeats)
         t[knob] = min(times, key=times.get)
         report[knob + "_ms"] = {str(k): v for k, v in times.items()}
-    times = {}
+    per_build = n_sub if subcycles_per_build is None else subcycles_per_build
+    rebuild, stepping, score = {}, {}, {}
     P0 = transport.diagnostics()["n_pairs"]
     for ce in CELL_EIGHTHS:
         transport.set_tuning(**dict(t, cell_eighths=ce))
-        times[ce] = _time_ms(transport.rebuild, repeats)
+        rebuild[ce] = _time_ms(transport.rebuild, repeats)
         if transport.diagnostics()["n_pairs"] != P0:
             raise RuntimeError("the cell size changed the pair count")
-    t["cell_eighths"] = min(times, key=times.get)
-    report["cell_eighths_rebuild_ms"] = {str(k): v for k, v in times.items()}
+        stepping[ce] = _time_ms(steps, repeats)
+        score[ce] = rebuild[ce] + stepping[ce] * per_build / n_sub
+    t["cell_eighths"] = min(score, key=score.get)
+    report["cell_eighths_rebuild_ms"] = {str(k): v for k, v in rebuild.items()}
+    report["cell_eighths_steps_ms"] = {str(k): v for k, v in stepping.items()}
+    report["cell_eighths_score_ms"] = {str(k): v for k, v in score.items()}
     transport.set_tuning(**t)
     transport.rebuild()
     return t, report
 
 
 def autotune(transport, U, dt, n_sub, L=None, alpha=None, repeats=3, cache_path: str = DEFAULT_CACHE,
-             retune: bool = False, shapes: bool = True) -> dict:
-    """Tune a ``Transport`` on the device state U (torch tensor [G, 4, N])."""
+             retune: bool = False, shapes: bool = True, subcycles_per_build=None) -> dict:
+    """Tune a ``Transport`` on the device state U (torch tensor [G, 4, N]); n_sub steps
+    are timed per candidate, and `subcycles_per_build` (default n_sub) weighs the steps
+    against a rebuild when the cell size is chosen."""
     d = rt_diagnostics(transport.ctx)
     key = shape_key(transport.n, transport.G, d["n_pairs"], transport.riemann, transport.precision)
 
@@ -135,7 +145,8 @@ def autotune(transport, U, dt, n_sub, L=None, alpha=None, repeats=3, cache_path:
         best, ms = rt_autotune(transport.ctx, U, dt, n_sub, L, alpha, repeats)
         report = {"variants_ms": ms}
         if shapes and transport.precision == "fp32":
-            best, more = tune_shapes(transport, U, dt, n_sub, L, alpha, max(1, repeats - 1), best)
+            best, more = tune_shapes(transport, U, dt, n_sub, L, alpha, max(1, repeats - 1), best,
+                                     subcycles_per_build)
             report.update(more)
         return best, report
 
