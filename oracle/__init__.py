@@ -72,6 +72,9 @@ def _load():
         lib.orc_run.restype = C.c_long
         lib.orc_run.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp]
         lib.orc_inject.argtypes = [vp, C.c_double, dp, dp]
+        lib.orc_transport_given_gradients.restype = C.c_long
+        lib.orc_transport_given_gradients.argtypes = [vp, C.c_double, dp, dp, dp]
+        lib.orc_set_fields.argtypes = [vp, C.c_long, C.c_long, dp, dp]
         lib.orc_jvp.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp]
         lib.orc_jvp_kinks.restype = C.c_long
         lib.orc_jvp_kinks.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, C.c_double]
@@ -282,6 +285,22 @@ class Oracle:
         L = _c(np.zeros((self.n_src, self.G)) if L is None else L).reshape(self.n_src, self.G)
         self.lib.orc_inject(self._p, float(dt), _dp(U), _dp(L) if L.size else _dp(np.zeros(1)))
         return U
+
+    def transport_given_gradients(self, U0, grad, dt, alpha=None):
+        """The transport and sink of one step with the gradients grad [G, 4, 3, N] given (no
+        injection); returns (U, clamp_count)."""
+        U = _c(U0).copy().reshape(self.G, 4, self.n)
+        g = _c(grad).reshape(self.G, 4, 3, self.n)
+        a = None if alpha is None else _c(alpha)
+        nclamp = self.lib.orc_transport_given_gradients(self._p, float(dt), _dp(U), _dp(g), _dp(a))
+        return U, nclamp
+
+    def set_fields(self, first, omega, B):
+        """Give omega (V = 1 / omega) and B [k, 3, 3] of particles first, first + 1, ..."""
+        om = _c(omega).reshape(-1)
+        b = _c(B).reshape(len(om), 3, 3)
+        self.lib.orc_set_fields(self._p, int(first), len(om), _dp(om), _dp(b))
+        self._cache.clear()
 
     def jvp(self, U0, dU0, n_sub, dt, L, dL, alpha=None):
         U0 = _c(U0).reshape(self.G, 4, self.n)

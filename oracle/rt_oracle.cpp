@@ -863,21 +863,23 @@ static void inject(const Model& M, double dt, std::vector<T>& U, const std::vect
 }
 
 // One time step: injection -> transport -> grey sink (-> optional fix-up).
-// U: [G][4][N] in/out, L: [S][G], alpha: [N] or null.
+// U: [G][4][N] in/out, L: [S][G], alpha: [N] or null.  With grad_given ([G][4][3][N]) the
+// step is the transport and sink alone, with those gradients (the caller has injected).
 template <class T>
 static void step(const Model& M, double dt, std::vector<T>& U, const std::vector<T>& L, const double* alpha,
-                 StepStats* st, const double* alpha_g = nullptr) {
+                 StepStats* st, const double* alpha_g = nullptr, const std::vector<T>* grad_given = nullptr) {
     const long n = M.P.n;
     const int G = M.cfg.n_groups;
     const int C = 4 * G;
     const double c = M.cfg.c_red;
 
     // 1. injection
-    inject(M, dt, U, L);
+    if (!grad_given) inject(M, dt, U, L);
 
     // 2. gradients of the injected state
-    std::vector<T> grad;
-    gradients(M, U, grad);
+    std::vector<T> grad_own;
+    if (!grad_given) gradients(M, U, grad_own);
+    const std::vector<T>& grad = grad_given ? *grad_given : grad_own;
 
     // 3. each particle k sums F_kl . A_kl over its neighbours l, with k as the left state
     std::vector<T> Unew(U.size());
@@ -1127,6 +1129,32 @@ long orc_run(void* p, int n_sub, double dt, double* U, const double* L, const do
     for (int k = 0; k < n_sub; ++k) step(*M, dt, u, l, alpha, &st);
     std::memcpy(U, u.data(), C * n * sizeof(double));
     return st.clamped;
+}
+
+// the transport and sink of one step with the gradients given (the stages after the
+// injection and the gradients); U in/out [G][4][N], grad [G][4][3][N], alpha [N] or null;
+// returns the fix-up count
+long orc_transport_given_gradients(void* p, double dt, double* U, const double* grad, const double* alpha) {
+    Model* M = (Model*)p;
+    size_t n = M->P.n, C = 4 * M->cfg.n_groups;
+    std::vector<double> u(U, U + C * n), g(grad, grad + 3 * C * n), l;
+    StepStats st;
+    step(*M, dt, u, l, alpha, &st, nullptr, &g);
+    std::memcpy(U, u.data(), C * n * sizeof(double));
+    return st.clamped;
+}
+
+// omega_i (hence V_i = 1 / omega_i) and B_i [3][3] of particles [first, first + count) given by
+// the caller instead of the model's own: a rank of a domain decomposition takes them from
+// the particles' owners, whose neighbourhoods are complete
+void orc_set_fields(void* p, long first, long count, const double* omega, const double* B) {
+    Model* M = (Model*)p;
+    for (long k = 0; k < count; ++k) {
+        const long i = first + k;
+        M->omega[i] = omega[k];
+        M->V[i] = 1.0 / omega[k];
+        for (int e = 0; e < 9; ++e) M->B[9 * i + e] = B[9 * k + e];
+    }
 }
 
 // the injection of one step alone (the first stage of orc_run's step); U in/out [G][4][N]

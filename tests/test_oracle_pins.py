@@ -839,3 +839,32 @@ def test_pair_lists_in_other_boxes_are_the_brute_force_lists(box, periodic):
         # truncated supports at the walls: the particles nearest a wall have the largest h
         wall = np.min(np.minimum(x, np.asarray(box)[:, None] - x) / np.asarray(box)[:, None], axis=0)
         assert o.h[wall < 0.03].mean() > 1.1 * o.h[wall > 0.25].mean()
+
+
+def test_given_gradients_and_fields_reproduce_the_step():
+    """The decomposition's entries into the oracle add no arithmetic: a step is the
+    injection, then the transport and sink with the oracle's own gradients of the injected
+    state, bitwise; setting a particle's omega and B to its own values changes nothing, and
+    setting omega changes V to 1 / omega."""
+    rng = np.random.default_rng(71)
+    x = W.jittered_lattice(10, 0.25, rng)
+    n = x.shape[1]
+    xsrc = np.array([[0.4], [0.5], [0.6]])
+    o = oracle.Oracle(x, np.full(n, 1.0 / n), xsrc, n_groups=2, clamp_negative=True)
+    U = np.zeros((2, 4, n))
+    U[:, 0] = rng.uniform(0.5, 1.5, size=(2, n))
+    U[:, 1:] = 0.3 * U[:, :1] * rng.normal(size=(2, 3, n)) / np.sqrt(3)
+    L = np.array([[1.0, 2.0]])
+    alpha = rng.uniform(0.0, 1.0, size=n)
+    dt = 0.01
+    ref, nref = o.run(U, 1, dt, L, alpha)
+    Ui = o.inject(U, dt, L)
+    got, ngot = o.transport_given_gradients(Ui, o.gradients(Ui).reshape(2, 4, 3, n), dt, alpha)
+    assert np.array_equal(got, ref) and ngot == nref
+    p = o.particles()
+    om, B = p["omega"].copy(), p["B"].copy()
+    o.set_fields(n // 2, om[n // 2:], B[n // 2:])
+    again, _ = o.run(U, 1, dt, L, alpha)
+    assert np.array_equal(again, ref)
+    o.set_fields(3, 2.0 * om[3:4], B[3:4])
+    assert o.V[3] == 1.0 / (2.0 * om[3]) and o.omega[3] == 2.0 * om[3]
