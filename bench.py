@@ -717,7 +717,7 @@ def run_decomposed(args):
     w = workload(args.workload)
     G, n_sub = w.n_groups, w.n_steps
     eng = domain.CudaEngine(G, w.c_red, precision=args.precision, device=dev, riemann=args.riemann)
-    D = domain.DistributedTransport(w.x, w.m, w.xsrc, eng)
+    D = domain.DistributedTransport(w.x, w.m, w.xsrc, eng, exchange=args.exchange)
     # every particle's row is exact in its owner's context: the owned rows sum to 2P
     rows_owned = float(eng.pair_counts()[:D.plan.n_owned].sum())
     om_own = eng.t.fields()["omega"].cpu().numpy()[:D.plan.n_owned]
@@ -748,6 +748,7 @@ def run_decomposed(args):
         times.append(time.perf_counter() - t0)
     t_max = max_over_ranks(sum(times), ws, dev if args.backend == "nccl" else torch.device("cpu"))
     P = int(D._all_sum([rows_owned])[0]) // 2
+    held = float(D._all_sum([len(D.plan.local)])[0]) / w.n      # every rank takes part
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": P * G * n_sub * args.steps / t_max, "unit": UNIT, "n_gpus": ws,
@@ -756,7 +757,8 @@ def run_decomposed(args):
             "scaling": "strong", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": w.name, "particles": w.n, "groups": G, "sub_cycles": n_sub,
-                       "parallelism": f"domain decomposition x{ws}", "pairs": P,
+                       "parallelism": f"domain decomposition x{ws}", "exchange": args.exchange,
+                       "particles_held_over_owned": held, "pairs": P,
                        "note": "host-timed steps (sub-cycles with halo exchanges + energy all-reduce); "
                                "the decomposition's build is not timed"}}))
     D.close()
@@ -791,6 +793,9 @@ def main():
                     help="move the particles at this fraction of c (drift correction + new neighbours every step)")
     ap.add_argument("--backend", default="nccl", choices=["nccl", "gloo"],
                     help="process-group backend of --decompose (gloo: exchanges through the host)")
+    ap.add_argument("--exchange", default="state", choices=["state", "gradients"],
+                    help="what --decompose exchanges per sub-cycle: the ghosts' states (deep halo) or "
+                         "states and gradients (the thesis's pattern, shallow halo)")
     ap.add_argument("--decompose", action="store_true",
                     help="with N > 1 ranks: one particle set split over the ranks by the spatial domain "
                          "decomposition (halo exchanges over NCCL) instead of N independent replicas")

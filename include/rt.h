@@ -234,6 +234,25 @@ rt_status rt_transport_step(rt_ctx* ctx, double dt, void* U_dev, const double* L
  * same values).  RT_ERR_INVALID for a NULL U_dev or a dt that is negative or not finite. */
 rt_status rt_inject(rt_ctx* ctx, double dt, void* U_dev, const double* Lsrc_dev);
 
+/* The transport and sink of one step (Eqs. transport-update-explicit, riemann-GLF or
+ * riemann-HLL, and the sink) with the gradients given instead of computed: gradU_dev
+ * [G][4][3][N] in caller order, element type per precision (as rt_gradients writes them);
+ * no injection.  With gradU_dev from rt_gradients on the same U_dev it gives bitwise the
+ * result of rt_transport_step without sources.  A domain decomposition that exchanges
+ * gradients (the thesis's RT gradient send/recv) supplies its ghosts' gradients from their
+ * owners this way.  Plain launches; RT_ERR_INVALID for NULL arrays or a bad dt. */
+rt_status rt_transport_step_given_gradients(rt_ctx* ctx, double dt, void* U_dev, const void* gradU_dev,
+                                            const double* alpha_dev);
+
+/* Per-particle fields of caller particles [first, first + count) given instead of the
+ * context's own (Eqs. omega, particle-volume, matrix_B): omega_dev [count] and B_dev
+ * [count][3][3] (double, device, caller order); V = 1 / omega follows, and the pair
+ * kernels' records are derived from them as the neighbour search derives its own.  Valid
+ * until the next rt_neighbours.  A rank of a domain decomposition gives its ghosts the
+ * fields their owners computed with complete neighbourhoods.  RT_ERR_INVALID for a range
+ * outside [0, N) or NULL arrays with count > 0. */
+rt_status rt_set_fields(rt_ctx* ctx, int64_t first, int64_t count, const double* omega_dev, const double* B_dev);
+
 /* n_sub steps of size dt without any neighbour search in between (Sec. "Dynamic
  * Sub-Cycling"), replayed from one CUDA graph that the library captures once per
  * (n_sub, source/sink presence) and reuses; dt, Lsrc and alpha live in device buffers,

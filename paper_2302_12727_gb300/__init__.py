@@ -20,7 +20,8 @@ _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4
            5: "RT_ERR_GEOMETRY", 6: "RT_ERR_TIMEOUT", 7: "RT_ERR_STATE"}
 
 EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_neighbours_given_h", "rt_source_fields",
-            "rt_set_owned", "rt_gradients", "rt_transport_step", "rt_inject", "rt_subcycle",
+            "rt_set_owned", "rt_gradients", "rt_transport_step", "rt_inject", "rt_transport_step_given_gradients",
+            "rt_set_fields", "rt_subcycle",
             "rt_drift", "rt_set_time_bins", "rt_get_time_bins", "rt_step_bins", "rt_set_absorbers", "rt_cross_section", "rt_blackbody_groups",
             "rt_photon_number_to_luminosity",
             "rt_adjoint", "rt_energy", "rt_particle_fields", "rt_pairs", "rt_diagnostics", "rt_set_profiling",
@@ -99,6 +100,8 @@ def load_library():
     lib.rt_gradients.argtypes = [vp, dp, dp]
     lib.rt_transport_step.argtypes = [vp, C.c_double, dp, dp, dp]
     lib.rt_inject.argtypes = [vp, C.c_double, dp, dp]
+    lib.rt_transport_step_given_gradients.argtypes = [vp, C.c_double, dp, dp, dp]
+    lib.rt_set_fields.argtypes = [vp, i64, i64, dp, dp]
     lib.rt_subcycle.argtypes = [vp, C.c_int32, C.c_double, dp, dp, dp]
     lib.rt_adjoint.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, dp, dp, dp, dp, dp, dp]
     lib.rt_energy.argtypes = [vp, dp, C.POINTER(C.c_double)]
@@ -207,6 +210,14 @@ def rt_transport_step(ctx, dt, U, Lsrc=None, alpha=None):
 
 def rt_inject(ctx, dt, U, Lsrc=None):
     _check(ctx, load_library().rt_inject(ctx, float(dt), _ptr(U), _ptr(Lsrc)))
+
+
+def rt_transport_step_given_gradients(ctx, dt, U, gradU, alpha=None):
+    _check(ctx, load_library().rt_transport_step_given_gradients(ctx, float(dt), _ptr(U), _ptr(gradU), _ptr(alpha)))
+
+
+def rt_set_fields(ctx, first, count, omega, B):
+    _check(ctx, load_library().rt_set_fields(ctx, int(first), int(count), _ptr(omega), _ptr(B)))
 
 
 def rt_subcycle(ctx, n_sub, dt, U, Lsrc=None, alpha=None):

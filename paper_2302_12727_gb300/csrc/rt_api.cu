@@ -304,6 +304,27 @@ rt_status rt_transport_step(rt_ctx* c, double dt, void* U, const double* Lsrc, c
     return RT_OK;
 }
 
+rt_status rt_transport_step_given_gradients(rt_ctx* c, double dt, void* U, const void* gradU, const double* alpha) {
+    RT_TRY(check_ready(c));
+    if (!U || !gradU) return fail(c, RT_ERR_INVALID, "U_dev or gradU_dev is NULL");
+    if (!std::isfinite(dt) || dt < 0) return fail(c, RT_ERR_INVALID, "dt must be finite and >= 0");
+    const int G = c->cfg.n_groups;
+    RT_TRY(state_in(c, U, c->U_a.p, 4 * G, 4 * G, 0));
+    RT_TRY(state_in(c, gradU, c->grad_t.p, 12 * G, 12 * G, 0));
+    RT_TRY(set_step_inputs(c, dt, nullptr, alpha));
+    RT_TRY(launch_flux_given(c, c->stream, c->U_a.p, c->U_b.p, alpha != nullptr));
+    RT_TRY(state_out(c, c->U_b.p, U, 4 * G, 4 * G, 0));
+    return RT_OK;
+}
+
+rt_status rt_set_fields(rt_ctx* c, int64_t first, int64_t count, const double* omega, const double* B) {
+    RT_TRY(check_ready(c));
+    if (first < 0 || count < 0 || first > c->n || count > c->n - first)
+        return fail(c, RT_ERR_INVALID, "rt_set_fields: [first, first + count) must lie in [0, N)");
+    if (count > 0 && (!omega || !B)) return fail(c, RT_ERR_INVALID, "rt_set_fields: NULL omega or B");
+    return set_fields(c, first, count, omega, B);
+}
+
 rt_status rt_inject(rt_ctx* c, double dt, void* U, const double* Lsrc) {
     RT_TRY(check_ready(c));
     if (!U) return fail(c, RT_ERR_INVALID, "U_dev is NULL");

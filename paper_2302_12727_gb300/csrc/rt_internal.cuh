@@ -198,6 +198,10 @@ rt_status wait_selftest(rt_ctx* c, unsigned long long budget, bool* ran_out);
 rt_status launch_step(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_src, bool has_alpha,
                       bool inject_first = true, bool inject_after = false);
 rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec);
+// the flux stage (pair fluxes, update, sink) with the gradients already in grad_t (sorted)
+rt_status launch_flux_given(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_alpha);
+// omega, V and B of caller particles [first, first + count) given (device, double)
+rt_status set_fields(rt_ctx* c, int64_t first, int64_t count, const double* omega, const double* B);
 // one min-step `step` of a hydro step with individual time bins (c->bins_s, c->acc_t)
 rt_status launch_step_bins(rt_ctx* c, cudaStream_t s, int step, void* U, bool has_src, bool has_alpha);
 // rec += grad_t . (v dt) per component (needs launch_gradient on rec first)

@@ -1280,6 +1280,86 @@ rt_status launch_gradient(rt_ctx* c, cudaStream_t s, void* rec) {
     return RT_OK;
 }
 
+// packed flux rows from sorted states and gradients given in grad_t (one thread per
+// particle and group): what the gradient kernels write beside their gradients
+__global__ void k_pack_rows(PairArgs<float> a, const float* __restrict__ rec, const float* __restrict__ grad) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = t / a.G;
+    if (i >= a.n) return;
+    const int g = (int)(t - i * a.G);
+    float* row = packed_row(a, i);
+    float gq[12], u[4];
+    vload<12>(grad + i * 12 * a.G + 12 * g, gq);
+    vload<4>(rec + i * 4 * a.G + 4 * g, u);
+    row_store<12>(a, row, 12 + 4 * a.G + 12 * g, gq);
+    row_store<4>(a, row, 12 + 4 * g, u);
+    if (g == 0) packed_static(a, i, row);
+}
+
+rt_status launch_flux_given(rt_ctx* c, cudaStream_t s, void* Uin, void* Uout, bool has_alpha) {
+    if (c->fp64) {
+        launch_flux_t<double>(c, s, (const double*)Uin, (double*)Uout, has_alpha);
+    } else {
+        const bool packed = c->tune.flux_variant == 2 && c->cfg.n_groups <= kMaxGC && packed_rows_map(c);
+        if (packed) {
+            PairArgs<float> a = pair_args<float>(c);
+            a.frec = c->frec.as<float>();
+            k_pack_rows<<<nblk(c->n * c->cfg.n_groups, 256), 256, 0, s>>>(a, (const float*)Uin,
+                                                                          c->grad_t.as<float>());
+            ++c->launches;
+        }
+        launch_flux_t<float>(c, s, (const float*)Uin, (float*)Uout, has_alpha, packed);
+    }
+    RT_CUDA(c, cudaGetLastError());
+    return RT_OK;
+}
+
+// omega, V = 1 / omega and B of caller particles [first, first + count) from the caller
+// (omega [count], B [count][3][3], double), with the pair kernels' records derived from them
+// as k_geometry derives its own
+template <class T>
+__global__ void k_set_fields(const double* __restrict__ omega, const double* __restrict__ B9,
+                             const int32_t* __restrict__ inv_perm, int64_t first, int64_t count, int64_t n,
+                             const double* __restrict__ h, double* omega_d, double* V_d, double* B_d, T* geo_t,
+                             T* om_t) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int64_t p = inv_perm[first + k];
+    const double om = omega[k];
+    const double* b = B9 + 9 * k;
+    const double B[6] = {b[0], b[4], b[8], b[1], b[2], b[5]};   // xx yy zz xy xz yz
+    const double hi = h[p], H = kKappa * hi, iH = 1.0 / H;
+    const double V = 1.0 / om;
+    const double bp = V * V * kSigma * iH * iH * iH;
+    omega_d[p] = om;
+    V_d[p] = V;
+    geo_t[8 * p] = (T)iH;
+    geo_t[8 * p + 1] = (T)hi;
+    for (int e = 0; e < 6; ++e) {
+        B_d[e * n + p] = B[e];
+        geo_t[8 * p + 2 + e] = (T)(bp * B[e]);
+    }
+    om_t[p] = (T)om;
+}
+
+rt_status set_fields(rt_ctx* c, int64_t first, int64_t count, const double* omega, const double* B) {
+    if (count <= 0) return RT_OK;
+    const unsigned nb = nblk(count, 128);
+    if (c->fp64)
+        k_set_fields<double><<<nb, 128, 0, c->stream>>>(omega, B, c->inv_perm.as<int32_t>(), first, count, c->n,
+                                                        c->h_d.as<double>(), c->omega_d.as<double>(),
+                                                        c->V_d.as<double>(), c->B_d.as<double>(),
+                                                        c->geo_t.as<double>(), c->omega_t.as<double>());
+    else
+        k_set_fields<float><<<nb, 128, 0, c->stream>>>(omega, B, c->inv_perm.as<int32_t>(), first, count, c->n,
+                                                       c->h_d.as<double>(), c->omega_d.as<double>(),
+                                                       c->V_d.as<double>(), c->B_d.as<double>(),
+                                                       c->geo_t.as<float>(), c->omega_t.as<float>());
+    ++c->launches;
+    RT_CUDA(c, cudaGetLastError());
+    return RT_OK;
+}
+
 // one min-step of a hydro step with individual time bins, on the active sets only: the
 // injection and gradients of the starting particles, the pair fluxes of the pairs with a
 // starting member, the gather of the particles they touch (finalising those whose step ends

@@ -38,6 +38,13 @@ discarded: the next refresh overwrites them.  Unlike the thesis's scheme, gradie
 exchanged: the ghosts within H_max of the domain compute them (the halo is one H_max deeper),
 so a sub-cycle has one exchange instead of two.
 
+exchange="gradients" follows the thesis's pattern instead: the ghosts are only
+max(H_max, 2 H_s,max) deep (H_max for the transport), their omega and B come from their
+owners once per build (rt_set_fields), and each sub-cycle exchanges U, then the gradients
+(rt_gradients on every rank, the ghosts' rows replaced by their owners'), then runs the
+transport with those gradients (rt_transport_step_given_gradients).  An owned particle's
+pairs, its partners' states, gradients, omega, V, B and h are then all the owners' values.
+
 The exchanges are grouped point-to-point sends and receives (torch.distributed: NCCL between
 GPUs, gloo between CPU ranks); the energy all-reduce is in float64.  A rank's engine is the
 library (``CudaEngine``); the tests drive the same decomposition with the FP64 oracle as the
@@ -260,6 +267,19 @@ class CudaEngine:
     def inject(self, U, dt, L):
         self.t.inject(U, dt, L)
 
+    def fields(self):
+        f = self.t.fields()
+        return f["omega"], f["B"]
+
+    def set_fields(self, first, omega, B):
+        self.t.set_fields(first, omega, B)
+
+    def gradients(self, U):
+        return self.t.gradients(U)
+
+    def step_given_gradients(self, U, g, dt, alpha):
+        self.t.step_given_gradients(U, g, dt, alpha)
+
     def step(self, U, dt, L, alpha):
         self.t.step(U, dt, L, alpha)
 
@@ -282,10 +302,16 @@ class DistributedTransport:
 
     x [3, N], m [N], xsrc [3, S] are the whole set on every rank (a rank keeps what its plan
     holds).  ``engine`` runs one rank's share; ``nb`` is the number of partition blocks per
-    axis (a power of two)."""
+    axis (a power of two).  ``exchange`` chooses what crosses ranks in a sub-cycle: "state"
+    (the ghosts' U only, with ghosts 2 max(H_max, H_s,max) deep) or "gradients" (U, then the
+    ghosts' gradients, with ghosts max(H_max, 2 H_s,max) deep and their omega and B taken
+    from their owners once per build)."""
 
     def __init__(self, x, m, xsrc, engine, *, box=(1.0, 1.0, 1.0), periodic=True, nb=32, group=None,
-                 work=None, eta_res=1.2348):
+                 work=None, eta_res=1.2348, exchange="state"):
+        if exchange not in ("state", "gradients"):
+            raise ValueError("exchange must be 'state' or 'gradients'")
+        self.exchange_mode = exchange
         import torch.distributed as dist
         self.dist = dist
         self.group = group
@@ -323,11 +349,13 @@ class DistributedTransport:
         self.H_max = H_OVER_h * self._all_max(float(self.h[plan.owned].max(initial=0.0)))
         self.Hs_max = H_OVER_h * float(self.hs.max(initial=0.0))
         # 2.-3. the halo of the transport and the build with every h given: the transport
-        #    needs 2 H_max, the injection into owned particles the sources within H_s,max
-        #    and their gas neighbours
-        self.depth = 2.0 * max(self.H_max, self.Hs_max)
+        #    needs 2 H_max (H_max when the ghosts' gradients and fields come from their
+        #    owners), the injection into owned particles the sources within H_s,max and their
+        #    gas neighbours
+        t_depth = self.H_max if exchange == "gradients" else 2.0 * self.H_max
+        self.depth = max(t_depth, 2.0 * self.Hs_max)
         reach_src = reach_blocks(self.Hs_max, box, nb)
-        reach = max(reach_blocks(2.0 * self.H_max, box, nb), reach_src + reach_blocks(self.Hs_max, box, nb))
+        reach = max(reach_blocks(t_depth, box, nb), reach_src + reach_blocks(self.Hs_max, box, nb))
         self.plan = make_plan(self.x, box, periodic, nb, self.block_owner, self.rank, reach)
         self.reach = reach
         self._exchange_owned_h()
@@ -335,6 +363,8 @@ class DistributedTransport:
         loc = self.plan.local
         engine.build(self.x[:, loc], self.m[loc], self.xsrc[:, self.src_mask], self.h[loc],
                      self.hs[self.src_mask], self.plan.n_owned)
+        if exchange == "gradients":
+            self._exchange_fields()
 
     # collectives on host scalars / arrays (float64)
     def _tensor(self, v):
@@ -365,6 +395,20 @@ class DistributedTransport:
         exchange(hl, self.plan, self.group)
         self.h[loc] = hl.cpu().numpy()
 
+    def _exchange_fields(self):
+        """Owners send omega and B; the ghosts take them (their own neighbourhoods are cut
+        by the halo)."""
+        import torch
+        om, B = self.engine.fields()
+        k = self.plan.n_owned
+        fb = torch.cat([om.reshape(1, -1), B.reshape(-1, 9).T], dim=0).to(torch.float64).contiguous()
+        if self.dist.get_backend(self.group) == "gloo" and fb.is_cuda:
+            fb = fb.cpu()
+        exchange(fb, self.plan, self.group)
+        n_loc = fb.shape[1]
+        if n_loc > k:
+            self.engine.set_fields(k, fb[0, k:].contiguous(), fb[1:, k:].T.reshape(-1, 3, 3).contiguous())
+
     # ----- state
     def local_state(self, U_global):
         """This rank's [G, 4, n_local] share of a global [G, 4, N] state, in the engine's type."""
@@ -380,12 +424,19 @@ class DistributedTransport:
 
     def subcycle(self, U, n_sub, dt, L=None, alpha=None):
         """n_sub transport steps of the local state U (in place): the injection, the ghost
-        refresh (carrying the owners' injected states), then the rest of the step."""
+        refresh (carrying the owners' injected states), then the rest of the step; with
+        exchange="gradients" the ghosts' gradients are refreshed from their owners before the
+        transport, as the thesis's RT gradient send/recv tasks do."""
         for _ in range(n_sub):
             if L is not None:
                 self.engine.inject(U, dt, L)
             exchange(U, self.plan, self.group)
-            self.engine.step(U, dt, None, alpha)
+            if self.exchange_mode == "gradients":
+                g = self.engine.gradients(U)
+                exchange(g, self.plan, self.group)
+                self.engine.step_given_gradients(U, g, dt, alpha)
+            else:
+                self.engine.step(U, dt, None, alpha)
         return U
 
     def energy(self, U):

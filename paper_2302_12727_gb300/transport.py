@@ -13,8 +13,8 @@ import torch
 
 from . import (RT_FP32_MIXED, RT_FP64, make_config, rt_adjoint, rt_create, rt_destroy, rt_diagnostics, rt_drift,
                rt_energy, rt_get_tuning, rt_gradients, rt_neighbours, rt_neighbours_given_h, rt_pairs,
-               rt_inject, rt_particle_fields, rt_set_owned, rt_set_stream, rt_set_tuning, rt_source_fields,
-               rt_subcycle, rt_transport_step)
+               rt_inject, rt_particle_fields, rt_set_fields, rt_set_owned, rt_set_stream, rt_set_tuning,
+               rt_source_fields, rt_subcycle, rt_transport_step, rt_transport_step_given_gradients)
 
 
 def _dev(a, dtype, device):
@@ -117,6 +117,21 @@ class Transport:
         self._sync_stream()
         rt_transport_step(self.ctx, dt, U, L, alpha)
         return U
+
+    def step_given_gradients(self, U, gradU, dt, alpha=None):
+        """Transport and sink of one step with the gradients gradU [G, 4, 3, N] given, in place
+        (no injection; rt_transport_step_given_gradients)."""
+        self._sync_stream()
+        rt_transport_step_given_gradients(self.ctx, dt, U, gradU.contiguous(), alpha)
+        return U
+
+    def set_fields(self, first, omega, B):
+        """Give omega [k] and B [k, 3, 3] (float64) of particles first, first + 1, ...
+        (rt_set_fields)."""
+        self._sync_stream()
+        om = _dev(omega, torch.float64, self.device)
+        b = _dev(B, torch.float64, self.device)
+        rt_set_fields(self.ctx, first, om.numel(), om, b)
 
     def inject(self, U, dt, L=None):
         """The injection stage of one step alone, in place (rt_inject)."""

@@ -52,6 +52,20 @@ class OracleEngine:
         if self.ns:
             U.copy_(torch.from_numpy(self.o.inject(U.numpy(), dt, L)))
 
+    def fields(self):
+        p = self.o.particles()
+        return torch.from_numpy(p["omega"].copy()), torch.from_numpy(p["B"].copy())
+
+    def set_fields(self, first, omega, B):
+        self.o.set_fields(first, np.asarray(omega), np.asarray(B))
+
+    def gradients(self, U):
+        return torch.from_numpy(self.o.gradients(U.numpy()).reshape(self.G, 4, 3, -1).copy())
+
+    def step_given_gradients(self, U, g, dt, alpha):
+        Un, _ = self.o.transport_given_gradients(U.numpy(), g.numpy(), dt, alpha)
+        U.copy_(torch.from_numpy(Un))
+
     def step(self, U, dt, L, alpha):
         Un, _ = self.o.run(U.numpy(), 1, dt, L if self.ns else None, alpha)
         U.copy_(torch.from_numpy(Un))
@@ -86,6 +100,11 @@ def _case(name):
     if name == "lattice-point-source":
         w = W.lattice_point_source()
         return w.x, w.m, w.xsrc, w.U0, w.Lsrc, None, w.n_groups, w.c_red, 4
+    if name == "lattice-48-dark":
+        # no sources: the gradient-exchange halo is one support radius deep, so the ghosts'
+        # own neighbourhoods are cut and their fields and gradients must be their owners'
+        x, m, _, U0, _, alpha, G, c, nsteps = _case("lattice-48")
+        return x, m, np.zeros((3, 0)), U0, None, alpha, G, c, nsteps
     rng = np.random.default_rng(512)
     x = W.jittered_lattice(48, 0.2, rng)
     n = x.shape[1]
@@ -99,7 +118,7 @@ def _case(name):
     return x, np.full(n, 1.0 / n), xsrc, U0, Ls, alpha, G, 1.0, 3
 
 
-def _rank_main(rank, ws, port, name, out_path):
+def _rank_main(rank, ws, port, name, out_path, exchange="state"):
     os.environ["OMP_NUM_THREADS"] = str(max(1, (os.cpu_count() or 2) // ws))
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
     try:
@@ -108,7 +127,7 @@ def _rank_main(rank, ws, port, name, out_path):
         eng = OracleEngine(G, c, periodic=periodic)
         dt_ = 0.6 * float(np.load(out_path + ".dt.npy"))
         D = domain.DistributedTransport(x, m, xsrc, eng, nb=16 if name == "lattice-point-source" else 32,
-                                        periodic=periodic)
+                                        periodic=periodic, exchange=exchange)
         U = D.local_state(U0)
         D.subcycle(U, nsteps, dt_, D.local_luminosities(Ls), D.local_alpha(alpha))
         full = D.gather(U)
@@ -117,28 +136,36 @@ def _rank_main(rank, ws, port, name, out_path):
         counts = D._all_sum(np.eye(ws)[rank] * n_local)
         owned = D._all_sum(np.eye(ws)[rank] * D.plan.n_owned)
         if rank == 0:
-            np.savez(out_path, U=full, E=E, n_local=counts, owned=owned)
+            np.savez(out_path, U=full, E=E, n_local=counts, owned=owned, reach=D.reach)
         D.close()
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name, ws", [("lattice-point-source", 2), ("lattice-48", 2), ("lattice-48", 4),
-                                      ("lattice-40-walls", 3)])
-def test_decomposed_oracle_run_equals_single_rank(tmp_path, name, ws):
+@pytest.mark.parametrize("name, ws, exchange", [("lattice-point-source", 2, "state"), ("lattice-48", 2, "state"),
+                                                ("lattice-48", 4, "state"), ("lattice-40-walls", 3, "state"),
+                                                ("lattice-48", 2, "gradients"), ("lattice-48-dark", 2, "gradients"),
+                                                ("lattice-48-dark", 4, "gradients"),
+                                                ("lattice-40-walls", 3, "gradients")])
+def test_decomposed_oracle_run_equals_single_rank(tmp_path, name, ws, exchange):
+    """Both exchange modes: the ghosts' states only (deep halo), or states and gradients
+    with the ghosts' omega and B from their owners (the thesis's pattern, shallow halo)."""
     x, m, xsrc, U0, Ls, alpha, G, c, nsteps = _case(name)
-    o = oracle.Oracle(x, m, xsrc, n_groups=G, c_red=c, periodic=name != "lattice-40-walls")
+    o = oracle.Oracle(x, m, xsrc if xsrc.shape[1] else None, n_groups=G, c_red=c, periodic=name != "lattice-40-walls")
     dxm = ((o.V / (4 * np.pi / 3)) ** (1 / 3)).min()
     out = str(tmp_path / "dd")
     np.save(out + ".dt.npy", np.array(dxm / c))
     ref, _ = o.run(U0, nsteps, 0.6 * dxm / c, Ls, alpha)
     E_ref = o.energy(ref)
-    mp.start_processes(_rank_main, args=(ws, _free_port(), name, out), nprocs=ws, start_method="spawn")
+    mp.start_processes(_rank_main, args=(ws, _free_port(), name, out, exchange), nprocs=ws, start_method="spawn")
     r = np.load(out + ".npz")
     n = x.shape[1]
     assert r["owned"].sum() == n                       # every particle has exactly one owner
     if name != "lattice-point-source":
         assert r["n_local"].max() < n                  # the halos are proper subsets
+    if name == "lattice-48-dark":                      # one support radius of halo, not two
+        H = oracle.H_OVER_h * o.h.max()
+        assert int(r["reach"]) < domain.reach_blocks(2.0 * H, (1.0, 1.0, 1.0), 32)
     scale = np.abs(ref).reshape(G, -1).max(axis=1)[:, None, None]
     err = np.abs(r["U"] - ref) / (1e-12 * np.abs(ref) + 1e-14 * scale)
     assert err.max() <= 1.0, err.max()

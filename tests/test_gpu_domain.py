@@ -23,13 +23,13 @@ from test_gpu_parity import rel_l1  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-def _rank_main(rank, ws, port, name, precision, dt, out_path):
+def _rank_main(rank, ws, port, name, precision, dt, out_path, exchange="state"):
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
     try:
         torch.cuda.set_device(0)
         x, m, xsrc, U0, Ls, alpha, G, c, nsteps = _case(name)
         eng = domain.CudaEngine(G, c, precision=precision, device=torch.device("cuda", 0))
-        D = domain.DistributedTransport(x, m, xsrc, eng, nb=32)
+        D = domain.DistributedTransport(x, m, xsrc, eng, nb=32, exchange=exchange)
         U = D.local_state(U0)
         D.subcycle(U, nsteps, dt, D.local_luminosities(Ls), D.local_alpha(alpha))
         full = D.gather(U)
@@ -42,24 +42,30 @@ def _rank_main(rank, ws, port, name, precision, dt, out_path):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_decomposed_library_run_equals_single_context(tmp_path, precision):
+@pytest.mark.parametrize("precision, name, exchange", [("fp64", "lattice-48", "state"),
+                                                       ("fp32", "lattice-48", "state"),
+                                                       ("fp64", "lattice-48-dark", "gradients"),
+                                                       ("fp32", "lattice-48-dark", "gradients")])
+def test_decomposed_library_run_equals_single_context(tmp_path, precision, name, exchange):
+    """Both exchange modes; the gradient-exchange case has no sources, so its halo is one
+    support radius deep and the ghosts' fields and gradients must come from their owners."""
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    name, ws = "lattice-48", 2
+    ws = 2
     x, m, xsrc, U0, Ls, alpha, G, c, nsteps = _case(name)
-    o = oracle.Oracle(x, m, xsrc, n_groups=G, c_red=c)
+    xs = xsrc if xsrc.shape[1] else None
+    o = oracle.Oracle(x, m, xs, n_groups=G, c_red=c)
     dt = 0.6 * ((o.V / (4 * np.pi / 3)) ** (1 / 3)).min() / c
     out = str(tmp_path / "dd")
-    mp.start_processes(_rank_main, args=(ws, _free_port(), name, precision, dt, out), nprocs=ws,
+    mp.start_processes(_rank_main, args=(ws, _free_port(), name, precision, dt, out, exchange), nprocs=ws,
                        start_method="spawn")
     r = np.load(out + ".npz")
     assert r["n_local"].max() < x.shape[1]
     if precision == "fp64":
-        t = Transport(x, m, xsrc, n_groups=G, c_red=c, precision="fp64")
+        t = Transport(x, m, xs, n_groups=G, c_red=c, precision="fp64")
         U = t.state(U0)
         for _ in range(nsteps):
-            t.step(U, dt, t.luminosities(Ls), t.alpha(alpha))
+            t.step(U, dt, None if Ls is None else t.luminosities(Ls), t.alpha(alpha))
         ref = U.cpu().numpy()
         E_ref = t.energy(U)
         t.close()
@@ -113,7 +119,39 @@ def test_inject_then_sourceless_step_equals_step(precision):
     t.close()
 
 
-def test_bench_decomposed_mode_runs():
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_given_gradients_and_fields(precision):
+    """rt_transport_step_given_gradients with rt_gradients' own output is bitwise
+    rt_transport_step without sources; rt_set_fields with the context's own omega and B
+    changes nothing, and with another omega it changes V to 1 / omega."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2302_12727_gb300 import RTError
+    x, m, xsrc, U0, Ls, alpha, G, c, _ = _case("lattice-48")
+    t = Transport(x, m, xsrc, n_groups=G, c_red=c, precision=precision)
+    dt = 0.5 * t.diagnostics()["dx_min"] / c
+    al = t.alpha(alpha)
+    U1 = t.state(U0)
+    t.step(U1, dt, None, al)
+    U2 = t.state(U0)
+    t.step_given_gradients(U2, t.gradients(U2), dt, al)
+    assert torch.equal(U1, U2)
+    f = t.fields()
+    n = t.n
+    t.set_fields(n // 3, f["omega"][n // 3:], f["B"][n // 3:])
+    U3 = t.state(U0)
+    t.step(U3, dt, None, al)
+    assert torch.equal(U1, U3)
+    t.set_fields(5, 2.0 * f["omega"][5:6], f["B"][5:6])
+    g = t.fields()
+    assert float(g["V"][5]) == 1.0 / (2.0 * float(f["omega"][5]))
+    with pytest.raises(RTError):
+        t.set_fields(n - 1, f["omega"][:2], f["B"][:2])
+    t.close()
+
+
+@pytest.mark.parametrize("exchange", ["state", "gradients"])
+def test_bench_decomposed_mode_runs(exchange):
     """bench.py --decompose under torchrun: two ranks split one particle set (gloo backend,
     sharing the one GPU) and print one JSON line whose pair count is the whole set's."""
     if not torch.cuda.is_available():
@@ -126,7 +164,8 @@ def test_bench_decomposed_mode_runs():
     env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
            "127.0.0.1", "--master-port", str(_free_port()), os.path.join(root, "bench.py"), "--gpus", "2",
-           "--decompose", "--backend", "gloo", "--workload", "lattice-sources", "--steps", "2", "--warmup", "1"]
+           "--decompose", "--backend", "gloo", "--workload", "lattice-sources", "--steps", "2", "--warmup", "1",
+           "--exchange", exchange]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600, cwd=root)
     assert r.returncode == 0, r.stderr[-3000:]
     line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1]
@@ -136,3 +175,4 @@ def test_bench_decomposed_mode_runs():
     o = oracle.Oracle(w.x, w.m, w.xsrc, n_groups=w.n_groups, c_red=w.c_red)
     assert d["config"]["pairs"] == int(o.pairs()[0][-1]) // 2
     assert d["n_gpus"] == 2 and d["value"] > 0 and d["scaling"] == "strong"
+    assert d["config"]["exchange"] == exchange and d["config"]["particles_held_over_owned"] >= 1.0
