@@ -56,7 +56,7 @@ def _load():
         lib.orc_create.argtypes = [C.POINTER(_Cfg), C.c_long, dp, dp, C.c_long, dp, C.POINTER(C.c_int)]
         lib.orc_destroy.argtypes = [vp]
         lib.orc_create_given_h.restype = vp
-        lib.orc_create_given_h.argtypes = [C.POINTER(_Cfg), C.c_long, dp, dp, C.c_long, dp, dp, dp,
+        lib.orc_create_given_h.argtypes = [C.POINTER(_Cfg), C.c_long, dp, dp, C.c_long, dp, dp, dp, dp, dp,
                                            C.POINTER(C.c_int)]
         lib.orc_num_directed_pairs.restype = C.c_long
         lib.orc_num_directed_pairs.argtypes = [vp]
@@ -133,10 +133,13 @@ class Oracle:
 
     def __init__(self, x, m, xsrc=None, *, n_groups=1, c_red=1.0, eta_res=1.2348, eta_res_star=1.2348,
                  box=(1.0, 1.0, 1.0), periodic=True, clamp_negative=False, h_tol=1e-15, h_max_iter=200,
-                 brute_force=False, riemann="glf", wave_table=None, h=None, hs=None):
+                 brute_force=False, riemann="glf", wave_table=None, h=None, hs=None, omegas=None,
+                 octw=None):
         """riemann: "glf" (Eq. riemann-GLF) or "hll" (Eq. riemann-HLL); for HLL the wave-speed
         table (lmax, lmin) over (f, theta) defaults to m1_eigen.default_table().  h [N] and hs
-        [S]: smoothing lengths given instead of solved (omega is then evaluated at them)."""
+        [S]: smoothing lengths given instead of solved (omega is then evaluated at them);
+        with them, omegas [S] and octw [S, 8]: the sources' omega_s and octant sums given
+        instead of formed from this set's gas."""
         lib = _load()
         self.lib = lib
         self.x = _c(x)
@@ -157,9 +160,12 @@ class Oracle:
         else:
             hh = _c(h)
             hsa = _c(hs if hs is not None and self.n_src else np.zeros(1))
+            oms = None if omegas is None or not self.n_src else _c(omegas)
+            ow = None if octw is None or not self.n_src else _c(octw).reshape(self.n_src, 8)
             self._p = lib.orc_create_given_h(C.byref(cfg), self.n, _dp(self.x), _dp(self.m), self.n_src,
                                              _dp(self.xsrc) if self.n_src else _dp(np.zeros(3)), _dp(hh),
-                                             _dp(hsa), C.byref(st))
+                                             _dp(hsa), None if oms is None else _dp(oms),
+                                             None if ow is None else _dp(ow), C.byref(st))
         if st.value != 0:
             lib.orc_destroy(self._p)
             self._p = None

@@ -413,6 +413,10 @@ struct Model {
     // smoothing lengths given by the caller instead of solved (a rank of a domain
     // decomposition takes them from the particles' owners); empty: solve
     std::vector<double> h_given, hs_given;
+    // the sources' omega_s and octant sums w_a given by the caller (a rank of a domain
+    // decomposition takes them from the sources' owners, whose gas neighbourhoods are
+    // complete); empty: formed from the model's own gas
+    std::vector<double> omegas_given, octw_given;
 };
 
 // psi_j(x_i) = W(|x_i - x_j|, h_i) / omega_i     (Eq. psi with h evaluated at x_i)
@@ -538,7 +542,7 @@ static int build(Model& M) {
         HSolve hsol;
         if (!M.hs_given.empty()) {
             hsol.h = M.hs_given[s];
-            hsol.omega = omega_given(M.P, cl, p, hsol.h);
+            hsol.omega = M.omegas_given.empty() ? omega_given(M.P, cl, p, hsol.h) : M.omegas_given[s];
             if (!(hsol.h > 0.0) || !(hsol.omega > 0.0)) return ERR_INVALID;
         } else {
             hsol = solve_h(M.P, cl, p, c.eta_res_star, h0, c.h_tol, c.h_max_iter, h_cap);
@@ -567,6 +571,8 @@ static int build(Model& M) {
             oct.push_back(a);
             w[a] += ps;
         }
+        if (!M.octw_given.empty())
+            for (int a = 0; a < 8; ++a) w[a] = M.octw_given[8 * s + a];
         double wsum = 0;
         int qnz = 0;
         for (int a = 0; a < 8; ++a) {
@@ -989,10 +995,13 @@ void* orc_create(const orc_config* cfg, long n, const double* x, const double* m
 // as orc_create, with the smoothing lengths given: h [n] for the particles, hs [n_src] for the
 // sources (omega then evaluated at them)
 void* orc_create_given_h(const orc_config* cfg, long n, const double* x, const double* m, long n_src,
-                         const double* xsrc, const double* h, const double* hs, int* status) {
+                         const double* xsrc, const double* h, const double* hs, const double* omegas,
+                         const double* octw, int* status) {
     Model* M = new Model();
     M->h_given.assign(h, h + n);
     if (n_src > 0) M->hs_given.assign(hs, hs + n_src);
+    if (n_src > 0 && omegas) M->omegas_given.assign(omegas, omegas + n_src);
+    if (n_src > 0 && octw) M->octw_given.assign(octw, octw + 8 * n_src);
     M->cfg.n_groups = cfg->n_groups;
     M->cfg.c_red = cfg->c_red;
     M->cfg.eta_res = cfg->eta_res;

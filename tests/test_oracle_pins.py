@@ -868,3 +868,28 @@ def test_given_gradients_and_fields_reproduce_the_step():
     assert np.array_equal(again, ref)
     o.set_fields(3, 2.0 * om[3:4], B[3:4])
     assert o.V[3] == 1.0 / (2.0 * om[3]) and o.omega[3] == 2.0 * om[3]
+
+
+def test_given_source_normalisation_gives_the_full_sets_weights():
+    """A source's weights xi_sg (Sec. "Weights For Distribution Of Energy Density") depend
+    on its gas only through omega_s and the octant sums: given the whole set's, a subset of
+    the gas that lacks part of the source's neighbourhood gets exactly the whole set's xi for
+    the gas it has; without them it does not (the weights renormalise over what is left)."""
+    rng = np.random.default_rng(29)
+    x = W.jittered_lattice(12, 0.3, rng)
+    n = x.shape[1]
+    m = np.full(n, 1.0 / n)
+    xsrc = np.array([[0.5], [0.5], [0.5]])
+    full = oracle.Oracle(x, m, xsrc, n_groups=1)
+    s = full.sources()
+    keep = np.flatnonzero(x[0] < 0.52)                 # cuts the source's support in half
+    sub_args = dict(n_groups=1, h=full.h[keep], hs=s.hs)
+    given = oracle.Oracle(x[:, keep], m[keep], xsrc, omegas=s.omegas, octw=s.octw, **sub_args)
+    own = oracle.Oracle(x[:, keep], m[keep], xsrc, **sub_args)
+    xi_full = dict(zip(s.e_gas.tolist(), s.e_xi.tolist()))
+    sg = given.sources()
+    assert len(sg.e_gas) > 10 and len(sg.e_gas) < len(s.e_gas)
+    for g, xi in zip(sg.e_gas, sg.e_xi):
+        assert xi == xi_full[int(keep[g])]
+    so = own.sources()
+    assert not np.allclose(so.e_xi, sg.e_xi)
