@@ -206,9 +206,24 @@ rt_status rt_neighbours(rt_ctx* ctx, const double* x_dev, const double* m_dev, c
 rt_status rt_neighbours_given_h(rt_ctx* ctx, const double* x_dev, const double* m_dev, const double* xsrc_dev,
                                 const double* h_dev, const double* hs_dev);
 
+/* As rt_neighbours_given_h, with each source's omega_s (omegas_dev [S]) and octant sums
+ * w_a (octw_dev [S][8]) given too (Sec. "Weights For Distribution Of Energy Density", Eq.
+ * isotropy-correction-with-zero), device doubles read during the call: the weights xi_sg
+ * of the gas this context holds are then the ones the whole set gives, however much of the
+ * source's support it holds.  A rank of a domain decomposition takes them from the source's
+ * owner (the thesis's star send/recv), so that it needs no gas halo for the injection.  All
+ * four arrays may be NULL only when S = 0; errors as rt_neighbours_given_h. */
+rt_status rt_neighbours_given_fields(rt_ctx* ctx, const double* x_dev, const double* m_dev, const double* xsrc_dev,
+                                     const double* h_dev, const double* hs_dev, const double* omegas_dev,
+                                     const double* octw_dev);
+
 /* Smoothing lengths h_s of the sources from the last rt_neighbours (hs_dev [S], device
  * doubles, source order as given; written asynchronously on the context's stream). */
 rt_status rt_source_fields(rt_ctx* ctx, double* hs_dev);
+
+/* Each source's omega_s (omegas_dev [S]) and octant sums w_a (octw_dev [S][8]) from the
+ * last rt_neighbours, device doubles, written asynchronously; nothing when S = 0. */
+rt_status rt_source_norms(rt_ctx* ctx, double* omegas_dev, double* octw_dev);
 
 /* Particles owned by this context: caller indices [0, n_owned); the rest are ghost copies of
  * particles another rank owns (a domain decomposition places them last).  rt_energy then

@@ -19,7 +19,8 @@ RT_OK = 0
 _STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4: "RT_ERR_NOCONV",
            5: "RT_ERR_GEOMETRY", 6: "RT_ERR_TIMEOUT", 7: "RT_ERR_STATE"}
 
-EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_neighbours_given_h", "rt_source_fields",
+EXPORTED = ["rt_create", "rt_set_stream", "rt_neighbours", "rt_neighbours_given_h", "rt_neighbours_given_fields",
+            "rt_source_fields", "rt_source_norms",
             "rt_set_owned", "rt_gradients", "rt_transport_step", "rt_inject", "rt_transport_step_given_gradients",
             "rt_set_fields", "rt_subcycle",
             "rt_drift", "rt_set_time_bins", "rt_get_time_bins", "rt_step_bins", "rt_set_absorbers", "rt_cross_section", "rt_blackbody_groups",
@@ -96,6 +97,8 @@ def load_library():
     lib.rt_neighbours.argtypes = [vp, dp, dp, dp, dp]
     lib.rt_neighbours_given_h.argtypes = [vp, dp, dp, dp, dp, dp]
     lib.rt_source_fields.argtypes = [vp, dp]
+    lib.rt_neighbours_given_fields.argtypes = [vp, dp, dp, dp, dp, dp, dp, dp]
+    lib.rt_source_norms.argtypes = [vp, dp, dp]
     lib.rt_set_owned.argtypes = [vp, i64]
     lib.rt_gradients.argtypes = [vp, dp, dp]
     lib.rt_transport_step.argtypes = [vp, C.c_double, dp, dp, dp]
@@ -192,8 +195,17 @@ def rt_neighbours_given_h(ctx, x, m, xsrc, h, hs):
     _check(ctx, load_library().rt_neighbours_given_h(ctx, _ptr(x), _ptr(m), _ptr(xsrc), _ptr(h), _ptr(hs)))
 
 
+def rt_neighbours_given_fields(ctx, x, m, xsrc, h, hs, omegas, octw):
+    _check(ctx, load_library().rt_neighbours_given_fields(ctx, _ptr(x), _ptr(m), _ptr(xsrc), _ptr(h), _ptr(hs),
+                                                          _ptr(omegas), _ptr(octw)))
+
+
 def rt_source_fields(ctx, hs_out):
     _check(ctx, load_library().rt_source_fields(ctx, _ptr(hs_out)))
+
+
+def rt_source_norms(ctx, omegas_out, octw_out):
+    _check(ctx, load_library().rt_source_norms(ctx, _ptr(omegas_out), _ptr(octw_out)))
 
 
 def rt_set_owned(ctx, n_owned):

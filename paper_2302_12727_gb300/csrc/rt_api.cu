@@ -189,7 +189,8 @@ rt_status rt_set_stream(rt_ctx* c, void* s) {
 }
 
 static rt_status neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc, double* h_out,
-                            const double* h_in, const double* hs_in) {
+                            const double* h_in, const double* hs_in, const double* oms_in = nullptr,
+                            const double* octw_in = nullptr) {
     if (!c) return RT_ERR_INVALID;
     c->err.clear();
     if (!x) return fail(c, RT_ERR_INVALID, "x_dev is NULL");
@@ -199,7 +200,7 @@ static rt_status neighbours(rt_ctx* c, const double* x, const double* m, const d
     c->has_bins = false;   // bins live in the sorted order and depend on the pair lists
     int64_t gen0 = g_generation;
     int64_t targets0 = c->n_inj_targets;
-    rt_status s = build_neighbours(c, x, m, xsrc, h_in, hs_in);
+    rt_status s = build_neighbours(c, x, m, xsrc, h_in, hs_in, oms_in, octw_in);
     if (s != RT_OK) {
         drop_graphs(c);
         return s;
@@ -228,6 +229,26 @@ rt_status rt_neighbours_given_h(rt_ctx* c, const double* x, const double* m, con
     if (!h_in) return fail(c, RT_ERR_INVALID, "h_dev is NULL");
     if (c->n_src > 0 && !hs_in) return fail(c, RT_ERR_INVALID, "hs_dev is NULL with n_src > 0");
     return neighbours(c, x, m, xsrc, nullptr, h_in, hs_in);
+}
+
+rt_status rt_neighbours_given_fields(rt_ctx* c, const double* x, const double* m, const double* xsrc,
+                                     const double* h_in, const double* hs_in, const double* omegas_in,
+                                     const double* octw_in) {
+    if (!c) return RT_ERR_INVALID;
+    if (!h_in) return fail(c, RT_ERR_INVALID, "h_dev is NULL");
+    if (c->n_src > 0 && (!hs_in || !omegas_in || !octw_in))
+        return fail(c, RT_ERR_INVALID, "hs_dev, omegas_dev or octw_dev is NULL with n_src > 0");
+    return neighbours(c, x, m, xsrc, nullptr, h_in, hs_in, omegas_in, octw_in);
+}
+
+rt_status rt_source_norms(rt_ctx* c, double* omegas_dev, double* octw_dev) {
+    RT_TRY(check_ready(c));
+    if (c->n_src == 0) return RT_OK;
+    if (!omegas_dev || !octw_dev) return fail(c, RT_ERR_INVALID, "NULL omegas_dev or octw_dev");
+    RT_CUDA(c, cudaMemcpyAsync(omegas_dev, c->omegas_d.p, (size_t)c->n_src * 8, cudaMemcpyDeviceToDevice, c->stream));
+    RT_CUDA(c, cudaMemcpyAsync(octw_dev, c->omegas_d.as<double>() + c->n_src, (size_t)c->n_src * 64,
+                               cudaMemcpyDeviceToDevice, c->stream));
+    return RT_OK;
 }
 
 rt_status rt_source_fields(rt_ctx* c, double* hs_dev) {

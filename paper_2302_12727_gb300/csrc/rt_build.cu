@@ -1272,12 +1272,14 @@ constexpr int kSrcWarps = 8, kSrcRowsMax = 1024;
 // r mod kSrcWarps); the fill pass first counts every row, scans the counts in row order and
 // then writes each row's entries from its offset, so the entries come in the row-major
 // candidate order of a single warp's walk.  Cubes of more than kSrcRowsMax rows are walked
-// by warp 0 alone.  The fill pass also forms xi.
+// by warp 0 alone.  The fill pass also forms xi, from the octant sums of its own entries or,
+// when octw_given is set, from the caller's (a source's owner's, over its whole support).
 template <bool FILL>
 __global__ void __launch_bounds__(kSrcWarps * 32)
 k_src_entries(Grid g, const double* __restrict__ xs, int64_t n, const double* __restrict__ xsrc, int64_t S,
               const double* __restrict__ hs, const double* __restrict__ oms, int32_t* counts,
-              const int64_t* __restrict__ off, int32_t* e_gas, double* e_xi, double* octw_out) {
+              const int64_t* __restrict__ off, int32_t* e_gas, double* e_xi, double* octw_out,
+              const double* __restrict__ octw_given = nullptr) {
     __shared__ int row_n[kSrcRowsMax];
     __shared__ double w8s[kSrcWarps][8];
     __shared__ int total;
@@ -1372,6 +1374,7 @@ k_src_entries(Grid g, const double* __restrict__ xs, int64_t n, const double* __
     for (int a = 0; a < 8; ++a) {
         double v = 0.0;
         for (int w = 0; w < kSrcWarps; ++w) v += w8s[w][a];
+        if (octw_given) v = octw_given[8 * src + a];
         ws8[a] = v;
         wsum += v;
         qnz += (v > 0.0);
@@ -1433,7 +1436,7 @@ static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / 
 
 // ------------------------------------------------------------------------------------
 rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc, const double* h_in,
-                           const double* hs_in) {
+                           const double* hs_in, const double* oms_in, const double* octw_in) {
     const int64_t n = c->n, S = c->n_src;
     const rt_config& cfg = c->cfg;
     cudaStream_t st = c->stream;
@@ -1770,6 +1773,8 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         const unsigned sb = (unsigned)S;   // one block of kSrcWarps warps per source
         k_src_h<<<(unsigned)S, kSrcThreads, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S, sp,
                                                      c->hs_d.as<double>(), c->omegas_d.as<double>(), flags);
+        if (hs_in && oms_in)   // the sources' own omega_s, from their owners
+            RT_CUDA(c, cudaMemcpyAsync(c->omegas_d.p, oms_in, S * 8, cudaMemcpyDeviceToDevice, st));
         k_src_entries<false><<<sb, kSrcWarps * 32, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S,
                                                  c->hs_d.as<double>(), c->omegas_d.as<double>(),
                                                  c->src_counts.as<int32_t>(), nullptr, nullptr, nullptr, nullptr);
@@ -1801,7 +1806,7 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         k_src_entries<true><<<sb, kSrcWarps * 32, 0, st>>>(g, c->xs_d.as<double>(), n, c->xsrc_d.as<double>(), S,
                                                 c->hs_d.as<double>(), c->omegas_d.as<double>(), nullptr,
                                                 c->src_off.as<int64_t>(), c->src_entry_gas.as<int32_t>(),
-                                                c->src_entry_xi.as<double>(), octw);
+                                                c->src_entry_xi.as<double>(), octw, hs_in ? octw_in : nullptr);
         ++c->launches;
         if (NE > 0) {
             c->launches += 3;

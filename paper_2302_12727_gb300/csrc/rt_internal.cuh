@@ -179,9 +179,11 @@ void prof_end(rt_ctx* c, cudaStream_t s, int idx);
 
 // entry points of the kernel files
 namespace rt {
-// h_in [N] / hs_in [S] (caller order, device): given smoothing lengths (no solve), or NULL
+// h_in [N] / hs_in [S] (caller order, device): given smoothing lengths (no solve), or NULL;
+// with them, oms_in [S] / octw_in [S][8]: the sources' omega_s and octant sums, or NULL
 rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const double* xsrc,
-                           const double* h_in = nullptr, const double* hs_in = nullptr);
+                           const double* h_in = nullptr, const double* hs_in = nullptr,
+                           const double* oms_in = nullptr, const double* octw_in = nullptr);
 // caller-order component-major arrays <-> sorted records (comps values at record offset off)
 rt_status state_in(rt_ctx* c, const void* U_user, void* rec, int comps, int RS, int off);
 rt_status state_out(rt_ctx* c, const void* rec, void* U_user, int comps, int RS, int off);

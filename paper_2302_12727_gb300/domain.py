@@ -13,23 +13,24 @@ its domain, and only the ghosts' data crosses ranks:
   halo        a rank's ghosts are the particles of every block within `reach` blocks (per
               axis) of one of its own blocks;
   hydro step  (once per particle configuration)
-              1. each rank solves h for its own particles, and h_s for the sources inside its
-                 blocks, with ghosts out to the largest support radius;
+              1. each rank solves h for its own particles, and h_s, omega_s and the octant
+                 sums for the sources inside its blocks, with ghosts out to the largest
+                 support radius;
               2. the owners send h to the ranks holding the particles as ghosts, and every
-                 rank learns every h_s (a sum over ranks);
-              3. each rank builds its lists, geometry and injection weights with all h given
-                 (rt_neighbours_given_h), on ghosts out to D = 2 max(H_max, H_s,max), with
-                 the sources within H_s,max of its blocks;
+                 rank learns every source's h_s, omega_s and octant sums (sums over ranks);
+              3. each rank builds its lists, geometry and injection weights with all of them
+                 given (rt_neighbours_given_fields), on ghosts out to D = 2 H_max, with the
+                 sources within H_s,max of its blocks;
   sub-cycle   every rank injects its sources' energy (rt_inject), the owners send the
               ghosts' injected states (U), then every rank runs the rest of the step
               (rt_transport_step without sources: gradients, fluxes, update, sink) on its own
               particles and ghosts; the energy is summed over owned particles in double and
               over ranks by an all-reduce.
 
-Why D = 2 max(H_max, H_s,max) reproduces the single-rank result on every owned particle.
-Injection: an owned particle receives energy from sources within H_s,max, whose weights are
-normalised over their gas neighbours, within 2 H_s,max of the domain; the target's volume is
-its own.  Transport: an owned particle's pairs reach at most H_max, so its partners j lie
+Why D = 2 H_max reproduces the single-rank result on every owned particle.  Injection: an
+owned particle receives energy from sources within H_s,max, whose weights depend on their
+gas only through omega_s and the octant sums, which come from the sources' owners; the
+target's volume is its own.  Transport: an owned particle's pairs reach at most H_max, so its partners j lie
 within H_max of the domain; the flux of (i, j) needs grad U_j and B_j, i.e. j's own pair list
 and the states of j's neighbours, all within 2 H_max, and those states are the owners'
 injected states, refreshed after the injection.  Every h is the owner's, so every rank
@@ -38,8 +39,8 @@ discarded: the next refresh overwrites them.  Unlike the thesis's scheme, gradie
 exchanged: the ghosts within H_max of the domain compute them (the halo is one H_max deeper),
 so a sub-cycle has one exchange instead of two.
 
-exchange="gradients" follows the thesis's pattern instead: the ghosts are only
-max(H_max, 2 H_s,max) deep (H_max for the transport), their omega and B come from their
+exchange="gradients" follows the thesis's pattern instead: the ghosts are only H_max deep,
+their omega and B come from their
 owners once per build (rt_set_fields), and each sub-cycle exchanges U, then the gradients
 (rt_gradients on every rank, the ghosts' rows replaced by their owners'), then runs the
 transport with those gradients (rt_transport_step_given_gradients).  An owned particle's
@@ -238,21 +239,23 @@ class CudaEngine:
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.t = None
 
-    def _new(self, x, m, xsrc, h=None, hs=None):
+    def _new(self, x, m, xsrc, h=None, hs=None, omegas=None, octw=None):
         from .transport import Transport
         if self.t is not None:
             self.t.close()
         self.t = Transport(x, m, xsrc if xsrc.shape[1] else None, n_groups=self.G, c_red=self.c_red,
                            precision=self.precision, device=self.device, riemann=self.riemann, box=self.box,
-                           periodic=self.periodic, h=h, hs=hs)
+                           periodic=self.periodic, h=h, hs=hs, omegas=omegas, octw=octw)
 
     def solve(self, x, m, xsrc):
-        """Solve h (and h_s); returns (h [N], hs [S]) as float64 numpy arrays."""
+        """Solve h (and h_s); returns h [N], hs [S] and the sources' omega_s [S] and octant
+        sums [S, 8] as float64 numpy arrays."""
         self._new(x, m, xsrc)
-        return self.t.h.cpu().numpy(), self.t.source_h().cpu().numpy()
+        om, ow = self.t.source_norms()
+        return self.t.h.cpu().numpy(), self.t.source_h().cpu().numpy(), om.cpu().numpy(), ow.cpu().numpy()
 
-    def build(self, x, m, xsrc, h, hs, n_owned):
-        self._new(x, m, xsrc, h=h, hs=hs)
+    def build(self, x, m, xsrc, h, hs, n_owned, omegas=None, octw=None):
+        self._new(x, m, xsrc, h=h, hs=hs, omegas=omegas, octw=octw)
         self.t.set_owned(n_owned)
 
     def state(self, U):
@@ -303,8 +306,8 @@ class DistributedTransport:
     x [3, N], m [N], xsrc [3, S] are the whole set on every rank (a rank keeps what its plan
     holds).  ``engine`` runs one rank's share; ``nb`` is the number of partition blocks per
     axis (a power of two).  ``exchange`` chooses what crosses ranks in a sub-cycle: "state"
-    (the ghosts' U only, with ghosts 2 max(H_max, H_s,max) deep) or "gradients" (U, then the
-    ghosts' gradients, with ghosts max(H_max, 2 H_s,max) deep and their omega and B taken
+    (the ghosts' U only, with ghosts 2 H_max deep) or "gradients" (U, then the
+    ghosts' gradients, with ghosts H_max deep and their omega and B taken
     from their owners once per build)."""
 
     def __init__(self, x, m, xsrc, engine, *, box=(1.0, 1.0, 1.0), periodic=True, nb=32, group=None,
@@ -335,7 +338,7 @@ class DistributedTransport:
             reach = reach_blocks(depth, box, nb)
             plan = make_plan(self.x, box, periodic, nb, self.block_owner, self.rank, reach)
             loc = plan.local
-            h, hs = engine.solve(self.x[:, loc], self.m[loc], self.xsrc[:, s_own])
+            h, hs, oms, octw = engine.solve(self.x[:, loc], self.m[loc], self.xsrc[:, s_own])
             H_need = H_OVER_h * max(h[:plan.n_owned].max(initial=0.0), hs.max(initial=0.0))
             ok = self._all_min(float(H_need <= reach * min(box) / nb))
             if ok > 0.5 or reach >= nb:
@@ -343,26 +346,34 @@ class DistributedTransport:
             depth = 1.5 * max(depth, self._all_max(H_need))
         self.h = np.zeros(n)
         self.h[plan.owned] = h[:plan.n_owned]
-        self.hs = np.zeros(self.xsrc.shape[1])
+        S = self.xsrc.shape[1]
+        self.hs = np.zeros(S)
         self.hs[s_own] = hs
         self.hs = self._all_sum(self.hs)
+        # each source's normalisation (omega_s, octant sums) from its owner, whose gas
+        # neighbourhood is complete: no rank needs a gas halo for the injection
+        self.oms = np.zeros(S)
+        self.oms[s_own] = oms
+        self.oms = self._all_sum(self.oms)
+        self.octw = np.zeros((S, 8))
+        self.octw[s_own] = np.asarray(octw).reshape(-1, 8)
+        self.octw = self._all_sum(self.octw.reshape(-1)).reshape(S, 8)
         self.H_max = H_OVER_h * self._all_max(float(self.h[plan.owned].max(initial=0.0)))
         self.Hs_max = H_OVER_h * float(self.hs.max(initial=0.0))
         # 2.-3. the halo of the transport and the build with every h given: the transport
         #    needs 2 H_max (H_max when the ghosts' gradients and fields come from their
-        #    owners), the injection into owned particles the sources within H_s,max and their
-        #    gas neighbours
-        t_depth = self.H_max if exchange == "gradients" else 2.0 * self.H_max
-        self.depth = max(t_depth, 2.0 * self.Hs_max)
+        #    owners); the injection into owned particles needs the sources within H_s,max,
+        #    with their owners' normalisations, and no gas beyond the owned particles
+        self.depth = self.H_max if exchange == "gradients" else 2.0 * self.H_max
         reach_src = reach_blocks(self.Hs_max, box, nb)
-        reach = max(reach_blocks(t_depth, box, nb), reach_src + reach_blocks(self.Hs_max, box, nb))
+        reach = reach_blocks(self.depth, box, nb)
         self.plan = make_plan(self.x, box, periodic, nb, self.block_owner, self.rank, reach)
         self.reach = reach
         self._exchange_owned_h()
         self.src_mask = source_mask(self.xsrc, box, periodic, nb, self.block_owner, self.rank, reach_src)
         loc = self.plan.local
         engine.build(self.x[:, loc], self.m[loc], self.xsrc[:, self.src_mask], self.h[loc],
-                     self.hs[self.src_mask], self.plan.n_owned)
+                     self.hs[self.src_mask], self.plan.n_owned, self.oms[self.src_mask], self.octw[self.src_mask])
         if exchange == "gradients":
             self._exchange_fields()
 

@@ -13,8 +13,9 @@ import torch
 
 from . import (RT_FP32_MIXED, RT_FP64, make_config, rt_adjoint, rt_create, rt_destroy, rt_diagnostics, rt_drift,
                rt_energy, rt_get_tuning, rt_gradients, rt_neighbours, rt_neighbours_given_h, rt_pairs,
-               rt_inject, rt_particle_fields, rt_set_fields, rt_set_owned, rt_set_stream, rt_set_tuning,
-               rt_source_fields, rt_subcycle, rt_transport_step, rt_transport_step_given_gradients)
+               rt_inject, rt_neighbours_given_fields, rt_particle_fields, rt_set_fields, rt_set_owned,
+               rt_set_stream, rt_set_tuning, rt_source_fields, rt_source_norms, rt_subcycle, rt_transport_step,
+               rt_transport_step_given_gradients)
 
 
 def _dev(a, dtype, device):
@@ -34,7 +35,7 @@ class Transport:
 
     def __init__(self, x, m=None, xsrc=None, *, n_groups=1, c_red=1.0, eta_res=1.2348, eta_res_star=None,
                  box=(1.0, 1.0, 1.0), periodic=True, precision="fp32", clamp_negative=False, h_tol=1e-6,
-                 h_max_iter=100, device="cuda:0", riemann="glf", h=None, hs=None):
+                 h_max_iter=100, device="cuda:0", riemann="glf", h=None, hs=None, omegas=None, octw=None):
         self.device = torch.device(device)
         self.x = _dev(x, torch.float64, self.device)
         self.n = int(self.x.shape[1])
@@ -57,18 +58,33 @@ class Transport:
             if h is None:
                 rt_neighbours(self.ctx, self.x, self.m, self.xsrc if self.n_src else None, self.h)
             else:
-                self.rebuild_given_h(h, hs)
+                self.rebuild_given_h(h, hs, omegas=omegas, octw=octw)
 
-    def rebuild_given_h(self, h, hs=None, x=None):
+    def rebuild_given_h(self, h, hs=None, x=None, omegas=None, octw=None):
         """Neighbour search with given smoothing lengths h [N] and source lengths hs [S]
-        (rt_neighbours_given_h)."""
+        (rt_neighbours_given_h), and with omegas [S] and octw [S, 8] also the sources'
+        normalisations (rt_neighbours_given_fields)."""
         if x is not None:
             self.x = _dev(x, torch.float64, self.device)
         self._sync_stream()
         hd = _dev(h, torch.float64, self.device)
         hsd = _dev(hs, torch.float64, self.device) if self.n_src else None
-        rt_neighbours_given_h(self.ctx, self.x, self.m, self.xsrc if self.n_src else None, hd, hsd)
+        xs = self.xsrc if self.n_src else None
+        if omegas is not None and self.n_src:
+            rt_neighbours_given_fields(self.ctx, self.x, self.m, xs, hd, hsd, _dev(omegas, torch.float64, self.device),
+                                       _dev(octw, torch.float64, self.device))
+        else:
+            rt_neighbours_given_h(self.ctx, self.x, self.m, xs, hd, hsd)
         self.h = hd.clone()
+
+    def source_norms(self):
+        """The sources' omega_s [S] and octant sums [S, 8] (device tensors)."""
+        self._sync_stream()
+        om = torch.zeros(self.n_src, dtype=torch.float64, device=self.device)
+        ow = torch.zeros((self.n_src, 8), dtype=torch.float64, device=self.device)
+        if self.n_src:
+            rt_source_norms(self.ctx, om, ow)
+        return om, ow
 
     def source_h(self):
         """Smoothing lengths of the sources [S] (device tensor)."""

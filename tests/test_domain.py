@@ -31,11 +31,14 @@ class OracleEngine:
     def solve(self, x, m, xsrc):
         o = oracle.Oracle(x, m, xsrc if xsrc.shape[1] else None, n_groups=self.G, c_red=self.c_red, box=self.box,
                           periodic=self.periodic)
-        return o.h.copy(), (o.sources().hs.copy() if xsrc.shape[1] else np.zeros(0))
+        if not xsrc.shape[1]:
+            return o.h.copy(), np.zeros(0), np.zeros(0), np.zeros((0, 8))
+        s = o.sources()
+        return o.h.copy(), s.hs.copy(), s.omegas.copy(), s.octw.copy()
 
-    def build(self, x, m, xsrc, h, hs, n_owned):
+    def build(self, x, m, xsrc, h, hs, n_owned, omegas=None, octw=None):
         self.o = oracle.Oracle(x, m, xsrc if xsrc.shape[1] else None, n_groups=self.G, c_red=self.c_red,
-                               box=self.box, periodic=self.periodic, h=h, hs=hs)
+                               box=self.box, periodic=self.periodic, h=h, hs=hs, omegas=omegas, octw=octw)
         self.n_owned = n_owned
         self.ns = xsrc.shape[1]
 
@@ -100,6 +103,12 @@ def _case(name):
     if name == "lattice-point-source":
         w = W.lattice_point_source()
         return w.x, w.m, w.xsrc, w.U0, w.Lsrc, None, w.n_groups, w.c_red, 4
+    if name == "lattice-48-edge":
+        # sources just inside one half of the box each: their supports cross the cut between
+        # two ranks and reach past the other rank's one-radius halo (the weights of the other
+        # rank's targets come from the owners' normalisations)
+        x, m, _, U0, Ls, alpha, G, c, nsteps = _case("lattice-48")
+        return x, m, np.array([[0.3, 0.7], [0.45, 0.6], [0.53, 0.47]]), U0, Ls, alpha, G, c, nsteps
     if name == "lattice-48-dark":
         # no sources: the gradient-exchange halo is one support radius deep, so the ghosts'
         # own neighbourhoods are cut and their fields and gradients must be their owners'
@@ -145,6 +154,7 @@ def _rank_main(rank, ws, port, name, out_path, exchange="state"):
 @pytest.mark.parametrize("name, ws, exchange", [("lattice-point-source", 2, "state"), ("lattice-48", 2, "state"),
                                                 ("lattice-48", 4, "state"), ("lattice-40-walls", 3, "state"),
                                                 ("lattice-48", 2, "gradients"), ("lattice-48-dark", 2, "gradients"),
+                                                ("lattice-48-edge", 2, "gradients"),
                                                 ("lattice-48-dark", 4, "gradients"),
                                                 ("lattice-40-walls", 3, "gradients")])
 def test_decomposed_oracle_run_equals_single_rank(tmp_path, name, ws, exchange):

@@ -45,6 +45,7 @@ def _rank_main(rank, ws, port, name, precision, dt, out_path, exchange="state"):
 @pytest.mark.parametrize("precision, name, exchange", [("fp64", "lattice-48", "state"),
                                                        ("fp32", "lattice-48", "state"),
                                                        ("fp64", "lattice-48-dark", "gradients"),
+                                                       ("fp64", "lattice-48-edge", "gradients"),
                                                        ("fp32", "lattice-48-dark", "gradients")])
 def test_decomposed_library_run_equals_single_context(tmp_path, precision, name, exchange):
     """Both exchange modes; the gradient-exchange case has no sources, so its halo is one
@@ -148,6 +149,32 @@ def test_step_given_gradients_and_fields(precision):
     with pytest.raises(RTError):
         t.set_fields(n - 1, f["omega"][:2], f["B"][:2])
     t.close()
+
+
+def test_given_source_norms_reproduce_the_build():
+    """rt_neighbours_given_fields with the normalisations (rt_source_norms) that a build with
+    the same given h and h_s forms itself gives bitwise that build's step with sources; the
+    normalisations of a build that solved its h are within rounding of them."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    x, m, xsrc, U0, Ls, alpha, G, c, _ = _case("lattice-48")
+    for precision in ("fp64", "fp32"):
+        a = Transport(x, m, xsrc, n_groups=G, c_red=c, precision=precision)
+        h, hs = a.h.clone(), a.source_h()
+        b = Transport(x, m, xsrc, n_groups=G, c_red=c, precision=precision, h=h, hs=hs)
+        om, ow = b.source_norms()
+        assert om.shape == (2,) and ow.shape == (2, 8) and bool((om > 0).all())
+        oma, owa = a.source_norms()
+        np.testing.assert_allclose(oma.cpu().numpy(), om.cpu().numpy(), rtol=1e-12)
+        np.testing.assert_allclose(owa.cpu().numpy(), ow.cpu().numpy(), rtol=1e-12, atol=1e-15)
+        d = Transport(x, m, xsrc, n_groups=G, c_red=c, precision=precision, h=h, hs=hs, omegas=om, octw=ow)
+        dt = 0.5 * b.diagnostics()["dx_min"] / c
+        Ub, Ud = b.state(U0), d.state(U0)
+        b.step(Ub, dt, b.luminosities(Ls), b.alpha(alpha))
+        d.step(Ud, dt, d.luminosities(Ls), d.alpha(alpha))
+        assert torch.equal(Ub, Ud), precision
+        for t in (a, b, d):
+            t.close()
 
 
 @pytest.mark.parametrize("exchange", ["state", "gradients"])
