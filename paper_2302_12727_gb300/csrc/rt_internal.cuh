@@ -245,8 +245,5 @@ __device__ __forceinline__ T spline_dw(T q) {
     return d;
 }
 
-template <class T>
-__device__ __forceinline__ T fast_rcp(T x) { return T(1) / x; }
-
 
 }  // namespace rt
