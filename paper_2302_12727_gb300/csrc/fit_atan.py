@@ -1,4 +1,4 @@
-"""Coefficients of the float arctangent in rt_pair.cuh (atan_0_pi).
+"""Coefficients of the float arctangent in rt_pair.cuh (angle_0_pi).
 
 atan(a) on a in [0, 1] is written a * q(a^2) with q a polynomial of degree 7, fitted by
 iteratively reweighted least squares towards the smallest largest error on 4001
