@@ -327,12 +327,27 @@ __global__ void __launch_bounds__(kGradBlockMax, GC == 4 ? 1280 / kGradBlockMax 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nit = max(nit, __shfl_xor_sync(FULL, nit, o));
     const int base = q * GC;                       // first lane of this particle
+    // this lane's pair of neighbours; below four groups their indices load one iteration
+    // ahead (at four, the register cap of five blocks per SM leaves no room for them)
+    constexpr bool PF = GC < 4;
+    int64_t ea = e0 + 2 * g;
+    int j0 = 0, j1 = 0;
+    if constexpr (PF) {
+        j0 = ea < e1 ? a.cols[ea] : 0;
+        j1 = ea + 1 < e1 ? a.cols[ea + 1] : j0;
+    }
     for (int it = 0; it < nit; ++it) {
-        // this lane's pair of neighbours
-        const int64_t ea = e0 + (int64_t)it * 2 * GC + 2 * g;
         const bool has = ea < e1, two = ea + 1 < e1;
-        const int j0 = has ? a.cols[ea] : 0;
-        const int j1 = two ? a.cols[ea + 1] : j0;
+        if constexpr (!PF) {
+            j0 = has ? a.cols[ea] : 0;
+            j1 = two ? a.cols[ea + 1] : j0;
+        }
+        const int64_t en = ea + 2 * GC;
+        int j0n = 0, j1n = 0;
+        if constexpr (PF) {
+            j0n = en < e1 ? a.cols[en] : 0;
+            j1n = en + 1 < e1 ? a.cols[en + 1] : j0n;
+        }
         const Pos<float> p0 = load_pos(tag, a.pos, j0);
         const Pos<float> p1 = load_pos(tag, a.pos, j1);
         float dx0, dy0, dz0, dx1, dy1, dz1;
@@ -363,6 +378,11 @@ __global__ void __launch_bounds__(kGradBlockMax, GC == 4 ? 1280 / kGradBlockMax 
                 acc[c][1] += dq0 * Y0 + dq1 * Y1;
                 acc[c][2] += dq0 * Z0 + dq1 * Z1;
             }
+        }
+        ea = en;
+        if constexpr (PF) {
+            j0 = j0n;
+            j1 = j1n;
         }
     }
     if (!act) return;
@@ -932,36 +952,32 @@ __global__ void __launch_bounds__(kGatherBlockMax) k_flux_gather_g(PairArgs<floa
     FluxAcc<float> acc;
     acc.zero();
     const int64_t r0 = a.row_off[i], s0 = a.up_off[i], s1 = a.up_off[i + 1];
-    int64_t sl = s0;
-    for (; sl + 8 <= s1; sl += 8) {   // eight loads in flight, added in order
+    // batches of up to eight loads in flight (the last one predicated), added in order
+    for (int64_t sl = s0; sl < s1; sl += 8) {
+        const int m = s1 - sl < 8 ? (int)(s1 - sl) : 8;
         float p[8][4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) vload<4>(pb + (sl + u) * NC, p[u]);
+        for (int u = 0; u < 8; ++u)
+            if (u < m) vload<4>(pb + (sl + u) * NC, p[u]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc.add(p[u]);
-    }
-    for (; sl < s1; ++sl) {
-        float phi[4];
-        vload<4>(pb + sl * NC, phi);
-        acc.add(phi);
+        for (int u = 0; u < 8; ++u)
+            if (u < m) acc.add(p[u]);
     }
     const int nl = a.n_low[i];
     const int32_t* ls = a.low_slot + (r0 - s0);
-    int e = 0;
-    for (; e + 8 <= nl; e += 8) {   // eight slot indices, then eight loads in flight
+    for (int e = 0; e < nl; e += 8) {   // up to eight slot indices, then their loads in flight
+        const int m = nl - e < 8 ? nl - e : 8;
         int32_t q[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) q[u] = ls[e + u];
+        for (int u = 0; u < 8; ++u)
+            if (u < m) q[u] = ls[e + u];
         float p[8][4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) vload<4>(pb + (int64_t)q[u] * NC, p[u]);
+        for (int u = 0; u < 8; ++u)
+            if (u < m) vload<4>(pb + (int64_t)q[u] * NC, p[u]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc.sub(p[u]);
-    }
-    for (; e < nl; ++e) {
-        float phi[4];
-        vload<4>(pb + (int64_t)ls[e] * NC, phi);
-        acc.sub(phi);
+        for (int u = 0; u < 8; ++u)
+            if (u < m) acc.sub(p[u]);
     }
     const float dt = (float)(*x.dt_dev);
     const float f = dt * a.omega[i];
