@@ -134,6 +134,24 @@ __device__ __forceinline__ void for_each_candidate(const Grid& g, float px, floa
     });
 }
 
+// every candidate with its quantised position record, read four at a time: the loads of a
+// batch are in flight together, and f still sees the candidates one by one, in order
+template <bool ASC = false, class F>
+__device__ __forceinline__ void for_each_candidate_q(const Grid& g, const uint4* __restrict__ xq, float px, float py,
+                                                     float pz, float R, F&& f) {
+    for_each_candidate_range<ASC>(g, px, py, pz, R, [&](int b, int e) {
+        for (int j0 = b; j0 < e; j0 += 4) {
+            uint4 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j0 + u < e) q[u] = xq[j0 + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j0 + u < e) f(j0 + u, q[u]);
+        }
+    });
+}
+
 // number of particles in the 3 x 3 x 3 cells around (cx, cy, cz): a local density for the
 // first guess of h
 __device__ __forceinline__ int count_27(const Grid& g, int cx, int cy, int cz) {
@@ -502,10 +520,10 @@ __global__ void k_h_solve(Grid g, const double* __restrict__ xs, const uint4* __
             double sw = 0.0;
             float sdw = 0.f;
             bool nb = false;
-            for_each_candidate(g, pxf, pyf, pzf, H, [&](int j) {
-                float dx = fsep(xq[j].x, qx, hp.scale[0]);
-                float dy = fsep(xq[j].y, qy, hp.scale[1]);
-                float dz = fsep(xq[j].z, qz, hp.scale[2]);
+            for_each_candidate_q(g, xq, pxf, pyf, pzf, H, [&](int, uint4 qj) {
+                float dx = fsep(qj.x, qx, hp.scale[0]);
+                float dy = fsep(qj.y, qy, hp.scale[1]);
+                float dz = fsep(qj.z, qz, hp.scale[2]);
                 float r2 = dx * dx + dy * dy + dz * dz;
                 nb |= fabsf(r2 - H2) < kNearBand * H2;
                 if (r2 < H2) {
@@ -767,11 +785,11 @@ __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint4* __re
         const float Hr = reach[block_of(bk, px, py, pz)];
         float R = sqrtf(fmaxf(H2i, Hr * Hr)) * 1.0001f;
         int64_t base = FILL ? row_off[p] : p * (int64_t)cap;
-        for_each_candidate<true>(g, (float)px, (float)py, (float)pz, R, [&](int j) {
+        for_each_candidate_q<true>(g, xq, (float)px, (float)py, (float)pz, R, [&](int j, uint4 qj) {
             if (j == p) return;
-            float dx = fsep(xq[j].x, qx, pp.scale[0]);
-            float dy = fsep(xq[j].y, qy, pp.scale[1]);
-            float dz = fsep(xq[j].z, qz, pp.scale[2]);
+            float dx = fsep(qj.x, qx, pp.scale[0]);
+            float dy = fsep(qj.y, qy, pp.scale[1]);
+            float dz = fsep(qj.z, qz, pp.scale[2]);
             float r2f = dx * dx + dy * dy + dz * dz;
             float H2m = fmaxf(H2i, H2f[j]);
             bool in;
