@@ -504,6 +504,8 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_secondary and args.workload == "poisson-sine-beam":
         out["secondary"] = {name: run_secondary(name, args, dev, flush, fp64=(name == "lognormal-sources"))
                             for name in ("lognormal-sources", "lognormal-sources-large")}
+    if rank == 0 and ws == 1 and not args.no_secondary and args.workload == "poisson-sine-beam":
+        out["adjoint"] = run_adjoint(args, dev)
     if ws > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -563,6 +565,53 @@ def run_secondary(name, args, dev, flush, fp64=False, steps=2, warmup=1):
         torch.cuda.empty_cache()
     if fp64:
         res["speedup_of_fp32_graph"] = res["fp64"]["ms_per_step"] / res["fp32"]["ms_per_step"]
+    return res
+
+
+def run_adjoint(args, dev, steps=3, warmup=1):
+    """The differentiation workload (jittered 32^3 lattice, 2 groups, 8 sources, 16 sub-cycles,
+    a checkpoint every 4): the forward sub-cycles and the library adjoint of the loss "E
+    summed over the particles within 0.15 of the box centre" (gradients with respect to the
+    initial state and the luminosities), in FP64 and FP32.  Wall-clock with the device
+    synchronised on both sides (the adjoint call returns after its last kernel); value counts
+    the forward pair-group interactions the backward pass differentiates, per second."""
+    import torch
+    from paper_2302_12727_gb300 import Transport
+    w = workload("lattice-sources")
+    G, n_sub, k = w.n_groups, w.n_steps, w.ckpt_every
+    d = w.x - 0.5
+    d -= np.rint(d)
+    wt = np.zeros((G, 4, w.n))
+    wt[:, 0, np.sqrt((d ** 2).sum(0)) < 0.15] = 1.0
+    res = {"workload": w.name, "particles": w.n, "groups": G, "sub_cycles": n_sub, "sources": w.n_src,
+           "checkpoint_every": k}
+    for prec in ("fp64", "fp32"):
+        T = Transport(w.x, w.m, w.xsrc, n_groups=G, c_red=w.c_red, precision=prec, device=dev)
+        dg = T.diagnostics()
+        P = dg["n_pairs"]
+        dt = args.cfl * dg["dx_min"] / w.c_red
+        L = T.luminosities(w.Lsrc)
+        U0 = T.state(w.U0)
+        lam = T.state(wt)
+        fwd, bwd = [], []
+        for it in range(warmup + steps):
+            U = U0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            T.subcycle(U, n_sub, dt, L)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            dU0, dL = T.adjoint(U0, n_sub, dt, lam, L, None, k)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            if it >= warmup:
+                fwd.append(1e3 * (t1 - t0))
+                bwd.append(1e3 * (t2 - t1))
+        f_ms, b_ms = sum(fwd) / len(fwd), sum(bwd) / len(bwd)
+        res[prec] = {"forward_ms": f_ms, "adjoint_ms": b_ms, "adjoint_over_forward": b_ms / f_ms,
+                     "value": P * G * n_sub / (b_ms / 1e3), "unit": UNIT, "pairs": P, "steps": len(bwd),
+                     "finite": bool(torch.isfinite(dU0).all().item() and torch.isfinite(dL).all().item())}
+        T.close()
     return res
 
 
@@ -780,7 +829,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
-                    help="skip the secondary measurements of the 2,097,152- and 16,777,216-particle workloads")
+                    help="skip the secondary measurements (the 2,097,152- and 16,777,216-particle workloads "
+                         "and the adjoint on the 32,768-particle differentiation workload)")
     ap.add_argument("--riemann", default="glf", choices=["glf", "hll"],
                     help="pair-flux Riemann solver (Eq. riemann-GLF or Eq. riemann-HLL)")
     ap.add_argument("--tuning", default="", help="flux,gather,gradient variants of the float pair kernels")
