@@ -67,14 +67,16 @@ __device__ __forceinline__ void m1_vjp(const T u4[4], T Ax, T Ay, T Az, T c, con
     ub[3] += cf * Fz + bE * (phF * Az + FA * pb[3]);
 }
 
-// adjoint of the flux stage for the groups [g0, g0 + GC): per particle i, over its whole row
+// adjoint of the flux stage for group g0 + g of a group chunk of GC: one thread per (particle i,
+// group), over i's whole row; the pair geometry is recomputed by each group's thread
 template <class T, int GC>
 __global__ void __launch_bounds__(128) k_adj_flux(PairArgs<T> a, FluxExtra<T> x, const T* __restrict__ lam,
                                                   const T* __restrict__ W, T* __restrict__ ubar, T* __restrict__ gam,
                                                   int g0) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = t / GC;
     if (i >= a.n) return;
-    constexpr int NC = 4 * GC;
+    const int gg = g0 + (int)(t - i * GC);
     const T* tag = nullptr;
     const int G = a.G, RS = 4 * G;
     const T dt = (T)(*x.dt_dev);
@@ -84,18 +86,20 @@ __global__ void __launch_bounds__(128) k_adj_flux(PairArgs<T> a, FluxExtra<T> x,
         return sk;
     };
     const T sink_i = sink_of(i), om_i = a.omega[i];
-    T li[NC], mui[NC], ub[NC], gb[NC][3];
-    vload<NC>(lam + i * RS + 4 * g0, li);
+    T li[4], mui[4], ub[4], gb[4][3];
+    vload<4>(lam + i * RS + 4 * gg, li);
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc) {
-        li[cc] *= sink_i;
-        mui[cc] = -dt * om_i * li[cc];   // same expression as for the other particle below
-        ub[cc] = li[cc];
-        gb[cc][0] = gb[cc][1] = gb[cc][2] = T(0);
+    for (int q = 0; q < 4; ++q) {
+        li[q] *= sink_i;
+        mui[q] = -dt * om_i * li[q];   // same expression as for the other particle below
+        ub[q] = li[q];
+        gb[q][0] = gb[q][1] = gb[q][2] = T(0);
     }
     const Pos<T> pi = load_pos(tag, a.pos, i);
-    T gi8[8];
+    T gi8[8], ui[4], gri[12];
     vload<8>(a.geo + 8 * i, gi8);
+    vload<4>(W + i * RS + 4 * gg, ui);
+    vload<12>(a.grad + i * 12 * G + 12 * gg, gri);
     for (int64_t e = a.row_off[i]; e < a.row_off[i + 1]; ++e) {
         const int64_t j = a.cols[e];
         const bool ik = i < j;                     // i is the left state k
@@ -119,84 +123,78 @@ __global__ void __launch_bounds__(128) k_adj_flux(PairArgs<T> a, FluxExtra<T> x,
         const T wk = gk8[1] * ih, wl = gl8[1] * ih;
         // mu of the other particle
         const T sink_j = sink_of(j), om_j = a.omega[j];
-        T lj[NC];
-        vload<NC>(lam + j * RS + 4 * g0, lj);
+        T lj[4], uj[4], grj[12];
+        vload<4>(lam + j * RS + 4 * gg, lj);
+        vload<4>(W + j * RS + 4 * gg, uj);
+        vload<12>(a.grad + j * 12 * G + 12 * gg, grj);
+        const T* uk = ik ? ui : uj;
+        const T* ul = ik ? uj : ui;
+        const T* gk = ik ? gri : grj;
+        const T* gl = ik ? grj : gri;
+        T L[4], R[4], s[4];
+        int sel[4];                          // 1: slope of k, 2: slope of l, 0: none
 #pragma unroll
-        for (int g = 0; g < GC; ++g) {
-            const int gg = g0 + g;
-            T ui[4], uj[4], gri[12], grj[12];
-            vload<4>(W + i * RS + 4 * gg, ui);
-            vload<4>(W + j * RS + 4 * gg, uj);
-            vload<12>(a.grad + i * 12 * G + 12 * gg, gri);
-            vload<12>(a.grad + j * 12 * G + 12 * gg, grj);
-            const T* uk = ik ? ui : uj;
-            const T* ul = ik ? uj : ui;
-            const T* gk = ik ? gri : grj;
-            const T* gl = ik ? grj : gri;
-            T L[4], R[4], s[4];
-            int sel[4];                          // 1: slope of k, 2: slope of l, 0: none
+        for (int q = 0; q < 4; ++q) {
+            T dqk = gk[3 * q] * dx + gk[3 * q + 1] * dy + gk[3 * q + 2] * dz;
+            T dql = gl[3 * q] * dx + gl[3 * q + 1] * dy + gl[3 * q + 2] * dz;
+            s[q] = minmod_(dqk, dql);
+            bool pos = dqk > T(0) && dql > T(0), neg = dqk < T(0) && dql < T(0);
+            sel[q] = (pos || neg) ? (((pos && dqk < dql) || (neg && dqk > dql)) ? 1 : 2) : 0;
+            L[q] = fma_rn(wk, s[q], uk[q]);
+            R[q] = fma_rn(-wl, s[q], ul[q]);
+        }
+        T pb[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                T dqk = gk[3 * q] * dx + gk[3 * q + 1] * dy + gk[3 * q + 2] * dz;
-                T dql = gl[3 * q] * dx + gl[3 * q + 1] * dy + gl[3 * q + 2] * dz;
-                s[q] = minmod_(dqk, dql);
-                bool pos = dqk > T(0) && dql > T(0), neg = dqk < T(0) && dql < T(0);
-                sel[q] = (pos || neg) ? (((pos && dqk < dql) || (neg && dqk > dql)) ? 1 : 2) : 0;
-                L[q] = fma_rn(wk, s[q], uk[q]);
-                R[q] = fma_rn(-wl, s[q], ul[q]);
-            }
-            T pb[4];
+        for (int q = 0; q < 4; ++q) {
+            const T muj = -dt * om_j * (lj[q] * sink_j);
+            const T muk = ik ? mui[q] : muj;
+            const T mul = ik ? muj : mui[q];
+            pb[q] = muk - mul;
+        }
+        T jL[4], jR[4];
+        m1_vjp(L, Ax, Ay, Az, x.c, pb, jL);
+        m1_vjp(R, Ax, Ay, Az, x.c, pb, jR);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const T muj = -dt * om_j * (lj[4 * g + q] * sink_j);
-                const T muk = ik ? mui[4 * g + q] : muj;
-                const T mul = ik ? muj : mui[4 * g + q];
-                pb[q] = muk - mul;
-            }
-            T jL[4], jR[4];
-            m1_vjp(L, Ax, Ay, Az, x.c, pb, jL);
-            m1_vjp(R, Ax, Ay, Az, x.c, pb, jR);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const T Lb = T(0.5) * jL[q] + diss * pb[q];
-                const T Rb = T(0.5) * jR[q] - diss * pb[q];
-                const T sb = wk * Lb - wl * Rb;
-                const int cc = 4 * g + q;
-                ub[cc] += ik ? Lb : Rb;
-                const bool mine = ik ? (sel[q] == 1) : (sel[q] == 2);
-                if (mine) {
-                    gb[cc][0] += sb * dx;
-                    gb[cc][1] += sb * dy;
-                    gb[cc][2] += sb * dz;
-                }
+        for (int q = 0; q < 4; ++q) {
+            const T Lb = T(0.5) * jL[q] + diss * pb[q];
+            const T Rb = T(0.5) * jR[q] - diss * pb[q];
+            const T sb = wk * Lb - wl * Rb;
+            ub[q] += ik ? Lb : Rb;
+            const bool mine = ik ? (sel[q] == 1) : (sel[q] == 2);
+            if (mine) {
+                gb[q][0] += sb * dx;
+                gb[q][1] += sb * dy;
+                gb[q][2] += sb * dz;
             }
         }
     }
-    vstore<NC>(ubar + i * RS + 4 * g0, ub);
+    vstore<4>(ubar + i * RS + 4 * gg, ub);
     // gamma_i = omega_i Bp_i gbar_i (the gradient is omega_i Bp_i sum_j (Q_j - Q_i) w d, Bp symmetric)
     T Mi[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) Mi[k] = om_i * gi8[2 + k];
-    T out[3 * NC];
+    T out[12];
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc) sym_mv(Mi, gb[cc][0], gb[cc][1], gb[cc][2], out[3 * cc], out[3 * cc + 1], out[3 * cc + 2]);
-    vstore<3 * NC>(gam + i * 12 * G + 12 * g0, out);
+    for (int q = 0; q < 4; ++q) sym_mv(Mi, gb[q][0], gb[q][1], gb[q][2], out[3 * q], out[3 * q + 1], out[3 * q + 2]);
+    vstore<12>(gam + i * 12 * G + 12 * gg, out);
 }
 
-// transpose of the gradient operator: lambda_i = ubar_i - sum_j d_ij . (gamma_i w_i + gamma_j w_j)
+// transpose of the gradient operator: lambda_i = ubar_i - sum_j d_ij . (gamma_i w_i + gamma_j w_j),
+// one thread per (particle i, group g0 + g of a chunk of GC)
 template <class T, int GC>
 __global__ void __launch_bounds__(128) k_adj_grad(PairArgs<T> a, const T* __restrict__ ubar,
                                                   const T* __restrict__ gam, T* __restrict__ lam_out, int g0) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = t / GC;
     if (i >= a.n) return;
-    constexpr int NC = 4 * GC;
+    const int gg = g0 + (int)(t - i * GC);
     const T* tag = nullptr;
     const int G = a.G, RS = 4 * G;
     const Pos<T> pi = load_pos(tag, a.pos, i);
     const T iHi = a.geo[8 * i];
-    T gi[3 * NC], acc[NC];
-    vload<3 * NC>(gam + i * 12 * G + 12 * g0, gi);
-    vload<NC>(ubar + i * RS + 4 * g0, acc);
+    T gi[12], acc[4];
+    vload<12>(gam + i * 12 * G + 12 * gg, gi);
+    vload<4>(ubar + i * RS + 4 * gg, acc);
     for (int64_t e = a.row_off[i]; e < a.row_off[i + 1]; ++e) {
         const int64_t j = a.cols[e];
         const Pos<T> pj = load_pos(tag, a.pos, j);
@@ -205,34 +203,46 @@ __global__ void __launch_bounds__(128) k_adj_grad(PairArgs<T> a, const T* __rest
         const T r = sqrt_(dx * dx + dy * dy + dz * dz);
         const T wi = spline_w_(r * iHi);
         const T wj = spline_w_(r * a.geo[8 * j]);
-        T gj[3 * NC];
-        vload<3 * NC>(gam + j * 12 * G + 12 * g0, gj);
+        T gj[12];
+        vload<12>(gam + j * 12 * G + 12 * gg, gj);
 #pragma unroll
-        for (int cc = 0; cc < NC; ++cc) {
-            const T vx = gi[3 * cc] * wi + gj[3 * cc] * wj;
-            const T vy = gi[3 * cc + 1] * wi + gj[3 * cc + 1] * wj;
-            const T vz = gi[3 * cc + 2] * wi + gj[3 * cc + 2] * wj;
-            acc[cc] -= dx * vx + dy * vy + dz * vz;
+        for (int q = 0; q < 4; ++q) {
+            const T vx = gi[3 * q] * wi + gj[3 * q] * wj;
+            const T vy = gi[3 * q + 1] * wi + gj[3 * q + 1] * wj;
+            const T vz = gi[3 * q + 2] * wi + gj[3 * q + 2] * wj;
+            acc[q] -= dx * vx + dy * vy + dz * vz;
         }
     }
-    vstore<NC>(lam_out + i * RS + 4 * g0, acc);
+    vstore<4>(lam_out + i * RS + 4 * gg, acc);
 }
 
-// dL/dL_s,g += dt sum over the source's entries of (xi / V_target) lambda_E,g(target)
+// dL/dL_s,g += dt sum over the source's entries of (xi / V_target) lambda_E,g(target): one
+// warp per (source, group); its lanes load 32 consecutive entries at a time and every lane adds
+// their terms in entry order (the same sum in all lanes)
 template <class T>
 __global__ void k_adj_inject(const int64_t* __restrict__ src_off, const int32_t* __restrict__ e_gas,
                              const double* __restrict__ e_xi, const double* __restrict__ V, const T* __restrict__ lam,
                              int64_t S, int G, const double* __restrict__ dt_dev, double* dLdL) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= S * G) return;
-    const int64_t s = t / G;
-    const int g = (int)(t % G);
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= S * G) return;   // whole warps
+    const int64_t s = w / G;
+    const int g = (int)(w % G);
+    const int64_t e0 = src_off[s], e1 = src_off[s + 1];
     double acc = 0.0;
-    for (int64_t e = src_off[s]; e < src_off[s + 1]; ++e) {
-        const int64_t p = e_gas[e];
-        acc += e_xi[e] / V[p] * (double)lam[p * 4 * G + 4 * g];
+    for (int64_t b = e0; b < e1; b += 32) {
+        const int64_t e = b + lane;
+        double q = 0.0, l = 0.0;
+        if (e < e1) {
+            const int64_t p = e_gas[e];
+            q = e_xi[e] / V[p];
+            l = (double)lam[p * 4 * G + 4 * g];
+        }
+        const int m = e1 - b < 32 ? (int)(e1 - b) : 32;
+        for (int u = 0; u < m; ++u)
+            acc = fma(__shfl_sync(0xffffffffu, q, u), __shfl_sync(0xffffffffu, l, u), acc);
     }
-    dLdL[t] += *dt_dev * acc;
+    if (lane == 0) dLdL[w] += *dt_dev * acc;
 }
 
 template <class T>
@@ -250,23 +260,24 @@ static void launch_adj_step(rt_ctx* c, cudaStream_t s, const T* lamN, const T* W
     x.clamp = 0;
     x.clamp_count = nullptr;
     const int G = c->cfg.n_groups;
-    unsigned nb = nblk_(c->n, 128);
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
+        const unsigned nbg = nblk_(c->n * gc, 128);
         switch (gc) {
-            case 1: k_adj_flux<T, 1><<<nb, 128, 0, s>>>(a, x, lamN, W, ub, gam, g0); break;
-            case 2: k_adj_flux<T, 2><<<nb, 128, 0, s>>>(a, x, lamN, W, ub, gam, g0); break;
-            case 3: k_adj_flux<T, 3><<<nb, 128, 0, s>>>(a, x, lamN, W, ub, gam, g0); break;
-            default: k_adj_flux<T, 4><<<nb, 128, 0, s>>>(a, x, lamN, W, ub, gam, g0); break;
+            case 1: k_adj_flux<T, 1><<<nbg, 128, 0, s>>>(a, x, lamN, W, ub, gam, g0); break;
+            case 2: k_adj_flux<T, 2><<<nbg, 128, 0, s>>>(a, x, lamN, W, ub, gam, g0); break;
+            case 3: k_adj_flux<T, 3><<<nbg, 128, 0, s>>>(a, x, lamN, W, ub, gam, g0); break;
+            default: k_adj_flux<T, 4><<<nbg, 128, 0, s>>>(a, x, lamN, W, ub, gam, g0); break;
         }
     }
     for (int g0 = 0; g0 < G; g0 += kMaxGC) {
         int gc = G - g0 < kMaxGC ? G - g0 : kMaxGC;
+        const unsigned nbg = nblk_(c->n * gc, 128);
         switch (gc) {
-            case 1: k_adj_grad<T, 1><<<nb, 128, 0, s>>>(a, ub, gam, lamO, g0); break;
-            case 2: k_adj_grad<T, 2><<<nb, 128, 0, s>>>(a, ub, gam, lamO, g0); break;
-            case 3: k_adj_grad<T, 3><<<nb, 128, 0, s>>>(a, ub, gam, lamO, g0); break;
-            default: k_adj_grad<T, 4><<<nb, 128, 0, s>>>(a, ub, gam, lamO, g0); break;
+            case 1: k_adj_grad<T, 1><<<nbg, 128, 0, s>>>(a, ub, gam, lamO, g0); break;
+            case 2: k_adj_grad<T, 2><<<nbg, 128, 0, s>>>(a, ub, gam, lamO, g0); break;
+            case 3: k_adj_grad<T, 3><<<nbg, 128, 0, s>>>(a, ub, gam, lamO, g0); break;
+            default: k_adj_grad<T, 4><<<nbg, 128, 0, s>>>(a, ub, gam, lamO, g0); break;
         }
     }
     c->launches += 2 * ((G + kMaxGC - 1) / kMaxGC);
@@ -324,13 +335,13 @@ rt_status run_adjoint(rt_ctx* c, int n_sub, int k, bool has_src, bool has_alpha,
                 launch_adj_step<float>(c, st, (const float*)lamN, c->adj_w.as<float>(), c->adj_ub.as<float>(),
                                        c->adj_gam.as<float>(), (float*)lamO, has_alpha);
             if (has_src && dLdL && c->n_inj_entries > 0) {
-                int64_t SG = c->n_src * G;
+                int64_t SG = c->n_src * G;   // one warp each
                 if (c->fp64)
-                    k_adj_inject<double><<<nblk_(SG, 128), 128, 0, st>>>(
+                    k_adj_inject<double><<<nblk_(SG * 32, 128), 128, 0, st>>>(
                         c->src_off.as<int64_t>(), c->src_entry_gas.as<int32_t>(), c->src_entry_xi.as<double>(),
                         c->V_d.as<double>(), (const double*)lamO, c->n_src, G, c->dt_dev.as<double>(), dLdL);
                 else
-                    k_adj_inject<float><<<nblk_(SG, 128), 128, 0, st>>>(
+                    k_adj_inject<float><<<nblk_(SG * 32, 128), 128, 0, st>>>(
                         c->src_off.as<int64_t>(), c->src_entry_gas.as<int32_t>(), c->src_entry_xi.as<double>(),
                         c->V_d.as<double>(), (const float*)lamO, c->n_src, G, c->dt_dev.as<double>(), dLdL);
                 ++c->launches;
