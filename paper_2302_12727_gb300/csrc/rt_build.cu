@@ -708,12 +708,16 @@ __device__ __forceinline__ int block_of(const Blocks& bk, double x, double y, do
 
 // Hb (float bits, ordered like integers for H > 0) of every block; the lanes of a warp that
 // fall in the same block (particles are sorted by cell) combine before one atomic
+// Also stores each particle's float H^2 in the free word of its position record, so that the
+// pair search reads a candidate's position and support radius with one 16-byte load.
 __global__ void k_block_hmax(const double* __restrict__ xs, const float* __restrict__ H2f, int64_t n, Blocks bk,
-                             unsigned* __restrict__ hb) {
+                             unsigned* __restrict__ hb, uint4* __restrict__ xq) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool in = p < n;
     const int b = in ? block_of(bk, xs[p], xs[n + p], xs[2 * n + p]) : -1;
-    const unsigned v = in ? __float_as_uint(sqrtf(H2f[p])) : 0u;
+    const float h2 = in ? H2f[p] : 0.f;
+    if (in) reinterpret_cast<unsigned*>(xq + p)[3] = __float_as_uint(h2);
+    const unsigned v = in ? __float_as_uint(sqrtf(h2)) : 0u;
     const unsigned peers = __match_any_sync(0xffffffffu, b);
     const unsigned m = __reduce_max_sync(peers, v);
     if (in && (threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(&hb[b], m);
@@ -791,7 +795,7 @@ __global__ void k_pairs(Grid g, const double* __restrict__ xs, const uint4* __re
             float dy = fsep(qj.y, qy, pp.scale[1]);
             float dz = fsep(qj.z, qz, pp.scale[2]);
             float r2f = dx * dx + dy * dy + dz * dz;
-            float H2m = fmaxf(H2i, H2f[j]);
+            float H2m = fmaxf(H2i, __uint_as_float(qj.w));   // H_j^2 (k_block_hmax)
             bool in;
             if (r2f < H2m * (1.f - 1e-5f)) in = true;
             else if (r2f > H2m * (1.f + 1e-5f)) in = false;
@@ -1640,7 +1644,8 @@ rt_status build_neighbours(rt_ctx* c, const double* x, const double* m, const do
         unsigned* hb = c->blk.as<unsigned>();
         float* reach = reinterpret_cast<float*>(hb + nbt);
         RT_CUDA(c, cudaMemsetAsync(hb, 0, (size_t)nbt * 4, st));
-        k_block_hmax<<<nblk(n, 256), 256, 0, st>>>(c->xs_d.as<double>(), c->H2f.as<float>(), n, bk, hb);
+        k_block_hmax<<<nblk(n, 256), 256, 0, st>>>(c->xs_d.as<double>(), c->H2f.as<float>(), n, bk, hb,
+                                                   c->xq.as<uint4>());
         k_block_reach<<<nblk((int64_t)nbt * 32, 128), 128, 0, st>>>(hb, bk, reach);
         c->launches += 2;
         // one walk counts the rows and, when the rows of the last call fit row_cap entries,
