@@ -68,6 +68,39 @@ def test_adjoint_matches_exact_directional_derivative():
         assert adj == pytest.approx(exact, rel=1e-9, abs=1e-12 * abs(exact))
 
 
+@pytest.mark.parametrize("G", [3, 5])
+def test_adjoint_group_chunks_match_exact_directional_derivative(G):
+    """Group counts that fill a group chunk of the kernels partly (3) or span two chunks
+    (5 = 4 + 1): <dL/dU0, v> + <dL/dLsrc, vL> equals the oracle's dual-number JVP, FP64."""
+    _need_gpu()
+    from types import SimpleNamespace
+    rng = np.random.default_rng(40 + G)
+    x = W.jittered_lattice(10, 0.2, rng)
+    n = x.shape[1]
+    m = np.full(n, 1.0 / n)
+    xsrc = rng.uniform(0.0, 1.0, size=(3, 3))
+    Ls = rng.lognormal(0.0, 1.0, size=(3, G))
+    E0 = 1e-3 * (1.0 + 0.1 * rng.uniform(-1.0, 1.0, size=(G, n)))
+    U0 = np.zeros((G, 4, n))
+    U0[:, 0] = E0
+    U0[:, 1:] = 0.05 * E0[:, None, :] * np.stack([W.random_unit_vectors(n, rng) for _ in range(G)])
+    w = SimpleNamespace(x=x, m=m, xsrc=xsrc, Lsrc=Ls, U0=U0, n=n, n_groups=G, c_red=1.0)
+    o = oracle.Oracle(x, m, xsrc, n_groups=G)
+    dt = 0.6 * ((o.V / (4 * np.pi / 3)) ** (1 / 3)).min()
+    a = 0.3 * m * o.omega
+    n_sub = 4
+    dU0, dL, _ = gpu_adjoint(w, dt, a, n_sub, 2)
+    wt = loss_weights(w)
+    assert wt.sum() > 0
+    for _ in range(2):
+        v = rng.normal(size=U0.shape) * np.abs(U0).max()
+        vL = rng.normal(size=Ls.shape)
+        _, dUf = o.jvp(U0, v, n_sub, dt, Ls, vL, a)
+        exact = (wt * dUf).sum()
+        adj = (dU0 * v).sum() + (dL * vL).sum()
+        assert adj == pytest.approx(exact, rel=1e-9, abs=1e-12 * abs(exact))
+
+
 def test_adjoint_homogeneity():
     """Without the fix-up the final state is degree-1 homogeneous in (U0, L):
     sum_s L_s dL/dL_s + <U0, dL/dU0> = L(final)."""
